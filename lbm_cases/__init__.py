@@ -1,0 +1,259 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA-path tests and the
+benchmark.
+
+This module holds no arithmetic of the lattice Boltzmann method. It only lays out
+problems: the flag map (0 = fluid, k >= 1 = solid cell of wall k), the wall table,
+the physical parameters (viscosity, diffusivity, buoyancy coefficient) obtained
+from the dimensionless groups that define each problem (Re, Pr, Ra, Ma), and the
+initial temperature field drawn from a counter-based generator (SplitMix64, with
+Box-Muller for Gaussian draws). Relaxation rates are derived from nu and alpha on
+each side separately.
+
+Geometry convention: walls sit half-way between the last fluid cell and a frame of
+solid cells, so a problem with H fluid rows has ny = H + 2 cells on a
+non-periodic y axis and the characteristic length is H.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+import math
+
+import numpy as np
+
+DIRICHLET = 0
+ADIABATIC = 1
+
+# kinetic rates used for the convection problems of Sec. 3.4 of the paper
+KINETIC_CONVECTION = dict(s_e=1.6, s_q=1.2, s_eps=1.8, zeta_e=1.9, zeta_nu=1.9)
+# "the remaining relaxation rates are set to be 1.0" (Secs. 3.1, 3.3)
+KINETIC_ONE = dict(s_e=1.0, s_q=1.0, s_eps=1.0, zeta_e=1.0, zeta_nu=1.0)
+
+CS2 = 1.0 / 3.0  # D2Q9 lattice sound speed squared (lattice units, c = 1)
+
+
+@dataclass
+class Wall:
+    ux: float = 0.0
+    uy: float = 0.0
+    kind: int = ADIABATIC
+    T: float = 0.0
+
+
+@dataclass
+class Case:
+    name: str
+    nx: int
+    ny: int
+    periodic_x: bool
+    periodic_y: bool
+    flags: np.ndarray               # (ny, nx) uint8
+    walls: list                     # wall k = walls[k-1]
+    nu: float
+    alpha: float
+    g_beta: float = 0.0
+    T0: float = 0.0
+    delta_T: float = 1.0
+    ax: float = 0.0
+    ay: float = 0.0
+    s_e: float = 1.0
+    s_q: float = 1.0
+    s_eps: float = 1.0
+    zeta_e: float = 1.0
+    zeta_nu: float = 1.0
+    varpi: float = 0.5
+    T_init: np.ndarray | None = None  # (ny, nx) float64
+    L: float = 1.0                  # characteristic length for Nu
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def fluid_nodes(self) -> int:
+        return int(np.count_nonzero(self.flags == 0))
+
+    def with_(self, **kw) -> "Case":
+        return replace(self, **kw)
+
+
+# ------------------------------------------------------------------ random --
+
+_GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+
+
+def splitmix64(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """n outputs of SplitMix64 (Steele, Lea, Flood 2014) starting at counter
+    `offset`: output k mixes seed + (k + 1) * 0x9E3779B97F4A7C15."""
+    with np.errstate(over="ignore"):
+        k = np.arange(offset + 1, offset + n + 1, dtype=np.uint64)
+        z = np.uint64(seed) + k * _GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform01(seed: int, n: int, offset: int = 0) -> np.ndarray:
+    """Doubles in [0, 1): the top 53 bits of SplitMix64 times 2^-53."""
+    return (splitmix64(seed, n, offset) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def gaussian(seed: int, n: int) -> np.ndarray:
+    """Standard normal draws by Box-Muller on consecutive uniform pairs."""
+    m = (n + 1) // 2
+    u = uniform01(seed, 2 * m)
+    u1 = 1.0 - u[0::2]  # in (0, 1]
+    u2 = u[1::2]
+    r = np.sqrt(-2.0 * np.log(u1))
+    z = np.concatenate([r * np.cos(2 * np.pi * u2), r * np.sin(2 * np.pi * u2)])
+    return z[:n]
+
+
+# ---------------------------------------------------------------- geometry --
+
+def _frame_y(nx: int, H: int, bottom: int, top: int) -> np.ndarray:
+    """Periodic-x channel: fluid rows 1..H, solid rows 0 (wall `bottom`) and H+1 (`top`)."""
+    flags = np.zeros((H + 2, nx), dtype=np.uint8)
+    flags[0, :] = bottom
+    flags[-1, :] = top
+    return flags
+
+
+def _frame_box(n_x: int, n_y: int, left: int, right: int, bottom: int, top: int) -> np.ndarray:
+    """Closed box of n_x x n_y fluid cells inside a one-cell solid frame. The four
+    corner cells take the side walls' ids (left / right)."""
+    flags = np.zeros((n_y + 2, n_x + 2), dtype=np.uint8)
+    flags[0, :] = bottom
+    flags[-1, :] = top
+    flags[:, 0] = left
+    flags[:, -1] = right
+    return flags
+
+
+def fluid_y(H: int) -> np.ndarray:
+    """Wall-normal positions of the fluid rows in units of H (halfway walls)."""
+    return (np.arange(H) + 0.5) / H
+
+
+# ----------------------------------------------------------------- problems --
+
+def porous_couette(H: int = 64, nx: int = 8, Re: float = 5.0, Pr: float = 0.71, Ra: float = 100.0,
+                   U0: float = 0.1, v0: float = 0.01, s_kin=(1.1, 1.2), T_h: float = 1.0,
+                   T_c: float = 0.0) -> Case:
+    """Thermal channel with wall injection (Sec. 3.3 of the paper): bottom plate
+    static and cold, top plate moving at U0 and hot, uniform injection v0 through
+    the bottom and suction through the top. Re = H v0 / nu, Pr = nu / alpha,
+    Ra = g beta dT H^3 / (nu alpha). s_kin = (a, b) sets s_e = s_eps = zeta_e = a
+    and s_q = zeta_nu = b."""
+    nu = H * v0 / Re
+    alpha = nu / Pr
+    dT = T_h - T_c
+    g_beta = Ra * nu * alpha / (dT * H ** 3)
+    walls = [Wall(0.0, v0, DIRICHLET, T_c), Wall(U0, v0, DIRICHLET, T_h)]
+    a, b = s_kin
+    return Case("porous_couette", nx, H + 2, True, False, _frame_y(nx, H, 1, 2), walls,
+                nu=nu, alpha=alpha, g_beta=g_beta, T0=0.5 * (T_h + T_c), delta_T=dT,
+                s_e=a, s_q=b, s_eps=a, zeta_e=a, zeta_nu=b, L=float(H),
+                meta=dict(Re=Re, Pr=Pr, Ra=Ra, U0=U0, v0=v0, T_h=T_h, T_c=T_c, H=H))
+
+
+def porous_couette_exact(case: Case):
+    """Closed-form steady profiles of the injection channel: Eq. 36 (u_x) and
+    Eq. 37 (T), at the fluid-row positions."""
+    m = case.meta
+    y = fluid_y(m["H"])
+    Re, Pr = m["Re"], m["Pr"]
+    ux = m["U0"] * np.expm1(Re * y) / np.expm1(Re)
+    T = m["T_c"] + (m["T_h"] - m["T_c"]) * np.expm1(Pr * Re * y) / np.expm1(Pr * Re)
+    return ux, T
+
+
+def couette(H: int = 16, nx: int = 4, U0: float = 0.05, nu: float = 0.1, T_bot: float = 0.0,
+            T_top: float = 1.0, alpha: float = 0.05, kinetic=None) -> Case:
+    """Plane Couette flow with conduction between two plates (no injection, no
+    buoyancy): steady u_x and T are linear in y."""
+    kin = dict(KINETIC_ONE if kinetic is None else kinetic)
+    walls = [Wall(0.0, 0.0, DIRICHLET, T_bot), Wall(U0, 0.0, DIRICHLET, T_top)]
+    return Case("couette", nx, H + 2, True, False, _frame_y(nx, H, 1, 2), walls, nu=nu,
+                alpha=alpha, T0=0.5 * (T_bot + T_top), delta_T=T_top - T_bot, L=float(H),
+                meta=dict(U0=U0, H=H, T_bot=T_bot, T_top=T_top), **kin)
+
+
+def poiseuille(H: int = 30, nx: int = 4, ax: float = 2e-6, nu: float = 1.0 / 6.0, kinetic=None) -> Case:
+    """Channel flow between static plates driven by a body force a = (ax, 0)
+    (Sec. 3.1). Steady profile u_x = ax y (H - y) / (2 nu)."""
+    kin = dict(KINETIC_ONE if kinetic is None else kinetic)
+    walls = [Wall(0.0, 0.0, ADIABATIC, 0.0), Wall(0.0, 0.0, ADIABATIC, 0.0)]
+    return Case("poiseuille", nx, H + 2, True, False, _frame_y(nx, H, 1, 2), walls, nu=nu,
+                alpha=0.1, ax=ax, L=float(H), meta=dict(H=H, ax=ax), **kin)
+
+
+def convection_params(L: float, Ra: float, Pr: float, Ma: float, dT: float = 1.0):
+    """nu, alpha, g beta from the definitions Ra = g beta dT L^3 / (nu alpha),
+    Pr = nu / alpha, Ma = u_c / c_s with u_c = sqrt(g beta dT L) (Sec. 3.4)."""
+    u_c = Ma * math.sqrt(CS2)
+    g_beta = u_c * u_c / (L * dT)
+    nu = u_c * L * math.sqrt(Pr / Ra)
+    return nu, nu / Pr, g_beta
+
+
+def cavity(n: int = 256, Ra: float = 1e5, Pr: float = 0.71, Ma: float = 0.1, seed: int = 0,
+           noise: float = 1e-6, T_h: float = 1.0, T_c: float = 0.0, n_y: int | None = None) -> Case:
+    """Differentially heated square cavity (Sec. 3.4): left wall hot, right wall
+    cold, top and bottom adiabatic, all no-slip. T_init = (T_h + T_c)/2 plus
+    uniform noise in [-noise, noise) from SplitMix64(seed)."""
+    n_y = n if n_y is None else n_y
+    dT = T_h - T_c
+    nu, alpha, g_beta = convection_params(float(n), Ra, Pr, Ma, dT)
+    walls = [Wall(0, 0, DIRICHLET, T_h), Wall(0, 0, DIRICHLET, T_c), Wall(0, 0, ADIABATIC, 0.0),
+             Wall(0, 0, ADIABATIC, 0.0)]
+    flags = _frame_box(n, n_y, 1, 2, 3, 4)
+    T0 = 0.5 * (T_h + T_c)
+    Ti = np.zeros(flags.shape)
+    fl = flags == 0
+    Ti[fl] = T0 + noise * (2.0 * uniform01(seed, int(fl.sum())) - 1.0)
+    return Case("cavity", n + 2, n_y + 2, False, False, flags, walls, nu=nu, alpha=alpha,
+                g_beta=g_beta, T0=T0, delta_T=dT, T_init=Ti, L=float(n),
+                meta=dict(Ra=Ra, Pr=Pr, Ma=Ma, seed=seed), **KINETIC_CONVECTION)
+
+
+def rayleigh_benard(nx: int = 4096, H: int = 2048, Ra: float = 1e6, Pr: float = 0.71, Ma: float = 0.1,
+                    seed: int = 0, sigma: float = 1e-3, T_h: float = 1.0, T_c: float = 0.0,
+                    L: float | None = None) -> Case:
+    """Rayleigh-Benard cell periodic in x: bottom plate hot, top plate cold,
+    both no-slip. T_init = the linear conduction profile plus N(0, sigma^2)
+    from SplitMix64(seed) with Box-Muller. The length scale is H unless L is
+    given (a crop run at the same nu, alpha, g beta as a larger cell)."""
+    Lc = float(H) if L is None else float(L)
+    dT = T_h - T_c
+    nu, alpha, g_beta = convection_params(Lc, Ra, Pr, Ma, dT)
+    walls = [Wall(0, 0, DIRICHLET, T_h), Wall(0, 0, DIRICHLET, T_c)]
+    flags = _frame_y(nx, H, 1, 2)
+    Ti = np.zeros(flags.shape)
+    prof = T_h - dT * fluid_y(H)
+    Ti[1:-1, :] = prof[:, None]
+    if sigma:
+        Ti[1:-1, :] += sigma * gaussian(seed, nx * H).reshape(H, nx)
+    return Case("rayleigh_benard", nx, H + 2, True, False, flags, walls, nu=nu, alpha=alpha,
+                g_beta=g_beta, T0=0.5 * (T_h + T_c), delta_T=dT, T_init=Ti, L=Lc,
+                meta=dict(Ra=Ra, Pr=Pr, Ma=Ma, seed=seed, sigma=sigma), **KINETIC_CONVECTION)
+
+
+def periodic_box(nx: int, ny: int, nu: float = 0.05, alpha: float = 0.05, g_beta: float = 0.0,
+                 T0: float = 0.0, T_init=None, kinetic=None, ax: float = 0.0, ay: float = 0.0) -> Case:
+    """Fully periodic lattice with no walls."""
+    kin = dict(KINETIC_ONE if kinetic is None else kinetic)
+    return Case("periodic", nx, ny, True, True, np.zeros((ny, nx), np.uint8), [], nu=nu, alpha=alpha,
+                g_beta=g_beta, T0=T0, T_init=T_init, ax=ax, ay=ay, L=float(ny), **kin)
+
+
+def random_state(case: Case, seed: int, amp_f: float = 0.02, amp_g: float = 0.05):
+    """A seeded non-equilibrium population state for parity checks: rest
+    weights w_i plus uniform noise for the flow, T0 shares plus noise for the
+    temperature; zeros on solid cells. Layout (9, ny, nx) and (5, ny, nx)."""
+    w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+    wT = np.array([1 - case.varpi] + [case.varpi / 4] * 4)
+    n = case.nx * case.ny
+    f = w9[:, None] + amp_f * (2 * uniform01(seed, 9 * n).reshape(9, n) - 1)
+    g = (case.T0 + 0.3) * wT[:, None] + amp_g * (2 * uniform01(seed + 1, 5 * n).reshape(5, n) - 1)
+    solid = (case.flags.reshape(-1) != 0)
+    f[:, solid] = 0.0
+    g[:, solid] = 0.0
+    return f.reshape(9, case.ny, case.nx), g.reshape(5, case.ny, case.nx)

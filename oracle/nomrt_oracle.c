@@ -1,0 +1,521 @@
+/*
+ * nomrt_oracle.c -- plain, slow FP64 CPU oracle for the double-distribution
+ * non-orthogonal MRT lattice Boltzmann method for incompressible thermal flow
+ * (Q. Liu, Y.-L. He, D. Li, Q. Li, arXiv:1510.08224).
+ *
+ * TEST INFRASTRUCTURE. This file exists to check the CUDA path, and to be timed
+ * as the CPU baseline. Only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark load it. It shares no code, header, table or helper with the
+ * CUDA library: the matrices below are the paper's printed tables, applied as
+ * dense products, in the order the paper states the algorithm.
+ *
+ * Method (Sec. 2):
+ *   flow   : D2Q9, f_bar = f - S/2 (Eq. 7); collision in moment space
+ *            m* = m - Lambda (m - m_eq) + (I - Lambda/2) S~   (Eq. 8)
+ *            with m = M f_bar (Eq. 10), M from Eq. 13, M^-1 from Eq. A1,
+ *            m_eq from Eq. 16, S~ from Eq. 17, Lambda from Eq. 20;
+ *            streaming f_bar_i(x + e_i, t + 1) = f_bar*_i(x, t) (Eq. 9).
+ *   heat   : D2Q5, n* = n - Q (n - n_eq) (Eq. 24), n = N g (Eq. 26),
+ *            n_eq from Eq. 28, Q from Eq. 29, N^-1 from Eq. A2; streaming Eq. 25.
+ *   force  : F = g beta (T - T0) j + a (Eq. 4).
+ *   macro  : rho = sum f_bar (Eq. 18), rho0 u = sum e f_bar + rho0 F / 2
+ *            (Eq. 19 under the incompressible approximation, Sec. 2.1),
+ *            T = sum g (Eq. 27).
+ *
+ * Readings where the paper is silent or inconsistent (identical on the CUDA side):
+ *   A1  incompressible approximation: rho appears only in the isotropic terms
+ *       (m0, the 2/3 rho of m3_eq, the rho/9 of m8_eq); every velocity-bearing
+ *       term carries rho0 (= 1, Sec. 3): j = rho0 u, rho0 |u|^2, rho0 F.
+ *   A2  S~_8 printed as (2/3) rho (ux Fy + uy Fx) in Eq. 17; M S of the
+ *       velocity-space forcing gives (2/3) rho (ux Fx + uy Fy). The derived form
+ *       is used; `s8_literal` selects the printed one (for an ablation test).
+ *   A4  initial state: f_bar_i = w_i rho0, g_i = g_eq_i(T_init, u = 0) (Eq. 30).
+ *   A5  halfway walls (the paper uses non-equilibrium extrapolation instead):
+ *       flow    f_i(x) = f*_opp(i)(x) + 2 w_i rho0 (e_i . u_w) / cs^2
+ *       T fixed g_i(x) = -g*_opp(i)(x) + 2 (varpi/4) T_w   (anti-bounce-back)
+ *       adiab.  g_i(x) =  g*_opp(i)(x)
+ *       for direction i arriving at fluid node x from solid node x - e_i; the
+ *       wall parameters are those of the solid cell x - e_i. Solid cells hold
+ *       zeros and are never updated.
+ *   A6  "the fields after N steps": pull with the wall rules, then the
+ *       macroscopics the (N+1)-th collision would use.
+ *   A8  Nusselt (Eq. 39): second-order one-sided gradient at the halfway wall,
+ *       dT/dn = (9 T_1/2 - T_3/2 - 8 T_w) / 3, midpoint average along the wall.
+ *   A9  residual: max(|u - u_prev|_2 / |u|_2, |T - T_prev|_2 / |T|_2) over
+ *       fluid nodes (u as a vector field), against the previous call's snapshot.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ---------------------------------------------------------------- tables -- */
+
+/* D2Q9 velocities, Eq. 5 with c = 1: rest, 4 axis, 4 diagonal. */
+static const int EX[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+static const int EY[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+/* Weights below Eq. 22. */
+static const double W9[9] = {4.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0,  1.0 / 9.0, 1.0 / 9.0,
+                             1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};
+static const double CS2 = 1.0 / 3.0; /* c_s^2, Sec. 2.1 */
+static const double RHO0 = 1.0;      /* reference density, Sec. 3 */
+
+/* Transformation matrix M, Eq. 13. */
+static const double M9[9][9] = {
+    {1, 1, 1, 1, 1, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0, 1, -1, -1, 1},
+    {0, 0, 1, 0, -1, 1, 1, -1, -1},
+    {0, 1, 1, 1, 1, 2, 2, 2, 2},
+    {0, 1, -1, 1, -1, 0, 0, 0, 0},
+    {0, 0, 0, 0, 0, 1, -1, 1, -1},
+    {0, 0, 0, 0, 0, 1, 1, -1, -1},
+    {0, 0, 0, 0, 0, 1, -1, -1, 1},
+    {0, 0, 0, 0, 0, 1, 1, 1, 1},
+};
+
+/* Its inverse, Eq. A1. */
+static const double MINV9[9][9] = {
+    {1, 0, 0, -1, 0, 0, 0, 0, 1},
+    {0, 0.5, 0, 0.25, 0.25, 0, 0, -0.5, -0.5},
+    {0, 0, 0.5, 0.25, -0.25, 0, -0.5, 0, -0.5},
+    {0, -0.5, 0, 0.25, 0.25, 0, 0, 0.5, -0.5},
+    {0, 0, -0.5, 0.25, -0.25, 0, 0.5, 0, -0.5},
+    {0, 0, 0, 0, 0, 0.25, 0.25, 0.25, 0.25},
+    {0, 0, 0, 0, 0, -0.25, 0.25, -0.25, 0.25},
+    {0, 0, 0, 0, 0, 0.25, -0.25, -0.25, 0.25},
+    {0, 0, 0, 0, 0, -0.25, -0.25, 0.25, 0.25},
+};
+
+/* D2Q5 transformation matrix N, Eq. 26. */
+static const double N5[5][5] = {
+    {1, 1, 1, 1, 1},
+    {0, 1, 0, -1, 0},
+    {0, 0, 1, 0, -1},
+    {0, 1, 1, 1, 1},
+    {0, 1, -1, 1, -1},
+};
+
+/* Its inverse, Eq. A2. */
+static const double NINV5[5][5] = {
+    {1, 0, 0, -1, 0},
+    {0, 0.5, 0, 0.25, 0.25},
+    {0, 0, 0.5, 0.25, -0.25},
+    {0, -0.5, 0, 0.25, 0.25},
+    {0, 0, -0.5, 0.25, -0.25},
+};
+
+/* Opposite directions under Eq. 5's numbering. */
+static const int OPP[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+
+/* ------------------------------------------------------------ interfaces -- */
+
+typedef struct {
+    int32_t nx, ny;
+    int32_t periodic_x, periodic_y;
+    const uint8_t *flags;      /* ny*nx row-major; 0 fluid, k >= 1 solid of wall k */
+    int32_t n_walls;
+    const double *wall_u;      /* 2*n_walls: (ux, uy) of wall k at [2(k-1)] */
+    const int32_t *wall_kind;  /* n_walls: 0 fixed temperature, 1 adiabatic */
+    const double *wall_T;      /* n_walls */
+    double nu, alpha;          /* viscosity, thermal diffusivity */
+    double g_beta, T0;         /* buoyancy coefficient and reference T, Eq. 4 */
+    double ax, ay;             /* external acceleration a, Eq. 4 */
+    double s_e, s_q, s_eps;    /* kinetic rates of Eq. 20 */
+    double zeta_e, zeta_nu;    /* kinetic rates of Eq. 29 */
+    double varpi;              /* model parameter of Eq. 28 */
+    int32_t s8_literal;        /* 1: the printed S~_8 of Eq. 17 (reading A2) */
+    const double *T_init;      /* ny*nx or NULL (T0 everywhere) */
+} orc_params;
+
+/* Per-node collision inputs. s[9] is Lambda of Eq. 20, z[5] is Q of Eq. 29. */
+typedef struct {
+    double s[9];
+    double z[5];
+    double g_beta, T0, ax, ay, varpi;
+    int32_t s8_literal;
+} orc_rates;
+
+typedef struct {
+    int nx, ny, px, py;
+    uint8_t *flags;
+    int n_walls;
+    double *wall_u, *wall_T;
+    int *wall_kind;
+    orc_rates r;
+    double *f[2]; /* [9][ny*nx] */
+    double *g[2]; /* [5][ny*nx] */
+    int cur;
+    double *snap; /* residual snapshot [3][ny*nx], NULL until first call */
+    int nthreads;
+} orc_lattice;
+
+/* ------------------------------------------------------------- collision -- */
+
+/* The flow collision of Sec. 2.1 at one node, followed by the heat collision of
+ * Sec. 2.2. fbar and g are the post-streaming populations; the outputs are the
+ * post-collision populations and (rho, ux, uy, T). */
+void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[5],
+                      double fstar[9], double gstar[5], double macro[4]) {
+    /* Eq. 27: temperature. */
+    double T = 0.0;
+    for (int i = 0; i < 5; ++i) T += g[i];
+    /* Eq. 4: Boussinesq buoyancy plus the external acceleration. */
+    double Fx = r->ax;
+    double Fy = r->ay + r->g_beta * (T - r->T0);
+    /* Eq. 18: density. */
+    double rho = 0.0;
+    for (int i = 0; i < 9; ++i) rho += fbar[i];
+    /* Eq. 19 with j = rho0 u (incompressible approximation, reading A1). */
+    double jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        jx += EX[i] * fbar[i];
+        jy += EY[i] * fbar[i];
+    }
+    double ux = (jx + 0.5 * RHO0 * Fx) / RHO0;
+    double uy = (jy + 0.5 * RHO0 * Fy) / RHO0;
+    double uu = ux * ux + uy * uy;
+
+    /* Eq. 10: m_bar = M f_bar. */
+    double m[9];
+    for (int k = 0; k < 9; ++k) {
+        m[k] = 0.0;
+        for (int i = 0; i < 9; ++i) m[k] += M9[k][i] * fbar[i];
+    }
+    /* Eq. 16 under reading A1. */
+    double meq[9];
+    meq[0] = rho;
+    meq[1] = RHO0 * ux;
+    meq[2] = RHO0 * uy;
+    meq[3] = 2.0 / 3.0 * rho + RHO0 * uu;
+    meq[4] = RHO0 * (ux * ux - uy * uy);
+    meq[5] = RHO0 * ux * uy;
+    meq[6] = 1.0 / 3.0 * RHO0 * uy;
+    meq[7] = 1.0 / 3.0 * RHO0 * ux;
+    meq[8] = 1.0 / 9.0 * rho + 1.0 / 3.0 * RHO0 * uu;
+    /* Eq. 17 under readings A1 and A2. */
+    double S[9];
+    S[0] = 0.0;
+    S[1] = RHO0 * Fx;
+    S[2] = RHO0 * Fy;
+    S[3] = 2.0 * RHO0 * (ux * Fx + uy * Fy);
+    S[4] = 2.0 * RHO0 * (ux * Fx - uy * Fy);
+    S[5] = RHO0 * (ux * Fy + uy * Fx);
+    S[6] = 1.0 / 3.0 * RHO0 * Fy;
+    S[7] = 1.0 / 3.0 * RHO0 * Fx;
+    S[8] = r->s8_literal ? 2.0 / 3.0 * RHO0 * (ux * Fy + uy * Fx)
+                         : 2.0 / 3.0 * RHO0 * (ux * Fx + uy * Fy);
+    /* Eq. 8 with the diagonal Lambda of Eq. 20 (delta_t = 1). */
+    double ms[9];
+    for (int k = 0; k < 9; ++k)
+        ms[k] = m[k] - r->s[k] * (m[k] - meq[k]) + (1.0 - 0.5 * r->s[k]) * S[k];
+    /* f_bar* = M^-1 m_bar* (Eq. A1). */
+    for (int i = 0; i < 9; ++i) {
+        fstar[i] = 0.0;
+        for (int k = 0; k < 9; ++k) fstar[i] += MINV9[i][k] * ms[k];
+    }
+
+    /* Eq. 26: n = N g. */
+    double n[5];
+    for (int k = 0; k < 5; ++k) {
+        n[k] = 0.0;
+        for (int i = 0; i < 5; ++i) n[k] += N5[k][i] * g[i];
+    }
+    /* Eq. 28. */
+    double neq[5] = {T, ux * T, uy * T, r->varpi * T, 0.0};
+    /* Eq. 24 with Q of Eq. 29. */
+    double ns[5];
+    for (int k = 0; k < 5; ++k) ns[k] = n[k] - r->z[k] * (n[k] - neq[k]);
+    /* g* = N^-1 n* (Eq. A2). */
+    for (int i = 0; i < 5; ++i) {
+        gstar[i] = 0.0;
+        for (int k = 0; k < 5; ++k) gstar[i] += NINV5[i][k] * ns[k];
+    }
+    if (macro) {
+        macro[0] = rho;
+        macro[1] = ux;
+        macro[2] = uy;
+        macro[3] = T;
+    }
+}
+
+/* Fill the rate vectors from the transport coefficients:
+ * nu = cs^2 (1/s_nu - 1/2) (Sec. 2.1), alpha = cs_T^2 (1/zeta_alpha - 1/2) with
+ * cs_T^2 = varpi / 2 (Sec. 2.2). s0 = s1 = s2 = 1 and zeta0 = 1 as in Eqs. 20, 29. */
+void orc_rates_from_params(const orc_params *p, orc_rates *r) {
+    double s_nu = 1.0 / (0.5 + p->nu / CS2);
+    double csT2 = 0.5 * p->varpi;
+    double z_alpha = 1.0 / (0.5 + p->alpha / csT2);
+    double s[9] = {1.0, 1.0, 1.0, p->s_e, s_nu, s_nu, p->s_q, p->s_q, p->s_eps};
+    double z[5] = {1.0, z_alpha, z_alpha, p->zeta_e, p->zeta_nu};
+    memcpy(r->s, s, sizeof s);
+    memcpy(r->z, z, sizeof z);
+    r->g_beta = p->g_beta;
+    r->T0 = p->T0;
+    r->ax = p->ax;
+    r->ay = p->ay;
+    r->varpi = p->varpi;
+    r->s8_literal = p->s8_literal;
+}
+
+/* -------------------------------------------------------------- lattice -- */
+
+static int wrap(int v, int n, int periodic) {
+    if (!periodic) return v;
+    if (v < 0) return v + n;
+    if (v >= n) return v - n;
+    return v;
+}
+
+/* Post-streaming populations at fluid node (x, y), pulled from the
+ * post-collision state (fsrc, gsrc) by Eqs. 9 and 25, with the wall rules of
+ * reading A5 on links whose source cell is solid. */
+static void gather(const orc_lattice *L, const double *fsrc, const double *gsrc, int x, int y,
+                   double fin[9], double gin[5]) {
+    const int nxy = L->nx * L->ny;
+    const int self = y * L->nx + x;
+    for (int i = 0; i < 9; ++i) {
+        int sx = wrap(x - EX[i], L->nx, L->px);
+        int sy = wrap(y - EY[i], L->ny, L->py);
+        int src = sy * L->nx + sx;
+        int k = L->flags[src];
+        if (k == 0) {
+            fin[i] = fsrc[i * nxy + src];
+        } else {
+            double uwx = L->wall_u[2 * (k - 1)], uwy = L->wall_u[2 * (k - 1) + 1];
+            fin[i] = fsrc[OPP[i] * nxy + self] + 2.0 * W9[i] * RHO0 * (EX[i] * uwx + EY[i] * uwy) / CS2;
+        }
+        if (i < 5) {
+            if (k == 0) {
+                gin[i] = gsrc[i * nxy + src];
+            } else if (L->wall_kind[k - 1] == 0) {
+                gin[i] = -gsrc[OPP[i] * nxy + self] + 2.0 * (L->r.varpi / 4.0) * L->wall_T[k - 1];
+            } else {
+                gin[i] = gsrc[OPP[i] * nxy + self];
+            }
+        }
+    }
+}
+
+void orc_destroy(orc_lattice *L);
+
+/* Returns NULL on invalid input: a fluid node whose pull source leaves a
+ * non-periodic edge, an unknown wall id, or a size below 1. */
+orc_lattice *orc_create(const orc_params *p) {
+    if (p->nx < 1 || p->ny < 1 || !p->flags) return NULL;
+    orc_lattice *L = (orc_lattice *)calloc(1, sizeof *L);
+    if (!L) return NULL;
+    L->nx = p->nx;
+    L->ny = p->ny;
+    L->px = p->periodic_x != 0;
+    L->py = p->periodic_y != 0;
+    L->nthreads = 1;
+    size_t nxy = (size_t)p->nx * p->ny;
+    L->flags = (uint8_t *)malloc(nxy);
+    memcpy(L->flags, p->flags, nxy);
+    L->n_walls = p->n_walls;
+    L->wall_u = (double *)calloc(2 * (size_t)(p->n_walls + 1), sizeof(double));
+    L->wall_T = (double *)calloc((size_t)p->n_walls + 1, sizeof(double));
+    L->wall_kind = (int *)calloc((size_t)p->n_walls + 1, sizeof(int));
+    for (int k = 0; k < p->n_walls; ++k) {
+        L->wall_u[2 * k] = p->wall_u[2 * k];
+        L->wall_u[2 * k + 1] = p->wall_u[2 * k + 1];
+        L->wall_T[k] = p->wall_T[k];
+        L->wall_kind[k] = p->wall_kind[k];
+    }
+    orc_rates_from_params(p, &L->r);
+    for (size_t c = 0; c < nxy; ++c)
+        if (L->flags[c] > p->n_walls) { orc_destroy(L); return NULL; }
+    for (int y = 0; y < L->ny; ++y)
+        for (int x = 0; x < L->nx; ++x) {
+            if (L->flags[y * L->nx + x]) continue;
+            for (int i = 1; i < 9; ++i) {
+                int sx = wrap(x - EX[i], L->nx, L->px), sy = wrap(y - EY[i], L->ny, L->py);
+                if (sx < 0 || sx >= L->nx || sy < 0 || sy >= L->ny) { orc_destroy(L); return NULL; }
+            }
+        }
+    for (int b = 0; b < 2; ++b) {
+        L->f[b] = (double *)calloc(9 * nxy, sizeof(double));
+        L->g[b] = (double *)calloc(5 * nxy, sizeof(double));
+    }
+    /* Reading A4: rest equilibrium, f_bar_i = w_i rho0, g_i = g_eq_i(T_init, 0) (Eqs. 22, 30). */
+    for (size_t c = 0; c < nxy; ++c) {
+        if (L->flags[c]) continue;
+        double T = p->T_init ? p->T_init[c] : p->T0;
+        for (int i = 0; i < 9; ++i) L->f[0][i * nxy + c] = W9[i] * RHO0;
+        L->g[0][0 * nxy + c] = (1.0 - p->varpi) * T;
+        for (int i = 1; i < 5; ++i) L->g[0][i * nxy + c] = 0.25 * p->varpi * T;
+    }
+    return L;
+}
+
+void orc_destroy(orc_lattice *L) {
+    if (!L) return;
+    free(L->flags);
+    free(L->wall_u);
+    free(L->wall_T);
+    free(L->wall_kind);
+    for (int b = 0; b < 2; ++b) { free(L->f[b]); free(L->g[b]); }
+    free(L->snap);
+    free(L);
+}
+
+void orc_set_threads(orc_lattice *L, int n) { L->nthreads = n < 1 ? 1 : n; }
+
+/* One time step (Eqs. 8-9, 24-25) for every fluid node, pull form. */
+void orc_step(orc_lattice *L, int64_t nsteps) {
+    const int nxy = L->nx * L->ny;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        const double *fs = L->f[L->cur], *gs = L->g[L->cur];
+        double *fd = L->f[1 - L->cur], *gd = L->g[1 - L->cur];
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(L->nthreads)
+#endif
+        for (int y = 0; y < L->ny; ++y) {
+            for (int x = 0; x < L->nx; ++x) {
+                int c = y * L->nx + x;
+                if (L->flags[c]) continue;
+                double fin[9], gin[5], fo[9], go[5];
+                gather(L, fs, gs, x, y, fin, gin);
+                orc_collide_node(&L->r, fin, gin, fo, go, NULL);
+                for (int i = 0; i < 9; ++i) fd[i * nxy + c] = fo[i];
+                for (int i = 0; i < 5; ++i) gd[i * nxy + c] = go[i];
+            }
+        }
+        L->cur = 1 - L->cur;
+    }
+}
+
+/* Reading A6: macroscopics at every node (solid nodes give zeros). */
+void orc_macro(const orc_lattice *L, double *rho, double *ux, double *uy, double *T) {
+    const int nxy = L->nx * L->ny;
+    for (int y = 0; y < L->ny; ++y)
+        for (int x = 0; x < L->nx; ++x) {
+            int c = y * L->nx + x;
+            double mac[4] = {0, 0, 0, 0};
+            if (!L->flags[c]) {
+                double fin[9], gin[5], fo[9], go[5];
+                gather(L, L->f[L->cur], L->g[L->cur], x, y, fin, gin);
+                orc_collide_node(&L->r, fin, gin, fo, go, mac);
+            }
+            if (rho) rho[c] = mac[0];
+            if (ux) ux[c] = mac[1];
+            if (uy) uy[c] = mac[2];
+            if (T) T[c] = mac[3];
+        }
+    (void)nxy;
+}
+
+/* The post-collision state, layout [9][ny*nx] and [5][ny*nx]. */
+void orc_get_populations(const orc_lattice *L, double *f, double *g) {
+    size_t nxy = (size_t)L->nx * L->ny;
+    if (f) memcpy(f, L->f[L->cur], 9 * nxy * sizeof(double));
+    if (g) memcpy(g, L->g[L->cur], 5 * nxy * sizeof(double));
+}
+
+void orc_set_populations(orc_lattice *L, const double *f, const double *g) {
+    size_t nxy = (size_t)L->nx * L->ny;
+    if (f) memcpy(L->f[L->cur], f, 9 * nxy * sizeof(double));
+    if (g) memcpy(L->g[L->cur], g, 5 * nxy * sizeof(double));
+    for (size_t c = 0; c < nxy; ++c)
+        if (L->flags[c]) {
+            for (int i = 0; i < 9; ++i) L->f[L->cur][i * nxy + c] = 0.0;
+            for (int i = 0; i < 5; ++i) L->g[L->cur][i * nxy + c] = 0.0;
+        }
+}
+
+/* One step at a single fluid node, reading an external post-collision state
+ * (fsrc [9][ny*nx], gsrc [5][ny*nx]) through this lattice's flags and walls.
+ * Used to check single sampled nodes of very large lattices. Returns -1 if the
+ * node is solid. */
+int orc_update_node(const orc_lattice *L, const double *fsrc, const double *gsrc, int x, int y,
+                    double fout[9], double gout[5]) {
+    if (L->flags[y * L->nx + x]) return -1;
+    double fin[9], gin[5];
+    gather(L, fsrc, gsrc, x, y, fin, gin);
+    orc_collide_node(&L->r, fin, gin, fout, gout, NULL);
+    return 0;
+}
+
+/* Eq. 39 with reading A8. side: 0 left (x min), 1 right, 2 bottom (y min), 3 top.
+ * The wall is the frame line of solid cells on that side; the average runs over
+ * the lines where the two nearest cells are fluid and the wall cell has a fixed
+ * temperature. Nu = -L (dT/dx_axis) / dT where x_axis is x for the side walls
+ * and y for the bottom and top. Returns NaN if no such line exists. */
+double orc_nusselt(const orc_lattice *L, int side, double Lref, double dT) {
+    double *T = (double *)malloc(sizeof(double) * (size_t)L->nx * L->ny);
+    orc_macro(L, NULL, NULL, NULL, T);
+    int along = (side < 2) ? L->ny : L->nx;
+    double sum = 0.0;
+    int count = 0;
+    for (int s = 0; s < along; ++s) {
+        int cw, c1, c2; /* wall cell, first and second fluid cells */
+        if (side == 0) { cw = s * L->nx + 0; c1 = cw + 1; c2 = cw + 2; }
+        else if (side == 1) { cw = s * L->nx + L->nx - 1; c1 = cw - 1; c2 = cw - 2; }
+        else if (side == 2) { cw = s; c1 = cw + L->nx; c2 = cw + 2 * L->nx; }
+        else { cw = (L->ny - 1) * L->nx + s; c1 = cw - L->nx; c2 = cw - 2 * L->nx; }
+        int k = L->flags[cw];
+        if (k == 0 || L->flags[c1] || L->flags[c2] || L->wall_kind[k - 1] != 0) continue;
+        /* dT/ds, s measured from the wall into the fluid. */
+        double dTds = (9.0 * T[c1] - T[c2] - 8.0 * L->wall_T[k - 1]) / 3.0;
+        double dTdaxis = (side == 0 || side == 2) ? dTds : -dTds;
+        sum += -Lref * dTdaxis / dT;
+        ++count;
+    }
+    free(T);
+    return count ? sum / count : NAN;
+}
+
+/* Reading A9. R = max(|u - u_prev|_2 / |u|_2, |T - T_prev|_2 / |T|_2), the norms
+ * taken over fluid nodes with u as a vector field. The first call stores the
+ * snapshot and returns +inf. NaN anywhere gives NaN. */
+double orc_residual(orc_lattice *L) {
+    size_t nxy = (size_t)L->nx * L->ny;
+    double *cur = (double *)malloc(3 * nxy * sizeof(double));
+    orc_macro(L, NULL, cur, cur + nxy, cur + 2 * nxy);
+    double R = INFINITY;
+    if (L->snap) {
+        double num_u = 0.0, den_u = 0.0, num_T = 0.0, den_T = 0.0;
+        for (size_t c = 0; c < nxy; ++c) {
+            if (L->flags[c]) continue;
+            for (int q = 0; q < 2; ++q) {
+                double d = cur[q * nxy + c] - L->snap[q * nxy + c];
+                num_u += d * d;
+                den_u += cur[q * nxy + c] * cur[q * nxy + c];
+            }
+            double d = cur[2 * nxy + c] - L->snap[2 * nxy + c];
+            num_T += d * d;
+            den_T += cur[2 * nxy + c] * cur[2 * nxy + c];
+        }
+        double du = sqrt(den_u), dT = sqrt(den_T);
+        double Ru = sqrt(num_u) / (du > 1e-300 ? du : 1e-300);
+        double RT = sqrt(num_T) / (dT > 1e-300 ? dT : 1e-300);
+        R = (Ru != Ru || RT != RT) ? NAN : (Ru > RT ? Ru : RT);
+        free(L->snap);
+    }
+    L->snap = cur;
+    return R;
+}
+
+/* Table export for the tests that pin the oracle to the paper. */
+void orc_tables(double *M, double *Minv, double *N, double *Ninv, int *ex, int *ey, double *w) {
+    if (M) memcpy(M, M9, sizeof M9);
+    if (Minv) memcpy(Minv, MINV9, sizeof MINV9);
+    if (N) memcpy(N, N5, sizeof N5);
+    if (Ninv) memcpy(Ninv, NINV5, sizeof NINV5);
+    if (ex) memcpy(ex, EX, sizeof EX);
+    if (ey) memcpy(ey, EY, sizeof EY);
+    if (w) memcpy(w, W9, sizeof W9);
+}
+
+void orc_get_rates(const orc_lattice *L, orc_rates *r) { *r = L->r; }
+
+int orc_threads_available(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
