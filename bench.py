@@ -1,0 +1,375 @@
+#!/usr/bin/env python3
+"""Throughput of the fused non-orthogonal MRT D2Q9+D2Q5 step on one GB300.
+
+Workload: Rayleigh-Benard cell, 4096 x 2048 fluid cells (plus the two wall
+rows), periodic in x, Ra = 1e6, Pr = 0.71, Ma = 0.1, seeded 1e-3 Gaussian
+temperature perturbation; FP32-shifted population storage by default.
+
+One bench step = one time step of the whole lattice (one fused kernel launch).
+value = fluid cells x steps / time / 1e6 (MLUPS), timed with CUDA events on the
+lattice's stream, inputs resident in HBM. The working set (two population
+buffers, > 1 GB) is far larger than L2, so no flush is needed between steps.
+
+--impl reference times the FP64 CPU oracle on the host cores instead, each
+step a bounded crop of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import lbm_cases as lc  # noqa: E402
+
+METRIC = "MLUPS (D2Q9+D2Q5) & % HBM roofline; solves/s and p50/p99 latency vs plain"
+# algorithmic bytes per fluid-cell update: 14 populations read + written, plus the 1-byte link map
+BYTES_PER_NODE = {"f64": 14 * 8 * 2 + 1, "f32": 14 * 4 * 2 + 1, "f16": 14 * 2 * 2 + 1}
+STORAGE_NAME = {"f64": "f64", "f32": "f32-shifted", "f16": "f16-shifted"}
+COMPUTE_DTYPE = {"f64": "f64", "f32": "f32", "f16": "f32"}
+PROFILE_DIR = os.path.join(ROOT, "profiles")
+
+
+def workload(nx: int, H: int):
+    return lc.rayleigh_benard(nx=nx, H=H, Ra=1e6, Pr=0.71, Ma=0.1, seed=0, sigma=1e-3)
+
+
+def kernel_source_hash() -> str:
+    d = os.path.join(ROOT, "paper_1510_08224_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def profiled_traffic(storage: str, nx: int, ny: int):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, or None
+    if there is none for this storage and size, or the kernel sources changed
+    since it was taken."""
+    path = os.path.join(PROFILE_DIR, f"k_step_{storage}_rb{nx}x{ny - 2}.md")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    with open(path) as f:
+        for line in f:
+            if line.startswith("<!--") and "=" in line:
+                for kv in line.strip("<!- >\n").split():
+                    if "=" in kv:
+                        k, v = kv.split("=", 1)
+                        vals[k] = v
+    if vals.get("kernel_hash") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["traffic_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, max clock, throttle reasons) every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.samples = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return self
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.perf_counter(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self, t0: float, t1: float):
+        inside = [s for t, s in self.samples if t0 <= t <= t1]
+        window = "timed"
+        if not inside:
+            inside = [s for _, s in self.samples]
+            window = "run"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"], "window": "none"}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in inside:
+            for k, n in enumerate(names):
+                if s[4 + k].lower().startswith("active"):
+                    reasons.add(n)
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(s[0]) for s in inside if num(s[0]) is not None]
+        mx = [num(s[1]) for s in inside if num(s[1]) is not None]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(inside), "window": window}
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def time_steps(P, torch, case, storage, steps, warmup):
+    """Device-timed K steps of one lattice. Returns (elapsed_ms, lattice)."""
+    lat = P.Lattice(case, storage=storage)
+    stream = torch.cuda.current_stream()
+    lat.step(warmup)
+    lat.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1), lat
+
+
+def e2e_run(P, torch, case, storage, steps):
+    """End to end through the public API with host buffers: create from host
+    flags and T_init (pinned), K steps, read rho, u, T back to host, destroy."""
+    T_pinned = torch.empty(case.T_init.shape, dtype=torch.float64).pin_memory()
+    T_pinned.numpy()[...] = case.T_init
+    ecase = case.with_(T_init=T_pinned.numpy())
+    out = [torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat = P.Lattice(ecase, storage=storage)
+    lat.step(steps)
+    import ctypes as C
+    L = P.load()
+    ptrs = [C.cast(o.data_ptr(), C.POINTER(C.c_double)) for o in out]
+    st = L.lbm_read_macro(lat.handle, *ptrs)
+    if st != 0:
+        raise RuntimeError(L.lbm_last_error(lat.handle).decode())
+    lat.close()
+    t1 = time.perf_counter()
+    h2d = case.nx * case.ny * (8 + 1)  # T_init + flags
+    d2h = 4 * 8 * case.nx * case.ny
+    return (t1 - t0), h2d, d2h
+
+
+def cpu_baseline(case_full, target_s: float = 15.0, crop=(512, 256)):
+    """The FP64 oracle as it stands on the host cores, on a crop of the
+    workload (same nu, alpha, g beta; crop x crop cells), timed for ~target_s."""
+    import oracle
+    threads = min(os.cpu_count() or 1, oracle.threads_available())
+    cx, cy = crop
+    crop_case = lc.rayleigh_benard(nx=cx, H=cy, Ra=1e6, Pr=0.71, Ma=0.1, seed=0, sigma=1e-3, L=case_full.L)
+    o = oracle.OracleLattice(crop_case, threads=threads)
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(2)
+    per = (time.perf_counter() - t0) / 2
+    n = max(3, int(target_s / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(n)
+    dt = time.perf_counter() - t0
+    mlups = crop_case.fluid_nodes * n / dt / 1e6
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{cx}x{cy} crop of the workload (same nu, alpha, g beta), {n} steps, {dt:.1f} s, "
+                      f"FP64 C oracle, OpenMP over rows"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    nx, H = args.nx, args.H
+    case_full = workload(nx, H)
+    threads = min(os.cpu_count() or 1, oracle.threads_available())
+    cx, cy = min(nx, 256), min(H, 128)
+    crop_case = lc.rayleigh_benard(nx=cx, H=cy, Ra=1e6, Pr=0.71, Ma=0.1, seed=0, sigma=1e-3, L=case_full.L)
+    o = oracle.OracleLattice(crop_case, threads=threads)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    mlups = crop_case.fluid_nodes * args.steps / dt / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups, 3), "unit": "MLUPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"rayleigh_benard_{nx}x{H}_ra1e6", "nx": nx, "ny": H, "storage": "f64 (CPU oracle)",
+                   "sample": f"each step: one {cx}x{cy} crop step"},
+        "cpu_baseline": {"value": round(mlups, 3), "unit": "MLUPS", "cores": threads, "kind": "oracle",
+                         "sample": f"{cx}x{cy} crop of the workload, {args.steps} steps"},
+        "e2e": {"value": round(mlups, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "f64"])
+    ap.add_argument("--nx", type=int, default=4096)
+    ap.add_argument("--H", type=int, default=2048)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1510_08224_gb300 as P
+
+    world, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    case = workload(args.nx, args.H)
+    fluid = case.fluid_nodes
+    sampler = ClockSampler(local).start()
+    # every rank advances its own replica of the workload (independent lattices)
+    lat = P.Lattice(case, storage=args.storage)
+    stream = torch.cuda.current_stream()
+    lat.step(args.warmup)
+    lat.sync()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = time.perf_counter()
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    t_end = time.perf_counter()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    sampler.stop()
+    clocks = sampler.summary(t_start, t_end)
+    r = lat.residual()  # finite-state check of the run (first call: snapshot)
+    lat.close()
+    del lat
+
+    value = world * fluid * args.steps / (ms_max * 1e-3) / 1e6
+    ms_step = ms_max / args.steps
+    peak, peak_src = measured_peak()
+    achieved = BYTES_PER_NODE[args.storage] * fluid / (ms / args.steps * 1e-3) / 1e9
+    traffic = profiled_traffic(args.storage, args.nx, args.H + 2)
+    roof = {"bound": "hbm" if args.storage != "f64" else "alu", "achieved": round(achieved, 1),
+            "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+            "kernel": "k_step", "bytes_per_node": BYTES_PER_NODE[args.storage],
+            "peak_source": f"{peak_src} HBM copy bandwidth (burst)"}
+    if args.storage == "f64":
+        roof["note"] = "FP64 arithmetic bound; GB/s shown against the HBM peak for reference"
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 5), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": COMPUTE_DTYPE[args.storage], "data": "synthetic",
+        "config": {"workload": f"rayleigh_benard_{args.nx}x{args.H}_ra1e6", "nx": args.nx, "ny": args.H,
+                   "fluid_cells": fluid, "storage": STORAGE_NAME[args.storage],
+                   "l2": "no flush: working set > L2 (two population buffers of "
+                         f"{BYTES_PER_NODE[args.storage] // 2 * fluid / 1e9:.2f} GB each)",
+                   "parallelism": f"replicas{world}"},
+        "roofline": roof,
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+        "residual_check": r,
+    }
+
+    if rank == 0 and not args.no_e2e:
+        e2e_steps = args.steps
+        secs, h2d, d2h = e2e_run(P, torch, case, args.storage, e2e_steps)
+        line["e2e"] = {"value": round(fluid * e2e_steps / secs / 1e6, 1), "unit": "MLUPS",
+                       "h2d_bytes_per_step": int(h2d / e2e_steps), "d2h_bytes_per_step": int(d2h / e2e_steps),
+                       "what": "lbm_create from pinned host flags+T_init, lbm_step(K), lbm_read_macro to pinned "
+                               "host, lbm_destroy; wall clock"}
+    if rank == 0 and not args.no_variants:
+        var = {}
+        for st in ("f32", "f16", "f64"):
+            if st == args.storage:
+                continue
+            k = max(10, min(args.steps, 500))
+            vms, vl = time_steps(P, torch, case, st, k, args.warmup)
+            vl.close()
+            vach = BYTES_PER_NODE[st] * fluid / (vms / k * 1e-3) / 1e9
+            var[STORAGE_NAME[st]] = {"MLUPS": round(fluid * k / (vms * 1e-3) / 1e6, 1), "steps": k,
+                                     "GB/s": round(vach, 1), "frac": round(vach / peak, 4)}
+        line["variants"] = var
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(case)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

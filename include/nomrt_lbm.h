@@ -1,0 +1,155 @@
+/*
+ * nomrt_lbm.h -- C ABI of the GB300 solver for the double-distribution
+ * non-orthogonal multiple-relaxation-time lattice Boltzmann method for
+ * incompressible thermal flow (Q. Liu, Y.-L. He, D. Li, Q. Li, arXiv:1510.08224).
+ *
+ * One call of lbm_step advances, at every fluid node, the D2Q9 flow populations
+ * f_bar (Eqs. 7-9: pull streaming, raw-moment map with the non-orthogonal M of
+ * Eq. 13, relaxation Eq. 8 with Eqs. 16, 17, 20, back map with M^-1 of Eq. A1)
+ * and the D2Q5 temperature populations g (Eqs. 24-29, N^-1 of Eq. A2), with the
+ * Boussinesq force of Eq. 4, in one fused CUDA kernel.
+ *
+ * Conventions common to every call:
+ *  - Every call returns an lbm_status and never throws or aborts.
+ *  - Pointers passed in are borrowed; inputs are copied before the call returns.
+ *  - A lattice is bound to one CUDA stream; its calls are not thread-safe.
+ *    Different lattices are independent.
+ *  - Host arrays are row-major [ny][nx] planes (x fastest); population exports
+ *    are [9][ny][nx] (f, directions of Eq. 5) and [5][ny][nx] (g).
+ *  - Lengths are lattice units (delta_x = delta_t = 1, c = 1, rho0 = 1: Sec. 3).
+ *  - Walls are half-way between a fluid cell and a solid cell (halfway
+ *    bounce-back). A fluid cell at a non-periodic edge is an error: the flag map
+ *    must carry a frame of solid cells there.
+ */
+#ifndef NOMRT_LBM_H
+#define NOMRT_LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,    /* invalid argument; lbm_last_error says which */
+    LBM_ENOMEM = 2,    /* device allocation failed or caller block too small */
+    LBM_ECUDA = 3,     /* a CUDA runtime call or launch failed */
+    LBM_EDIVERGED = 4, /* NaN/Inf found in the fields (unstable run) */
+    LBM_ETIMEOUT = 5   /* reserved for bounded device-side waits */
+} lbm_status;
+
+/* Population storage. The FP32/FP16 forms store deviations from the rest state,
+ * f_bar_i - w_i rho0 and g_i - w^T_i T0 (w^T = (1 - varpi, varpi/4 x4)), and
+ * compute moments and collision in FP32. LBM_F64 stores f_bar and g as they are
+ * and computes in FP64. */
+typedef enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1, LBM_F16_SHIFTED = 2 } lbm_storage;
+
+typedef enum { LBM_T_DIRICHLET = 0, LBM_T_ADIABATIC = 1 } lbm_thermal_kind;
+
+typedef enum { LBM_SIDE_LEFT = 0, LBM_SIDE_RIGHT = 1, LBM_SIDE_BOTTOM = 2, LBM_SIDE_TOP = 3 } lbm_side;
+
+/* One wall. Wall id k (the flag value of its solid cells) is walls[k-1].
+ * Flow: halfway bounce-back with Ladd's moving-wall term,
+ *   f_i(x) = f*_opp(i)(x) + 2 w_i rho0 (e_i . u_w) / c_s^2
+ * for a direction i arriving at fluid cell x from a solid cell of this wall;
+ * u_w may be tangential (a lid) or normal (a porous wall injecting fluid).
+ * Temperature: LBM_T_DIRICHLET holds T = T by anti-bounce-back,
+ *   g_i(x) = -g*_opp(i)(x) + 2 (varpi/4) T;
+ * LBM_T_ADIABATIC is a zero-flux wall, g_i(x) = g*_opp(i)(x). */
+typedef struct {
+    double ux, uy;
+    int32_t kind; /* lbm_thermal_kind */
+    int32_t reserved;
+    double T;
+} lbm_wall;
+
+/* Problem statement (Sec. 2, Eqs. 1-4) and the model's rates. */
+typedef struct {
+    int32_t nx, ny;               /* cells, frame included, x fastest */
+    int32_t periodic_x, periodic_y;
+    const uint8_t *flags;         /* ny*nx: 0 fluid, k >= 1 solid cell of wall k */
+    const lbm_wall *walls;        /* n_walls entries */
+    int32_t n_walls;              /* 0..254 */
+    int32_t storage;              /* lbm_storage */
+    double nu;                    /* viscosity: s_nu = 1 / (1/2 + nu / c_s^2), Sec. 2.1 */
+    double alpha;                 /* diffusivity: zeta_alpha = 1 / (1/2 + alpha / c_sT^2), c_sT^2 = varpi/2, Sec. 2.2 */
+    double g_beta;                /* buoyancy: F_y = g_beta (T - T0), Eq. 4 */
+    double T0;                    /* reference temperature of Eq. 4 */
+    double ax, ay;                /* external acceleration a of Eq. 4 */
+    double s_e, s_q, s_eps;       /* kinetic rates of Eq. 20, each in (0, 2) */
+    double zeta_e, zeta_nu;       /* kinetic rates of Eq. 29, each in (0, 2) */
+    double varpi;                 /* Eq. 28 parameter, in (0, 1); the paper uses 1/2 */
+    const double *T_init;         /* optional ny*nx initial temperature; NULL = T0 */
+} lbm_params;
+
+typedef struct lbm_lattice lbm_lattice; /* opaque; owned by the library */
+
+/* Device bytes lbm_create needs for these parameters (populations in two
+ * buffers, flag and link maps, residual snapshot, staging and reduction
+ * scratch), or 0 if the parameters are invalid. Admission control uses it. */
+size_t lbm_footprint_bytes(const lbm_params *p);
+
+/* Validate p, upload flags, walls and T_init, and set the initial state
+ * f_bar_i = w_i rho0, g_i = g_eq_i(T_init, u = 0) of Eqs. 22 and 30 (solid cells
+ * hold zeros). cuda_stream: a cudaStream_t, NULL for the legacy default stream.
+ * device_mem: NULL to let the library allocate, else a caller-owned device block
+ * of at least lbm_footprint_bytes(p) bytes, 256-byte aligned, that must outlive
+ * the lattice. On error *out is NULL and lbm_last_error(NULL) gives the reason.
+ * Synchronises the stream before returning. */
+lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, size_t device_bytes,
+                      lbm_lattice **out);
+
+/* Advance nsteps >= 0 time steps (Eqs. 8-9 and 24-25, fused, one kernel launch
+ * per step). Asynchronous on the lattice's stream. */
+lbm_status lbm_step(lbm_lattice *h, int64_t nsteps);
+
+/* Wait for the lattice's stream. */
+lbm_status lbm_sync(lbm_lattice *h);
+
+/* Macroscopic fields into caller-owned host arrays of ny*nx doubles (any may be
+ * NULL): the values the next collision would use (pull with the wall rules,
+ * then rho = sum f_bar (Eq. 18), rho0 u = sum e f_bar + F/2 (Eq. 19),
+ * T = sum g (Eq. 27)). Solid cells read 0. Synchronises. */
+lbm_status lbm_read_macro(lbm_lattice *h, double *rho, double *ux, double *uy, double *T);
+
+/* Mean Nusselt number on a frame wall (Eq. 39): Nu = -L (dT/dx_n) / delta_T,
+ * x_n = x for LEFT/RIGHT and y for BOTTOM/TOP, with the wall gradient
+ * (9 T_1/2 - T_3/2 - 8 T_w) / 3 from the two nearest fluid cells and the wall's
+ * fixed temperature, averaged over the lines where both cells are fluid and
+ * the frame cell is a fixed-temperature wall. L <= 0 means the number of
+ * fluid cells across the lattice along x_n. FP64 reduction. Synchronises.
+ * LBM_EINVAL if no such line exists. */
+lbm_status lbm_nusselt(lbm_lattice *h, int32_t side, double L, double delta_T, double *nu_mean);
+
+/* Steady-state residual R = max(|u - u'|_2 / |u|_2, |T - T'|_2 / |T|_2) over
+ * fluid cells, u a vector field, against the snapshot (u', T') the previous
+ * call stored; every call replaces the snapshot. The first call returns
+ * +infinity. FP64 reduction. LBM_EDIVERGED (and *r = NaN) if any value is NaN
+ * or infinite. Synchronises. */
+lbm_status lbm_residual(lbm_lattice *h, double *r);
+
+/* Export / import the post-collision state as FP64 f_bar [9][ny][nx] and
+ * g [5][ny][nx] host arrays (shift added back or removed; solid cells read 0
+ * and are forced to 0 on import). Either pointer may be NULL. Synchronises. */
+lbm_status lbm_get_populations(lbm_lattice *h, double *f9, double *g5);
+lbm_status lbm_set_populations(lbm_lattice *h, const double *f9, const double *g5);
+
+/* Sizes and layout: fluid cell count, row pitch in elements, bytes of one
+ * population element, steps taken since create. Any pointer may be NULL. */
+lbm_status lbm_info(const lbm_lattice *h, int64_t *fluid_cells, int32_t *pitch, int32_t *elem_bytes,
+                    int64_t *steps_done);
+
+/* Last error message of h (never NULL); with h == NULL, the calling thread's
+ * last lbm_create / lbm_footprint_bytes error. */
+const char *lbm_last_error(const lbm_lattice *h);
+
+/* Free the lattice (and its device memory if the library allocated it). */
+void lbm_destroy(lbm_lattice *h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NOMRT_LBM_H */

@@ -1,0 +1,12 @@
+"""GB300 solver for the double-distribution non-orthogonal MRT lattice
+Boltzmann method for incompressible thermal flow (Liu, He, Li & Li,
+arXiv:1510.08224).
+
+The hot path is one fused CUDA kernel per time step (sm_103a) behind the C ABI
+of ``include/nomrt_lbm.h``; :mod:`.lbm` is its ctypes binding.
+"""
+from .lbm import (EXPORTED, LBMError, Lattice, STORAGE, STORAGE_BYTES, SIDES, load, make_params,
+                  lbm_footprint_bytes, library_path)
+
+__all__ = ["EXPORTED", "LBMError", "Lattice", "STORAGE", "STORAGE_BYTES", "SIDES", "load", "make_params",
+           "lbm_footprint_bytes", "library_path"]

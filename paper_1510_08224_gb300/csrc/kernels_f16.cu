@@ -1,0 +1,9 @@
+// Instantiation of the fused stream-and-collide kernels for f16 population storage.
+#include "nomrt_kernels.cuh"
+
+namespace nomrt {
+const Launchers &launchers_f16() {
+    static const Launchers L = make_launchers<__half>();
+    return L;
+}
+}  // namespace nomrt

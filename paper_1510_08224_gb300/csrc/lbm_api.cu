@@ -1,0 +1,505 @@
+// Host side of the C ABI declared in include/nomrt_lbm.h: parameter
+// validation, device-memory layout, uploads, the step loop and the
+// synchronising read-outs. The arithmetic of the method runs in the kernels
+// of nomrt_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "nomrt_internal.h"
+#include "nomrt_lbm.h"
+
+using nomrt::KParams;
+using nomrt::kQ;
+using nomrt::kSolid;
+using nomrt::WallDev;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+constexpr double kCs2 = 1.0 / 3.0;  // D2Q9 c_s^2 (Sec. 2.1)
+constexpr size_t kAlign = 256;
+constexpr size_t kStageBytes = 16u << 20;  // row-chunked host transfers
+
+const int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};  // Eq. 5
+const int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+const double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t elem_bytes(int storage) { return storage == LBM_F64 ? 8 : storage == LBM_F32_SHIFTED ? 4 : 2; }
+
+// Device layout of one lattice, all offsets from the block base.
+struct Layout {
+    int pitch = 0;
+    size_t plane = 0;           // elements per plane
+    size_t pop_bytes = 0;       // one buffer
+    size_t off_pop[2] = {0, 0};
+    size_t off_mask = 0, off_flags = 0, off_walls = 0, off_snap = 0, off_stage = 0, off_part = 0, off_res = 0;
+    int stage_rows = 0;
+    size_t total = 0;
+};
+
+Layout make_layout(int nx, int ny, int storage, int n_walls) {
+    Layout L;
+    const size_t eb = elem_bytes(storage);
+    L.pitch = (int)align_up((size_t)nx, 128 / eb);
+    L.plane = (size_t)ny * L.pitch;
+    L.pop_bytes = align_up(L.plane * eb * kQ, kAlign);
+    size_t o = 0;
+    L.off_pop[0] = o; o += L.pop_bytes;
+    L.off_pop[1] = o; o += L.pop_bytes;
+    L.off_mask = o; o += align_up(L.plane, kAlign);
+    L.off_flags = o; o += align_up(L.plane, kAlign);
+    L.off_walls = o; o += align_up(sizeof(WallDev) * (size_t)(n_walls + 1), kAlign);
+    L.off_snap = o; o += align_up(3 * L.plane * sizeof(double), kAlign);
+    const size_t row_bytes = (size_t)kQ * nx * sizeof(double);
+    // at most 8192 rows per chunk keeps every chunked launch under the 65535 grid-y limit
+    L.stage_rows = (int)std::max<size_t>(1, std::min<size_t>({(size_t)ny, kStageBytes / row_bytes, (size_t)8192}));
+    L.off_stage = o; o += align_up(row_bytes * L.stage_rows, kAlign);
+    L.off_part = o; o += align_up(sizeof(double) * nomrt::kRedBlocks * 8, kAlign);
+    L.off_res = o; o += align_up(sizeof(double) * 8, kAlign);
+    L.total = o;
+    return L;
+}
+
+struct Derived {
+    double s_nu, z_a;
+};
+
+// Rates from the transport coefficients: nu = c_s^2 (1/s_nu - 1/2) (Sec. 2.1),
+// alpha = c_sT^2 (1/zeta_alpha - 1/2) with c_sT^2 = varpi/2 (Sec. 2.2).
+Derived derive(const lbm_params *p) {
+    Derived d;
+    d.s_nu = 1.0 / (0.5 + p->nu / kCs2);
+    d.z_a = 1.0 / (0.5 + p->alpha / (0.5 * p->varpi));
+    return d;
+}
+
+bool in_open_02(double v) { return std::isfinite(v) && v > 0.0 && v < 2.0; }
+
+// Returns an empty string if p is valid, else the reason.
+std::string validate(const lbm_params *p) {
+    char buf[256];
+    if (!p) return "params is NULL";
+    if (p->nx < 1 || p->ny < 1) return "nx and ny must be >= 1";
+    if (!p->flags) return "flags is NULL";
+    if (p->n_walls < 0 || p->n_walls > 254) return "n_walls must be in 0..254";
+    if (p->n_walls > 0 && !p->walls) return "walls is NULL";
+    if (p->storage < LBM_F64 || p->storage > LBM_F16_SHIFTED) return "unknown storage";
+    if (!(std::isfinite(p->varpi) && p->varpi > 0.0 && p->varpi < 1.0)) return "varpi must be in (0, 1)";
+    if (!(std::isfinite(p->nu) && p->nu > 0.0)) return "nu must be > 0";
+    if (!(std::isfinite(p->alpha) && p->alpha > 0.0)) return "alpha must be > 0";
+    Derived d = derive(p);
+    const double rates[7] = {d.s_nu, p->s_e, p->s_q, p->s_eps, d.z_a, p->zeta_e, p->zeta_nu};
+    const char *names[7] = {"s_nu", "s_e", "s_q", "s_eps", "zeta_alpha", "zeta_e", "zeta_nu"};
+    for (int k = 0; k < 7; ++k)
+        if (!in_open_02(rates[k])) {
+            snprintf(buf, sizeof buf, "rate %s = %g is outside (0, 2)", names[k], rates[k]);
+            return buf;
+        }
+    const double finite[6] = {p->g_beta, p->T0, p->ax, p->ay, 0, 0};
+    for (double v : finite)
+        if (!std::isfinite(v)) return "g_beta, T0, ax, ay must be finite";
+    for (int k = 0; k < p->n_walls; ++k) {
+        const lbm_wall &w = p->walls[k];
+        if (!std::isfinite(w.ux) || !std::isfinite(w.uy) || !std::isfinite(w.T)) return "wall values must be finite";
+        if (w.kind != LBM_T_DIRICHLET && w.kind != LBM_T_ADIABATIC) return "unknown wall thermal kind";
+    }
+    const size_t eb = elem_bytes(p->storage);
+    const size_t pitch = align_up((size_t)p->nx, 128 / eb);
+    if ((size_t)p->ny * pitch >= (size_t)INT32_MAX) return "lattice too large (ny * pitch must be < 2^31)";
+    const int nx = p->nx, ny = p->ny;
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const uint8_t k = p->flags[(size_t)y * nx + x];
+            if (k > p->n_walls) {
+                snprintf(buf, sizeof buf, "cell (%d, %d) has wall id %d > n_walls", x, y, (int)k);
+                return buf;
+            }
+            if (k) continue;
+            int solid = 0;
+            for (int i = 1; i < 9; ++i) {
+                int sx = x - kEx[i], sy = y - kEy[i];
+                if (p->periodic_x) sx = (sx + nx) % nx;
+                if (p->periodic_y) sy = (sy + ny) % ny;
+                if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
+                    snprintf(buf, sizeof buf,
+                             "fluid cell (%d, %d) touches a non-periodic edge; add a frame of solid cells", x, y);
+                    return buf;
+                }
+                solid += p->flags[(size_t)sy * nx + sx] != 0;
+            }
+            if (solid == 8) {
+                snprintf(buf, sizeof buf, "fluid cell (%d, %d) has no fluid neighbour", x, y);
+                return buf;
+            }
+        }
+    return std::string();
+}
+
+const nomrt::Launchers &launchers_for(int storage) {
+    return storage == LBM_F64 ? nomrt::launchers_f64()
+           : storage == LBM_F32_SHIFTED ? nomrt::launchers_f32()
+                                        : nomrt::launchers_f16();
+}
+
+}  // namespace
+
+struct lbm_lattice {
+    int nx = 0, ny = 0, px = 0, py = 0, storage = 0, n_walls = 0;
+    cudaStream_t stream = nullptr;
+    char *mem = nullptr;
+    bool owns_mem = false;
+    Layout lay;
+    KParams kp;
+    int cur = 0;
+    int have_snap = 0;
+    int64_t fluid = 0;
+    int64_t steps = 0;
+    std::vector<uint8_t> flags;
+    std::string err;
+    const nomrt::Launchers *L = nullptr;
+
+    double *stage() const { return reinterpret_cast<double *>(mem + lay.off_stage); }
+    double *partials() const { return reinterpret_cast<double *>(mem + lay.off_part); }
+    double *result() const { return reinterpret_cast<double *>(mem + lay.off_res); }
+    double *snap() const { return reinterpret_cast<double *>(mem + lay.off_snap); }
+};
+
+namespace {
+
+lbm_status fail(lbm_lattice *h, lbm_status st, const std::string &msg) {
+    if (h) h->err = msg;
+    else g_create_error = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_lattice *h, cudaError_t e, const char *what) {
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(h, LBM_ECUDA, m);
+}
+
+#define LBM_CUDA(h, call, what)                      \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+}  // namespace
+
+extern "C" {
+
+size_t lbm_footprint_bytes(const lbm_params *p) {
+    std::string why = validate(p);
+    if (!why.empty()) {
+        g_create_error = why;
+        return 0;
+    }
+    return make_layout(p->nx, p->ny, p->storage, p->n_walls).total;
+}
+
+lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, size_t device_bytes,
+                      lbm_lattice **out) {
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    std::string why = validate(p);
+    if (!why.empty()) return fail(nullptr, LBM_EINVAL, why);
+    lbm_lattice *h = new (std::nothrow) lbm_lattice();
+    if (!h) return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    h->nx = p->nx;
+    h->ny = p->ny;
+    h->px = p->periodic_x != 0;
+    h->py = p->periodic_y != 0;
+    h->storage = p->storage;
+    h->n_walls = p->n_walls;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->lay = make_layout(p->nx, p->ny, p->storage, p->n_walls);
+    h->L = &launchers_for(p->storage);
+    const size_t need = h->lay.total;
+    auto bail = [&](lbm_status st, const std::string &m) {
+        g_create_error = m;
+        lbm_destroy(h);
+        return st;
+    };
+    if (device_mem) {
+        uintptr_t a = reinterpret_cast<uintptr_t>(device_mem);
+        if (a % kAlign) return bail(LBM_EINVAL, "device_mem must be 256-byte aligned");
+        if (device_bytes < need) return bail(LBM_ENOMEM, "device_mem smaller than lbm_footprint_bytes");
+        h->mem = static_cast<char *>(device_mem);
+    } else {
+        void *m = nullptr;
+        cudaError_t e = cudaMalloc(&m, need);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return bail(LBM_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+        }
+        h->mem = static_cast<char *>(m);
+        h->owns_mem = true;
+    }
+
+    // host-side maps: wall ids and the link map (bit i-1: direction i pulls from a solid cell)
+    const int nx = p->nx, ny = p->ny, pitch = h->lay.pitch;
+    h->flags.assign(p->flags, p->flags + (size_t)nx * ny);
+    std::vector<uint8_t> hmask((size_t)ny * pitch, kSolid), hflags((size_t)ny * pitch, 0);
+    for (int y = 0; y < ny; ++y)
+        for (int x = 0; x < nx; ++x) {
+            const uint8_t k = p->flags[(size_t)y * nx + x];
+            hflags[(size_t)y * pitch + x] = k;
+            if (k) continue;
+            ++h->fluid;
+            unsigned m = 0;
+            for (int i = 1; i < 9; ++i) {
+                int sx = x - kEx[i], sy = y - kEy[i];
+                if (h->px) sx = (sx + nx) % nx;
+                if (h->py) sy = (sy + ny) % ny;
+                if (p->flags[(size_t)sy * nx + sx]) m |= 1u << (i - 1);
+            }
+            hmask[(size_t)y * pitch + x] = (uint8_t)m;
+        }
+    std::vector<WallDev> hw((size_t)p->n_walls + 1);
+    std::memset(hw.data(), 0, sizeof(WallDev) * hw.size());
+    const double T_ref = p->storage == LBM_F64 ? 0.0 : p->T0;
+    for (int k = 1; k <= p->n_walls; ++k) {
+        const lbm_wall &w = p->walls[k - 1];
+        for (int i = 0; i < 9; ++i) hw[k].cf[i] = 2.0 * kW[i] * 1.0 * (kEx[i] * w.ux + kEy[i] * w.uy) / kCs2;
+        if (w.kind == LBM_T_DIRICHLET) {
+            hw[k].tsgn = -1.0;
+            hw[k].tb = 0.5 * p->varpi * (w.T - T_ref);
+        } else {
+            hw[k].tsgn = 1.0;
+            hw[k].tb = 0.0;
+        }
+        hw[k].Tw = w.T;
+    }
+
+    KParams &kp = h->kp;
+    kp.nx = nx;
+    kp.ny = ny;
+    kp.pitch = pitch;
+    kp.px = h->px;
+    kp.py = h->py;
+    kp.plane = h->lay.plane;
+    kp.pop[0] = h->mem + h->lay.off_pop[0];
+    kp.pop[1] = h->mem + h->lay.off_pop[1];
+    kp.mask = reinterpret_cast<const uint8_t *>(h->mem + h->lay.off_mask);
+    kp.flags = reinterpret_cast<const uint8_t *>(h->mem + h->lay.off_flags);
+    kp.walls = reinterpret_cast<const WallDev *>(h->mem + h->lay.off_walls);
+    Derived d = derive(p);
+    kp.s_e = p->s_e;
+    kp.s_nu = d.s_nu;
+    kp.s_q = p->s_q;
+    kp.s_eps = p->s_eps;
+    kp.z_a = d.z_a;
+    kp.z_e = p->zeta_e;
+    kp.z_nu = p->zeta_nu;
+    kp.g_beta = p->g_beta;
+    kp.T0 = p->T0;
+    kp.ax = p->ax;
+    kp.ay = p->ay;
+    kp.varpi = p->varpi;
+    kp.rho_ref = p->storage == LBM_F64 ? 0.0 : 1.0;
+    kp.T_ref = T_ref;
+
+    cudaStream_t st = h->stream;
+    auto cuda_bail = [&](cudaError_t e, const char *what) {
+        return bail(LBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(h->mem, 0, need, st)) != cudaSuccess) return cuda_bail(e, "memset");
+    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_mask, hmask.data(), hmask.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return cuda_bail(e, "upload link map");
+    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_flags, hflags.data(), hflags.size(), cudaMemcpyHostToDevice,
+                             st)) != cudaSuccess)
+        return cuda_bail(e, "upload flags");
+    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_walls, hw.data(), sizeof(WallDev) * hw.size(),
+                             cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_bail(e, "upload walls");
+    // initial state, row chunks of T through the staging area
+    std::vector<double> Trow((size_t)h->lay.stage_rows * nx);
+    for (int r0 = 0; r0 < ny; r0 += h->lay.stage_rows) {
+        const int r1 = std::min(ny, r0 + h->lay.stage_rows);
+        const size_t n = (size_t)(r1 - r0) * nx;
+        if (p->T_init)
+            std::memcpy(Trow.data(), p->T_init + (size_t)r0 * nx, n * sizeof(double));
+        else
+            std::fill(Trow.begin(), Trow.begin() + n, p->T0);
+        if ((e = cudaMemcpyAsync(h->stage(), Trow.data(), n * sizeof(double), cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+            return cuda_bail(e, "upload T_init");
+        if ((e = h->L->init_rows(kp, 0, r0, r1, h->stage(), st)) != cudaSuccess) return cuda_bail(e, "init kernel");
+        // the staging buffer is reused by the next chunk: wait for this one
+        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_bail(e, "init sync");
+    }
+    h->cur = 0;
+    *out = h;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_lattice *h, int64_t nsteps) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
+    for (int64_t s = 0; s < nsteps; ++s) {
+        cudaError_t e = h->L->step(h->kp, h->cur, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+        h->cur ^= 1;
+        ++h->steps;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_lattice *h) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream sync");
+    return LBM_OK;
+}
+
+lbm_status lbm_read_macro(lbm_lattice *h, double *rho, double *ux, double *uy, double *T) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    double *outs[4] = {rho, ux, uy, T};
+    const int nx = h->nx;
+    const int rows = std::max(1, h->lay.stage_rows * kQ / 4);
+    for (int r0 = 0; r0 < h->ny; r0 += rows) {
+        const int r1 = std::min(h->ny, r0 + rows);
+        const size_t n = (size_t)(r1 - r0) * nx;
+        LBM_CUDA(h, h->L->macro_rows(h->kp, h->cur, r0, r1, h->stage(), h->stream), "macro kernel");
+        for (int k = 0; k < 4; ++k)
+            if (outs[k])
+                LBM_CUDA(h,
+                         cudaMemcpyAsync(outs[k] + (size_t)r0 * nx, h->stage() + k * n, n * sizeof(double),
+                                         cudaMemcpyDeviceToHost, h->stream),
+                         "read macro");
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "read macro sync");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_nusselt(lbm_lattice *h, int32_t side, double L, double delta_T, double *nu_mean) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    if (!nu_mean) return fail(h, LBM_EINVAL, "nu_mean is NULL");
+    if (side < 0 || side > 3) return fail(h, LBM_EINVAL, "side must be 0..3");
+    if (!(std::isfinite(delta_T) && delta_T != 0.0)) return fail(h, LBM_EINVAL, "delta_T must be finite, non-zero");
+    if (!(L > 0.0)) {
+        // fluid cells across the lattice along the wall normal, on the middle line
+        int count = 0;
+        if (side < 2) {
+            const int y = h->ny / 2;
+            for (int x = 0; x < h->nx; ++x) count += h->flags[(size_t)y * h->nx + x] == 0;
+        } else {
+            const int x = h->nx / 2;
+            for (int y = 0; y < h->ny; ++y) count += h->flags[(size_t)y * h->nx + x] == 0;
+        }
+        L = (double)count;
+    }
+    LBM_CUDA(h, h->L->nusselt(h->kp, h->cur, side, L, delta_T, h->partials(), h->stream), "nusselt kernel");
+    LBM_CUDA(h, nomrt::reduce_partials(h->partials(), 2, h->result(), h->stream), "reduce kernel");
+    double r[2];
+    LBM_CUDA(h, cudaMemcpyAsync(r, h->result(), sizeof r, cudaMemcpyDeviceToHost, h->stream), "read nusselt");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "nusselt sync");
+    if (r[1] <= 0.0) return fail(h, LBM_EINVAL, "no fixed-temperature wall line on that side");
+    *nu_mean = r[0] / r[1];
+    return LBM_OK;
+}
+
+lbm_status lbm_residual(lbm_lattice *h, double *r) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    if (!r) return fail(h, LBM_EINVAL, "r is NULL");
+    const int had = h->have_snap;
+    LBM_CUDA(h, h->L->residual(h->kp, h->cur, h->snap(), had, h->partials(), h->stream), "residual kernel");
+    LBM_CUDA(h, nomrt::reduce_partials(h->partials(), 5, h->result(), h->stream), "reduce kernel");
+    double s[5];
+    LBM_CUDA(h, cudaMemcpyAsync(s, h->result(), sizeof s, cudaMemcpyDeviceToHost, h->stream), "read residual");
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "residual sync");
+    h->have_snap = 1;
+    if (s[4] > 0.0 || !std::isfinite(s[0]) || !std::isfinite(s[1]) || !std::isfinite(s[2]) ||
+        !std::isfinite(s[3])) {
+        *r = NAN;
+        return fail(h, LBM_EDIVERGED, "non-finite velocity or temperature");
+    }
+    if (!had) {
+        *r = INFINITY;
+        return LBM_OK;
+    }
+    const double du = std::sqrt(s[1]), dT = std::sqrt(s[3]);
+    const double Ru = std::sqrt(s[0]) / std::max(du, 1e-300);
+    const double RT = std::sqrt(s[2]) / std::max(dT, 1e-300);
+    *r = std::max(Ru, RT);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_populations(lbm_lattice *h, double *f9, double *g5) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    const int nx = h->nx;
+    const size_t nxy = (size_t)nx * h->ny;
+    for (int r0 = 0; r0 < h->ny; r0 += h->lay.stage_rows) {
+        const int r1 = std::min(h->ny, r0 + h->lay.stage_rows);
+        const size_t n = (size_t)(r1 - r0) * nx;
+        LBM_CUDA(h, h->L->export_rows(h->kp, h->cur, r0, r1, h->stage(), h->stream), "export kernel");
+        for (int q = 0; q < kQ; ++q) {
+            double *dst = q < 9 ? (f9 ? f9 + q * nxy : nullptr) : (g5 ? g5 + (q - 9) * nxy : nullptr);
+            if (dst)
+                LBM_CUDA(h,
+                         cudaMemcpyAsync(dst + (size_t)r0 * nx, h->stage() + q * n, n * sizeof(double),
+                                         cudaMemcpyDeviceToHost, h->stream),
+                         "export copy");
+        }
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "export sync");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_populations(lbm_lattice *h, const double *f9, const double *g5) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    const int nx = h->nx;
+    const size_t nxy = (size_t)nx * h->ny;
+    const int which = (f9 ? 1 : 0) | (g5 ? 2 : 0);
+    if (!which) return LBM_OK;
+    for (int r0 = 0; r0 < h->ny; r0 += h->lay.stage_rows) {
+        const int r1 = std::min(h->ny, r0 + h->lay.stage_rows);
+        const size_t n = (size_t)(r1 - r0) * nx;
+        for (int q = 0; q < kQ; ++q) {
+            const double *src = q < 9 ? (f9 ? f9 + q * nxy : nullptr) : (g5 ? g5 + (q - 9) * nxy : nullptr);
+            if (src)
+                LBM_CUDA(h,
+                         cudaMemcpyAsync(h->stage() + q * n, src + (size_t)r0 * nx, n * sizeof(double),
+                                         cudaMemcpyHostToDevice, h->stream),
+                         "import copy");
+        }
+        LBM_CUDA(h, h->L->import_rows(h->kp, h->cur, r0, r1, h->stage(), which, h->stream), "import kernel");
+        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "import sync");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_info(const lbm_lattice *h, int64_t *fluid_cells, int32_t *pitch, int32_t *elem, int64_t *steps_done) {
+    if (!h) return LBM_EINVAL;
+    if (fluid_cells) *fluid_cells = h->fluid;
+    if (pitch) *pitch = h->lay.pitch;
+    if (elem) *elem = (int32_t)elem_bytes(h->storage);
+    if (steps_done) *steps_done = h->steps;
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_lattice *h) {
+    if (!h) return g_create_error.c_str();
+    return h->err.c_str();
+}
+
+void lbm_destroy(lbm_lattice *h) {
+    if (!h) return;
+    if (h->owns_mem && h->mem) {
+        cudaStreamSynchronize(h->stream);
+        cudaFree(h->mem);
+    }
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,79 @@
+// Internal interface between the C-ABI host code (lbm_api.cu) and the
+// per-storage kernel translation units (kernels_f64.cu, kernels_f32.cu,
+// kernels_f16.cu). Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace nomrt {
+
+// Number of populations per node: 9 (D2Q9 flow, Eq. 5) + 5 (D2Q5 temperature).
+constexpr int kQ = 14;
+// Link-map value of a solid cell (and of the row padding).
+constexpr uint8_t kSolid = 0xFF;
+// Fixed number of blocks of the reduction kernels (deterministic sums).
+constexpr int kRedBlocks = 512;
+constexpr int kRedThreads = 256;
+
+// Per-wall constants, indexed by wall id (entry 0 unused). cf[i] is Ladd's
+// moving-wall term 2 w_i rho0 (e_i . u_w) / c_s^2 for direction i; a
+// temperature link from the wall gives g_i = tsgn * g*_opp(i) + tb, with
+// tsgn = -1, tb = (varpi/2)(T_w - T_ref) for a fixed temperature T_w
+// (anti-bounce-back) and tsgn = +1, tb = 0 for an adiabatic wall.
+struct WallDev {
+    double cf[9];
+    double tsgn;
+    double tb;
+    double Tw;
+    double pad[4];
+};
+
+// Everything a kernel needs to know about one lattice, in FP64; each kernel
+// translation unit converts the rates to its compute type.
+struct KParams {
+    int nx, ny, pitch;
+    int px, py;                 // periodic x / y
+    size_t plane;               // elements per population plane (ny * pitch)
+    void *pop[2];               // the two ping-pong buffers, kQ planes each
+    const uint8_t *mask;        // link map: bit i-1 set if direction i pulls from a solid cell
+    const uint8_t *flags;       // wall ids
+    const WallDev *walls;
+    // rates and constants
+    double s_e, s_nu, s_q, s_eps;     // Eq. 20
+    double z_a, z_e, z_nu;            // Eq. 29
+    double g_beta, T0, ax, ay, varpi; // Eq. 4, Eq. 28
+    double rho_ref, T_ref;            // storage shift (0 for FP64 storage)
+};
+
+// Launchers, one set per storage type (0 = f64, 1 = f32-shifted, 2 = f16-shifted).
+// All are asynchronous on `st` and return the launch error.
+struct Launchers {
+    // one fused stream-and-collide step reading buffer `src`, writing 1 - src
+    cudaError_t (*step)(const KParams &, int src, cudaStream_t st);
+    // initial state into buffer `buf`, rows [r0, r1); T rows in `T` (device, (r1-r0)*nx)
+    cudaError_t (*init_rows)(const KParams &, int buf, int r0, int r1, const double *T, cudaStream_t st);
+    // macroscopics of rows [r0, r1) into out[4][(r1-r0)*nx] (rho, ux, uy, T)
+    cudaError_t (*macro_rows)(const KParams &, int buf, int r0, int r1, double *out, cudaStream_t st);
+    // FP64 export / import of rows [r0, r1): out/in [kQ][(r1-r0)*nx]
+    cudaError_t (*export_rows)(const KParams &, int buf, int r0, int r1, double *out, cudaStream_t st);
+    cudaError_t (*import_rows)(const KParams &, int buf, int r0, int r1, const double *in, int which,
+                               cudaStream_t st);
+    // Nusselt partial sums (sum, count) per block into partials[kRedBlocks][2]
+    cudaError_t (*nusselt)(const KParams &, int buf, int side, double L, double dT, double *partials,
+                           cudaStream_t st);
+    // residual partial sums (|du|^2, |u|^2, dT^2, T^2, nonfinite) per block into
+    // partials[kRedBlocks][5]; updates snap[3][plane] (ux, uy, T)
+    cudaError_t (*residual)(const KParams &, int buf, double *snap, int have_snap, double *partials,
+                            cudaStream_t st);
+};
+
+const Launchers &launchers_f64();
+const Launchers &launchers_f32();
+const Launchers &launchers_f16();
+
+// Final fixed-order reduction of partials[kRedBlocks][width] into out[width].
+cudaError_t reduce_partials(const double *partials, int width, double *out, cudaStream_t st);
+
+}  // namespace nomrt

@@ -1,0 +1,553 @@
+// Device code of the fused non-orthogonal MRT stream-and-collide update
+// (Liu, He, Li & Li, arXiv:1510.08224, Sec. 2), templated on the population
+// storage type. Included once by each of kernels_f64.cu, kernels_f32.cu and
+// kernels_f16.cu, which instantiate it and fill a Launchers table.
+//
+// Data layout in HBM (structure of arrays, ping-pong):
+//   pop[b] = kQ planes of ny rows x pitch elements; planes 0..8 hold f_bar_i,
+//   planes 9..13 hold g_i, in the direction order of Eq. 5. pitch is nx rounded
+//   up to a 128-byte multiple. A node is read from the source buffer by the pull
+//   form of the streaming steps (Eqs. 9, 25): f_bar_i(x) <- f_bar*_i(x - e_i),
+//   collided in registers, and written back at x in the other buffer.
+//
+// Arithmetic: the 9x9 map of Eq. 13 and its inverse (Eq. A1) are applied as
+// add/sub chains on shared pair sums; the 1/2 and 1/4 of Eq. A1 are exact
+// scalings. No tensor cores: each node is a separate 9-vector.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "nomrt_internal.h"
+
+namespace nomrt {
+
+// ------------------------------------------------------------ storage traits
+
+template <typename S>
+struct Store;
+
+template <>
+struct Store<double> {
+    using C = double;
+    static constexpr bool kShifted = false;
+    static __device__ __forceinline__ C ld(const double *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(double *p, C v) { *p = v; }
+};
+
+template <>
+struct Store<float> {
+    using C = float;
+    static constexpr bool kShifted = true;
+    static __device__ __forceinline__ C ld(const float *p) { return __ldg(p); }
+    static __device__ __forceinline__ void st(float *p, C v) { *p = v; }
+};
+
+template <>
+struct Store<__half> {
+    using C = float;
+    static constexpr bool kShifted = true;
+    static __device__ __forceinline__ C ld(const __half *p) { return __half2float(__ldg(p)); }
+    static __device__ __forceinline__ void st(__half *p, C v) { *p = __float2half_rn(v); }
+};
+
+// Rates and constants in the compute type, precomputed once per launch on the
+// host side of the launcher.
+template <typename C>
+struct RatesC {
+    C om_e, om_nu, om_q, om_eps;  // 1 - s_k
+    C s_e, s_nu, s_q, s_eps;      // s_k
+    C h_e, h_nu, h_eps;           // 1 - s_k / 2
+    C om_a, z_a, om_ze, zv_e, om_zn;  // thermal: 1 - zeta_alpha, zeta_alpha, 1 - zeta_e, zeta_e varpi, 1 - zeta_nu
+    C ax, Fy0, g_beta;            // F = (ax, Fy0 + g_beta (T - T_ref))
+    C T_ref;
+};
+
+template <typename C>
+inline RatesC<C> make_rates(const KParams &p) {
+    RatesC<C> r;
+    r.s_e = (C)p.s_e;
+    r.s_nu = (C)p.s_nu;
+    r.s_q = (C)p.s_q;
+    r.s_eps = (C)p.s_eps;
+    r.om_e = (C)(1.0 - p.s_e);
+    r.om_nu = (C)(1.0 - p.s_nu);
+    r.om_q = (C)(1.0 - p.s_q);
+    r.om_eps = (C)(1.0 - p.s_eps);
+    r.h_e = (C)(1.0 - 0.5 * p.s_e);
+    r.h_nu = (C)(1.0 - 0.5 * p.s_nu);
+    r.h_eps = (C)(1.0 - 0.5 * p.s_eps);
+    r.om_a = (C)(1.0 - p.z_a);
+    r.z_a = (C)p.z_a;
+    r.om_ze = (C)(1.0 - p.z_e);
+    r.zv_e = (C)(p.z_e * p.varpi);
+    r.om_zn = (C)(1.0 - p.z_nu);
+    r.ax = (C)p.ax;
+    r.Fy0 = (C)(p.ay + p.g_beta * (p.T_ref - p.T0));
+    r.g_beta = (C)p.g_beta;
+    r.T_ref = (C)p.T_ref;
+    return r;
+}
+
+// Kernel arguments: typed plane pointers of both buffers.
+template <typename S>
+struct Planes {
+    const S *src[kQ];
+    S *dst[kQ];
+};
+
+template <typename S>
+inline Planes<S> make_planes(const KParams &p, int src) {
+    Planes<S> pl;
+    S *a = static_cast<S *>(p.pop[src]);
+    S *b = static_cast<S *>(p.pop[1 - src]);
+    for (int q = 0; q < kQ; ++q) {
+        pl.src[q] = a + (size_t)q * p.plane;
+        pl.dst[q] = b + (size_t)q * p.plane;
+    }
+    return pl;
+}
+
+struct Geom {
+    int nx, ny, pitch, px, py;
+    const uint8_t *mask;
+    const uint8_t *flags;
+    const WallDev *walls;
+};
+
+inline Geom make_geom(const KParams &p) {
+    return Geom{p.nx, p.ny, p.pitch, p.px, p.py, p.mask, p.flags, p.walls};
+}
+
+// --------------------------------------------------------------- pull step
+
+// Post-streaming populations at fluid cell (x, y): Eq. 9 and Eq. 25 in pull
+// form, then the halfway wall rules on the links flagged in `m`.
+template <typename S>
+__device__ __forceinline__ void pull(const S *const *src, const Geom &g, int x, int y, unsigned m,
+                                     typename Store<S>::C f[9], typename Store<S>::C t[5]) {
+    using St = Store<S>;
+    int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1;
+    if (g.px) {
+        xm = (xm < 0) ? xm + g.nx : xm;
+        xp = (xp >= g.nx) ? xp - g.nx : xp;
+    }
+    if (g.py) {
+        ym = (ym < 0) ? ym + g.ny : ym;
+        yp = (yp >= g.ny) ? yp - g.ny : yp;
+    }
+    const int r0 = y * g.pitch, rm = ym * g.pitch, rp = yp * g.pitch;
+    // direction i pulls from x - e_i (Eq. 5 numbering)
+    f[0] = St::ld(src[0] + r0 + x);
+    f[1] = St::ld(src[1] + r0 + xm);
+    f[2] = St::ld(src[2] + rm + x);
+    f[3] = St::ld(src[3] + r0 + xp);
+    f[4] = St::ld(src[4] + rp + x);
+    f[5] = St::ld(src[5] + rm + xm);
+    f[6] = St::ld(src[6] + rm + xp);
+    f[7] = St::ld(src[7] + rp + xp);
+    f[8] = St::ld(src[8] + rp + xm);
+    t[0] = St::ld(src[9] + r0 + x);
+    t[1] = St::ld(src[10] + r0 + xm);
+    t[2] = St::ld(src[11] + rm + x);
+    t[3] = St::ld(src[12] + r0 + xp);
+    t[4] = St::ld(src[13] + rp + x);
+    if (m) {
+        using C = typename St::C;
+        const int sidx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+        const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+        for (int i = 1; i < 9; ++i) {
+            if (m & (1u << (i - 1))) {
+                const WallDev *w = g.walls + g.flags[sidx[i]];
+                f[i] = St::ld(src[opp[i]] + r0 + x) + (C)__ldg(&w->cf[i]);
+                if (i < 5) t[i] = (C)__ldg(&w->tsgn) * St::ld(src[9 + opp[i]] + r0 + x) + (C)__ldg(&w->tb);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- collisions
+
+// Macroscopic values from post-streaming populations (Eqs. 4, 18, 19, 27) in
+// the storage's frame: returns d_rho = rho - rho_ref, u, dT = T - T_ref, F.
+template <typename C>
+struct Macro {
+    C drho, ux, uy, dT, Fx, Fy;
+};
+
+template <typename C>
+__device__ __forceinline__ Macro<C> macro_of(const RatesC<C> &r, const C f[9], const C t[5]) {
+    Macro<C> M;
+    M.dT = ((t[0] + t[1]) + (t[2] + t[3])) + t[4];
+    M.Fx = r.ax;
+    M.Fy = r.Fy0 + r.g_beta * M.dT;
+    M.drho = (((f[0] + f[1]) + (f[2] + f[3])) + (f[4] + f[5])) + ((f[6] + f[7]) + f[8]);
+    const C jx = (f[1] - f[3]) + ((f[5] - f[7]) - (f[6] - f[8]));
+    const C jy = (f[2] - f[4]) + ((f[5] - f[7]) + (f[6] - f[8]));
+    M.ux = jx + C(0.5) * M.Fx;
+    M.uy = jy + C(0.5) * M.Fy;
+    return M;
+}
+
+// Flow collision (Eq. 8 with Eqs. 16, 17, 20 under the incompressible reading,
+// rho0 = 1) and temperature collision (Eq. 24 with Eqs. 28, 29), in place.
+template <typename C>
+__device__ __forceinline__ void collide(const RatesC<C> &r, C f[9], C t[5]) {
+    // ---- D2Q5: n = N g (Eq. 26), relax (Eq. 24), g = N^-1 n (Eq. A2)
+    const C n0 = ((t[0] + t[1]) + (t[2] + t[3])) + t[4];  // T - T_ref
+    const C n1 = t[1] - t[3];
+    const C n2 = t[2] - t[4];
+    const C n3 = (t[1] + t[3]) + (t[2] + t[4]);
+    const C n4 = (t[1] + t[3]) - (t[2] + t[4]);
+    const C Fx = r.ax;
+    const C Fy = r.Fy0 + r.g_beta * n0;  // Eq. 4
+
+    // ---- D2Q9 forward map m = M f (Eq. 13) on pair sums
+    const C a13 = f[1] + f[3], d13 = f[1] - f[3];
+    const C a24 = f[2] + f[4], d24 = f[2] - f[4];
+    const C a57 = f[5] + f[7], d57 = f[5] - f[7];
+    const C a68 = f[6] + f[8], d68 = f[6] - f[8];
+    const C D = a57 + a68;
+    const C m0 = (f[0] + (a13 + a24)) + D;  // rho - rho_ref
+    const C m6 = d57 + d68;
+    const C m7 = d57 - d68;
+    const C jx = d13 + m7;
+    const C jy = d24 + m6;
+    const C m3 = (a13 + a24) + (D + D);
+    const C m4 = a13 - a24;
+    const C m5 = a57 - a68;
+    const C m8 = D;
+
+    // Eq. 19 with rho0 = 1
+    const C ux = jx + C(0.5) * Fx;
+    const C uy = jy + C(0.5) * Fy;
+    const C uu = ux * ux + uy * uy;
+    const C uF = ux * Fx + uy * Fy;
+
+    // ---- Eq. 8: m* = (1 - s) m + s m_eq + (1 - s/2) S~
+    const C p1 = jx + Fx;  // any s1: conserved moment plus the force impulse
+    const C p2 = jy + Fy;
+    const C p3 = r.om_e * m3 + r.s_e * (C(2.0 / 3.0) * m0 + uu) + r.h_e * (C(2) * uF);
+    const C p4 = r.om_nu * m4 + r.s_nu * (ux * ux - uy * uy) + r.h_nu * (C(2) * (ux * Fx - uy * Fy));
+    const C p5 = r.om_nu * m5 + r.s_nu * (ux * uy) + r.h_nu * (ux * Fy + uy * Fx);
+    // s_q m_eq + (1 - s_q/2) S~ for q_xxy, q_xyy reduces to (s_q j + F) / 3
+    const C p6 = r.om_q * m6 + C(1.0 / 3.0) * (r.s_q * jy + Fy);
+    const C p7 = r.om_q * m7 + C(1.0 / 3.0) * (r.s_q * jx + Fx);
+    const C p8 = r.om_eps * m8 + r.s_eps * (C(1.0 / 9.0) * m0 + C(1.0 / 3.0) * uu) + r.h_eps * (C(2.0 / 3.0) * uF);
+
+    // ---- back map f = M^-1 m* (Eq. A1)
+    const C A = C(0.25) * p3 - C(0.5) * p8;
+    const C B = C(0.25) * p4;
+    const C h1 = C(0.5) * (p1 - p7);
+    const C h2 = C(0.5) * (p2 - p6);
+    const C P = C(0.25) * (p8 + p5);
+    const C Q = C(0.25) * (p6 + p7);
+    const C R = C(0.25) * (p8 - p5);
+    const C Sx = C(0.25) * (p6 - p7);
+    f[0] = (m0 - p3) + p8;
+    f[1] = (A + B) + h1;
+    f[3] = (A + B) - h1;
+    f[2] = (A - B) + h2;
+    f[4] = (A - B) - h2;
+    f[5] = P + Q;
+    f[7] = P - Q;
+    f[6] = R + Sx;
+    f[8] = R - Sx;
+
+    // ---- D2Q5 relaxation with n_eq = (T, ux T, uy T, varpi T, 0)
+    const C T = r.T_ref + n0;
+    const C q1 = r.om_a * n1 + r.z_a * (ux * T);
+    const C q2 = r.om_a * n2 + r.z_a * (uy * T);
+    const C q3 = r.om_ze * n3 + r.zv_e * n0;
+    const C q4 = r.om_zn * n4;
+    const C c3 = C(0.25) * q3, c4 = C(0.25) * q4;
+    t[0] = n0 - q3;
+    t[1] = (c3 + c4) + C(0.5) * q1;
+    t[3] = (c3 + c4) - C(0.5) * q1;
+    t[2] = (c3 - c4) + C(0.5) * q2;
+    t[4] = (c3 - c4) - C(0.5) * q2;
+}
+
+// ------------------------------------------------------------------ kernels
+
+template <typename S>
+__global__ void __launch_bounds__(256) k_step(const Planes<S> pl, const Geom g, const RatesC<typename Store<S>::C> r) {
+    using C = typename Store<S>::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= g.nx) return;
+    for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < g.ny; y += gridDim.y * blockDim.y) {
+        const int off = y * g.pitch + x;
+        const unsigned m = __ldg(g.mask + off);
+        if (m == kSolid) continue;
+        C f[9], t[5];
+        pull<S>(pl.src, g, x, y, m, f, t);
+        collide<C>(r, f, t);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) Store<S>::st(pl.dst[q] + off, f[q]);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) Store<S>::st(pl.dst[9 + q] + off, t[q]);
+    }
+}
+
+// Initial state (rest equilibrium, Eqs. 22, 30 at u = 0) in the storage frame.
+template <typename S>
+__global__ void k_init_rows(const Planes<S> pl, const Geom g, int r0, int r1, const double *T, double T_ref,
+                            double varpi, int shifted) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = r0 + blockIdx.y;
+    if (x >= g.pitch || y >= r1) return;
+    const int off = y * g.pitch + x;
+    const bool fluid = x < g.nx && g.mask[off] != kSolid;
+    const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const double Tn = fluid ? T[(size_t)(y - r0) * g.nx + x] : 0.0;
+    for (int q = 0; q < 9; ++q) {
+        double v = fluid ? (shifted ? 0.0 : w9[q]) : 0.0;
+        Store<S>::st(const_cast<S *>(pl.src[q]) + off, (typename Store<S>::C)v);
+    }
+    for (int q = 0; q < 5; ++q) {
+        const double wT = q == 0 ? 1.0 - varpi : 0.25 * varpi;
+        double v = fluid ? wT * (Tn - T_ref) : 0.0;
+        Store<S>::st(const_cast<S *>(pl.src[9 + q]) + off, (typename Store<S>::C)v);
+    }
+}
+
+template <typename S>
+__global__ void k_macro_rows(const Planes<S> pl, const Geom g, const RatesC<typename Store<S>::C> r, int r0,
+                             int r1, double rho_ref, double T_ref, double *out) {
+    using C = typename Store<S>::C;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = r0 + blockIdx.y;
+    if (x >= g.nx || y >= r1) return;
+    const size_t n = (size_t)(r1 - r0) * g.nx;
+    const size_t o = (size_t)(y - r0) * g.nx + x;
+    const unsigned m = g.mask[y * g.pitch + x];
+    double v[4] = {0, 0, 0, 0};
+    if (m != kSolid) {
+        C f[9], t[5];
+        pull<S>(pl.src, g, x, y, m, f, t);
+        Macro<C> M = macro_of<C>(r, f, t);
+        v[0] = rho_ref + (double)M.drho;
+        v[1] = (double)M.ux;
+        v[2] = (double)M.uy;
+        v[3] = T_ref + (double)M.dT;
+    }
+    for (int k = 0; k < 4; ++k) out[k * n + o] = v[k];
+}
+
+template <typename S>
+__global__ void k_export_rows(const Planes<S> pl, const Geom g, int r0, int r1, double rho_ref, double T_ref,
+                              double varpi, double *out) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = r0 + blockIdx.y;
+    if (x >= g.nx || y >= r1) return;
+    const size_t n = (size_t)(r1 - r0) * g.nx;
+    const size_t o = (size_t)(y - r0) * g.nx + x;
+    const int off = y * g.pitch + x;
+    const bool fluid = g.mask[off] != kSolid;
+    const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    for (int q = 0; q < kQ; ++q) {
+        double v = 0.0;
+        if (fluid) {
+            double shift = q < 9 ? w9[q] * rho_ref : (q == 9 ? 1.0 - varpi : 0.25 * varpi) * T_ref;
+            v = (double)Store<S>::ld(pl.src[q] + off) + shift;
+        }
+        out[q * n + o] = v;
+    }
+}
+
+// which: bit 0 = f planes present, bit 1 = g planes present
+template <typename S>
+__global__ void k_import_rows(const Planes<S> pl, const Geom g, int r0, int r1, double rho_ref, double T_ref,
+                              double varpi, const double *in, int which) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = r0 + blockIdx.y;
+    if (x >= g.nx || y >= r1) return;
+    const size_t n = (size_t)(r1 - r0) * g.nx;
+    const size_t o = (size_t)(y - r0) * g.nx + x;
+    const int off = y * g.pitch + x;
+    const bool fluid = g.mask[off] != kSolid;
+    const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    for (int q = 0; q < kQ; ++q) {
+        if (q < 9 && !(which & 1)) continue;
+        if (q >= 9 && !(which & 2)) continue;
+        double shift = q < 9 ? w9[q] * rho_ref : (q == 9 ? 1.0 - varpi : 0.25 * varpi) * T_ref;
+        double v = fluid ? in[q * n + o] - shift : 0.0;
+        Store<S>::st(const_cast<S *>(pl.src[q]) + off, (typename Store<S>::C)v);
+    }
+}
+
+// ------------------------------------------------------------- reductions
+
+template <int W>
+__device__ __forceinline__ void block_reduce_store(double (&v)[W], double *partials) {
+    __shared__ double sh[kRedThreads / 32][W];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < W; ++k)
+        for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+    if (lane == 0)
+        for (int k = 0; k < W; ++k) sh[warp][k] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < W; ++k) {
+            double a = lane < kRedThreads / 32 ? sh[lane][k] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+            if (lane == 0) partials[blockIdx.x * W + k] = a;
+        }
+    }
+}
+
+// Temperature after the pull at one fluid cell (Eq. 27), FP64 accumulation.
+template <typename S>
+__device__ __forceinline__ double temperature_at(const Planes<S> &pl, const Geom &g, int x, int y, double T_ref) {
+    using C = typename Store<S>::C;
+    const unsigned m = g.mask[y * g.pitch + x];
+    C f[9], t[5];
+    pull<S>(pl.src, g, x, y, m, f, t);
+    return T_ref + ((((double)t[0] + (double)t[1]) + ((double)t[2] + (double)t[3])) + (double)t[4]);
+}
+
+// Eq. 39 with the one-sided wall gradient; one thread per line along the wall.
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads) k_nusselt(const Planes<S> pl, const Geom g, int side, double L,
+                                                         double dT, double T_ref, double *partials) {
+    const int along = side < 2 ? g.ny : g.nx;
+    double v[2] = {0.0, 0.0};
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < along; s += gridDim.x * blockDim.x) {
+        int wx, wy, dx, dy;
+        if (side == 0) { wx = 0; wy = s; dx = 1; dy = 0; }
+        else if (side == 1) { wx = g.nx - 1; wy = s; dx = -1; dy = 0; }
+        else if (side == 2) { wx = s; wy = 0; dx = 0; dy = 1; }
+        else { wx = s; wy = g.ny - 1; dx = 0; dy = -1; }
+        const int x1 = wx + dx, y1 = wy + dy, x2 = wx + 2 * dx, y2 = wy + 2 * dy;
+        if (x2 < 0 || x2 >= g.nx || y2 < 0 || y2 >= g.ny) continue;
+        const int k = g.flags[wy * g.pitch + wx];
+        if (k == 0) continue;
+        if (g.mask[y1 * g.pitch + x1] == kSolid || g.mask[y2 * g.pitch + x2] == kSolid) continue;
+        const WallDev *w = g.walls + k;
+        if (w->tsgn > 0.0) continue;  // adiabatic: no wall temperature
+        const double Tw = w->Tw;
+        const double T1 = temperature_at<S>(pl, g, x1, y1, T_ref);
+        const double T2 = temperature_at<S>(pl, g, x2, y2, T_ref);
+        const double dTds = (9.0 * T1 - T2 - 8.0 * Tw) / 3.0;
+        const double dTdn = (side == 0 || side == 2) ? dTds : -dTds;
+        v[0] += -L * dTdn / dT;
+        v[1] += 1.0;
+    }
+    block_reduce_store<2>(v, partials);
+}
+
+template <typename S>
+__global__ void __launch_bounds__(kRedThreads) k_residual(const Planes<S> pl, const Geom g,
+                                                          const RatesC<typename Store<S>::C> r, double T_ref,
+                                                          double *snap, size_t plane, int have_snap,
+                                                          double *partials) {
+    using C = typename Store<S>::C;
+    double v[5] = {0, 0, 0, 0, 0};
+    const long long total = (long long)g.ny * g.nx;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(c / g.nx), x = (int)(c - (long long)y * g.nx);
+        const int off = y * g.pitch + x;
+        const unsigned m = g.mask[off];
+        if (m == kSolid) continue;
+        C f[9], t[5];
+        pull<S>(pl.src, g, x, y, m, f, t);
+        Macro<C> M = macro_of<C>(r, f, t);
+        const double ux = (double)M.ux, uy = (double)M.uy, T = T_ref + (double)M.dT;
+        if (have_snap) {
+            const double a = ux - snap[off], b = uy - snap[plane + off], d = T - snap[2 * plane + off];
+            v[0] += a * a + b * b;
+            v[2] += d * d;
+        }
+        v[1] += ux * ux + uy * uy;
+        v[3] += T * T;
+        if (!isfinite(ux) || !isfinite(uy) || !isfinite(T)) v[4] += 1.0;
+        snap[off] = ux;
+        snap[plane + off] = uy;
+        snap[2 * plane + off] = T;
+    }
+    block_reduce_store<5>(v, partials);
+}
+
+// ---------------------------------------------------------------- launchers
+
+inline dim3 step_block() { return dim3(128, 2); }
+
+template <typename S>
+cudaError_t launch_step(const KParams &p, int src, cudaStream_t st) {
+    using C = typename Store<S>::C;
+    const dim3 b = step_block();
+    const int gy = (p.ny + (int)b.y - 1) / (int)b.y;
+    const dim3 grid((p.nx + b.x - 1) / b.x, gy < 65535 ? gy : 65535);
+    k_step<S><<<grid, b, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p));
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_init_rows(const KParams &p, int buf, int r0, int r1, const double *T, cudaStream_t st) {
+    const dim3 grid((p.pitch + 127) / 128, r1 - r0);
+    k_init_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, T, p.T_ref, p.varpi,
+                                         Store<S>::kShifted ? 1 : 0);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_macro_rows(const KParams &p, int buf, int r0, int r1, double *out, cudaStream_t st) {
+    using C = typename Store<S>::C;
+    const dim3 grid((p.nx + 127) / 128, r1 - r0);
+    k_macro_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p), r0, r1,
+                                          p.rho_ref, p.T_ref, out);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_export_rows(const KParams &p, int buf, int r0, int r1, double *out, cudaStream_t st) {
+    const dim3 grid((p.nx + 127) / 128, r1 - r0);
+    k_export_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, p.rho_ref, p.T_ref,
+                                           p.varpi, out);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_import_rows(const KParams &p, int buf, int r0, int r1, const double *in, int which,
+                               cudaStream_t st) {
+    const dim3 grid((p.nx + 127) / 128, r1 - r0);
+    k_import_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, p.rho_ref, p.T_ref,
+                                           p.varpi, in, which);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_nusselt(const KParams &p, int buf, int side, double L, double dT, double *partials,
+                           cudaStream_t st) {
+    k_nusselt<S><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), side, L, dT, p.T_ref,
+                                                    partials);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_residual(const KParams &p, int buf, double *snap, int have_snap, double *partials,
+                            cudaStream_t st) {
+    using C = typename Store<S>::C;
+    k_residual<S><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p),
+                                                     p.T_ref, snap, p.plane, have_snap, partials);
+    return cudaGetLastError();
+}
+
+template <typename S>
+Launchers make_launchers() {
+    Launchers L;
+    L.step = &launch_step<S>;
+    L.init_rows = &launch_init_rows<S>;
+    L.macro_rows = &launch_macro_rows<S>;
+    L.export_rows = &launch_export_rows<S>;
+    L.import_rows = &launch_import_rows<S>;
+    L.nusselt = &launch_nusselt<S>;
+    L.residual = &launch_residual<S>;
+    return L;
+}
+
+}  // namespace nomrt

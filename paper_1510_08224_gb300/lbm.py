@@ -1,0 +1,231 @@
+"""ctypes binding of the C ABI in ``include/nomrt_lbm.h``.
+
+Argument marshalling only: every step of the method runs in the CUDA library
+``_build/libnomrt_lbm.so``. PyTorch supplies device memory and the stream.
+There is no CPU fallback: if the library cannot be built or loaded, importing
+the binding's functions raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_EINVAL, LBM_ENOMEM, LBM_ECUDA, LBM_EDIVERGED, LBM_ETIMEOUT = range(6)
+STORAGE = {"f64": 0, "f32": 1, "f16": 2}
+STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
+SIDES = {"left": 0, "right": 1, "bottom": 2, "top": 3}
+
+# Every symbol include/nomrt_lbm.h declares.
+EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_read_macro", "lbm_nusselt",
+            "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
+            "lbm_destroy")
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lbm status {status}: {msg}")
+        self.status = status
+
+
+class lbm_wall(C.Structure):
+    _fields_ = [("ux", C.c_double), ("uy", C.c_double), ("kind", C.c_int32), ("reserved", C.c_int32),
+                ("T", C.c_double)]
+
+
+class lbm_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("periodic_x", C.c_int32), ("periodic_y", C.c_int32),
+        ("flags", C.c_void_p), ("walls", C.c_void_p), ("n_walls", C.c_int32), ("storage", C.c_int32),
+        ("nu", C.c_double), ("alpha", C.c_double), ("g_beta", C.c_double), ("T0", C.c_double),
+        ("ax", C.c_double), ("ay", C.c_double),
+        ("s_e", C.c_double), ("s_q", C.c_double), ("s_eps", C.c_double),
+        ("zeta_e", C.c_double), ("zeta_nu", C.c_double), ("varpi", C.c_double),
+        ("T_init", C.c_void_p),
+    ]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Build (if stale) and load the CUDA library. Raises if that fails."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        L = C.CDLL(path)
+        vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        L.lbm_footprint_bytes.restype = C.c_size_t
+        L.lbm_footprint_bytes.argtypes = [C.POINTER(lbm_params)]
+        L.lbm_create.restype = C.c_int
+        L.lbm_create.argtypes = [C.POINTER(lbm_params), vp, vp, C.c_size_t, C.POINTER(vp)]
+        L.lbm_step.restype = C.c_int
+        L.lbm_step.argtypes = [vp, C.c_int64]
+        L.lbm_sync.restype = C.c_int
+        L.lbm_sync.argtypes = [vp]
+        L.lbm_read_macro.restype = C.c_int
+        L.lbm_read_macro.argtypes = [vp, dp, dp, dp, dp]
+        L.lbm_nusselt.restype = C.c_int
+        L.lbm_nusselt.argtypes = [vp, C.c_int32, C.c_double, C.c_double, dp]
+        L.lbm_residual.restype = C.c_int
+        L.lbm_residual.argtypes = [vp, dp]
+        L.lbm_get_populations.restype = C.c_int
+        L.lbm_get_populations.argtypes = [vp, dp, dp]
+        L.lbm_set_populations.restype = C.c_int
+        L.lbm_set_populations.argtypes = [vp, dp, dp]
+        L.lbm_info.restype = C.c_int
+        L.lbm_info.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                               C.POINTER(C.c_int64)]
+        L.lbm_last_error.restype = C.c_char_p
+        L.lbm_last_error.argtypes = [vp]
+        L.lbm_destroy.restype = None
+        L.lbm_destroy.argtypes = [vp]
+        _lib = L
+        return L
+
+
+def _dptr(a):
+    if a is None:
+        return None
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _check(status: int, handle=None):
+    if status != LBM_OK:
+        msg = load().lbm_last_error(handle)
+        raise LBMError(status, msg.decode() if msg else "")
+
+
+def make_params(case, storage: str = "f32"):
+    """lbm_params from any object with the problem's attributes (nx, ny,
+    periodic_x, periodic_y, flags, walls, nu, alpha, g_beta, T0, ax, ay, s_e,
+    s_q, s_eps, zeta_e, zeta_nu, varpi, T_init). Returns (params, keepalive)."""
+    flags = np.ascontiguousarray(case.flags, dtype=np.uint8)
+    assert flags.shape == (case.ny, case.nx)
+    walls = (lbm_wall * max(1, len(case.walls)))()
+    for k, w in enumerate(case.walls):
+        walls[k] = lbm_wall(float(w.ux), float(w.uy), int(w.kind), 0, float(w.T))
+    Ti = None
+    if getattr(case, "T_init", None) is not None:
+        Ti = np.ascontiguousarray(case.T_init, dtype=np.float64)
+        assert Ti.shape == (case.ny, case.nx)
+    p = lbm_params()
+    p.nx, p.ny = int(case.nx), int(case.ny)
+    p.periodic_x, p.periodic_y = int(bool(case.periodic_x)), int(bool(case.periodic_y))
+    p.flags = flags.ctypes.data
+    p.walls = C.addressof(walls)
+    p.n_walls = len(case.walls)
+    p.storage = STORAGE[storage]
+    for name in ("nu", "alpha", "g_beta", "T0", "ax", "ay", "s_e", "s_q", "s_eps", "zeta_e", "zeta_nu", "varpi"):
+        setattr(p, name, float(getattr(case, name)))
+    p.T_init = Ti.ctypes.data if Ti is not None else None
+    return p, (flags, walls, Ti)
+
+
+def lbm_footprint_bytes(params) -> int:
+    return int(load().lbm_footprint_bytes(C.byref(params)))
+
+
+class Lattice:
+    """A lattice resident on the GPU. Device memory is a torch uint8 tensor
+    (``device_mem="torch"``, the default) or allocated by the library
+    (``device_mem="library"``); work is queued on ``stream`` (a
+    ``torch.cuda.Stream``; default: the current stream)."""
+
+    def __init__(self, case, storage: str = "f32", stream=None, device_mem: str = "torch", device=None):
+        import torch
+
+        L = load()
+        self.case = case
+        self.storage = storage
+        self.nx, self.ny = int(case.nx), int(case.ny)
+        p, keep = make_params(case, storage)
+        need = L.lbm_footprint_bytes(C.byref(p))
+        if need == 0:
+            raise LBMError(LBM_EINVAL, L.lbm_last_error(None).decode())
+        self.footprint = int(need)
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self._stream = stream if stream is not None else torch.cuda.current_stream(dev)
+        self._mem = None
+        mem_ptr, mem_bytes = None, 0
+        if device_mem == "torch":
+            self._mem = torch.empty(int(need), dtype=torch.uint8, device=dev)
+            mem_ptr, mem_bytes = self._mem.data_ptr(), int(need)
+        elif device_mem != "library":
+            raise ValueError("device_mem must be 'torch' or 'library'")
+        h = C.c_void_p()
+        with torch.cuda.device(dev):
+            st = L.lbm_create(C.byref(p), C.c_void_p(self._stream.cuda_stream), C.c_void_p(mem_ptr),
+                              C.c_size_t(mem_bytes), C.byref(h))
+        _check(st, None)
+        self._h = h
+        del keep
+
+    # -- lifetime
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().lbm_destroy(h)
+            self._h = None
+        self._mem = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- calls
+    def step(self, n: int = 1):
+        _check(load().lbm_step(self._h, int(n)), self._h)
+
+    def sync(self):
+        _check(load().lbm_sync(self._h), self._h)
+
+    def macro(self):
+        """(rho, ux, uy, T), each (ny, nx) float64 on the host."""
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        _check(load().lbm_read_macro(self._h, *[_dptr(a) for a in out]), self._h)
+        return tuple(out)
+
+    def nusselt(self, side, L: float = 0.0, delta_T: float = 1.0) -> float:
+        side = SIDES[side] if isinstance(side, str) else int(side)
+        v = C.c_double()
+        _check(load().lbm_nusselt(self._h, side, float(L), float(delta_T), C.byref(v)), self._h)
+        return v.value
+
+    def residual(self) -> float:
+        v = C.c_double()
+        _check(load().lbm_residual(self._h, C.byref(v)), self._h)
+        return v.value
+
+    def populations(self):
+        f = np.empty((9, self.ny, self.nx)); g = np.empty((5, self.ny, self.nx))
+        _check(load().lbm_get_populations(self._h, _dptr(f), _dptr(g)), self._h)
+        return f, g
+
+    def set_populations(self, f=None, g=None):
+        f = None if f is None else np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.ny, self.nx)
+        g = None if g is None else np.ascontiguousarray(g, dtype=np.float64).reshape(5, self.ny, self.nx)
+        _check(load().lbm_set_populations(self._h, _dptr(f), _dptr(g)), self._h)
+
+    def info(self):
+        fl, st = C.c_int64(), C.c_int64()
+        pitch, eb = C.c_int32(), C.c_int32()
+        _check(load().lbm_info(self._h, C.byref(fl), C.byref(pitch), C.byref(eb), C.byref(st)), self._h)
+        return dict(fluid_cells=fl.value, pitch=pitch.value, elem_bytes=eb.value, steps=st.value)

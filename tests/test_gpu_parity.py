@@ -1,0 +1,269 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+FP64 storage: element-by-element on populations and fields, max-norm relative
+error <= 1e-12 (also after 10^4 steps). FP32/FP16-shifted storage: one step
+from the same (quantised) state against the oracle within the rounding of the
+storage format, and the accumulated max-norm error in u and T after many steps
+is checked against a stated bound.
+"""
+import numpy as np
+import pytest
+
+import lbm_cases as lc
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+
+
+def _P():
+    import paper_1510_08224_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _cases_small():
+    return [
+        lc.periodic_box(7, 5, nu=0.03, alpha=0.04, g_beta=2e-3, T0=0.5,
+                        kinetic=dict(s_e=1.3, s_q=1.1, s_eps=1.5, zeta_e=1.2, zeta_nu=0.9), ax=1e-5),
+        lc.couette(H=9, nx=5, U0=0.05),
+        lc.porous_couette(H=16, nx=3),
+        lc.cavity(n=20, Ra=1e4, n_y=13, noise=1e-3),
+        lc.rayleigh_benard(nx=133, H=7, Ra=1e5, sigma=1e-2),  # two x blocks plus a ragged tail
+        lc.poiseuille(H=11, nx=1, ax=1e-5),                   # nx = 1: periodic self-neighbour
+    ]
+
+
+@pytest.mark.parametrize("idx", range(6))
+@pytest.mark.parametrize("nsteps", [0, 1, 2, 10])
+def test_fp64_populations_match_oracle(idx, nsteps):
+    P = _P()
+    case = _cases_small()[idx]
+    g = P.Lattice(case, storage="f64")
+    o = oracle.OracleLattice(case)
+    if idx == 0:  # start off-equilibrium
+        f0, g0 = lc.random_state(case, seed=11)
+        g.set_populations(f0, g0)
+        o.set_populations(f0, g0)
+    g.step(nsteps)
+    o.step(nsteps)
+    fg, gg = g.populations()
+    fo, go = o.populations()
+    assert _rel(fg, fo) <= FP64_TOL
+    assert _rel(gg, go) <= FP64_TOL
+    for a, b in zip(g.macro(), o.macro()):
+        assert np.abs(a - b).max() <= FP64_TOL * max(np.abs(b).max(), 1.0)
+
+
+def test_fp64_injection_channel_1e4_steps():
+    """Porous-plate thermal Couette, 8 x 64 fluid cells, 10^4 steps."""
+    P = _P()
+    case = lc.porous_couette(H=64, nx=8)
+    g = P.Lattice(case, storage="f64")
+    o = oracle.OracleLattice(case)
+    g.step(10000)
+    o.step(10000)
+    for a, b in zip(g.macro(), o.macro()):
+        assert _rel(a, b) <= FP64_TOL
+    fg, gg = g.populations()
+    fo, go = o.populations()
+    assert _rel(fg, fo) <= FP64_TOL and _rel(gg, go) <= FP64_TOL
+    # mass: the injecting and sucking walls balance exactly
+    assert abs(fg.sum() - fo.sum()) / fo.sum() < 1e-13
+
+
+def test_fp64_convective_cavity_1e4_steps():
+    P = _P()
+    case = lc.cavity(n=32, Ra=1e4, noise=1e-3)
+    g = P.Lattice(case, storage="f64")
+    o = oracle.OracleLattice(case, threads=4)
+    g.step(10000)
+    o.step(10000)
+    for a, b in zip(g.macro()[1:], o.macro()[1:]):
+        assert _rel(a, b) <= FP64_TOL
+    for side in (0, 1):
+        assert abs(g.nusselt(side) - o.nusselt(side)) <= 1e-11
+
+
+def _quantised_start(P, case, storage, seed):
+    """Load a random state into the GPU lattice and read back what the storage
+    format holds, so the oracle starts from exactly the same numbers."""
+    g = P.Lattice(case, storage=storage)
+    f0, g0 = lc.random_state(case, seed=seed)
+    g.set_populations(f0, g0)
+    fq, gq = g.populations()
+    return g, fq, gq
+
+
+# one-step bound on |gpu - oracle| relative to the deviation scale of the state
+ONE_STEP_TOL = {"f32": 2e-6, "f16": 2e-3}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("idx", range(6))
+def test_reduced_precision_one_step(storage, idx):
+    P = _P()
+    case = _cases_small()[idx]
+    g, fq, gq = _quantised_start(P, case, storage, seed=5 + idx)
+    o = oracle.OracleLattice(case)
+    o.set_populations(fq, gq)
+    g.step(1)
+    o.step(1)
+    fg, gg = g.populations()
+    fo, go = o.populations()
+    w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+    wT = np.array([1 - case.varpi] + [case.varpi / 4] * 4)[:, None, None]
+    solid = case.flags != 0
+    dev_f = np.where(solid, 0.0, fo - w9)
+    dev_g = np.where(solid, 0.0, go - wT * case.T0)
+    scale_f, scale_g = np.abs(dev_f).max(), np.abs(dev_g).max()
+    assert np.abs(fg - fo).max() <= ONE_STEP_TOL[storage] * scale_f
+    assert np.abs(gg - go).max() <= ONE_STEP_TOL[storage] * scale_g
+
+
+# accumulated max-norm error after many steps against the FP64 oracle
+MANY_STEP_TOL = {"f32": {"u": 1e-6, "T": 1e-6}, "f16": {"u": 2e-3, "T": 2e-3}}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_reduced_precision_cavity_error(storage):
+    """Cavity at Ra = 1e4 from rest, 4000 steps: max-norm error in u (relative
+    to max |u|) and T (relative to delta T) against the FP64 oracle."""
+    P = _P()
+    case = lc.cavity(n=32, Ra=1e4, noise=1e-3)
+    g = P.Lattice(case, storage=storage)
+    o = oracle.OracleLattice(case, threads=4)
+    g.step(4000)
+    o.step(4000)
+    _, uxg, uyg, Tg = g.macro()
+    _, uxo, uyo, To = o.macro()
+    umax = max(np.abs(uxo).max(), np.abs(uyo).max())
+    eu = max(np.abs(uxg - uxo).max(), np.abs(uyg - uyo).max()) / umax
+    eT = np.abs(Tg - To).max() / case.delta_T
+    print(f"{storage}: max-norm error u {eu:.3e} (of max|u|), T {eT:.3e} (of dT)")
+    assert eu <= MANY_STEP_TOL[storage]["u"] and eT <= MANY_STEP_TOL[storage]["T"]
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_macro_nusselt_residual_match_oracle(storage):
+    P = _P()
+    case = lc.cavity(n=24, Ra=1e4, noise=1e-3)
+    g, fq, gq = _quantised_start(P, case, storage, seed=3)
+    o = oracle.OracleLattice(case)
+    o.set_populations(fq, gq)
+    tol = {"f64": 1e-12, "f32": 1e-6, "f16": 1e-6}[storage]
+    for a, b in zip(g.macro(), o.macro()):
+        assert np.abs(a - b).max() <= tol * max(1.0, np.abs(b).max())
+    for side in (0, 1):
+        assert abs(g.nusselt(side) - o.nusselt(side)) <= 50 * tol * abs(o.nusselt(side)) + 1e-12
+    assert np.isinf(g.residual()) and np.isinf(o.residual())
+    g.step(7)
+    o.step(7)
+    rg, ro = g.residual(), o.residual()
+    rtol = {"f64": 1e-10, "f32": 1e-3, "f16": 1e-2}[storage]
+    assert abs(rg - ro) <= rtol * ro
+    with pytest.raises(P.LBMError):
+        g.nusselt("top")  # adiabatic wall
+
+
+def _full_size_sampled(storage, seed, nsample=3000):
+    """Rayleigh-Benard at the benchmark size (4096 x 2048 fluid cells plus the
+    two wall rows), the benchmark's launch configuration: one step from a
+    seeded random state, every population of sampled nodes against the
+    oracle's single-node update."""
+    P = _P()
+    case = lc.rayleigh_benard(nx=4096, H=2048, sigma=0.0)
+    g, fq, gq = _quantised_start(P, case, storage, seed=seed)
+    g.step(1)
+    f1, g1 = g.populations()
+    o = oracle.OracleLattice(case.with_(T_init=None))
+    rng = np.random.default_rng(seed)
+    xs = rng.integers(0, case.nx, nsample)
+    ys = rng.integers(1, case.ny - 1, nsample)
+    # always include the seam of the periodic wrap and the wall rows
+    xs[:4] = [0, case.nx - 1, 0, case.nx - 1]
+    ys[:4] = [1, 1, case.ny - 2, case.ny - 2]
+    fq = np.ascontiguousarray(fq); gq = np.ascontiguousarray(gq)
+    ef = eg = 0.0
+    sf = sg = 0.0
+    for x, y in zip(xs, ys):
+        fo, go = o.update_node(fq, gq, int(x), int(y))
+        ef = max(ef, np.abs(f1[:, y, x] - fo).max())
+        eg = max(eg, np.abs(g1[:, y, x] - go).max())
+        sf = max(sf, np.abs(fo - np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)).max())
+        sg = max(sg, np.abs(go - np.array([0.5] + [0.125] * 4) * case.T0).max())
+    # the rest of the lattice: mass and T are conserved away from the walls' exchange
+    return ef, eg, sf, sg
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_full_size_sampled_nodes(storage):
+    ef, eg, sf, sg = _full_size_sampled(storage, seed=17)
+    if storage == "f64":
+        assert ef <= FP64_TOL and eg <= FP64_TOL
+    else:
+        assert ef <= ONE_STEP_TOL[storage] * sf and eg <= ONE_STEP_TOL[storage] * sg
+
+
+def test_library_allocated_memory_and_side_stream():
+    import torch
+    P = _P()
+    case = lc.cavity(n=16, Ra=1e4, noise=1e-3)
+    s = torch.cuda.Stream()
+    a = P.Lattice(case, storage="f64", stream=s, device_mem="library")
+    b = P.Lattice(case, storage="f64")
+    a.step(50)
+    b.step(50)
+    for x, y in zip(a.populations(), b.populations()):
+        assert np.array_equal(x, y)
+    info = a.info()
+    assert info["steps"] == 50 and info["fluid_cells"] == 256
+
+
+def test_invalid_inputs_are_rejected():
+    P = _P()
+    c = lc.couette(H=4, nx=3)
+    with pytest.raises(P.LBMError):
+        P.Lattice(c.with_(periodic_x=False))          # open edge without a frame
+    with pytest.raises(P.LBMError):
+        P.Lattice(c.with_(nu=-1.0))                   # rate outside (0, 2)
+    with pytest.raises(P.LBMError):
+        P.Lattice(c.with_(s_q=2.0))
+    iso = lc.cavity(n=3, noise=0.0)
+    fl = iso.flags.copy(); fl[1:-1, 1:-1] = 1; fl[2, 2] = 0  # a fluid cell with no fluid neighbour
+    with pytest.raises(P.LBMError):
+        P.Lattice(iso.with_(flags=fl))
+    g = P.Lattice(c)
+    with pytest.raises(P.LBMError):
+        g.step(-1)
+
+
+def test_caller_memory_too_small():
+    import ctypes as C
+    import torch
+    P = _P()
+    L = P.load()
+    c = lc.couette(H=4, nx=3)
+    p, keep = P.make_params(c, "f32")
+    need = L.lbm_footprint_bytes(C.byref(p))
+    buf = torch.empty(need - 256, dtype=torch.uint8, device="cuda")
+    h = C.c_void_p()
+    st = L.lbm_create(C.byref(p), None, C.c_void_p(buf.data_ptr()), C.c_size_t(need - 256), C.byref(h))
+    assert st == 2 and not h.value  # LBM_ENOMEM
+
+
+def test_nan_state_is_reported_as_diverged():
+    P = _P()
+    c = lc.couette(H=4, nx=3)
+    g = P.Lattice(c, storage="f64")
+    f, t = g.populations()
+    f[1, 2, 1] = np.nan
+    g.set_populations(f, t)
+    g.step(2)
+    with pytest.raises(P.LBMError) as e:
+        g.residual()
+    assert e.value.status == 4  # LBM_EDIVERGED
