@@ -257,3 +257,27 @@ def random_state(case: Case, seed: int, amp_f: float = 0.02, amp_g: float = 0.05
     f[:, solid] = 0.0
     g[:, solid] = 0.0
     return f.reshape(9, case.ny, case.nx), g.reshape(5, case.ny, case.nx)
+
+
+def obstacle_channel(nx: int = 37, H: int = 11, frac: float = 0.12, seed: int = 1, U0: float = 0.04,
+                     nu: float = 0.04, alpha: float = 0.05, g_beta: float = 1e-3) -> Case:
+    """Periodic-x channel with a moving, heated lid (wall 2), a cold static
+    bottom (wall 1) and randomly placed solid cells (adiabatic wall 3) drawn
+    from SplitMix64(seed). Fluid cells left without a fluid neighbour are
+    filled, so every fluid cell has at least one fluid neighbour."""
+    flags = _frame_y(nx, H, 1, 2)
+    u = uniform01(seed, nx * H).reshape(H, nx)
+    inner = flags[1:-1]
+    inner[u < frac] = 3
+    EXY = [(1, 0), (0, 1), (-1, 0), (0, -1), (1, 1), (-1, 1), (-1, -1), (1, -1)]
+    ny = H + 2
+    for y in range(1, ny - 1):
+        for x in range(nx):
+            if flags[y, x]:
+                continue
+            if all(flags[y - dy, (x - dx) % nx] for dx, dy in EXY):
+                flags[y, x] = 3
+    walls = [Wall(0, 0, DIRICHLET, 0.0), Wall(U0, 0, DIRICHLET, 1.0), Wall(0, 0, ADIABATIC, 0.0)]
+    Ti = np.where(flags == 0, 0.5, 0.0)
+    return Case("obstacle_channel", nx, ny, True, False, flags, walls, nu=nu, alpha=alpha, g_beta=g_beta,
+                T0=0.5, T_init=Ti, L=float(H), meta=dict(seed=seed), **KINETIC_CONVECTION)

@@ -472,6 +472,179 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(const Planes<S> pl, co
     block_reduce_store<5>(v, partials);
 }
 
+// ------------------------------------------------- vectorised step kernel
+
+// Four consecutive storage elements <-> four compute values (128-bit FP32,
+// 64-bit FP16 accesses).
+template <typename S>
+struct Vec4;
+
+template <>
+struct Vec4<float> {
+    static __device__ __forceinline__ void ld(const float *p, float a[4]) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float a[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
+    }
+};
+
+template <>
+struct Vec4<__half> {
+    static __device__ __forceinline__ void ld(const __half *p, float a[4]) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
+        __half2 h0, h1;
+        memcpy(&h0, &v.x, 4);
+        memcpy(&h1, &v.y, 4);
+        const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+        a[0] = f0.x; a[1] = f0.y; a[2] = f1.x; a[3] = f1.y;
+    }
+    static __device__ __forceinline__ void st(__half *p, const float a[4]) {
+        const __half2 h0 = __floats2half2_rn(a[0], a[1]), h1 = __floats2half2_rn(a[2], a[3]);
+        uint2 v;
+        memcpy(&v.x, &h0, 4);
+        memcpy(&v.y, &h1, 4);
+        *reinterpret_cast<uint2 *>(p) = v;
+    }
+};
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// The four values of one population plane that cells x0..x0+3 of a row pull.
+// DX = +1: a direction with e_x = +1 pulls from x - 1; DX = -1 pulls from
+// x + 1. The in-row neighbour comes from the adjacent lane's vector; lanes at
+// the warp's edges load it directly, and the periodic seam (x = 0 pulling from
+// nx - 1, x = nx - 1 pulling from 0) is loaded directly too. Every lane of the
+// warp must call this (shuffles). `inrow` (x0 < pitch) gates the loads, not the
+// lane's own fluid cells: a lane of solid cells still supplies its neighbours.
+template <typename S, int DX>
+__device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, int lane, bool inrow, float out[4]) {
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    if (inrow) Vec4<S>::ld(row + x0, a);
+    if (DX == 0) {
+        out[0] = a[0]; out[1] = a[1]; out[2] = a[2]; out[3] = a[3];
+    } else if (DX == 1) {
+        float left = __shfl_up_sync(kFull, a[3], 1);
+        if (lane == 0) {
+            left = 0.f;
+            int xs = x0 - 1;
+            if (xs < 0 && g.px) xs += g.nx;
+            if (inrow && xs >= 0) left = Store<S>::ld(row + xs);
+        }
+        out[0] = left; out[1] = a[0]; out[2] = a[1]; out[3] = a[2];
+    } else {
+        float right = __shfl_down_sync(kFull, a[0], 1);
+        if (lane == 31) {
+            right = 0.f;
+            const int xs = x0 + 4;
+            if (inrow && xs < g.nx) right = Store<S>::ld(row + xs);
+        }
+        out[0] = a[1]; out[1] = a[2]; out[2] = a[3]; out[3] = right;
+        if (g.px && inrow) {
+            const int k = g.nx - 1 - x0;
+            if (k >= 0 && k < 4) {
+                const float v = Store<S>::ld(row);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) out[j] = (j == k) ? v : out[j];  // constant indices only
+            }
+        }
+    }
+}
+
+// Wall links and collision of cell K of a four-cell group, in place in f, t
+// (K is a template parameter so every array index is a constant).
+template <typename S, int K>
+__device__ __forceinline__ void cell4(const Planes<S> &pl, const Geom &g, const RatesC<float> &r, uint32_t m4,
+                                      int x0, int r0, int rm, int rp, float f[9][4], float t[5][4]) {
+    const unsigned m = (m4 >> (8 * K)) & 0xFFu;
+    float fk[9], tk[5];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fk[i] = f[i][K];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tk[i] = t[i][K];
+    if (m == kSolid) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fk[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) tk[i] = 0.f;
+    } else {
+        if (m) {
+            // halfway wall links: bounce the cell's own post-collision population
+            const int x = x0 + K;
+            int xm = x - 1, xp = x + 1;
+            if (g.px) {
+                xm = (xm < 0) ? xm + g.nx : xm;
+                xp = (xp >= g.nx) ? xp - g.nx : xp;
+            }
+            const int sidx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+            const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                if (m & (1u << (i - 1))) {
+                    const WallDev *w = g.walls + g.flags[sidx[i]];
+                    fk[i] = Store<S>::ld(pl.src[opp[i]] + r0 + x) + (float)__ldg(&w->cf[i]);
+                    if (i < 5)
+                        tk[i] = (float)__ldg(&w->tsgn) * Store<S>::ld(pl.src[9 + opp[i]] + r0 + x) +
+                                (float)__ldg(&w->tb);
+                }
+            }
+        }
+        collide<float>(r, fk, tk);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i][K] = fk[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) t[i][K] = tk[i];
+}
+
+// Fused step, four cells of one row per thread. Same arithmetic as k_step;
+// solid cells in a group are written as zeros (they hold zeros already).
+template <typename S>
+__global__ void __launch_bounds__(128, 4) k_step4(const Planes<S> pl, const Geom g, const RatesC<float> r) {
+    const int lane = threadIdx.x & 31;
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
+    for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {
+        const int r0 = y * g.pitch;
+        const bool inrow = x0 < g.pitch;
+        uint32_t m4 = 0xFFFFFFFFu;
+        if (inrow) m4 = __ldg(reinterpret_cast<const uint32_t *>(g.mask + r0 + x0));
+        const bool any = m4 != 0xFFFFFFFFu;
+        if (!__any_sync(kFull, any)) continue;
+        int ym = y - 1, yp = y + 1;
+        if (g.py) {
+            ym = (ym < 0) ? ym + g.ny : ym;
+            yp = (yp >= g.ny) ? yp - g.ny : yp;
+        }
+        // rows of a non-periodic edge hold no fluid cell, so a warp that gets here has 0 < y < ny - 1
+        const int rm = ym * g.pitch, rp = yp * g.pitch;
+        float f[9][4], t[5][4];
+        ld_plane<S, 0>(pl.src[0] + r0, g, x0, lane, inrow, f[0]);
+        ld_plane<S, 1>(pl.src[1] + r0, g, x0, lane, inrow, f[1]);
+        ld_plane<S, 0>(pl.src[2] + rm, g, x0, lane, inrow, f[2]);
+        ld_plane<S, -1>(pl.src[3] + r0, g, x0, lane, inrow, f[3]);
+        ld_plane<S, 0>(pl.src[4] + rp, g, x0, lane, inrow, f[4]);
+        ld_plane<S, 1>(pl.src[5] + rm, g, x0, lane, inrow, f[5]);
+        ld_plane<S, -1>(pl.src[6] + rm, g, x0, lane, inrow, f[6]);
+        ld_plane<S, -1>(pl.src[7] + rp, g, x0, lane, inrow, f[7]);
+        ld_plane<S, 1>(pl.src[8] + rp, g, x0, lane, inrow, f[8]);
+        ld_plane<S, 0>(pl.src[9] + r0, g, x0, lane, inrow, t[0]);
+        ld_plane<S, 1>(pl.src[10] + r0, g, x0, lane, inrow, t[1]);
+        ld_plane<S, 0>(pl.src[11] + rm, g, x0, lane, inrow, t[2]);
+        ld_plane<S, -1>(pl.src[12] + r0, g, x0, lane, inrow, t[3]);
+        ld_plane<S, 0>(pl.src[13] + rp, g, x0, lane, inrow, t[4]);
+        if (!any) continue;
+        cell4<S, 0>(pl, g, r, m4, x0, r0, rm, rp, f, t);
+        cell4<S, 1>(pl, g, r, m4, x0, r0, rm, rp, f, t);
+        cell4<S, 2>(pl, g, r, m4, x0, r0, rm, rp, f, t);
+        cell4<S, 3>(pl, g, r, m4, x0, r0, rm, rp, f, t);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) Vec4<S>::st(pl.dst[i] + r0 + x0, f[i]);
+#pragma unroll
+        for (int i = 0; i < 5; ++i) Vec4<S>::st(pl.dst[9 + i] + r0 + x0, t[i]);
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 
 inline dim3 step_block() { return dim3(128, 2); }
@@ -479,10 +652,17 @@ inline dim3 step_block() { return dim3(128, 2); }
 template <typename S>
 cudaError_t launch_step(const KParams &p, int src, cudaStream_t st) {
     using C = typename Store<S>::C;
-    const dim3 b = step_block();
-    const int gy = (p.ny + (int)b.y - 1) / (int)b.y;
-    const dim3 grid((p.nx + b.x - 1) / b.x, gy < 65535 ? gy : 65535);
-    k_step<S><<<grid, b, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p));
+    if constexpr (Store<S>::kShifted) {
+        // four cells per thread, 128 threads per block, one row per block row
+        const int threads_x = p.pitch / 4;
+        const dim3 grid((threads_x + 127) / 128, p.ny < 65535 ? p.ny : 65535);
+        k_step4<S><<<grid, 128, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<float>(p));
+    } else {
+        const dim3 b = step_block();
+        const int gy = (p.ny + (int)b.y - 1) / (int)b.y;
+        const dim3 grid((p.nx + b.x - 1) / b.x, gy < 65535 ? gy : 65535);
+        k_step<S><<<grid, b, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p));
+    }
     return cudaGetLastError();
 }
 

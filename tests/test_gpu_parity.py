@@ -35,17 +35,23 @@ def _cases_small():
         lc.cavity(n=20, Ra=1e4, n_y=13, noise=1e-3),
         lc.rayleigh_benard(nx=133, H=7, Ra=1e5, sigma=1e-2),  # two x blocks plus a ragged tail
         lc.poiseuille(H=11, nx=1, ax=1e-5),                   # nx = 1: periodic self-neighbour
+        lc.obstacle_channel(nx=261, H=9, frac=0.15, seed=4),  # scattered solid cells, moving lid
+        lc.periodic_box(6, 9, nu=0.02, alpha=0.03, T0=0.2,
+                        T_init=0.2 + 0.1 * lc.uniform01(9, 54).reshape(9, 6)),  # periodic in x and y
     ]
 
 
-@pytest.mark.parametrize("idx", range(6))
+N_SMALL = 8
+
+
+@pytest.mark.parametrize("idx", range(N_SMALL))
 @pytest.mark.parametrize("nsteps", [0, 1, 2, 10])
 def test_fp64_populations_match_oracle(idx, nsteps):
     P = _P()
     case = _cases_small()[idx]
     g = P.Lattice(case, storage="f64")
     o = oracle.OracleLattice(case)
-    if idx == 0:  # start off-equilibrium
+    if idx in (0, 6, 7):  # start off-equilibrium
         f0, g0 = lc.random_state(case, seed=11)
         g.set_populations(f0, g0)
         o.set_populations(f0, g0)
@@ -104,7 +110,7 @@ ONE_STEP_TOL = {"f32": 2e-6, "f16": 2e-3}
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-@pytest.mark.parametrize("idx", range(6))
+@pytest.mark.parametrize("idx", range(N_SMALL))
 def test_reduced_precision_one_step(storage, idx):
     P = _P()
     case = _cases_small()[idx]
