@@ -260,6 +260,8 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "f64"])
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--H", type=int, default=2048)
+    ap.add_argument("--variant", default="auto", choices=["auto", "scalar", "vec4", "tma"],
+                    help="step kernel variant (lbm_set_step_variant)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -286,6 +288,7 @@ def main():
     sampler = ClockSampler(local).start()
     # every rank advances its own replica of the workload (independent lattices)
     lat = P.Lattice(case, storage=args.storage)
+    lat.set_step_variant(args.variant)
     stream = torch.cuda.current_stream()
     lat.step(args.warmup)
     lat.sync()
@@ -335,7 +338,7 @@ def main():
                    "fluid_cells": fluid, "storage": STORAGE_NAME[args.storage],
                    "l2": "no flush: working set > L2 (two population buffers of "
                          f"{BYTES_PER_NODE[args.storage] // 2 * fluid / 1e9:.2f} GB each)",
-                   "parallelism": f"replicas{world}"},
+                   "parallelism": f"replicas{world}", "step_variant": args.variant},
         "roofline": roof,
         "gpu_launches": args.steps,
         "clocks": clocks,

@@ -37,7 +37,7 @@ typedef enum {
     LBM_ENOMEM = 2,    /* device allocation failed or caller block too small */
     LBM_ECUDA = 3,     /* a CUDA runtime call or launch failed */
     LBM_EDIVERGED = 4, /* NaN/Inf found in the fields (unstable run) */
-    LBM_ETIMEOUT = 5   /* reserved for bounded device-side waits */
+    LBM_ETIMEOUT = 5   /* a kernel gave up one of its bounded waits */
 } lbm_status;
 
 /* Population storage. The FP32/FP16 forms store deviations from the rest state,
@@ -105,8 +105,21 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
  * per step). Asynchronous on the lattice's stream. */
 lbm_status lbm_step(lbm_lattice *h, int64_t nsteps);
 
-/* Wait for the lattice's stream. */
+/* Wait for the lattice's stream. LBM_ETIMEOUT if a step kernel gave up one of
+ * its bounded waits since the last check (the state is then undefined). */
 lbm_status lbm_sync(lbm_lattice *h);
+
+/* Step kernel variants. AUTO picks the fastest for the storage: the TMA-staged
+ * kernel for FP32/FP16 storage, the scalar kernel for FP64. SCALAR: one cell
+ * per thread. VEC4: four cells per thread with 128-bit (FP32) / 64-bit (FP16)
+ * loads and warp shuffles. TMA: row segments of 512 cells staged in shared
+ * memory by bulk copies in a multi-stage pipeline. All give the same result
+ * to the last bit for a given storage. */
+typedef enum { LBM_STEP_AUTO = 0, LBM_STEP_SCALAR = 1, LBM_STEP_VEC4 = 2, LBM_STEP_TMA = 3 } lbm_step_variant;
+
+/* Select the step kernel of h (an lbm_step_variant). LBM_EINVAL for an unknown
+ * variant or VEC4/TMA with FP64 storage. */
+lbm_status lbm_set_step_variant(lbm_lattice *h, int32_t variant);
 
 /* Macroscopic fields into caller-owned host arrays of ny*nx doubles (any may be
  * NULL): the values the next collision would use (pull with the wall rules,

@@ -1,5 +1,5 @@
 // Instantiation of the fused stream-and-collide kernels for f16 population storage.
-#include "nomrt_kernels.cuh"
+#include "launchers.cuh"
 
 namespace nomrt {
 const Launchers &launchers_f16() {

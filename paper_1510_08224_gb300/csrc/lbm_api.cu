@@ -42,7 +42,8 @@ struct Layout {
     size_t plane = 0;           // elements per plane
     size_t pop_bytes = 0;       // one buffer
     size_t off_pop[2] = {0, 0};
-    size_t off_mask = 0, off_flags = 0, off_walls = 0, off_snap = 0, off_stage = 0, off_part = 0, off_res = 0;
+    size_t off_mask = 0, off_flags = 0, off_walls = 0, off_snap = 0, off_stage = 0, off_part = 0, off_res = 0,
+           off_status = 0;
     int stage_rows = 0;
     size_t total = 0;
 };
@@ -66,6 +67,7 @@ Layout make_layout(int nx, int ny, int storage, int n_walls) {
     L.off_stage = o; o += align_up(row_bytes * L.stage_rows, kAlign);
     L.off_part = o; o += align_up(sizeof(double) * nomrt::kRedBlocks * 8, kAlign);
     L.off_res = o; o += align_up(sizeof(double) * 8, kAlign);
+    L.off_status = o; o += kAlign;
     L.total = o;
     return L;
 }
@@ -193,6 +195,25 @@ lbm_status cuda_fail(lbm_lattice *h, cudaError_t e, const char *what) {
         if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
     } while (0)
 
+// After a stream synchronisation: a kernel that gave up a bounded wait left a
+// non-zero status word; report it once and clear it.
+lbm_status check_status(lbm_lattice *h) {
+    int st = 0;
+    cudaError_t e = cudaMemcpy(&st, h->kp.status, sizeof st, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "read status");
+    if (st == nomrt::kStatusOk) return LBM_OK;
+    const int zero = 0;
+    e = cudaMemcpy(h->kp.status, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "clear status");
+    return fail(h, LBM_ETIMEOUT, "a kernel gave up a bounded wait (device status word set)");
+}
+
+#define LBM_STATUS(h)                      \
+    do {                                   \
+        lbm_status s_ = check_status(h);   \
+        if (s_ != LBM_OK) return s_;       \
+    } while (0)
+
 }  // namespace
 
 extern "C" {
@@ -307,6 +328,8 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     kp.varpi = p->varpi;
     kp.rho_ref = p->storage == LBM_F64 ? 0.0 : 1.0;
     kp.T_ref = T_ref;
+    kp.variant = nomrt::kStepAuto;
+    kp.status = reinterpret_cast<int *>(h->mem + h->lay.off_status);
 
     cudaStream_t st = h->stream;
     auto cuda_bail = [&](cudaError_t e, const char *what) {
@@ -359,6 +382,16 @@ lbm_status lbm_step(lbm_lattice *h, int64_t nsteps) {
 lbm_status lbm_sync(lbm_lattice *h) {
     if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "stream sync");
+    LBM_STATUS(h);
+    return LBM_OK;
+}
+
+lbm_status lbm_set_step_variant(lbm_lattice *h, int32_t variant) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    if (variant < LBM_STEP_AUTO || variant > LBM_STEP_TMA) return fail(h, LBM_EINVAL, "unknown step variant");
+    if (h->storage == LBM_F64 && variant != LBM_STEP_AUTO && variant != LBM_STEP_SCALAR)
+        return fail(h, LBM_EINVAL, "FP64 storage has only the scalar step kernel");
+    h->kp.variant = variant;
     return LBM_OK;
 }
 
@@ -379,6 +412,7 @@ lbm_status lbm_read_macro(lbm_lattice *h, double *rho, double *ux, double *uy, d
                          "read macro");
         LBM_CUDA(h, cudaStreamSynchronize(h->stream), "read macro sync");
     }
+    LBM_STATUS(h);
     return LBM_OK;
 }
 
@@ -404,6 +438,7 @@ lbm_status lbm_nusselt(lbm_lattice *h, int32_t side, double L, double delta_T, d
     double r[2];
     LBM_CUDA(h, cudaMemcpyAsync(r, h->result(), sizeof r, cudaMemcpyDeviceToHost, h->stream), "read nusselt");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "nusselt sync");
+    LBM_STATUS(h);
     if (r[1] <= 0.0) return fail(h, LBM_EINVAL, "no fixed-temperature wall line on that side");
     *nu_mean = r[0] / r[1];
     return LBM_OK;
@@ -418,6 +453,7 @@ lbm_status lbm_residual(lbm_lattice *h, double *r) {
     double s[5];
     LBM_CUDA(h, cudaMemcpyAsync(s, h->result(), sizeof s, cudaMemcpyDeviceToHost, h->stream), "read residual");
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "residual sync");
+    LBM_STATUS(h);
     h->have_snap = 1;
     if (s[4] > 0.0 || !std::isfinite(s[0]) || !std::isfinite(s[1]) || !std::isfinite(s[2]) ||
         !std::isfinite(s[3])) {
@@ -453,6 +489,7 @@ lbm_status lbm_get_populations(lbm_lattice *h, double *f9, double *g5) {
         }
         LBM_CUDA(h, cudaStreamSynchronize(h->stream), "export sync");
     }
+    LBM_STATUS(h);
     return LBM_OK;
 }
 

@@ -16,6 +16,14 @@ constexpr uint8_t kSolid = 0xFF;
 // Fixed number of blocks of the reduction kernels (deterministic sums).
 constexpr int kRedBlocks = 512;
 constexpr int kRedThreads = 256;
+// Device status word values (set by kernels, read and cleared by the host).
+constexpr int kStatusOk = 0;
+constexpr int kStatusTimeout = 1;
+// Step kernel variants (lbm_set_step_variant).
+constexpr int kStepAuto = 0;
+constexpr int kStepScalar = 1;
+constexpr int kStepVec4 = 2;
+constexpr int kStepTma = 3;
 
 // Per-wall constants, indexed by wall id (entry 0 unused). cf[i] is Ladd's
 // moving-wall term 2 w_i rho0 (e_i . u_w) / c_s^2 for direction i; a
@@ -45,6 +53,8 @@ struct KParams {
     double z_a, z_e, z_nu;            // Eq. 29
     double g_beta, T0, ax, ay, varpi; // Eq. 4, Eq. 28
     double rho_ref, T_ref;            // storage shift (0 for FP64 storage)
+    int variant;                      // step kernel variant (kStep*)
+    int *status;                      // device status word
 };
 
 // Launchers, one set per storage type (0 = f64, 1 = f32-shifted, 2 = f16-shifted).

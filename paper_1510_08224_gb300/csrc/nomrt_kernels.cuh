@@ -488,6 +488,10 @@ struct Vec4<float> {
     static __device__ __forceinline__ void st(float *p, const float a[4]) {
         *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
     }
+    static __device__ __forceinline__ void ld_shared(const float *p, float a[4]) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+    }
 };
 
 template <>
@@ -506,6 +510,14 @@ struct Vec4<__half> {
         memcpy(&v.x, &h0, 4);
         memcpy(&v.y, &h1, 4);
         *reinterpret_cast<uint2 *>(p) = v;
+    }
+    static __device__ __forceinline__ void ld_shared(const __half *p, float a[4]) {
+        const uint2 v = *reinterpret_cast<const uint2 *>(p);
+        __half2 h0, h1;
+        memcpy(&h0, &v.x, 4);
+        memcpy(&h1, &v.y, 4);
+        const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+        a[0] = f0.x; a[1] = f0.y; a[2] = f1.x; a[3] = f1.y;
     }
 };
 
@@ -643,91 +655,6 @@ __global__ void __launch_bounds__(128, 4) k_step4(const Planes<S> pl, const Geom
 #pragma unroll
         for (int i = 0; i < 5; ++i) Vec4<S>::st(pl.dst[9 + i] + r0 + x0, t[i]);
     }
-}
-
-// ---------------------------------------------------------------- launchers
-
-inline dim3 step_block() { return dim3(128, 2); }
-
-template <typename S>
-cudaError_t launch_step(const KParams &p, int src, cudaStream_t st) {
-    using C = typename Store<S>::C;
-    if constexpr (Store<S>::kShifted) {
-        // four cells per thread, 128 threads per block, one row per block row
-        const int threads_x = p.pitch / 4;
-        const dim3 grid((threads_x + 127) / 128, p.ny < 65535 ? p.ny : 65535);
-        k_step4<S><<<grid, 128, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<float>(p));
-    } else {
-        const dim3 b = step_block();
-        const int gy = (p.ny + (int)b.y - 1) / (int)b.y;
-        const dim3 grid((p.nx + b.x - 1) / b.x, gy < 65535 ? gy : 65535);
-        k_step<S><<<grid, b, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p));
-    }
-    return cudaGetLastError();
-}
-
-template <typename S>
-cudaError_t launch_init_rows(const KParams &p, int buf, int r0, int r1, const double *T, cudaStream_t st) {
-    const dim3 grid((p.pitch + 127) / 128, r1 - r0);
-    k_init_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, T, p.T_ref, p.varpi,
-                                         Store<S>::kShifted ? 1 : 0);
-    return cudaGetLastError();
-}
-
-template <typename S>
-cudaError_t launch_macro_rows(const KParams &p, int buf, int r0, int r1, double *out, cudaStream_t st) {
-    using C = typename Store<S>::C;
-    const dim3 grid((p.nx + 127) / 128, r1 - r0);
-    k_macro_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p), r0, r1,
-                                          p.rho_ref, p.T_ref, out);
-    return cudaGetLastError();
-}
-
-template <typename S>
-cudaError_t launch_export_rows(const KParams &p, int buf, int r0, int r1, double *out, cudaStream_t st) {
-    const dim3 grid((p.nx + 127) / 128, r1 - r0);
-    k_export_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, p.rho_ref, p.T_ref,
-                                           p.varpi, out);
-    return cudaGetLastError();
-}
-
-template <typename S>
-cudaError_t launch_import_rows(const KParams &p, int buf, int r0, int r1, const double *in, int which,
-                               cudaStream_t st) {
-    const dim3 grid((p.nx + 127) / 128, r1 - r0);
-    k_import_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, p.rho_ref, p.T_ref,
-                                           p.varpi, in, which);
-    return cudaGetLastError();
-}
-
-template <typename S>
-cudaError_t launch_nusselt(const KParams &p, int buf, int side, double L, double dT, double *partials,
-                           cudaStream_t st) {
-    k_nusselt<S><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), side, L, dT, p.T_ref,
-                                                    partials);
-    return cudaGetLastError();
-}
-
-template <typename S>
-cudaError_t launch_residual(const KParams &p, int buf, double *snap, int have_snap, double *partials,
-                            cudaStream_t st) {
-    using C = typename Store<S>::C;
-    k_residual<S><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p),
-                                                     p.T_ref, snap, p.plane, have_snap, partials);
-    return cudaGetLastError();
-}
-
-template <typename S>
-Launchers make_launchers() {
-    Launchers L;
-    L.step = &launch_step<S>;
-    L.init_rows = &launch_init_rows<S>;
-    L.macro_rows = &launch_macro_rows<S>;
-    L.export_rows = &launch_export_rows<S>;
-    L.import_rows = &launch_import_rows<S>;
-    L.nusselt = &launch_nusselt<S>;
-    L.residual = &launch_residual<S>;
-    return L;
 }
 
 }  // namespace nomrt

@@ -20,7 +20,9 @@ STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 SIDES = {"left": 0, "right": 1, "bottom": 2, "top": 3}
 
 # Every symbol include/nomrt_lbm.h declares.
-EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_read_macro", "lbm_nusselt",
+STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3}
+EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_set_step_variant", "lbm_read_macro",
+            "lbm_nusselt",
             "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
             "lbm_destroy")
 
@@ -73,6 +75,8 @@ def load():
         L.lbm_step.argtypes = [vp, C.c_int64]
         L.lbm_sync.restype = C.c_int
         L.lbm_sync.argtypes = [vp]
+        L.lbm_set_step_variant.restype = C.c_int
+        L.lbm_set_step_variant.argtypes = [vp, C.c_int32]
         L.lbm_read_macro.restype = C.c_int
         L.lbm_read_macro.argtypes = [vp, dp, dp, dp, dp]
         L.lbm_nusselt.restype = C.c_int
@@ -196,6 +200,11 @@ class Lattice:
 
     def sync(self):
         _check(load().lbm_sync(self._h), self._h)
+
+    def set_step_variant(self, variant):
+        """'auto', 'scalar', 'vec4' or 'tma' (see lbm_set_step_variant)."""
+        v = STEP_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        _check(load().lbm_set_step_variant(self._h, v), self._h)
 
     def macro(self):
         """(rho, ux, uy, T), each (ny, nx) float64 on the host."""

@@ -131,6 +131,34 @@ def test_reduced_precision_one_step(storage, idx):
     assert np.abs(gg - go).max() <= ONE_STEP_TOL[storage] * scale_g
 
 
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("idx", range(N_SMALL))
+def test_step_variants_agree_bitwise(storage, idx):
+    """The scalar, vectorised and TMA-staged step kernels run the same
+    arithmetic: five steps from the same state give the same bits."""
+    P = _P()
+    case = _cases_small()[idx]
+    f0, g0 = lc.random_state(case, seed=21 + idx)
+    out = {}
+    for v in ("scalar", "vec4", "tma"):
+        lat = P.Lattice(case, storage=storage)
+        lat.set_step_variant(v)
+        lat.set_populations(f0, g0)
+        lat.step(5)
+        out[v] = lat.populations()
+        lat.sync()
+    for v in ("vec4", "tma"):
+        assert np.array_equal(out[v][0], out["scalar"][0]) and np.array_equal(out[v][1], out["scalar"][1]), v
+
+
+def test_fp64_rejects_vector_variants():
+    P = _P()
+    lat = P.Lattice(lc.couette(H=4, nx=3), storage="f64")
+    lat.set_step_variant("scalar")
+    with pytest.raises(P.LBMError):
+        lat.set_step_variant("tma")
+
+
 # Accumulated max-norm error after 4000 steps against the FP64 oracle. FP16
 # deviations carry an 11-bit significand, so each step rounds every population
 # by up to ~1e-4 of its deviation; the measured error on this case is about
