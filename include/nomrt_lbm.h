@@ -109,8 +109,8 @@ lbm_status lbm_step(lbm_lattice *h, int64_t nsteps);
  * its bounded waits since the last check (the state is then undefined). */
 lbm_status lbm_sync(lbm_lattice *h);
 
-/* Step kernel variants. AUTO picks the fastest for the storage: the TMA-staged
- * kernel for FP32/FP16 storage, the scalar kernel for FP64. SCALAR: one cell
+/* Step kernel variants. AUTO picks the fastest measured for the storage: the
+ * four-cell vectorised kernel for FP32/FP16 storage, the scalar kernel for FP64. SCALAR: one cell
  * per thread. VEC4: four cells per thread with 128-bit (FP32) / 64-bit (FP16)
  * loads and warp shuffles. TMA: row segments of 512 cells staged in shared
  * memory by bulk copies in a multi-stage pipeline. All give the same result

@@ -58,7 +58,7 @@ cudaError_t launch_step(const KParams &p, int src, cudaStream_t st) {
     using C = typename Store<S>::C;
     int variant = p.variant;
     if constexpr (Store<S>::kShifted) {
-        if (variant == kStepAuto) variant = kStepTma;
+        if (variant == kStepAuto) variant = kStepVec4;
     } else {
         variant = kStepScalar;
     }
