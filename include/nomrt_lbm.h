@@ -154,8 +154,31 @@ lbm_status lbm_set_populations(lbm_lattice *h, const double *f9, const double *g
 lbm_status lbm_info(const lbm_lattice *h, int64_t *fluid_cells, int32_t *pitch, int32_t *elem_bytes,
                     int64_t *steps_done);
 
+/* Steady-state residual of two macroscopic snapshots held in caller-owned
+ * device memory, computed without allocating anything. The paper has no
+ * counterpart: this is a service for callers that cannot call cudaMalloc (a
+ * serving loop whose device memory is fully budgeted by admission control, a
+ * host framework that owns the allocator, a hot path that must not enter the
+ * driver's allocator). Same formula as lbm_residual:
+ *   R = max(|u - u_prev|_2 / |u|_2, |T - T_prev|_2 / |T|_2)
+ * over the n cells whose solid[c] is 0 (solid may be NULL: every cell counts).
+ * ux, uy, T, ux_prev, uy_prev, T_prev: device arrays of n doubles; solid: device
+ * array of n bytes or NULL; *r: host double written on return.
+ * Scratch: the reduction's block partial sums live in a fixed file-scope device
+ * array (about 164 KB, held on every GPU that loads the library until the
+ * process exits); n above 16,777,216 cells is rejected with LBM_EINVAL. All
+ * calls share that array: calls whose kernels overlap on the GPU race.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture. Runs on cuda_stream (NULL = legacy default stream) with
+ * the caller's current device, and synchronises that stream. LBM_EDIVERGED
+ * (and *r = NaN) if a value is not finite. Errors: lbm_last_error(NULL). */
+lbm_status lbm_residual_fields_noalloc(const double *ux, const double *uy, const double *T, const double *ux_prev,
+                                       const double *uy_prev, const double *T_prev, const uint8_t *solid,
+                                       int64_t n, void *cuda_stream, double *r);
+
 /* Last error message of h (never NULL); with h == NULL, the calling thread's
- * last lbm_create / lbm_footprint_bytes error. */
+ * last lbm_create / lbm_footprint_bytes / lbm_residual_fields_noalloc error. */
 const char *lbm_last_error(const lbm_lattice *h);
 
 /* Free the lattice (and its device memory if the library allocated it). */

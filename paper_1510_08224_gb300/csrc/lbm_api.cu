@@ -155,6 +155,8 @@ const nomrt::Launchers &launchers_for(int storage) {
 
 }  // namespace
 
+void nomrt::set_thread_error(const char *msg) { g_create_error = msg; }
+
 struct lbm_lattice {
     int nx = 0, ny = 0, px = 0, py = 0, storage = 0, n_walls = 0;
     cudaStream_t stream = nullptr;

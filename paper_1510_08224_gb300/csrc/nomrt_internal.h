@@ -83,6 +83,9 @@ const Launchers &launchers_f64();
 const Launchers &launchers_f32();
 const Launchers &launchers_f16();
 
+// Sets the calling thread's error message (lbm_last_error(NULL)).
+void set_thread_error(const char *msg);
+
 // Final fixed-order reduction of partials[kRedBlocks][width] into out[width].
 cudaError_t reduce_partials(const double *partials, int width, double *out, cudaStream_t st);
 

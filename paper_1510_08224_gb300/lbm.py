@@ -24,7 +24,7 @@ STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3}
 EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_set_step_variant", "lbm_read_macro",
             "lbm_nusselt",
             "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
-            "lbm_destroy")
+            "lbm_destroy", "lbm_residual_fields_noalloc")
 
 
 class LBMError(RuntimeError):
@@ -94,6 +94,8 @@ def load():
         L.lbm_last_error.argtypes = [vp]
         L.lbm_destroy.restype = None
         L.lbm_destroy.argtypes = [vp]
+        L.lbm_residual_fields_noalloc.restype = C.c_int
+        L.lbm_residual_fields_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_int64, vp, dp]
         _lib = L
         return L
 
@@ -135,6 +137,25 @@ def make_params(case, storage: str = "f32"):
         setattr(p, name, float(getattr(case, name)))
     p.T_init = Ti.ctypes.data if Ti is not None else None
     return p, (flags, walls, Ti)
+
+
+def residual_fields_noalloc(ux, uy, T, ux_prev, uy_prev, T_prev, solid=None, stream=None) -> float:
+    """lbm_residual_fields_noalloc on torch CUDA tensors (float64, same length;
+    solid: uint8 or None). Allocates nothing on the device."""
+    import torch
+    n = ux.numel()
+    for a in (ux, uy, T, ux_prev, uy_prev, T_prev):
+        assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous() and a.numel() == n
+    if solid is not None:
+        assert solid.is_cuda and solid.dtype == torch.uint8 and solid.is_contiguous() and solid.numel() == n
+    st = stream if stream is not None else torch.cuda.current_stream(ux.device)
+    r = C.c_double()
+    with torch.cuda.device(ux.device):
+        status = load().lbm_residual_fields_noalloc(
+            ux.data_ptr(), uy.data_ptr(), T.data_ptr(), ux_prev.data_ptr(), uy_prev.data_ptr(), T_prev.data_ptr(),
+            None if solid is None else solid.data_ptr(), C.c_int64(n), C.c_void_p(st.cuda_stream), C.byref(r))
+    _check(status, None)
+    return r.value
 
 
 def lbm_footprint_bytes(params) -> int:
