@@ -261,7 +261,8 @@ def main():
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--H", type=int, default=2048)
     ap.add_argument("--variant", default="auto", choices=["auto", "scalar", "vec4", "tma"],
-                    help="step kernel variant (lbm_set_step_variant)")
+                    help="step kernel variant (lbm_set_step_kernel)")
+    ap.add_argument("--config", type=int, default=0, help="shape index of the step variant")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -288,7 +289,7 @@ def main():
     sampler = ClockSampler(local).start()
     # every rank advances its own replica of the workload (independent lattices)
     lat = P.Lattice(case, storage=args.storage)
-    lat.set_step_variant(args.variant)
+    lat.set_step_kernel(args.variant, args.config)
     stream = torch.cuda.current_stream()
     lat.step(args.warmup)
     lat.sync()
@@ -338,7 +339,7 @@ def main():
                    "fluid_cells": fluid, "storage": STORAGE_NAME[args.storage],
                    "l2": "no flush: working set > L2 (two population buffers of "
                          f"{BYTES_PER_NODE[args.storage] // 2 * fluid / 1e9:.2f} GB each)",
-                   "parallelism": f"replicas{world}", "step_variant": args.variant},
+                   "parallelism": f"replicas{world}", "step_kernel": [args.variant, args.config]},
         "roofline": roof,
         "gpu_launches": args.steps,
         "clocks": clocks,

@@ -109,17 +109,23 @@ lbm_status lbm_step(lbm_lattice *h, int64_t nsteps);
  * its bounded waits since the last check (the state is then undefined). */
 lbm_status lbm_sync(lbm_lattice *h);
 
-/* Step kernel variants. AUTO picks the fastest measured for the storage: the
- * four-cell vectorised kernel for FP32/FP16 storage, the scalar kernel for FP64. SCALAR: one cell
- * per thread. VEC4: four cells per thread with 128-bit (FP32) / 64-bit (FP16)
- * loads and warp shuffles. TMA: row segments of 512 cells staged in shared
- * memory by bulk copies in a multi-stage pipeline. All give the same result
- * to the last bit for a given storage. */
+/* Step kernel variants. All compute the same arithmetic and give the same
+ * bits for a given storage. AUTO picks the fastest measured: the four-cell
+ * vectorised kernel for FP32/FP16 storage, the scalar kernel for FP64.
+ * SCALAR: one cell per thread. VEC4: four cells per thread with 128-bit (FP32)
+ * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls. TMA: row
+ * segments staged in shared memory by bulk copies in a multi-stage pipeline;
+ * its config index selects the shape (cells per thread, threads per CTA,
+ * stages). */
 typedef enum { LBM_STEP_AUTO = 0, LBM_STEP_SCALAR = 1, LBM_STEP_VEC4 = 2, LBM_STEP_TMA = 3 } lbm_step_variant;
 
-/* Select the step kernel of h (an lbm_step_variant). LBM_EINVAL for an unknown
- * variant or VEC4/TMA with FP64 storage. */
-lbm_status lbm_set_step_variant(lbm_lattice *h, int32_t variant);
+/* Number of configs of a variant for a storage (0 if the variant does not
+ * exist for it: FP64 has only SCALAR). Host only. */
+int32_t lbm_step_kernel_count(int32_t storage, int32_t variant);
+
+/* Select the step kernel of h: a variant and a config index below
+ * lbm_step_kernel_count(storage, variant). LBM_EINVAL otherwise. */
+lbm_status lbm_set_step_kernel(lbm_lattice *h, int32_t variant, int32_t config);
 
 /* Macroscopic fields into caller-owned host arrays of ny*nx doubles (any may be
  * NULL): the values the next collision would use (pull with the wall rules,

@@ -10,47 +10,83 @@ namespace nomrt {
 
 inline dim3 step_block() { return dim3(128, 2); }
 
-// Stages of the TMA pipeline per storage type: about 88 KB of shared memory per
-// CTA, so two CTAs fit on an SM.
-template <typename S>
-struct TmaStages;
-template <>
-struct TmaStages<float> {
-    static constexpr int value = 3;
-};
-template <>
-struct TmaStages<__half> {
-    static constexpr int value = 6;
-};
+// TMA kernel shapes selectable at run time (lbm_set_step_kernel config index):
+// cells per thread N, threads per CTA T, stages, CTAs per SM asked of ptxas.
+// Stage counts keep each CTA's shared memory near 60 or 90 KB.
+constexpr int kTmaConfigs = 5;
 
 template <typename S>
+struct TmaShape;
+// FP32: a 512-cell stage is 14 x 520 x 4 B = 29 KB, a 256-cell stage 14.8 KB
+template <>
+struct TmaShape<float> {
+    static constexpr int N[kTmaConfigs] = {4, 2, 1, 1, 2};
+    static constexpr int T[kTmaConfigs] = {128, 256, 512, 256, 128};
+    static constexpr int ST[kTmaConfigs] = {3, 3, 3, 4, 5};
+    static constexpr int MB[kTmaConfigs] = {2, 2, 2, 3, 3};
+};
+// FP16: half the bytes per stage, so twice the stages
+template <>
+struct TmaShape<__half> {
+    static constexpr int N[kTmaConfigs] = {4, 2, 1, 1, 2};
+    static constexpr int T[kTmaConfigs] = {128, 256, 512, 256, 128};
+    static constexpr int ST[kTmaConfigs] = {6, 6, 6, 8, 10};
+    static constexpr int MB[kTmaConfigs] = {2, 2, 2, 3, 3};
+};
+
+template <typename S, int N, int T, int STAGES>
 constexpr size_t tma_smem_bytes() {
     constexpr int HALO = 16 / (int)sizeof(S);
-    return (size_t)TmaStages<S>::value * kQ * (kTmaW + 2 * HALO) * sizeof(S) + 8 * TmaStages<S>::value;
+    return (size_t)STAGES * kQ * (N * T + 2 * HALO) * sizeof(S) + 8 * STAGES;
 }
 
-// Persistent grid of the TMA kernel: resident CTAs per SM x SMs, computed once
-// per device.
-template <typename S>
-cudaError_t tma_grid(int *blocks) {
+template <typename S, int N, int T, int STAGES, int MB>
+cudaError_t launch_tma_shape(const KParams &p, int src, cudaStream_t st) {
+    constexpr int W = N * T;
+    constexpr size_t smem = tma_smem_bytes<S, N, T, STAGES>();
+    auto kern = k_step_tma<S, N, T, STAGES, MB>;
+    // persistent grid: resident CTAs per SM x SMs, computed once per device
     static int cached_dev = -1, cached_blocks = 0;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev != cached_dev) {
-        auto kern = k_step_tma<S, TmaStages<S>::value>;
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tma_smem_bytes<S>());
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTmaThreads, tma_smem_bytes<S>());
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
         if (e != cudaSuccess) return e;
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         cached_blocks = (per_sm > 0 ? per_sm : 1) * sms;
         cached_dev = dev;
     }
-    *blocks = cached_blocks;
-    return cudaSuccess;
+    TmaUnits U;
+    U.y_lo = p.py ? 0 : 1;
+    U.nrows = p.py ? p.ny : p.ny - 2;
+    U.nseg = (p.pitch + W - 1) / W;
+    U.total = U.nrows > 0 ? U.nrows * U.nseg : 0;
+    if (U.total == 0) return cudaSuccess;
+    const int blocks = cached_blocks < U.total ? cached_blocks : U.total;
+    kern<<<blocks, T, smem, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<float>(p), U, p.status);
+    return cudaGetLastError();
+}
+
+template <typename S, int C>
+cudaError_t launch_tma_cfg(const KParams &p, int src, cudaStream_t st) {
+    using Sh = TmaShape<S>;
+    return launch_tma_shape<S, Sh::N[C], Sh::T[C], Sh::ST[C], Sh::MB[C]>(p, src, st);
+}
+
+template <typename S>
+cudaError_t launch_tma(const KParams &p, int src, cudaStream_t st) {
+    switch (p.config) {
+        case 1: return launch_tma_cfg<S, 1>(p, src, st);
+        case 2: return launch_tma_cfg<S, 2>(p, src, st);
+        case 3: return launch_tma_cfg<S, 3>(p, src, st);
+        case 4: return launch_tma_cfg<S, 4>(p, src, st);
+        default: return launch_tma_cfg<S, 0>(p, src, st);
+    }
 }
 
 template <typename S>
@@ -63,21 +99,7 @@ cudaError_t launch_step(const KParams &p, int src, cudaStream_t st) {
         variant = kStepScalar;
     }
     if constexpr (Store<S>::kShifted) {
-        if (variant == kStepTma) {
-            TmaUnits U;
-            U.y_lo = p.py ? 0 : 1;
-            U.nrows = p.py ? p.ny : p.ny - 2;
-            U.nseg = (p.pitch + kTmaW - 1) / kTmaW;
-            U.total = U.nrows > 0 ? U.nrows * U.nseg : 0;
-            if (U.total == 0) return cudaSuccess;
-            int blocks = 0;
-            cudaError_t e = tma_grid<S>(&blocks);
-            if (e != cudaSuccess) return e;
-            if (blocks > U.total) blocks = U.total;
-            k_step_tma<S, TmaStages<S>::value><<<blocks, kTmaThreads, tma_smem_bytes<S>(), st>>>(
-                make_planes<S>(p, src), make_geom(p), make_rates<float>(p), U, p.status);
-            return cudaGetLastError();
-        }
+        if (variant == kStepTma) return launch_tma<S>(p, src, st);
         if (variant == kStepVec4) {
             // four cells per thread, 128 threads per block, one row per block row
             const int threads_x = p.pitch / 4;

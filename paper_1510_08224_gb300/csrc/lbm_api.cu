@@ -331,6 +331,7 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     kp.rho_ref = p->storage == LBM_F64 ? 0.0 : 1.0;
     kp.T_ref = T_ref;
     kp.variant = nomrt::kStepAuto;
+    kp.config = 0;
     kp.status = reinterpret_cast<int *>(h->mem + h->lay.off_status);
 
     cudaStream_t st = h->stream;
@@ -388,12 +389,22 @@ lbm_status lbm_sync(lbm_lattice *h) {
     return LBM_OK;
 }
 
-lbm_status lbm_set_step_variant(lbm_lattice *h, int32_t variant) {
+int32_t lbm_step_kernel_count(int32_t storage, int32_t variant) {
+    if (storage < LBM_F64 || storage > LBM_F16_SHIFTED) return 0;
+    if (variant == LBM_STEP_AUTO || variant == LBM_STEP_SCALAR) return 1;
+    if (storage == LBM_F64) return 0;
+    if (variant == LBM_STEP_VEC4) return 1;
+    if (variant == LBM_STEP_TMA) return nomrt::kTmaConfigCount;
+    return 0;
+}
+
+lbm_status lbm_set_step_kernel(lbm_lattice *h, int32_t variant, int32_t config) {
     if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
-    if (variant < LBM_STEP_AUTO || variant > LBM_STEP_TMA) return fail(h, LBM_EINVAL, "unknown step variant");
-    if (h->storage == LBM_F64 && variant != LBM_STEP_AUTO && variant != LBM_STEP_SCALAR)
-        return fail(h, LBM_EINVAL, "FP64 storage has only the scalar step kernel");
+    const int32_t n = lbm_step_kernel_count(h->storage, variant);
+    if (n == 0) return fail(h, LBM_EINVAL, "step variant not available for this storage");
+    if (config < 0 || config >= n) return fail(h, LBM_EINVAL, "step kernel config out of range");
     h->kp.variant = variant;
+    h->kp.config = config;
     return LBM_OK;
 }
 

@@ -24,6 +24,8 @@ constexpr int kStepAuto = 0;
 constexpr int kStepScalar = 1;
 constexpr int kStepVec4 = 2;
 constexpr int kStepTma = 3;
+// Shapes of the TMA step kernel (see launchers.cuh).
+constexpr int kTmaConfigCount = 5;
 
 // Per-wall constants, indexed by wall id (entry 0 unused). cf[i] is Ladd's
 // moving-wall term 2 w_i rho0 (e_i . u_w) / c_s^2 for direction i; a
@@ -54,6 +56,7 @@ struct KParams {
     double g_beta, T0, ax, ay, varpi; // Eq. 4, Eq. 28
     double rho_ref, T_ref;            // storage shift (0 for FP64 storage)
     int variant;                      // step kernel variant (kStep*)
+    int config;                       // shape index within the variant (TMA: 0..kTmaConfigs-1)
     int *status;                      // device status word
 };
 

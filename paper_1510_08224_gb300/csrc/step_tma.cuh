@@ -18,9 +18,6 @@
 
 namespace nomrt {
 
-constexpr int kTmaThreads = 128;
-constexpr int kTmaCells = 4;
-constexpr int kTmaW = kTmaThreads * kTmaCells;  // cells per unit
 constexpr long long kWaitBudgetCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -93,21 +90,72 @@ struct TmaUnits {
     int total;  // nrows * nseg
 };
 
-// Issue the 14 copies of unit u into stage s (one elected thread).
+// N consecutive storage elements <-> N compute values.
+template <typename S, int N>
+struct VecN;
+
 template <typename S>
+struct VecN<S, 4> {
+    static __device__ __forceinline__ void ld_shared(const S *p, float a[4]) { Vec4<S>::ld_shared(p, a); }
+    static __device__ __forceinline__ void st(S *p, const float a[4]) { Vec4<S>::st(p, a); }
+};
+
+template <>
+struct VecN<float, 2> {
+    static __device__ __forceinline__ void ld_shared(const float *p, float a[2]) {
+        const float2 v = *reinterpret_cast<const float2 *>(p);
+        a[0] = v.x; a[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(float *p, const float a[2]) {
+        *reinterpret_cast<float2 *>(p) = make_float2(a[0], a[1]);
+    }
+};
+
+template <>
+struct VecN<__half, 2> {
+    static __device__ __forceinline__ void ld_shared(const __half *p, float a[2]) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        a[0] = f.x; a[1] = f.y;
+    }
+    static __device__ __forceinline__ void st(__half *p, const float a[2]) {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a[0], a[1]);
+    }
+};
+
+template <typename S>
+struct VecN<S, 1> {
+    static __device__ __forceinline__ void ld_shared(const S *p, float a[1]) { a[0] = (float)p[0]; }
+    static __device__ __forceinline__ void st(S *p, const float a[1]) { Store<S>::st(p, a[0]); }
+};
+
+// Link-map bytes of N consecutive cells (N-byte aligned), packed little-endian.
+template <int N>
+__device__ __forceinline__ uint32_t ld_mask(const uint8_t *p) {
+    if (N == 4) return __ldg(reinterpret_cast<const uint32_t *>(p));
+    if (N == 2) return (uint32_t)__ldg(reinterpret_cast<const uint16_t *>(p));
+    return (uint32_t)__ldg(p);
+}
+
+template <int N>
+__host__ __device__ constexpr uint32_t all_solid() {
+    return N == 4 ? 0xFFFFFFFFu : (N == 2 ? 0xFFFFu : 0xFFu);
+}
+
+// Issue the 14 copies of unit u into a stage (one elected thread).
+template <typename S, int W>
 __device__ __forceinline__ void tma_issue(const Planes<S> &pl, const Geom &g, const TmaUnits &U, int u, S *stage,
                                           uint64_t *bar) {
     constexpr int HALO = 16 / (int)sizeof(S);
-    constexpr int ROW = kTmaW + 2 * HALO;
+    constexpr int ROW = W + 2 * HALO;
     const int y = U.y_lo + u / U.nseg;
-    const int xs = (u % U.nseg) * kTmaW;
+    const int xs = (u % U.nseg) * W;
     int ym = y - 1, yp = y + 1;
     if (g.py) {
         ym = (ym < 0) ? ym + g.ny : ym;
         yp = (yp >= g.ny) ? yp - g.ny : yp;
     }
     const int lo = xs - HALO < 0 ? 0 : xs - HALO;
-    const int hi = xs + kTmaW + HALO > g.pitch ? g.pitch : xs + kTmaW + HALO;
+    const int hi = xs + W + HALO > g.pitch ? g.pitch : xs + W + HALO;
     const uint32_t bytes = (uint32_t)((hi - lo) * (int)sizeof(S));
     mbar_arrive_expect_tx(bar, bytes * kQ);
 #pragma unroll 1
@@ -118,41 +166,114 @@ __device__ __forceinline__ void tma_issue(const Planes<S> &pl, const Geom &g, co
     }
 }
 
-// Four values of one plane for cells x0..x0+3 from the staged row `sm`
-// (sm[HALO + j] holds cell xs + j). Same pull rules as ld_plane.
-template <typename S, int DX>
+// N values of one plane for cells x0..x0+N-1 from the staged row `sm`
+// (sm[HALO + j] holds cell xs + j), with the pull rules of ld_plane: DX = +1
+// pulls from x - 1, DX = -1 from x + 1; the periodic seam reads global memory.
+template <typename S, int DX, int N>
 __device__ __forceinline__ void sm_plane(const S *sm, const S *grow, const Geom &g, int j0, int x0, int lane,
-                                         float out[4]) {
+                                         float out[N]) {
     constexpr int HALO = 16 / (int)sizeof(S);
-    float a[4];
-    Vec4<S>::ld_shared(sm + HALO + j0, a);
-    if (DX == 0) {
-        out[0] = a[0]; out[1] = a[1]; out[2] = a[2]; out[3] = a[3];
-    } else if (DX == 1) {
-        float left = __shfl_up_sync(kFull, a[3], 1);
-        if (lane == 0) left = (float)sm[HALO + j0 - 1];
-        out[0] = left; out[1] = a[0]; out[2] = a[1]; out[3] = a[2];
-        if (g.px && x0 == 0) out[0] = Store<S>::ld(grow + g.nx - 1);  // periodic seam
+    if (N == 1) {
+        out[0] = (float)sm[HALO + j0 - DX];
     } else {
-        float right = __shfl_down_sync(kFull, a[0], 1);
-        if (lane == 31) right = (float)sm[HALO + j0 + 4];
-        out[0] = a[1]; out[1] = a[2]; out[2] = a[3]; out[3] = right;
-        if (g.px) {
-            const int k = g.nx - 1 - x0;
-            if (k >= 0 && k < 4) {
-                const float v = Store<S>::ld(grow);  // periodic seam: x = nx - 1 pulls from x = 0
+        float a[N];
+        VecN<S, N>::ld_shared(sm + HALO + j0, a);
+        if (DX == 0) {
 #pragma unroll
-                for (int j = 0; j < 4; ++j) out[j] = (j == k) ? v : out[j];
-            }
+            for (int k = 0; k < N; ++k) out[k] = a[k];
+        } else if (DX == 1) {
+            float left = __shfl_up_sync(kFull, a[N - 1], 1);
+            if (lane == 0) left = (float)sm[HALO + j0 - 1];
+            out[0] = left;
+#pragma unroll
+            for (int k = 1; k < N; ++k) out[k] = a[k - 1];
+        } else {
+            float right = __shfl_down_sync(kFull, a[0], 1);
+            if (lane == 31) right = (float)sm[HALO + j0 + N];
+#pragma unroll
+            for (int k = 0; k < N - 1; ++k) out[k] = a[k + 1];
+            out[N - 1] = right;
+        }
+    }
+    if (DX == 1 && g.px && x0 == 0) out[0] = Store<S>::ld(grow + g.nx - 1);  // periodic seam
+    if (DX == -1 && g.px) {
+        const int k = g.nx - 1 - x0;
+        if (k >= 0 && k < N) {
+            const float v = Store<S>::ld(grow);  // periodic seam: x = nx - 1 pulls from x = 0
+#pragma unroll
+            for (int j = 0; j < N; ++j) out[j] = (j == k) ? v : out[j];  // constant indices only
         }
     }
 }
 
-template <typename S, int STAGES>
-__global__ void __launch_bounds__(kTmaThreads) k_step_tma(const Planes<S> pl, const Geom g, const RatesC<float> r,
-                                                          const TmaUnits U, int *status) {
+// Wall links and collision of cell K of an N-cell group, in place.
+template <typename S, int K, int N>
+__device__ __forceinline__ void cellN(const Planes<S> &pl, const Geom &g, const RatesC<float> &r, uint32_t mN,
+                                      int x0, int r0, int rm, int rp, float f[9][N], float t[5][N]) {
+    const unsigned m = (mN >> (8 * K)) & 0xFFu;
+    float fk[9], tk[5];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fk[i] = f[i][K];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tk[i] = t[i][K];
+    if (m == kSolid) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fk[i] = 0.f;
+#pragma unroll
+        for (int i = 0; i < 5; ++i) tk[i] = 0.f;
+    } else {
+        if (m) {
+            const int x = x0 + K;
+            int xm = x - 1, xp = x + 1;
+            if (g.px) {
+                xm = (xm < 0) ? xm + g.nx : xm;
+                xp = (xp >= g.nx) ? xp - g.nx : xp;
+            }
+            const int sidx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+            const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                if (m & (1u << (i - 1))) {
+                    const WallDev *w = g.walls + g.flags[sidx[i]];
+                    fk[i] = Store<S>::ld(pl.src[opp[i]] + r0 + x) + (float)__ldg(&w->cf[i]);
+                    if (i < 5)
+                        tk[i] = (float)__ldg(&w->tsgn) * Store<S>::ld(pl.src[9 + opp[i]] + r0 + x) +
+                                (float)__ldg(&w->tb);
+                }
+            }
+        }
+        collide<float>(r, fk, tk);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i][K] = fk[i];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) t[i][K] = tk[i];
+}
+
+template <typename S, int N, int K>
+struct CellLoop {
+    static __device__ __forceinline__ void run(const Planes<S> &pl, const Geom &g, const RatesC<float> &r,
+                                               uint32_t mN, int x0, int r0, int rm, int rp, float f[9][N],
+                                               float t[5][N]) {
+        cellN<S, K, N>(pl, g, r, mN, x0, r0, rm, rp, f, t);
+        CellLoop<S, N, K + 1>::run(pl, g, r, mN, x0, r0, rm, rp, f, t);
+    }
+};
+
+template <typename S, int N>
+struct CellLoop<S, N, N> {
+    static __device__ __forceinline__ void run(const Planes<S> &, const Geom &, const RatesC<float> &, uint32_t, int,
+                                               int, int, int, float[9][N], float[5][N]) {}
+};
+
+// Shape of a TMA step kernel: N cells per thread, T threads per CTA (a unit of
+// W = N * T cells), STAGES pipeline stages, MINB CTAs per SM asked of ptxas.
+template <typename S, int N, int T, int STAGES, int MINB>
+__global__ void __launch_bounds__(T, MINB) k_step_tma(const Planes<S> pl, const Geom g, const RatesC<float> r,
+                                                      const TmaUnits U, int *status) {
+    constexpr int W = N * T;
     constexpr int HALO = 16 / (int)sizeof(S);
-    constexpr int ROW = kTmaW + 2 * HALO;
+    constexpr int ROW = W + 2 * HALO;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     S *stages = reinterpret_cast<S *>(smem_raw);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem_raw + (size_t)STAGES * kQ * ROW * sizeof(S));
@@ -171,7 +292,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_step_tma(const Planes<S> pl, co
         for (int s = 0; s < STAGES; ++s) {
             const int u = blockIdx.x + s * gridDim.x;
             if (u >= U.total) break;
-            tma_issue<S>(pl, g, U, u, stages + (size_t)s * kQ * ROW, &bars[s]);
+            tma_issue<S, W>(pl, g, U, u, stages + (size_t)s * kQ * ROW, &bars[s]);
             ++armed;
         }
     }
@@ -184,8 +305,8 @@ __global__ void __launch_bounds__(kTmaThreads) k_step_tma(const Planes<S> pl, co
         if (abort_flag) break;
         const S *st = stages + (size_t)s * kQ * ROW;
         const int y = U.y_lo + u / U.nseg;
-        const int xs = (u % U.nseg) * kTmaW;
-        const int j0 = tid * kTmaCells;
+        const int xs = (u % U.nseg) * W;
+        const int j0 = tid * N;
         const int x0 = xs + j0;
         const int r0 = y * g.pitch;
         int ym = y - 1, yp = y + 1;
@@ -195,34 +316,31 @@ __global__ void __launch_bounds__(kTmaThreads) k_step_tma(const Planes<S> pl, co
         }
         const int rm = ym * g.pitch, rp = yp * g.pitch;
         const bool inrow = x0 < g.pitch;
-        uint32_t m4 = 0xFFFFFFFFu;
-        if (inrow) m4 = __ldg(reinterpret_cast<const uint32_t *>(g.mask + r0 + x0));
-        const bool any = m4 != 0xFFFFFFFFu;
+        uint32_t mN = all_solid<N>();
+        if (inrow) mN = ld_mask<N>(g.mask + r0 + x0);
+        const bool any = mN != all_solid<N>();
         if (__any_sync(kFull, any)) {
-            float f[9][4], t[5][4];
-            sm_plane<S, 0>(st + 0 * ROW, pl.src[0] + r0, g, j0, x0, lane, f[0]);
-            sm_plane<S, 1>(st + 1 * ROW, pl.src[1] + r0, g, j0, x0, lane, f[1]);
-            sm_plane<S, 0>(st + 2 * ROW, pl.src[2] + rm, g, j0, x0, lane, f[2]);
-            sm_plane<S, -1>(st + 3 * ROW, pl.src[3] + r0, g, j0, x0, lane, f[3]);
-            sm_plane<S, 0>(st + 4 * ROW, pl.src[4] + rp, g, j0, x0, lane, f[4]);
-            sm_plane<S, 1>(st + 5 * ROW, pl.src[5] + rm, g, j0, x0, lane, f[5]);
-            sm_plane<S, -1>(st + 6 * ROW, pl.src[6] + rm, g, j0, x0, lane, f[6]);
-            sm_plane<S, -1>(st + 7 * ROW, pl.src[7] + rp, g, j0, x0, lane, f[7]);
-            sm_plane<S, 1>(st + 8 * ROW, pl.src[8] + rp, g, j0, x0, lane, f[8]);
-            sm_plane<S, 0>(st + 9 * ROW, pl.src[9] + r0, g, j0, x0, lane, t[0]);
-            sm_plane<S, 1>(st + 10 * ROW, pl.src[10] + r0, g, j0, x0, lane, t[1]);
-            sm_plane<S, 0>(st + 11 * ROW, pl.src[11] + rm, g, j0, x0, lane, t[2]);
-            sm_plane<S, -1>(st + 12 * ROW, pl.src[12] + r0, g, j0, x0, lane, t[3]);
-            sm_plane<S, 0>(st + 13 * ROW, pl.src[13] + rp, g, j0, x0, lane, t[4]);
+            float f[9][N], t[5][N];
+            sm_plane<S, 0, N>(st + 0 * ROW, pl.src[0] + r0, g, j0, x0, lane, f[0]);
+            sm_plane<S, 1, N>(st + 1 * ROW, pl.src[1] + r0, g, j0, x0, lane, f[1]);
+            sm_plane<S, 0, N>(st + 2 * ROW, pl.src[2] + rm, g, j0, x0, lane, f[2]);
+            sm_plane<S, -1, N>(st + 3 * ROW, pl.src[3] + r0, g, j0, x0, lane, f[3]);
+            sm_plane<S, 0, N>(st + 4 * ROW, pl.src[4] + rp, g, j0, x0, lane, f[4]);
+            sm_plane<S, 1, N>(st + 5 * ROW, pl.src[5] + rm, g, j0, x0, lane, f[5]);
+            sm_plane<S, -1, N>(st + 6 * ROW, pl.src[6] + rm, g, j0, x0, lane, f[6]);
+            sm_plane<S, -1, N>(st + 7 * ROW, pl.src[7] + rp, g, j0, x0, lane, f[7]);
+            sm_plane<S, 1, N>(st + 8 * ROW, pl.src[8] + rp, g, j0, x0, lane, f[8]);
+            sm_plane<S, 0, N>(st + 9 * ROW, pl.src[9] + r0, g, j0, x0, lane, t[0]);
+            sm_plane<S, 1, N>(st + 10 * ROW, pl.src[10] + r0, g, j0, x0, lane, t[1]);
+            sm_plane<S, 0, N>(st + 11 * ROW, pl.src[11] + rm, g, j0, x0, lane, t[2]);
+            sm_plane<S, -1, N>(st + 12 * ROW, pl.src[12] + r0, g, j0, x0, lane, t[3]);
+            sm_plane<S, 0, N>(st + 13 * ROW, pl.src[13] + rp, g, j0, x0, lane, t[4]);
             if (any) {
-                cell4<S, 0>(pl, g, r, m4, x0, r0, rm, rp, f, t);
-                cell4<S, 1>(pl, g, r, m4, x0, r0, rm, rp, f, t);
-                cell4<S, 2>(pl, g, r, m4, x0, r0, rm, rp, f, t);
-                cell4<S, 3>(pl, g, r, m4, x0, r0, rm, rp, f, t);
+                CellLoop<S, N, 0>::run(pl, g, r, mN, x0, r0, rm, rp, f, t);
 #pragma unroll
-                for (int q = 0; q < 9; ++q) Vec4<S>::st(pl.dst[q] + r0 + x0, f[q]);
+                for (int q = 0; q < 9; ++q) VecN<S, N>::st(pl.dst[q] + r0 + x0, f[q]);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) Vec4<S>::st(pl.dst[9 + q] + r0 + x0, t[q]);
+                for (int q = 0; q < 5; ++q) VecN<S, N>::st(pl.dst[9 + q] + r0 + x0, t[q]);
             }
         }
         // every thread is done reading stage s: refill it with this CTA's unit STAGES ahead
@@ -231,7 +349,7 @@ __global__ void __launch_bounds__(kTmaThreads) k_step_tma(const Planes<S> pl, co
             const int un = u + STAGES * gridDim.x;
             if (un < U.total) {
                 fence_proxy_async_smem();
-                tma_issue<S>(pl, g, U, un, stages + (size_t)s * kQ * ROW, &bars[s]);
+                tma_issue<S, W>(pl, g, U, un, stages + (size_t)s * kQ * ROW, &bars[s]);
                 ++armed;
             }
         }

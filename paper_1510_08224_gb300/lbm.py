@@ -21,7 +21,8 @@ SIDES = {"left": 0, "right": 1, "bottom": 2, "top": 3}
 
 # Every symbol include/nomrt_lbm.h declares.
 STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3}
-EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_set_step_variant", "lbm_read_macro",
+EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_step_kernel_count",
+            "lbm_set_step_kernel", "lbm_read_macro",
             "lbm_nusselt",
             "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
             "lbm_destroy", "lbm_residual_fields_noalloc")
@@ -75,8 +76,10 @@ def load():
         L.lbm_step.argtypes = [vp, C.c_int64]
         L.lbm_sync.restype = C.c_int
         L.lbm_sync.argtypes = [vp]
-        L.lbm_set_step_variant.restype = C.c_int
-        L.lbm_set_step_variant.argtypes = [vp, C.c_int32]
+        L.lbm_step_kernel_count.restype = C.c_int32
+        L.lbm_step_kernel_count.argtypes = [C.c_int32, C.c_int32]
+        L.lbm_set_step_kernel.restype = C.c_int
+        L.lbm_set_step_kernel.argtypes = [vp, C.c_int32, C.c_int32]
         L.lbm_read_macro.restype = C.c_int
         L.lbm_read_macro.argtypes = [vp, dp, dp, dp, dp]
         L.lbm_nusselt.restype = C.c_int
@@ -158,6 +161,16 @@ def residual_fields_noalloc(ux, uy, T, ux_prev, uy_prev, T_prev, solid=None, str
     return r.value
 
 
+def step_kernel_count(storage: str, variant) -> int:
+    v = STEP_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    return int(load().lbm_step_kernel_count(STORAGE[storage], v))
+
+
+def step_kernels(storage: str):
+    """Every (variant, config) pair available for a storage."""
+    return [(v, c) for v in ("scalar", "vec4", "tma") for c in range(step_kernel_count(storage, v))]
+
+
 def lbm_footprint_bytes(params) -> int:
     return int(load().lbm_footprint_bytes(C.byref(params)))
 
@@ -222,10 +235,12 @@ class Lattice:
     def sync(self):
         _check(load().lbm_sync(self._h), self._h)
 
-    def set_step_variant(self, variant):
-        """'auto', 'scalar', 'vec4' or 'tma' (see lbm_set_step_variant)."""
+    def set_step_kernel(self, variant, config: int = 0):
+        """variant 'auto', 'scalar', 'vec4' or 'tma' and a config index (see
+        lbm_set_step_kernel)."""
         v = STEP_VARIANTS[variant] if isinstance(variant, str) else int(variant)
-        _check(load().lbm_set_step_variant(self._h, v), self._h)
+        _check(load().lbm_set_step_kernel(self._h, v, int(config)), self._h)
+        self.kernel = (variant, int(config))
 
     def macro(self):
         """(rho, ux, uy, T), each (ny, nx) float64 on the host."""

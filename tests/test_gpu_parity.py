@@ -140,23 +140,25 @@ def test_step_variants_agree_bitwise(storage, idx):
     case = _cases_small()[idx]
     f0, g0 = lc.random_state(case, seed=21 + idx)
     out = {}
-    for v in ("scalar", "vec4", "tma"):
+    for v in P.step_kernels(storage):
         lat = P.Lattice(case, storage=storage)
-        lat.set_step_variant(v)
+        lat.set_step_kernel(*v)
         lat.set_populations(f0, g0)
         lat.step(5)
         out[v] = lat.populations()
         lat.sync()
-    for v in ("vec4", "tma"):
-        assert np.array_equal(out[v][0], out["scalar"][0]) and np.array_equal(out[v][1], out["scalar"][1]), v
+    ref = out[("scalar", 0)]
+    for v, o in out.items():
+        assert np.array_equal(o[0], ref[0]) and np.array_equal(o[1], ref[1]), v
 
 
 def test_fp64_rejects_vector_variants():
     P = _P()
     lat = P.Lattice(lc.couette(H=4, nx=3), storage="f64")
-    lat.set_step_variant("scalar")
+    lat.set_step_kernel("scalar")
     with pytest.raises(P.LBMError):
-        lat.set_step_variant("tma")
+        lat.set_step_kernel("tma")
+    assert P.step_kernel_count("f64", "tma") == 0 and P.step_kernel_count("f32", "tma") == 5
 
 
 # Accumulated max-norm error after 4000 steps against the FP64 oracle. FP16
