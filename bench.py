@@ -260,7 +260,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "f64"])
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--H", type=int, default=2048)
-    ap.add_argument("--variant", default="auto", choices=["auto", "scalar", "vec4", "tma"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "scalar", "vec4", "vec8", "tma"],
                     help="step kernel variant (lbm_set_step_kernel)")
     ap.add_argument("--config", type=int, default=0, help="shape index of the step variant")
     ap.add_argument("--no-variants", action="store_true")

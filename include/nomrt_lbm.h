@@ -113,11 +113,19 @@ lbm_status lbm_sync(lbm_lattice *h);
  * bits for a given storage. AUTO picks the fastest measured: the four-cell
  * vectorised kernel for FP32/FP16 storage, the scalar kernel for FP64.
  * SCALAR: one cell per thread. VEC4: four cells per thread with 128-bit (FP32)
- * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls. TMA: row
- * segments staged in shared memory by bulk copies in a multi-stage pipeline;
- * its config index selects the shape (cells per thread, threads per CTA,
- * stages). */
-typedef enum { LBM_STEP_AUTO = 0, LBM_STEP_SCALAR = 1, LBM_STEP_VEC4 = 2, LBM_STEP_TMA = 3 } lbm_step_variant;
+ * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls; configs 0-2 ask
+ * for 4, 5 or 6 resident blocks per SM. VEC8 (FP16 only): eight cells per
+ * thread, one 128-bit load per plane, x +- 1 realignment by byte permutes;
+ * configs 0-1 ask for 4 or 3 blocks per SM. TMA: row segments staged in shared
+ * memory by bulk copies in a multi-stage pipeline; its config index selects
+ * the shape (cells per thread, threads per CTA, stages). */
+typedef enum {
+    LBM_STEP_AUTO = 0,
+    LBM_STEP_SCALAR = 1,
+    LBM_STEP_VEC4 = 2,
+    LBM_STEP_TMA = 3,
+    LBM_STEP_VEC8 = 4
+} lbm_step_variant;
 
 /* Number of configs of a variant for a storage (0 if the variant does not
  * exist for it: FP64 has only SCALAR). Host only. */

@@ -3,6 +3,7 @@
 #pragma once
 
 #include "nomrt_kernels.cuh"
+#include "step8.cuh"
 #include "step_tma.cuh"
 
 namespace nomrt {
@@ -101,11 +102,30 @@ cudaError_t launch_step(const KParams &p, int src, cudaStream_t st) {
     if constexpr (Store<S>::kShifted) {
         if (variant == kStepTma) return launch_tma<S>(p, src, st);
         if (variant == kStepVec4) {
-            // four cells per thread, 128 threads per block, one row per block row
+            // four cells per thread, 128 threads per block, one row per block row; the
+            // config asks ptxas for 4, 5 or 6 resident blocks per SM
             const int threads_x = p.pitch / 4;
             const dim3 grid((threads_x + 127) / 128, p.ny < 65535 ? p.ny : 65535);
-            k_step4<S><<<grid, 128, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<float>(p));
+            const Planes<S> pl = make_planes<S>(p, src);
+            const Geom g = make_geom(p);
+            const RatesC<float> r = make_rates<float>(p);
+            if (p.config == 1) k_step4<S, 5><<<grid, 128, 0, st>>>(pl, g, r);
+            else if (p.config == 2) k_step4<S, 6><<<grid, 128, 0, st>>>(pl, g, r);
+            else k_step4<S, 4><<<grid, 128, 0, st>>>(pl, g, r);
             return cudaGetLastError();
+        }
+        if constexpr (sizeof(S) == 2) {
+            if (variant == kStepVec8) {
+                // eight cells per thread (FP16 only)
+                const int threads_x = p.pitch / 8;
+                const dim3 grid((threads_x + 127) / 128, p.ny < 65535 ? p.ny : 65535);
+                const Planes<S> pl = make_planes<S>(p, src);
+                const Geom g = make_geom(p);
+                const RatesC<float> r = make_rates<float>(p);
+                if (p.config == 1) k_step8h<3><<<grid, 128, 0, st>>>(pl, g, r);
+                else k_step8h<4><<<grid, 128, 0, st>>>(pl, g, r);
+                return cudaGetLastError();
+            }
         }
     }
     const dim3 b = step_block();

@@ -24,6 +24,7 @@ constexpr int kStepAuto = 0;
 constexpr int kStepScalar = 1;
 constexpr int kStepVec4 = 2;
 constexpr int kStepTma = 3;
+constexpr int kStepVec8 = 4;
 // Shapes of the TMA step kernel (see launchers.cuh).
 constexpr int kTmaConfigCount = 5;
 

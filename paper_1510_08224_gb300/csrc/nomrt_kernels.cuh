@@ -612,8 +612,8 @@ __device__ __forceinline__ void cell4(const Planes<S> &pl, const Geom &g, const 
 
 // Fused step, four cells of one row per thread. Same arithmetic as k_step;
 // solid cells in a group are written as zeros (they hold zeros already).
-template <typename S>
-__global__ void __launch_bounds__(128, 4) k_step4(const Planes<S> pl, const Geom g, const RatesC<float> r) {
+template <typename S, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const Geom g, const RatesC<float> r) {
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {

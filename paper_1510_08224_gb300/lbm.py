@@ -20,7 +20,7 @@ STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 SIDES = {"left": 0, "right": 1, "bottom": 2, "top": 3}
 
 # Every symbol include/nomrt_lbm.h declares.
-STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3}
+STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3, "vec8": 4}
 EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_step_kernel_count",
             "lbm_set_step_kernel", "lbm_read_macro",
             "lbm_nusselt",
@@ -168,7 +168,7 @@ def step_kernel_count(storage: str, variant) -> int:
 
 def step_kernels(storage: str):
     """Every (variant, config) pair available for a storage."""
-    return [(v, c) for v in ("scalar", "vec4", "tma") for c in range(step_kernel_count(storage, v))]
+    return [(v, c) for v in ("scalar", "vec4", "vec8", "tma") for c in range(step_kernel_count(storage, v))]
 
 
 def lbm_footprint_bytes(params) -> int:
