@@ -110,11 +110,11 @@ lbm_status lbm_step(lbm_lattice *h, int64_t nsteps);
 lbm_status lbm_sync(lbm_lattice *h);
 
 /* Step kernel variants. All compute the same arithmetic and give the same
- * bits for a given storage. AUTO picks the fastest measured: the four-cell
- * vectorised kernel for FP32/FP16 storage, the scalar kernel for FP64.
+ * bits for a given storage. AUTO picks the fastest measured on GB300: VEC4
+ * config 2 for FP32/FP16 storage, the scalar kernel for FP64.
  * SCALAR: one cell per thread. VEC4: four cells per thread with 128-bit (FP32)
- * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls; configs 0-2 ask
- * for 4, 5 or 6 resident blocks per SM. VEC8 (FP16 only): eight cells per
+ * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls; configs 0-4 ask
+ * for 4, 5, 6, 7 or 8 resident blocks per SM. VEC8 (FP16 only): eight cells per
  * thread, one 128-bit load per plane, x +- 1 realignment by byte permutes;
  * configs 0-1 ask for 4 or 3 blocks per SM. TMA: row segments staged in shared
  * memory by bulk copies in a multi-stage pipeline; its config index selects

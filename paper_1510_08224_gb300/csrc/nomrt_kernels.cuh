@@ -61,6 +61,8 @@ struct RatesC {
     C om_a, z_a, om_ze, zv_e, om_zn;  // thermal: 1 - zeta_alpha, zeta_alpha, 1 - zeta_e, zeta_e varpi, 1 - zeta_nu
     C ax, Fy0, g_beta;            // F = (ax, Fy0 + g_beta (T - T_ref))
     C T_ref;
+    C hx;                         // ax / 2
+    C h2e, h2nu, h23eps;          // 2 (1 - s_e/2), 2 (1 - s_nu/2), (2/3)(1 - s_eps/2)
 };
 
 template <typename C>
@@ -86,6 +88,10 @@ inline RatesC<C> make_rates(const KParams &p) {
     r.Fy0 = (C)(p.ay + p.g_beta * (p.T_ref - p.T0));
     r.g_beta = (C)p.g_beta;
     r.T_ref = (C)p.T_ref;
+    r.hx = (C)(0.5 * p.ax);
+    r.h2e = (C)(2.0 * (1.0 - 0.5 * p.s_e));
+    r.h2nu = (C)(2.0 * (1.0 - 0.5 * p.s_nu));
+    r.h23eps = (C)(2.0 / 3.0 * (1.0 - 0.5 * p.s_eps));
     return r;
 }
 
@@ -269,6 +275,178 @@ __device__ __forceinline__ void collide(const RatesC<C> &r, C f[9], C t[5]) {
     t[4] = (c3 - c4) - C(0.5) * q2;
 }
 
+// ------------------------------------------- FP32 collision, explicit rounding
+
+// Correctly rounded FP32 operations on one value (float) or on a pair of
+// values in one packed instruction (float2, the sm_100+ FFMA2/FADD2/FMUL2
+// path). The FP32/FP16 kernels all collide through collide_x, either per cell
+// or per pair of cells, with the same sequence of operations, so every kernel
+// variant produces the same bits.
+template <typename T>
+struct Ops;
+
+template <>
+struct Ops<float> {
+    static __device__ __forceinline__ float bc(float c) { return c; }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fadd_rn(a, -b); }
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+
+template <>
+struct Ops<float2> {
+    static __device__ __forceinline__ float2 bc(float c) { return make_float2(c, c); }
+    static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    // a - b as fma(b, -1, a): one rounding of the exact difference
+    static __device__ __forceinline__ float2 sub(float2 a, float2 b) {
+        return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+    }
+    static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+};
+
+// Same method as collide<float> (Eq. 8 with Eqs. 16, 17, 20; Eq. 24 with
+// Eqs. 28, 29; M and M^-1 of Eqs. 13 and A1 on pair sums), every rounding
+// explicit. T is float (one cell) or float2 (two cells).
+template <typename T>
+__device__ __forceinline__ void collide_x(const RatesC<float> &r, T f[9], T t[5]) {
+    using O = Ops<T>;
+    // D2Q5 forward map (Eq. 26)
+    const T s13 = O::add(t[1], t[3]), s24 = O::add(t[2], t[4]);
+    const T n0 = O::add(O::add(O::add(t[0], t[1]), O::add(t[2], t[3])), t[4]);  // T - T_ref
+    const T n1 = O::sub(t[1], t[3]);
+    const T n2 = O::sub(t[2], t[4]);
+    const T n3 = O::add(s13, s24);
+    const T n4 = O::sub(s13, s24);
+    const T Fx = O::bc(r.ax);
+    const T Fy = O::fma(O::bc(r.g_beta), n0, O::bc(r.Fy0));  // Eq. 4
+    // D2Q9 forward map (Eq. 13)
+    const T a13 = O::add(f[1], f[3]), d13 = O::sub(f[1], f[3]);
+    const T a24 = O::add(f[2], f[4]), d24 = O::sub(f[2], f[4]);
+    const T a57 = O::add(f[5], f[7]), d57 = O::sub(f[5], f[7]);
+    const T a68 = O::add(f[6], f[8]), d68 = O::sub(f[6], f[8]);
+    const T D = O::add(a57, a68);
+    const T A4 = O::add(a13, a24);
+    const T m0 = O::add(O::add(f[0], A4), D);
+    const T m6 = O::add(d57, d68);
+    const T m7 = O::sub(d57, d68);
+    const T jx = O::add(d13, m7);
+    const T jy = O::add(d24, m6);
+    const T m3 = O::add(A4, O::add(D, D));
+    const T m4 = O::sub(a13, a24);
+    const T m5 = O::sub(a57, a68);
+    // Eq. 19 with rho0 = 1
+    const T ux = O::add(jx, O::bc(r.hx));
+    const T uy = O::fma(O::bc(0.5f), Fy, jy);
+    const T uyuy = O::mul(uy, uy);
+    const T uu = O::fma(ux, ux, uyuy);
+    const T uF = O::fma(ux, Fx, O::mul(uy, Fy));
+    // Eq. 8
+    const T p1 = O::add(jx, Fx);
+    const T p2 = O::add(jy, Fy);
+    const T p3 = O::fma(O::bc(r.om_e), m3,
+                        O::fma(O::bc(r.s_e), O::fma(O::bc(2.0f / 3.0f), m0, uu), O::mul(O::bc(r.h2e), uF)));
+    const T dxy = O::fma(ux, ux, O::mul(O::bc(-1.f), uyuy));
+    const T dF = O::fma(ux, Fx, O::mul(O::bc(-1.f), O::mul(uy, Fy)));
+    const T p4 = O::fma(O::bc(r.om_nu), m4, O::fma(O::bc(r.s_nu), dxy, O::mul(O::bc(r.h2nu), dF)));
+    const T cF = O::fma(ux, Fy, O::mul(uy, Fx));
+    const T p5 = O::fma(O::bc(r.om_nu), m5, O::fma(O::bc(r.s_nu), O::mul(ux, uy), O::mul(O::bc(r.h_nu), cF)));
+    const T p6 = O::fma(O::bc(r.om_q), m6, O::mul(O::bc(1.0f / 3.0f), O::fma(O::bc(r.s_q), jy, Fy)));
+    const T p7 = O::fma(O::bc(r.om_q), m7, O::mul(O::bc(1.0f / 3.0f), O::fma(O::bc(r.s_q), jx, Fx)));
+    const T p8 = O::fma(O::bc(r.om_eps), D,
+                        O::fma(O::bc(r.s_eps), O::fma(O::bc(1.0f / 9.0f), m0, O::mul(O::bc(1.0f / 3.0f), uu)),
+                               O::mul(O::bc(r.h23eps), uF)));
+    // back map (Eq. A1); the 1/2 and 1/4 scalings are exact
+    const T A = O::fma(O::bc(0.25f), p3, O::mul(O::bc(-0.5f), p8));
+    const T B = O::mul(O::bc(0.25f), p4);
+    const T h1 = O::mul(O::bc(0.5f), O::sub(p1, p7));
+    const T h2 = O::mul(O::bc(0.5f), O::sub(p2, p6));
+    const T P = O::mul(O::bc(0.25f), O::add(p8, p5));
+    const T Q = O::mul(O::bc(0.25f), O::add(p6, p7));
+    const T R = O::mul(O::bc(0.25f), O::sub(p8, p5));
+    const T Sx = O::mul(O::bc(0.25f), O::sub(p6, p7));
+    const T AB = O::add(A, B), AmB = O::sub(A, B);
+    f[0] = O::add(O::sub(m0, p3), p8);
+    f[1] = O::add(AB, h1);
+    f[3] = O::sub(AB, h1);
+    f[2] = O::add(AmB, h2);
+    f[4] = O::sub(AmB, h2);
+    f[5] = O::add(P, Q);
+    f[7] = O::sub(P, Q);
+    f[6] = O::add(R, Sx);
+    f[8] = O::sub(R, Sx);
+    // D2Q5 relaxation (Eq. 24) and back map (Eq. A2)
+    const T Tm = O::add(O::bc(r.T_ref), n0);
+    const T q1 = O::fma(O::bc(r.om_a), n1, O::mul(O::bc(r.z_a), O::mul(ux, Tm)));
+    const T q2 = O::fma(O::bc(r.om_a), n2, O::mul(O::bc(r.z_a), O::mul(uy, Tm)));
+    const T q3 = O::fma(O::bc(r.om_ze), n3, O::mul(O::bc(r.zv_e), n0));
+    const T q4 = O::mul(O::bc(r.om_zn), n4);
+    const T c3 = O::mul(O::bc(0.25f), q3), c4 = O::mul(O::bc(0.25f), q4);
+    const T c34 = O::add(c3, c4), c3m4 = O::sub(c3, c4);
+    t[0] = O::sub(n0, q3);
+    t[1] = O::fma(O::bc(0.5f), q1, c34);
+    t[3] = O::fma(O::bc(-0.5f), q1, c34);
+    t[2] = O::fma(O::bc(0.5f), q2, c3m4);
+    t[4] = O::fma(O::bc(-0.5f), q2, c3m4);
+}
+
+// Collide cells K and K + 1 of an N-cell group as one float2 pair, in place.
+template <int K, int N>
+__device__ __forceinline__ void collide_pair(const RatesC<float> &r, float f[9][N], float t[5][N]) {
+    float2 fp[9], tp[5];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fp[i] = make_float2(f[i][K], f[i][K + 1]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tp[i] = make_float2(t[i][K], t[i][K + 1]);
+    collide_x<float2>(r, fp, tp);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        f[i][K] = fp[i].x;
+        f[i][K + 1] = fp[i].y;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        t[i][K] = tp[i].x;
+        t[i][K + 1] = tp[i].y;
+    }
+}
+
+// Halfway wall links of cell K of an N-cell group (link-map bytes mN), in place.
+template <typename S, int K, int N>
+__device__ __forceinline__ void wall_links(const Planes<S> &pl, const Geom &g, uint32_t mN, int x0, int r0, int rm,
+                                           int rp, float f[9][N], float t[5][N]) {
+    const unsigned m = (mN >> (8 * K)) & 0xFFu;
+    if (m == 0 || m == kSolid) return;
+    const int x = x0 + K;
+    int xm = x - 1, xp = x + 1;
+    if (g.px) {
+        xm = (xm < 0) ? xm + g.nx : xm;
+        xp = (xp >= g.nx) ? xp - g.nx : xp;
+    }
+    const int sidx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+    const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        if (m & (1u << (i - 1))) {
+            const WallDev *w = g.walls + g.flags[sidx[i]];
+            f[i][K] = Store<S>::ld(pl.src[opp[i]] + r0 + x) + (float)__ldg(&w->cf[i]);
+            if (i < 5)
+                t[i][K] = (float)__ldg(&w->tsgn) * Store<S>::ld(pl.src[9 + opp[i]] + r0 + x) + (float)__ldg(&w->tb);
+        }
+    }
+}
+
+// Solid cell K of a group: write zeros (solid cells hold zeros).
+template <int K, int N>
+__device__ __forceinline__ void zero_solid(uint32_t mN, float f[9][N], float t[5][N]) {
+    if (((mN >> (8 * K)) & 0xFFu) != kSolid) return;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i][K] = 0.f;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) t[i][K] = 0.f;
+}
+
 // ------------------------------------------------------------------ kernels
 
 template <typename S>
@@ -282,7 +460,8 @@ __global__ void __launch_bounds__(256) k_step(const Planes<S> pl, const Geom g, 
         if (m == kSolid) continue;
         C f[9], t[5];
         pull<S>(pl.src, g, x, y, m, f, t);
-        collide<C>(r, f, t);
+        if constexpr (Store<S>::kShifted) collide_x<float>(r, f, t);
+        else collide<C>(r, f, t);
 #pragma unroll
         for (int q = 0; q < 9; ++q) Store<S>::st(pl.dst[q] + off, f[q]);
 #pragma unroll
@@ -564,52 +743,6 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
     }
 }
 
-// Wall links and collision of cell K of a four-cell group, in place in f, t
-// (K is a template parameter so every array index is a constant).
-template <typename S, int K>
-__device__ __forceinline__ void cell4(const Planes<S> &pl, const Geom &g, const RatesC<float> &r, uint32_t m4,
-                                      int x0, int r0, int rm, int rp, float f[9][4], float t[5][4]) {
-    const unsigned m = (m4 >> (8 * K)) & 0xFFu;
-    float fk[9], tk[5];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fk[i] = f[i][K];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) tk[i] = t[i][K];
-    if (m == kSolid) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fk[i] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) tk[i] = 0.f;
-    } else {
-        if (m) {
-            // halfway wall links: bounce the cell's own post-collision population
-            const int x = x0 + K;
-            int xm = x - 1, xp = x + 1;
-            if (g.px) {
-                xm = (xm < 0) ? xm + g.nx : xm;
-                xp = (xp >= g.nx) ? xp - g.nx : xp;
-            }
-            const int sidx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
-            const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-#pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                if (m & (1u << (i - 1))) {
-                    const WallDev *w = g.walls + g.flags[sidx[i]];
-                    fk[i] = Store<S>::ld(pl.src[opp[i]] + r0 + x) + (float)__ldg(&w->cf[i]);
-                    if (i < 5)
-                        tk[i] = (float)__ldg(&w->tsgn) * Store<S>::ld(pl.src[9 + opp[i]] + r0 + x) +
-                                (float)__ldg(&w->tb);
-                }
-            }
-        }
-        collide<float>(r, fk, tk);
-    }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i][K] = fk[i];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) t[i][K] = tk[i];
-}
-
 // Fused step, four cells of one row per thread. Same arithmetic as k_step;
 // solid cells in a group are written as zeros (they hold zeros already).
 template <typename S, int MINB>
@@ -646,10 +779,20 @@ __global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const G
         ld_plane<S, -1>(pl.src[12] + r0, g, x0, lane, inrow, t[3]);
         ld_plane<S, 0>(pl.src[13] + rp, g, x0, lane, inrow, t[4]);
         if (!any) continue;
-        cell4<S, 0>(pl, g, r, m4, x0, r0, rm, rp, f, t);
-        cell4<S, 1>(pl, g, r, m4, x0, r0, rm, rp, f, t);
-        cell4<S, 2>(pl, g, r, m4, x0, r0, rm, rp, f, t);
-        cell4<S, 3>(pl, g, r, m4, x0, r0, rm, rp, f, t);
+        if (m4 != 0u) {
+            wall_links<S, 0, 4>(pl, g, m4, x0, r0, rm, rp, f, t);
+            wall_links<S, 1, 4>(pl, g, m4, x0, r0, rm, rp, f, t);
+            wall_links<S, 2, 4>(pl, g, m4, x0, r0, rm, rp, f, t);
+            wall_links<S, 3, 4>(pl, g, m4, x0, r0, rm, rp, f, t);
+        }
+        collide_pair<0, 4>(r, f, t);
+        collide_pair<2, 4>(r, f, t);
+        if (m4 != 0u) {
+            zero_solid<0, 4>(m4, f, t);
+            zero_solid<1, 4>(m4, f, t);
+            zero_solid<2, 4>(m4, f, t);
+            zero_solid<3, 4>(m4, f, t);
+        }
 #pragma unroll
         for (int i = 0; i < 9; ++i) Vec4<S>::st(pl.dst[i] + r0 + x0, f[i]);
 #pragma unroll

@@ -76,36 +76,26 @@ __device__ __forceinline__ void ld_plane8(const __half *row, const Geom &g, int 
     realign8<DX>(row, g, x0, lane, inrow, w);
 }
 
-// Wall links and collision of one cell with link-map byte m at column x.
-__device__ __forceinline__ void cell8(const Planes<__half> &pl, const Geom &g, const RatesC<float> &r, unsigned m,
-                                      int x, int r0, int rm, int rp, float f[9], float t[5]) {
-    if (m == kSolid) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) t[i] = 0.f;
-        return;
+// Halfway wall links of one cell with link-map byte m at column x, in place.
+__device__ __forceinline__ void links8(const Planes<__half> &pl, const Geom &g, unsigned m, int x, int r0, int rm,
+                                       int rp, float f[9], float t[5]) {
+    if (m == 0 || m == kSolid) return;
+    int xm = x - 1, xp = x + 1;
+    if (g.px) {
+        xm = (xm < 0) ? xm + g.nx : xm;
+        xp = (xp >= g.nx) ? xp - g.nx : xp;
     }
-    if (m) {
-        int xm = x - 1, xp = x + 1;
-        if (g.px) {
-            xm = (xm < 0) ? xm + g.nx : xm;
-            xp = (xp >= g.nx) ? xp - g.nx : xp;
-        }
-        const int sidx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
-        const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
+    const int sidx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
+    const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
 #pragma unroll
-        for (int i = 1; i < 9; ++i) {
-            if (m & (1u << (i - 1))) {
-                const WallDev *wd = g.walls + g.flags[sidx[i]];
-                f[i] = Store<__half>::ld(pl.src[opp[i]] + r0 + x) + (float)__ldg(&wd->cf[i]);
-                if (i < 5)
-                    t[i] = (float)__ldg(&wd->tsgn) * Store<__half>::ld(pl.src[9 + opp[i]] + r0 + x) +
-                           (float)__ldg(&wd->tb);
-            }
+    for (int i = 1; i < 9; ++i) {
+        if (m & (1u << (i - 1))) {
+            const WallDev *wd = g.walls + g.flags[sidx[i]];
+            f[i] = Store<__half>::ld(pl.src[opp[i]] + r0 + x) + (float)__ldg(&wd->cf[i]);
+            if (i < 5)
+                t[i] = (float)__ldg(&wd->tsgn) * Store<__half>::ld(pl.src[9 + opp[i]] + r0 + x) + (float)__ldg(&wd->tb);
         }
     }
-    collide<float>(r, f, t);
 }
 
 // The cell pair (2Q, 2Q+1): unpack word Q of every plane, collide, pack back.
@@ -129,8 +119,24 @@ __device__ __forceinline__ void pair8(const Planes<__half> &pl, const Geom &g, c
     const uint32_t mword = Q < 2 ? mlo : mhi;
     const unsigned ma = (mword >> (16 * (Q & 1))) & 0xFFu;
     const unsigned mb = (mword >> (16 * (Q & 1) + 8)) & 0xFFu;
-    cell8(pl, g, r, ma, x0 + 2 * Q, r0, rm, rp, fa, ta);
-    cell8(pl, g, r, mb, x0 + 2 * Q + 1, r0, rm, rp, fb, tb);
+    links8(pl, g, ma, x0 + 2 * Q, r0, rm, rp, fa, ta);
+    links8(pl, g, mb, x0 + 2 * Q + 1, r0, rm, rp, fb, tb);
+    float2 fp[9], tp[5];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fp[i] = make_float2(fa[i], fb[i]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) tp[i] = make_float2(ta[i], tb[i]);
+    collide_x<float2>(r, fp, tp);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        fa[i] = ma == kSolid ? 0.f : fp[i].x;
+        fb[i] = mb == kSolid ? 0.f : fp[i].y;
+    }
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        ta[i] = ma == kSolid ? 0.f : tp[i].x;
+        tb[i] = mb == kSolid ? 0.f : tp[i].y;
+    }
 #pragma unroll
     for (int i = 0; i < kQ; ++i) {
         const __half2 h = i < 9 ? __floats2half2_rn(fa[i], fb[i]) : __floats2half2_rn(ta[i - 9], tb[i - 9]);

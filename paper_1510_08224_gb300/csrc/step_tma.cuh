@@ -206,65 +206,43 @@ __device__ __forceinline__ void sm_plane(const S *sm, const S *grow, const Geom 
     }
 }
 
-// Wall links and collision of cell K of an N-cell group, in place.
-template <typename S, int K, int N>
-__device__ __forceinline__ void cellN(const Planes<S> &pl, const Geom &g, const RatesC<float> &r, uint32_t mN,
-                                      int x0, int r0, int rm, int rp, float f[9][N], float t[5][N]) {
-    const unsigned m = (mN >> (8 * K)) & 0xFFu;
-    float fk[9], tk[5];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fk[i] = f[i][K];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) tk[i] = t[i][K];
-    if (m == kSolid) {
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fk[i] = 0.f;
-#pragma unroll
-        for (int i = 0; i < 5; ++i) tk[i] = 0.f;
-    } else {
-        if (m) {
-            const int x = x0 + K;
-            int xm = x - 1, xp = x + 1;
-            if (g.px) {
-                xm = (xm < 0) ? xm + g.nx : xm;
-                xp = (xp >= g.nx) ? xp - g.nx : xp;
-            }
-            const int sidx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
-            const int opp[9] = {0, 3, 4, 1, 2, 7, 8, 5, 6};
-#pragma unroll
-            for (int i = 1; i < 9; ++i) {
-                if (m & (1u << (i - 1))) {
-                    const WallDev *w = g.walls + g.flags[sidx[i]];
-                    fk[i] = Store<S>::ld(pl.src[opp[i]] + r0 + x) + (float)__ldg(&w->cf[i]);
-                    if (i < 5)
-                        tk[i] = (float)__ldg(&w->tsgn) * Store<S>::ld(pl.src[9 + opp[i]] + r0 + x) +
-                                (float)__ldg(&w->tb);
-                }
-            }
-        }
-        collide<float>(r, fk, tk);
-    }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i][K] = fk[i];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) t[i][K] = tk[i];
-}
-
-template <typename S, int N, int K>
-struct CellLoop {
-    static __device__ __forceinline__ void run(const Planes<S> &pl, const Geom &g, const RatesC<float> &r,
-                                               uint32_t mN, int x0, int r0, int rm, int rp, float f[9][N],
-                                               float t[5][N]) {
-        cellN<S, K, N>(pl, g, r, mN, x0, r0, rm, rp, f, t);
-        CellLoop<S, N, K + 1>::run(pl, g, r, mN, x0, r0, rm, rp, f, t);
-    }
-};
-
+// Wall links, collision and solid zeroing of an N-cell group: pairs of cells
+// collide as float2, a single cell as float.
 template <typename S, int N>
-struct CellLoop<S, N, N> {
-    static __device__ __forceinline__ void run(const Planes<S> &, const Geom &, const RatesC<float> &, uint32_t, int,
-                                               int, int, int, float[9][N], float[5][N]) {}
-};
+__device__ __forceinline__ void cells_N(const Planes<S> &pl, const Geom &g, const RatesC<float> &r, uint32_t mN,
+                                        int x0, int r0, int rm, int rp, float f[9][N], float t[5][N]) {
+    if (mN != 0u) {
+        wall_links<S, 0, N>(pl, g, mN, x0, r0, rm, rp, f, t);
+        if constexpr (N >= 2) wall_links<S, 1, N>(pl, g, mN, x0, r0, rm, rp, f, t);
+        if constexpr (N >= 4) {
+            wall_links<S, 2, N>(pl, g, mN, x0, r0, rm, rp, f, t);
+            wall_links<S, 3, N>(pl, g, mN, x0, r0, rm, rp, f, t);
+        }
+    }
+    if constexpr (N == 1) {
+        float fk[9], tk[5];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fk[i] = f[i][0];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) tk[i] = t[i][0];
+        collide_x<float>(r, fk, tk);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i][0] = fk[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) t[i][0] = tk[i];
+    } else {
+        collide_pair<0, N>(r, f, t);
+        if constexpr (N >= 4) collide_pair<2, N>(r, f, t);
+    }
+    if (mN != 0u) {
+        zero_solid<0, N>(mN, f, t);
+        if constexpr (N >= 2) zero_solid<1, N>(mN, f, t);
+        if constexpr (N >= 4) {
+            zero_solid<2, N>(mN, f, t);
+            zero_solid<3, N>(mN, f, t);
+        }
+    }
+}
 
 // Shape of a TMA step kernel: N cells per thread, T threads per CTA (a unit of
 // W = N * T cells), STAGES pipeline stages, MINB CTAs per SM asked of ptxas.
@@ -336,7 +314,7 @@ __global__ void __launch_bounds__(T, MINB) k_step_tma(const Planes<S> pl, const 
             sm_plane<S, -1, N>(st + 12 * ROW, pl.src[12] + r0, g, j0, x0, lane, t[3]);
             sm_plane<S, 0, N>(st + 13 * ROW, pl.src[13] + rp, g, j0, x0, lane, t[4]);
             if (any) {
-                CellLoop<S, N, 0>::run(pl, g, r, mN, x0, r0, rm, rp, f, t);
+                cells_N<S, N>(pl, g, r, mN, x0, r0, rm, rp, f, t);
 #pragma unroll
                 for (int q = 0; q < 9; ++q) VecN<S, N>::st(pl.dst[q] + r0 + x0, f[q]);
 #pragma unroll
