@@ -111,7 +111,7 @@ lbm_status lbm_sync(lbm_lattice *h);
 
 /* Step kernel variants. All compute the same arithmetic and give the same
  * bits for a given storage. AUTO picks the fastest measured on GB300: VEC4
- * config 2 for FP32/FP16 storage, the scalar kernel for FP64.
+ * config 1 for FP32, VEC4 config 3 for FP16, the scalar kernel for FP64.
  * SCALAR: one cell per thread. VEC4: four cells per thread with 128-bit (FP32)
  * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls; configs 0-4 ask
  * for 4, 5, 6, 7 or 8 resident blocks per SM. VEC8 (FP16 only): eight cells per

@@ -98,11 +98,11 @@ cudaError_t launch_step(const KParams &p, int src, cudaStream_t st) {
     int variant = p.variant;
     KParams q = p;
     if constexpr (Store<S>::kShifted) {
-        // fastest measured on GB300 for both FP32 and FP16 storage: four cells per
-        // thread with six resident blocks per SM
+        // fastest measured on GB300 (4096 x 2048 cells): four cells per thread with
+        // five (FP32) or seven (FP16) resident blocks per SM
         if (variant == kStepAuto) {
             variant = kStepVec4;
-            q.config = 2;
+            q.config = sizeof(S) == 4 ? 1 : 3;
         }
     } else {
         variant = kStepScalar;
