@@ -191,6 +191,63 @@ lbm_status lbm_residual_fields_noalloc(const double *ux, const double *uy, const
                                        const double *uy_prev, const double *T_prev, const uint8_t *solid,
                                        int64_t n, void *cuda_stream, double *r);
 
+/* ---------------------------------------------------------------- batches --
+ * Many lattices of uneven size advanced together: one kernel launch steps
+ * every member (warp-sized work units of one lattice row segment each, read
+ * from a device work list with a per-lattice descriptor). The method is the
+ * same as lbm_step's and a batched lattice produces the same bits as when
+ * stepped alone. Members must be FP32 or FP16 storage (one storage per batch)
+ * and bound to the batch's stream; while batched, lbm_step on a member is
+ * rejected, but every other lattice call (read-outs, Nusselt, residual,
+ * populations) works and sees the batch's progress. The batch allocates its
+ * own small device buffers (descriptors, work list) with cudaMalloc. */
+typedef struct lbm_batch lbm_batch;
+
+/* cuda_stream: the stream every member uses (NULL = legacy default stream). */
+lbm_status lbm_batch_create(void *cuda_stream, lbm_batch **out);
+
+/* Add / remove a member. Membership changes take effect at the next step;
+ * lattices may join and leave between any two steps. lbm_destroy of a member
+ * removes it first. */
+lbm_status lbm_batch_add(lbm_batch *b, lbm_lattice *h);
+lbm_status lbm_batch_remove(lbm_batch *b, lbm_lattice *h);
+
+/* Execution mode. steps_per_launch = 1: one launch per step. k > 1: one
+ * cooperative persistent launch per k steps, with a clock-bounded grid
+ * barrier between steps (LBM_ETIMEOUT from lbm_batch_sync if it expires).
+ * graph_steps > 0 (even): steps are replayed from a captured CUDA graph of
+ * that many steps; 0 disables graphs. Defaults: 1 and 32. */
+lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t graph_steps);
+
+/* Kernel shape: config 0..4 asks for 4..8 resident 128-thread blocks per SM;
+ * -1 restores the default (1 for FP32, 3 for FP16). */
+lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config);
+
+/* Autotuner: times trial_launches launches of each config on the current
+ * members (each trial recomputes the current step into the other buffer, so
+ * the state is unchanged), selects the fastest, and returns it in
+ * *best_config and the mean ms per launch of each config in ms_per_launch[5]
+ * (either may be NULL). Synchronises. */
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_config, float *ms_per_launch);
+
+/* Advance every member by nsteps (asynchronous on the batch's stream). */
+lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
+
+/* Wait for the batch's stream; LBM_ETIMEOUT if a persistent launch gave up a
+ * grid barrier (the members' state is then undefined). */
+lbm_status lbm_batch_sync(lbm_batch *b);
+
+/* Members, their fluid cells, work units, active config, batch steps taken.
+ * Any pointer may be NULL. */
+lbm_status lbm_batch_info(const lbm_batch *b, int32_t *members, int64_t *cells, int32_t *units, int32_t *config,
+                          int64_t *steps_done);
+
+/* Last error of b (never NULL); with b == NULL, the thread's last error. */
+const char *lbm_batch_last_error(const lbm_batch *b);
+
+/* Free the batch; its members stay valid and become unbatched. */
+void lbm_batch_destroy(lbm_batch *b);
+
 /* Last error message of h (never NULL); with h == NULL, the calling thread's
  * last lbm_create / lbm_footprint_bytes / lbm_residual_fields_noalloc error. */
 const char *lbm_last_error(const lbm_lattice *h);

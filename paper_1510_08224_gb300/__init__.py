@@ -5,8 +5,8 @@ arXiv:1510.08224).
 The hot path is one fused CUDA kernel per time step (sm_103a) behind the C ABI
 of ``include/nomrt_lbm.h``; :mod:`.lbm` is its ctypes binding.
 """
-from .lbm import (EXPORTED, LBMError, Lattice, STORAGE, STORAGE_BYTES, SIDES, STEP_VARIANTS, load, make_params,
+from .lbm import (EXPORTED, Batch, LBMError, Lattice, STORAGE, STORAGE_BYTES, SIDES, STEP_VARIANTS, load, make_params,
                   lbm_footprint_bytes, library_path, residual_fields_noalloc, step_kernel_count, step_kernels)
 
-__all__ = ["EXPORTED", "LBMError", "Lattice", "STORAGE", "STORAGE_BYTES", "SIDES", "STEP_VARIANTS", "load", "make_params",
+__all__ = ["EXPORTED", "Batch", "LBMError", "Lattice", "STORAGE", "STORAGE_BYTES", "SIDES", "STEP_VARIANTS", "load", "make_params",
            "lbm_footprint_bytes", "library_path"]

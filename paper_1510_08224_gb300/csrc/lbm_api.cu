@@ -12,10 +12,12 @@
 #include <string>
 #include <vector>
 
+#include "lattice_impl.h"
 #include "nomrt_internal.h"
 #include "nomrt_lbm.h"
 
 using nomrt::KParams;
+using nomrt::Layout;
 using nomrt::kQ;
 using nomrt::kSolid;
 using nomrt::WallDev;
@@ -35,18 +37,6 @@ const double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 size_t elem_bytes(int storage) { return storage == LBM_F64 ? 8 : storage == LBM_F32_SHIFTED ? 4 : 2; }
-
-// Device layout of one lattice, all offsets from the block base.
-struct Layout {
-    int pitch = 0;
-    size_t plane = 0;           // elements per plane
-    size_t pop_bytes = 0;       // one buffer
-    size_t off_pop[2] = {0, 0};
-    size_t off_mask = 0, off_flags = 0, off_walls = 0, off_snap = 0, off_stage = 0, off_part = 0, off_res = 0,
-           off_status = 0;
-    int stage_rows = 0;
-    size_t total = 0;
-};
 
 Layout make_layout(int nx, int ny, int storage, int n_walls) {
     Layout L;
@@ -157,26 +147,7 @@ const nomrt::Launchers &launchers_for(int storage) {
 
 void nomrt::set_thread_error(const char *msg) { g_create_error = msg; }
 
-struct lbm_lattice {
-    int nx = 0, ny = 0, px = 0, py = 0, storage = 0, n_walls = 0;
-    cudaStream_t stream = nullptr;
-    char *mem = nullptr;
-    bool owns_mem = false;
-    Layout lay;
-    KParams kp;
-    int cur = 0;
-    int have_snap = 0;
-    int64_t fluid = 0;
-    int64_t steps = 0;
-    std::vector<uint8_t> flags;
-    std::string err;
-    const nomrt::Launchers *L = nullptr;
 
-    double *stage() const { return reinterpret_cast<double *>(mem + lay.off_stage); }
-    double *partials() const { return reinterpret_cast<double *>(mem + lay.off_part); }
-    double *result() const { return reinterpret_cast<double *>(mem + lay.off_res); }
-    double *snap() const { return reinterpret_cast<double *>(mem + lay.off_snap); }
-};
 
 namespace {
 
@@ -373,6 +344,7 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
 lbm_status lbm_step(lbm_lattice *h, int64_t nsteps) {
     if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
     if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
+    if (h->batch) return fail(h, LBM_EINVAL, "lattice belongs to a batch: step it with lbm_batch_step");
     for (int64_t s = 0; s < nsteps; ++s) {
         cudaError_t e = h->L->step(h->kp, h->cur, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
@@ -546,6 +518,7 @@ const char *lbm_last_error(const lbm_lattice *h) {
 
 void lbm_destroy(lbm_lattice *h) {
     if (!h) return;
+    if (h->batch) nomrt::batch_detach(h->batch, h);
     if (h->owns_mem && h->mem) {
         cudaStreamSynchronize(h->stream);
         cudaFree(h->mem);

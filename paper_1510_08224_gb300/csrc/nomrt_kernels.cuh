@@ -51,6 +51,37 @@ struct Store<__half> {
     static __device__ __forceinline__ void st(__half *p, C v) { *p = __float2half_rn(v); }
 };
 
+// Population loads of a step. NC = true: the read-only data path (the
+// source buffer is never written by the same launch). NC = false: L2-coherent
+// loads (ld.global.cg) for kernels that run several steps in one launch and
+// so read data the same launch wrote.
+template <typename S, bool NC>
+struct Ld;
+
+template <bool NC>
+struct Ld<float, NC> {
+    static __device__ __forceinline__ float one(const float *p) { return NC ? __ldg(p) : __ldcg(p); }
+    static __device__ __forceinline__ void four(const float *p, float a[4]) {
+        const float4 v = NC ? __ldg(reinterpret_cast<const float4 *>(p)) : __ldcg(reinterpret_cast<const float4 *>(p));
+        a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
+    }
+};
+
+template <bool NC>
+struct Ld<__half, NC> {
+    static __device__ __forceinline__ float one(const __half *p) {
+        return __half2float(NC ? __ldg(p) : __ldcg(p));
+    }
+    static __device__ __forceinline__ void four(const __half *p, float a[4]) {
+        const uint2 v = NC ? __ldg(reinterpret_cast<const uint2 *>(p)) : __ldcg(reinterpret_cast<const uint2 *>(p));
+        __half2 h0, h1;
+        memcpy(&h0, &v.x, 4);
+        memcpy(&h1, &v.y, 4);
+        const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
+        a[0] = f0.x; a[1] = f0.y; a[2] = f1.x; a[3] = f1.y;
+    }
+};
+
 // Rates and constants in the compute type, precomputed once per launch on the
 // host side of the launcher.
 template <typename C>
@@ -100,6 +131,19 @@ template <typename S>
 struct Planes {
     const S *src[kQ];
     S *dst[kQ];
+    __device__ __forceinline__ const S *src_at(int q) const { return src[q]; }
+    __device__ __forceinline__ S *dst_at(int q) const { return dst[q]; }
+};
+
+// Plane pointers computed from two buffer bases and the plane stride (used where
+// a kernel serves many lattices and cannot hold 28 pointers per lattice).
+template <typename S>
+struct StridedPlanes {
+    const S *src;
+    S *dst;
+    long long plane;
+    __device__ __forceinline__ const S *src_at(int q) const { return src + (long long)q * plane; }
+    __device__ __forceinline__ S *dst_at(int q) const { return dst + (long long)q * plane; }
 };
 
 template <typename S>
@@ -413,8 +457,8 @@ __device__ __forceinline__ void collide_pair(const RatesC<float> &r, float f[9][
 }
 
 // Halfway wall links of cell K of an N-cell group (link-map bytes mN), in place.
-template <typename S, int K, int N>
-__device__ __forceinline__ void wall_links(const Planes<S> &pl, const Geom &g, uint32_t mN, int x0, int r0, int rm,
+template <typename S, int K, int N, typename PA, bool NC = true>
+__device__ __forceinline__ void wall_links(const PA &pl, const Geom &g, uint32_t mN, int x0, int r0, int rm,
                                            int rp, float f[9][N], float t[5][N]) {
     const unsigned m = (mN >> (8 * K)) & 0xFFu;
     if (m == 0 || m == kSolid) return;
@@ -430,9 +474,9 @@ __device__ __forceinline__ void wall_links(const Planes<S> &pl, const Geom &g, u
     for (int i = 1; i < 9; ++i) {
         if (m & (1u << (i - 1))) {
             const WallDev *w = g.walls + g.flags[sidx[i]];
-            f[i][K] = Store<S>::ld(pl.src[opp[i]] + r0 + x) + (float)__ldg(&w->cf[i]);
+            f[i][K] = Ld<S, NC>::one(pl.src_at(opp[i]) + r0 + x) + (float)__ldg(&w->cf[i]);
             if (i < 5)
-                t[i][K] = (float)__ldg(&w->tsgn) * Store<S>::ld(pl.src[9 + opp[i]] + r0 + x) + (float)__ldg(&w->tb);
+                t[i][K] = (float)__ldg(&w->tsgn) * Ld<S, NC>::one(pl.src_at(9 + opp[i]) + r0 + x) + (float)__ldg(&w->tb);
         }
     }
 }
@@ -709,10 +753,10 @@ constexpr unsigned kFull = 0xffffffffu;
 // nx - 1, x = nx - 1 pulling from 0) is loaded directly too. Every lane of the
 // warp must call this (shuffles). `inrow` (x0 < pitch) gates the loads, not the
 // lane's own fluid cells: a lane of solid cells still supplies its neighbours.
-template <typename S, int DX>
+template <typename S, int DX, bool NC = true>
 __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, int lane, bool inrow, float out[4]) {
     float a[4] = {0.f, 0.f, 0.f, 0.f};
-    if (inrow) Vec4<S>::ld(row + x0, a);
+    if (inrow) Ld<S, NC>::four(row + x0, a);
     if (DX == 0) {
         out[0] = a[0]; out[1] = a[1]; out[2] = a[2]; out[3] = a[3];
     } else if (DX == 1) {
@@ -721,7 +765,7 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
             left = 0.f;
             int xs = x0 - 1;
             if (xs < 0 && g.px) xs += g.nx;
-            if (inrow && xs >= 0) left = Store<S>::ld(row + xs);
+            if (inrow && xs >= 0) left = Ld<S, NC>::one(row + xs);
         }
         out[0] = left; out[1] = a[0]; out[2] = a[1]; out[3] = a[2];
     } else {
@@ -729,13 +773,13 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
         if (lane == 31) {
             right = 0.f;
             const int xs = x0 + 4;
-            if (inrow && xs < g.nx) right = Store<S>::ld(row + xs);
+            if (inrow && xs < g.nx) right = Ld<S, NC>::one(row + xs);
         }
         out[0] = a[1]; out[1] = a[2]; out[2] = a[3]; out[3] = right;
         if (g.px && inrow) {
             const int k = g.nx - 1 - x0;
             if (k >= 0 && k < 4) {
-                const float v = Store<S>::ld(row);
+                const float v = Ld<S, NC>::one(row);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) out[j] = (j == k) ? v : out[j];  // constant indices only
             }
@@ -745,59 +789,65 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
 
 // Fused step, four cells of one row per thread. Same arithmetic as k_step;
 // solid cells in a group are written as zeros (they hold zeros already).
+// One warp's share of a row: cells x0..x0+3 of row y for each lane (x0 = base +
+// 4 lane). Every lane of the warp calls it with the same y. PA gives the plane
+// pointers (Planes or StridedPlanes).
+template <typename S, typename PA, bool NC = true>
+__device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<float> &r, int x0, int y, int lane) {
+    const int r0 = y * g.pitch;
+    const bool inrow = x0 < g.pitch;
+    uint32_t m4 = 0xFFFFFFFFu;
+    if (inrow) m4 = __ldg(reinterpret_cast<const uint32_t *>(g.mask + r0 + x0));
+    const bool any = m4 != 0xFFFFFFFFu;
+    if (!__any_sync(kFull, any)) return;
+    int ym = y - 1, yp = y + 1;
+    if (g.py) {
+        ym = (ym < 0) ? ym + g.ny : ym;
+        yp = (yp >= g.ny) ? yp - g.ny : yp;
+    }
+    // rows of a non-periodic edge hold no fluid cell, so a warp that gets here has 0 < y < ny - 1
+    const int rm = ym * g.pitch, rp = yp * g.pitch;
+    float f[9][4], t[5][4];
+    ld_plane<S, 0, NC>(pl.src_at(0) + r0, g, x0, lane, inrow, f[0]);
+    ld_plane<S, 1, NC>(pl.src_at(1) + r0, g, x0, lane, inrow, f[1]);
+    ld_plane<S, 0, NC>(pl.src_at(2) + rm, g, x0, lane, inrow, f[2]);
+    ld_plane<S, -1, NC>(pl.src_at(3) + r0, g, x0, lane, inrow, f[3]);
+    ld_plane<S, 0, NC>(pl.src_at(4) + rp, g, x0, lane, inrow, f[4]);
+    ld_plane<S, 1, NC>(pl.src_at(5) + rm, g, x0, lane, inrow, f[5]);
+    ld_plane<S, -1, NC>(pl.src_at(6) + rm, g, x0, lane, inrow, f[6]);
+    ld_plane<S, -1, NC>(pl.src_at(7) + rp, g, x0, lane, inrow, f[7]);
+    ld_plane<S, 1, NC>(pl.src_at(8) + rp, g, x0, lane, inrow, f[8]);
+    ld_plane<S, 0, NC>(pl.src_at(9) + r0, g, x0, lane, inrow, t[0]);
+    ld_plane<S, 1, NC>(pl.src_at(10) + r0, g, x0, lane, inrow, t[1]);
+    ld_plane<S, 0, NC>(pl.src_at(11) + rm, g, x0, lane, inrow, t[2]);
+    ld_plane<S, -1, NC>(pl.src_at(12) + r0, g, x0, lane, inrow, t[3]);
+    ld_plane<S, 0, NC>(pl.src_at(13) + rp, g, x0, lane, inrow, t[4]);
+    if (!any) return;
+    if (m4 != 0u) {
+        wall_links<S, 0, 4, PA, NC>(pl, g, m4, x0, r0, rm, rp, f, t);
+        wall_links<S, 1, 4, PA, NC>(pl, g, m4, x0, r0, rm, rp, f, t);
+        wall_links<S, 2, 4, PA, NC>(pl, g, m4, x0, r0, rm, rp, f, t);
+        wall_links<S, 3, 4, PA, NC>(pl, g, m4, x0, r0, rm, rp, f, t);
+    }
+    collide_pair<0, 4>(r, f, t);
+    collide_pair<2, 4>(r, f, t);
+    if (m4 != 0u) {
+        zero_solid<0, 4>(m4, f, t);
+        zero_solid<1, 4>(m4, f, t);
+        zero_solid<2, 4>(m4, f, t);
+        zero_solid<3, 4>(m4, f, t);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) Vec4<S>::st(pl.dst_at(i) + r0 + x0, f[i]);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Vec4<S>::st(pl.dst_at(9 + i) + r0 + x0, t[i]);
+}
+
 template <typename S, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const Geom g, const RatesC<float> r) {
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {
-        const int r0 = y * g.pitch;
-        const bool inrow = x0 < g.pitch;
-        uint32_t m4 = 0xFFFFFFFFu;
-        if (inrow) m4 = __ldg(reinterpret_cast<const uint32_t *>(g.mask + r0 + x0));
-        const bool any = m4 != 0xFFFFFFFFu;
-        if (!__any_sync(kFull, any)) continue;
-        int ym = y - 1, yp = y + 1;
-        if (g.py) {
-            ym = (ym < 0) ? ym + g.ny : ym;
-            yp = (yp >= g.ny) ? yp - g.ny : yp;
-        }
-        // rows of a non-periodic edge hold no fluid cell, so a warp that gets here has 0 < y < ny - 1
-        const int rm = ym * g.pitch, rp = yp * g.pitch;
-        float f[9][4], t[5][4];
-        ld_plane<S, 0>(pl.src[0] + r0, g, x0, lane, inrow, f[0]);
-        ld_plane<S, 1>(pl.src[1] + r0, g, x0, lane, inrow, f[1]);
-        ld_plane<S, 0>(pl.src[2] + rm, g, x0, lane, inrow, f[2]);
-        ld_plane<S, -1>(pl.src[3] + r0, g, x0, lane, inrow, f[3]);
-        ld_plane<S, 0>(pl.src[4] + rp, g, x0, lane, inrow, f[4]);
-        ld_plane<S, 1>(pl.src[5] + rm, g, x0, lane, inrow, f[5]);
-        ld_plane<S, -1>(pl.src[6] + rm, g, x0, lane, inrow, f[6]);
-        ld_plane<S, -1>(pl.src[7] + rp, g, x0, lane, inrow, f[7]);
-        ld_plane<S, 1>(pl.src[8] + rp, g, x0, lane, inrow, f[8]);
-        ld_plane<S, 0>(pl.src[9] + r0, g, x0, lane, inrow, t[0]);
-        ld_plane<S, 1>(pl.src[10] + r0, g, x0, lane, inrow, t[1]);
-        ld_plane<S, 0>(pl.src[11] + rm, g, x0, lane, inrow, t[2]);
-        ld_plane<S, -1>(pl.src[12] + r0, g, x0, lane, inrow, t[3]);
-        ld_plane<S, 0>(pl.src[13] + rp, g, x0, lane, inrow, t[4]);
-        if (!any) continue;
-        if (m4 != 0u) {
-            wall_links<S, 0, 4>(pl, g, m4, x0, r0, rm, rp, f, t);
-            wall_links<S, 1, 4>(pl, g, m4, x0, r0, rm, rp, f, t);
-            wall_links<S, 2, 4>(pl, g, m4, x0, r0, rm, rp, f, t);
-            wall_links<S, 3, 4>(pl, g, m4, x0, r0, rm, rp, f, t);
-        }
-        collide_pair<0, 4>(r, f, t);
-        collide_pair<2, 4>(r, f, t);
-        if (m4 != 0u) {
-            zero_solid<0, 4>(m4, f, t);
-            zero_solid<1, 4>(m4, f, t);
-            zero_solid<2, 4>(m4, f, t);
-            zero_solid<3, 4>(m4, f, t);
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) Vec4<S>::st(pl.dst[i] + r0 + x0, f[i]);
-#pragma unroll
-        for (int i = 0; i < 5; ++i) Vec4<S>::st(pl.dst[9 + i] + r0 + x0, t[i]);
-    }
+    for (int y = blockIdx.y; y < g.ny; y += gridDim.y) row4<S>(pl, g, r, x0, y, lane);
 }
 
 }  // namespace nomrt

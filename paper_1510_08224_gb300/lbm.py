@@ -25,7 +25,9 @@ EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_st
             "lbm_set_step_kernel", "lbm_read_macro",
             "lbm_nusselt",
             "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
-            "lbm_destroy", "lbm_residual_fields_noalloc")
+            "lbm_destroy", "lbm_residual_fields_noalloc", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
+            "lbm_batch_set_mode", "lbm_batch_set_config", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
+            "lbm_batch_info", "lbm_batch_last_error", "lbm_batch_destroy")
 
 
 class LBMError(RuntimeError):
@@ -97,6 +99,19 @@ def load():
         L.lbm_last_error.argtypes = [vp]
         L.lbm_destroy.restype = None
         L.lbm_destroy.argtypes = [vp]
+        for name, args in (("lbm_batch_create", [vp, C.POINTER(vp)]), ("lbm_batch_add", [vp, vp]),
+                           ("lbm_batch_remove", [vp, vp]), ("lbm_batch_set_mode", [vp, C.c_int32, C.c_int32]),
+                           ("lbm_batch_set_config", [vp, C.c_int32]),
+                           ("lbm_batch_tune", [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+                           ("lbm_batch_step", [vp, C.c_int64]), ("lbm_batch_sync", [vp]),
+                           ("lbm_batch_info", [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                               C.POINTER(C.c_int32), C.POINTER(C.c_int64)])):
+            getattr(L, name).restype = C.c_int
+            getattr(L, name).argtypes = args
+        L.lbm_batch_last_error.restype = C.c_char_p
+        L.lbm_batch_last_error.argtypes = [vp]
+        L.lbm_batch_destroy.restype = None
+        L.lbm_batch_destroy.argtypes = [vp]
         L.lbm_residual_fields_noalloc.restype = C.c_int
         L.lbm_residual_fields_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_int64, vp, dp]
         _lib = L
@@ -274,3 +289,75 @@ class Lattice:
         pitch, eb = C.c_int32(), C.c_int32()
         _check(load().lbm_info(self._h, C.byref(fl), C.byref(pitch), C.byref(eb), C.byref(st)), self._h)
         return dict(fluid_cells=fl.value, pitch=pitch.value, elem_bytes=eb.value, steps=st.value)
+
+
+class Batch:
+    """Lattices of uneven size advanced together by one launch per step (see
+    the lbm_batch_* calls). Members must share the batch's stream and one of
+    the FP32/FP16 storages."""
+
+    def __init__(self, stream=None):
+        import torch
+        L = load()
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        st = L.lbm_batch_create(C.c_void_p(self._stream.cuda_stream), C.byref(h))
+        if st != LBM_OK:
+            raise LBMError(st, L.lbm_last_error(None).decode())
+        self._h = h
+        self.members = []
+
+    def _check(self, st):
+        if st != LBM_OK:
+            raise LBMError(st, load().lbm_batch_last_error(self._h).decode())
+
+    @property
+    def stream(self):
+        return self._stream
+
+    def add(self, lat: "Lattice"):
+        self._check(load().lbm_batch_add(self._h, lat.handle))
+        self.members.append(lat)
+
+    def remove(self, lat: "Lattice"):
+        self._check(load().lbm_batch_remove(self._h, lat.handle))
+        self.members.remove(lat)
+
+    def set_mode(self, steps_per_launch: int = 1, graph_steps: int = 32):
+        self._check(load().lbm_batch_set_mode(self._h, int(steps_per_launch), int(graph_steps)))
+
+    def set_config(self, config: int):
+        self._check(load().lbm_batch_set_config(self._h, int(config)))
+
+    def tune(self, trial_launches: int = 5):
+        """Autotune the kernel shape; returns (best config, ms per launch of each config)."""
+        best = C.c_int32()
+        ms = (C.c_float * 5)()
+        self._check(load().lbm_batch_tune(self._h, int(trial_launches), C.byref(best), ms))
+        return best.value, list(ms)
+
+    def step(self, n: int = 1):
+        self._check(load().lbm_batch_step(self._h, int(n)))
+
+    def sync(self):
+        self._check(load().lbm_batch_sync(self._h))
+
+    def info(self):
+        m, u, cfg = C.c_int32(), C.c_int32(), C.c_int32()
+        cells, steps = C.c_int64(), C.c_int64()
+        self._check(load().lbm_batch_info(self._h, C.byref(m), C.byref(cells), C.byref(u), C.byref(cfg),
+                                          C.byref(steps)))
+        return dict(members=m.value, cells=cells.value, units=u.value, config=cfg.value, steps=steps.value)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h:
+            load().lbm_batch_destroy(h)
+            self._h = None
+        self.members = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,116 @@
+"""Batched execution of lattices of uneven size: every member must produce the
+same bits as when stepped alone, whatever the mode (one launch per step,
+cooperative persistent launches with a grid barrier, CUDA-graph replay), and
+whenever lattices join or leave."""
+import numpy as np
+import pytest
+
+import lbm_cases as lc
+
+pytestmark = pytest.mark.gpu
+
+
+def _P():
+    import paper_1510_08224_gb300 as P
+    return P
+
+
+def _mix():
+    return [
+        lc.cavity(n=40, Ra=1e4, n_y=33, noise=1e-3),
+        lc.rayleigh_benard(nx=300, H=17, Ra=1e5, sigma=1e-2),
+        lc.obstacle_channel(nx=133, H=11, frac=0.12, seed=5),
+        lc.periodic_box(37, 9, nu=0.02, alpha=0.03, T0=0.2,
+                        T_init=0.2 + 0.1 * lc.uniform01(4, 333).reshape(9, 37)),
+        lc.cavity(n=130, Ra=1e5, noise=1e-3),
+    ]
+
+
+def _alone(P, case, storage, nsteps, seed):
+    lat = P.Lattice(case, storage=storage)
+    f0, g0 = lc.random_state(case, seed=seed)
+    lat.set_populations(f0, g0)
+    lat.step(nsteps)
+    return lat.populations()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("mode", [(1, 0), (1, 4), (3, 0), (3, 6)])
+def test_batch_equals_alone(storage, mode):
+    P = _P()
+    cases = _mix()
+    total = 11
+    ref = [_alone(P, c, storage, total, 30 + i) for i, c in enumerate(cases)]
+    b = P.Batch()
+    b.set_mode(*mode)
+    lats = []
+    for i, c in enumerate(cases):
+        lat = P.Lattice(c, storage=storage)
+        f0, g0 = lc.random_state(c, seed=30 + i)
+        lat.set_populations(f0, g0)
+        lats.append(lat)
+    # lattice 0 takes 3 steps alone before joining; the others join at once
+    lats[0].step(3)
+    for lat in lats[1:]:
+        b.add(lat)
+    b.step(2)
+    b.add(lats[0])
+    b.step(total - 3)  # lattice 0: 3 + 8 = 11 steps; the others: 2 + 8 = 10
+    b.remove(lats[1])
+    b.step(0)
+    lats[1].step(1)    # lattice 1 leaves and takes its 11th step alone
+    b.step(1)          # lattice 0 reaches 12, lattices 2-4 reach 11
+    b.sync()
+    for i, lat in enumerate(lats):
+        want_steps = 12 if i == 0 else 11
+        assert lat.info()["steps"] == want_steps
+        if i == 0:
+            ref0 = _alone(P, cases[0], storage, 12, 30)
+            f, g = lat.populations()
+            assert np.array_equal(f, ref0[0]) and np.array_equal(g, ref0[1])
+            continue
+        f, g = lat.populations()
+        assert np.array_equal(f, ref[i][0]) and np.array_equal(g, ref[i][1]), i
+    b.close()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_tuner_keeps_state_and_picks_a_config(storage):
+    P = _P()
+    cases = _mix()
+    b = P.Batch()
+    lats = [P.Lattice(c, storage=storage) for c in cases]
+    for lat in lats:
+        b.add(lat)
+    b.step(5)
+    b.sync()
+    before = [lat.populations() for lat in lats]
+    best, ms = b.tune(trial_launches=3)
+    assert 0 <= best < 5 and all(m > 0 for m in ms)
+    after = [lat.populations() for lat in lats]
+    for (f0, g0), (f1, g1) in zip(before, after):
+        assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    b.step(4)
+    b.sync()
+    for c, lat in zip(cases, lats):
+        ref = P.Lattice(c, storage=storage)
+        ref.step(9)
+        f, g = lat.populations()
+        fr, gr = ref.populations()
+        assert np.array_equal(f, fr) and np.array_equal(g, gr)
+    assert b.info()["config"] == best
+
+
+def test_batched_lattice_rejects_lbm_step_and_fp64():
+    P = _P()
+    b = P.Batch()
+    lat = P.Lattice(lc.couette(H=4, nx=3), storage="f32")
+    b.add(lat)
+    with pytest.raises(P.LBMError):
+        lat.step(1)
+    with pytest.raises(P.LBMError):
+        b.add(P.Lattice(lc.couette(H=4, nx=3), storage="f64"))
+    with pytest.raises(P.LBMError):
+        b.add(P.Lattice(lc.couette(H=4, nx=3), storage="f16"))  # storage mix
+    b.remove(lat)
+    lat.step(1)
