@@ -219,16 +219,20 @@ lbm_status lbm_batch_remove(lbm_batch *b, lbm_lattice *h);
  * that many steps; 0 disables graphs. Defaults: 1 and 32. */
 lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t graph_steps);
 
-/* Kernel shape: config 0..4 asks for 4..8 resident 128-thread blocks per SM;
- * -1 restores the default (1 for FP32, 3 for FP16). */
-lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config);
+/* Kernel shape: config 0..4 asks for 4..8 resident 128-thread blocks per SM
+ * (-1: the default, 1 for FP32 and 3 for FP16); rows_per_unit (1..1024) is the
+ * number of consecutive rows of one 128-cell segment a warp takes per work
+ * unit (default 4). */
+lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_unit);
 
-/* Autotuner: times trial_launches launches of each config on the current
- * members (each trial recomputes the current step into the other buffer, so
- * the state is unchanged), selects the fastest, and returns it in
- * *best_config and the mean ms per launch of each config in ms_per_launch[5]
- * (either may be NULL). Synchronises. */
-lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_config, float *ms_per_launch);
+/* Autotuner: for rows_per_unit in {1, 4, 16} and each config, times
+ * trial_launches launches on the current members (each trial recomputes the
+ * current step into the other buffer, so the state is unchanged), selects the
+ * fastest pair and returns it in *best_config, *best_rows, and the mean ms per
+ * launch of every pair in ms_per_launch[15] (row-count major). Any output may
+ * be NULL. Synchronises. */
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_config, int32_t *best_rows,
+                          float *ms_per_launch);
 
 /* Advance every member by nsteps (asynchronous on the batch's stream). */
 lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
@@ -237,10 +241,10 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
  * grid barrier (the members' state is then undefined). */
 lbm_status lbm_batch_sync(lbm_batch *b);
 
-/* Members, their fluid cells, work units, active config, batch steps taken.
- * Any pointer may be NULL. */
+/* Members, their fluid cells, work units, active config and rows per unit,
+ * batch steps taken. Any pointer may be NULL. */
 lbm_status lbm_batch_info(const lbm_batch *b, int32_t *members, int64_t *cells, int32_t *units, int32_t *config,
-                          int64_t *steps_done);
+                          int32_t *rows_per_unit, int64_t *steps_done);
 
 /* Last error of b (never NULL); with b == NULL, the thread's last error. */
 const char *lbm_batch_last_error(const lbm_batch *b);

@@ -281,3 +281,15 @@ def obstacle_channel(nx: int = 37, H: int = 11, frac: float = 0.12, seed: int = 
     Ti = np.where(flags == 0, 0.5, 0.0)
     return Case("obstacle_channel", nx, ny, True, False, flags, walls, nu=nu, alpha=alpha, g_beta=g_beta,
                 T0=0.5, T_init=Ti, L=float(H), meta=dict(seed=seed), **KINETIC_CONVECTION)
+
+
+def batched_cavities(count: int = 64, side_lo: int = 128, side_hi: int = 1024, ra_lo: float = 1e3,
+                     ra_hi: float = 1e6, Pr: float = 0.71, Ma: float = 0.1, seed: int = 0):
+    """Differentially heated cavities of uneven size: side lengths uniform over
+    the integers side_lo..side_hi and Ra log-uniform in [ra_lo, ra_hi], both
+    drawn from SplitMix64(seed); each cavity's initial noise uses seed + 1 + k."""
+    u = uniform01(seed, 2 * count)
+    sides = side_lo + np.floor(u[0::2] * (side_hi - side_lo + 1)).astype(int)
+    ras = np.exp(np.log(ra_lo) + u[1::2] * (np.log(ra_hi) - np.log(ra_lo)))
+    return [cavity(n=int(n), Ra=float(ra), Pr=Pr, Ma=Ma, seed=seed + 1 + k) for k, (n, ra) in
+            enumerate(zip(sides, ras))]

@@ -2,10 +2,12 @@
 // storage): one kernel launch advances every member lattice by one time step
 // (or, in persistent mode, by k steps with a grid barrier between them).
 //
-// Work list: one unit per warp = (lattice, row, 128-cell segment). Each warp
-// reads its lattice's descriptor (buffers, geometry, rates) from device memory
-// and runs the same row code as the single-lattice VEC4 kernel, so a lattice
-// stepped in a batch produces the same bits as when stepped alone.
+// Work list: units of (lattice, first row, 128-cell segment, row count). A warp
+// takes a unit, reads its lattice's descriptor (buffers, geometry, rates) once
+// and runs the same row code as the single-lattice VEC4 kernel on each of the
+// unit's rows, so a lattice stepped in a batch produces the same bits as when
+// stepped alone. Launches are persistent: a grid of resident CTAs strides over
+// the units.
 //
 // Ping-pong: member l reads buffer (s + flip_l) & 1 at batch step s, where
 // flip_l is fixed when the lattice joins, so lattices that joined at different
@@ -42,6 +44,7 @@ struct __align__(16) BatchLat {
 
 template <typename S, bool NC>
 __device__ __forceinline__ void batch_unit(const BatchLat *lats, const int4 u, int parity, int lane) {
+    // u = (lattice, first row, segment start, rows)
     const BatchLat *L = lats + u.x;
     Geom g;
     g.nx = L->nx;
@@ -58,16 +61,39 @@ __device__ __forceinline__ void batch_unit(const BatchLat *lats, const int4 u, i
     pa.dst = static_cast<S *>(const_cast<void *>(sel ? L->pop0 : L->pop1));
     pa.plane = L->plane;
     const RatesC<float> r = L->r;
-    row4<S, StridedPlanes<S>, NC>(pa, g, r, u.z + 4 * lane, u.y, lane);
+    for (int k = 0; k < u.w; ++k) row4<S, StridedPlanes<S>, NC>(pa, g, r, u.z + 4 * lane, u.y + k, lane);
 }
 
-// One step of every member: one warp per unit.
+// One step of every member: warps stride over the units.
 template <typename S, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     k_batch_step(const BatchLat *lats, const int4 *units, int nunits, int parity) {
-    const int w = blockIdx.x * kBatchWarps + (threadIdx.x >> 5);
-    if (w >= nunits) return;  // warp-uniform
-    batch_unit<S, true>(lats, units[w], parity, threadIdx.x & 31);
+    const int stride = gridDim.x * kBatchWarps;
+    for (int w = blockIdx.x * kBatchWarps + (threadIdx.x >> 5); w < nunits; w += stride)
+        batch_unit<S, true>(lats, units[w], parity, threadIdx.x & 31);
+}
+
+template <typename S, int MINB, bool PERSISTENT>
+struct GridTag {};
+
+// Resident CTAs per SM x SMs for a kernel, computed once per device (one cache
+// per kernel instantiation: TAG distinguishes kernels of the same signature).
+template <typename TAG, typename K>
+cudaError_t resident_grid(K kern, int *blocks) {
+    static int cached_dev = -1, cached = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev != cached_dev) {
+        int per_sm = 0, sms = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, 0);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        cached = (per_sm > 0 ? per_sm : 1) * sms;
+        cached_dev = dev;
+    }
+    *blocks = cached;
+    return cudaSuccess;
 }
 
 // Grid-wide barrier of a cooperative launch. Clock-bounded: on expiry it
@@ -117,31 +143,38 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
     }
 }
 
+template <typename S, int MINB>
+cudaError_t launch_step_shape(const BatchLat *lats, const int4 *units, int nunits, int parity, cudaStream_t st) {
+    auto kern = k_batch_step<S, MINB>;
+    int blocks = 0;
+    cudaError_t e = resident_grid<GridTag<S, MINB, false>>(kern, &blocks);
+    if (e != cudaSuccess) return e;
+    const int need = (nunits + kBatchWarps - 1) / kBatchWarps;
+    if (blocks > need) blocks = need;
+    if (blocks == 0) return cudaSuccess;
+    kern<<<blocks, kBatchThreads, 0, st>>>(lats, units, nunits, parity);
+    return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_batch_step(int config, const BatchLat *lats, const int4 *units, int nunits, int parity,
                               cudaStream_t st) {
-    const int blocks = (nunits + kBatchWarps - 1) / kBatchWarps;
-    if (blocks == 0) return cudaSuccess;
     switch (config) {
-        case 1: k_batch_step<S, 5><<<blocks, kBatchThreads, 0, st>>>(lats, units, nunits, parity); break;
-        case 2: k_batch_step<S, 6><<<blocks, kBatchThreads, 0, st>>>(lats, units, nunits, parity); break;
-        case 3: k_batch_step<S, 7><<<blocks, kBatchThreads, 0, st>>>(lats, units, nunits, parity); break;
-        case 4: k_batch_step<S, 8><<<blocks, kBatchThreads, 0, st>>>(lats, units, nunits, parity); break;
-        default: k_batch_step<S, 4><<<blocks, kBatchThreads, 0, st>>>(lats, units, nunits, parity); break;
+        case 1: return launch_step_shape<S, 5>(lats, units, nunits, parity, st);
+        case 2: return launch_step_shape<S, 6>(lats, units, nunits, parity, st);
+        case 3: return launch_step_shape<S, 7>(lats, units, nunits, parity, st);
+        case 4: return launch_step_shape<S, 8>(lats, units, nunits, parity, st);
+        default: return launch_step_shape<S, 4>(lats, units, nunits, parity, st);
     }
-    return cudaGetLastError();
 }
 
 template <typename S, int MINB>
 cudaError_t launch_persistent_shape(const BatchLat *lats, const int4 *units, int nunits, int parity, int nsteps,
                                     unsigned *bar, int *status, cudaStream_t st) {
     auto kern = k_batch_persistent<S, MINB>;
-    int dev = 0, per_sm = 0, sms = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, 0);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int blocks = 0;
+    cudaError_t e = resident_grid<GridTag<S, MINB, true>>(kern, &blocks);
     if (e != cudaSuccess) return e;
-    int blocks = std::max(1, per_sm) * sms;
     const int need = (nunits + kBatchWarps - 1) / kBatchWarps;
     if (blocks > need) blocks = std::max(1, need);
     cudaLaunchConfig_t cfg = {};
@@ -193,6 +226,7 @@ struct lbm_batch {
     int config = -1;  // -1: default per storage
     int steps_per_launch = 1;
     int graph_steps = 32;
+    int rows_per_unit = 4;
     cudaGraphExec_t graph = nullptr;
     std::string err;
 
@@ -200,6 +234,10 @@ struct lbm_batch {
 };
 
 namespace {
+
+// Rows per unit the tuner tries.
+constexpr int kTuneRows[] = {1, 4, 16};
+constexpr int kTuneRowCount = 3;
 
 lbm_status bfail(lbm_batch *b, lbm_status st, const std::string &m) {
     if (b) b->err = m;
@@ -243,12 +281,22 @@ lbm_status rebuild(lbm_batch *b) {
         d.flip = b->flip[l];
         d.r = nomrt::make_rates<float>(kp);
         b->cells += h->fluid;
-        // units: rows that can hold fluid cells, 128-cell segments holding at least one
-        for (int y = 0; y < kp.ny; ++y)
+        // units: runs of up to rows_per_unit consecutive rows of a 128-cell segment,
+        // skipping rows of the segment that hold no fluid cell
+        const int R = b->rows_per_unit;
+        for (int y0 = 0; y0 < kp.ny; y0 += R)
             for (int xs = 0; xs < kp.pitch; xs += 128) {
-                bool any = false;
-                for (int x = xs; x < std::min(xs + 128, kp.nx) && !any; ++x) any = h->flags[(size_t)y * kp.nx + x] == 0;
-                if (any) units.push_back(make_int4((int)l, y, xs, 0));
+                int first = -1, last = -1;
+                for (int y = y0; y < std::min(y0 + R, kp.ny); ++y) {
+                    bool any = false;
+                    for (int x = xs; x < std::min(xs + 128, kp.nx) && !any; ++x)
+                        any = h->flags[(size_t)y * kp.nx + x] == 0;
+                    if (any) {
+                        if (first < 0) first = y;
+                        last = y;
+                    }
+                }
+                if (first >= 0) units.push_back(make_int4((int)l, first, xs, last - first + 1));
             }
     }
     auto grow = [&](void **p, size_t *capacity, size_t need, size_t elem) -> cudaError_t {
@@ -393,10 +441,15 @@ lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t gr
     return LBM_OK;
 }
 
-lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config) {
+lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_unit) {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     if (config < -1 || config >= nomrt::kBatchConfigs) return bfail(b, LBM_EINVAL, "config out of range");
+    if (rows_per_unit < 1 || rows_per_unit > 1024) return bfail(b, LBM_EINVAL, "rows_per_unit must be 1..1024");
     b->config = config;
+    if (rows_per_unit != b->rows_per_unit) {
+        b->rows_per_unit = rows_per_unit;
+        b->dirty = true;
+    }
     drop_graph(b);
     return LBM_OK;
 }
@@ -450,12 +503,11 @@ lbm_status lbm_batch_sync(lbm_batch *b) {
     return LBM_OK;
 }
 
-lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_config, float *ms_per_launch) {
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_config, int32_t *best_rows,
+                          float *ms_per_launch) {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     if (trial_launches < 1) return bfail(b, LBM_EINVAL, "trial_launches must be >= 1");
     if (b->members.empty()) return bfail(b, LBM_EINVAL, "batch is empty");
-    lbm_status st = rebuild(b);
-    if (st != LBM_OK) return st;
     // Each trial re-runs the current step with the same source parity: it
     // rewrites the destination buffers with the same values and leaves the
     // state the next real step reads untouched.
@@ -463,50 +515,59 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_co
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bfail(b, LBM_ECUDA, "event create");
-    int best = 0;
+    int best = 0, best_r = b->rows_per_unit;
     float best_ms = 1e30f;
     lbm_status out = LBM_OK;
-    for (int c = 0; c < nomrt::kBatchConfigs && out == LBM_OK; ++c) {
-        auto run = [&](int n) -> cudaError_t {
-            for (int k = 0; k < n; ++k) {
-                cudaError_t e = b->storage == LBM_F16_SHIFTED
-                                    ? nomrt::launch_batch_step<__half>(c, b->d_lats, b->d_units, b->nunits, parity,
-                                                                       b->stream)
-                                    : nomrt::launch_batch_step<float>(c, b->d_lats, b->d_units, b->nunits, parity,
-                                                                      b->stream);
-                if (e != cudaSuccess) return e;
+    for (int ri = 0; ri < kTuneRowCount && out == LBM_OK; ++ri) {
+        b->rows_per_unit = kTuneRows[ri];
+        b->dirty = true;
+        out = rebuild(b);
+        for (int c = 0; c < nomrt::kBatchConfigs && out == LBM_OK; ++c) {
+            auto run = [&](int n) -> cudaError_t {
+                for (int k = 0; k < n; ++k) {
+                    cudaError_t e = b->storage == LBM_F16_SHIFTED
+                                        ? nomrt::launch_batch_step<__half>(c, b->d_lats, b->d_units, b->nunits,
+                                                                           parity, b->stream)
+                                        : nomrt::launch_batch_step<float>(c, b->d_lats, b->d_units, b->nunits,
+                                                                          parity, b->stream);
+                    if (e != cudaSuccess) return e;
+                }
+                return cudaSuccess;
+            };
+            cudaError_t e = run(1);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+            if (e == cudaSuccess) e = run(trial_launches);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                out = bcuda(b, e, "tuning launch");
+                break;
             }
-            return cudaSuccess;
-        };
-        cudaError_t e = run(1);  // warm-up
-        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-        if (e == cudaSuccess) e = run(trial_launches);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            out = bcuda(b, e, "tuning launch");
-            break;
-        }
-        ms /= (float)trial_launches;
-        if (ms_per_launch) ms_per_launch[c] = ms;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = c;
+            ms /= (float)trial_launches;
+            if (ms_per_launch) ms_per_launch[ri * nomrt::kBatchConfigs + c] = ms;
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
+                best_r = kTuneRows[ri];
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (out != LBM_OK) return out;
     b->config = best;
+    b->rows_per_unit = best_r;
+    b->dirty = true;
     drop_graph(b);
     if (best_config) *best_config = best;
+    if (best_rows) *best_rows = best_r;
     return LBM_OK;
 }
 
 lbm_status lbm_batch_info(const lbm_batch *b, int32_t *members, int64_t *cells, int32_t *units, int32_t *config,
-                          int64_t *steps_done) {
+                          int32_t *rows_per_unit, int64_t *steps_done) {
     if (!b) return LBM_EINVAL;
     if (members) *members = (int32_t)b->members.size();
     if (cells) {
@@ -516,6 +577,7 @@ lbm_status lbm_batch_info(const lbm_batch *b, int32_t *members, int64_t *cells, 
     }
     if (units) *units = b->nunits;
     if (config) *config = b->cfg();
+    if (rows_per_unit) *rows_per_unit = b->rows_per_unit;
     if (steps_done) *steps_done = b->s;
     return LBM_OK;
 }

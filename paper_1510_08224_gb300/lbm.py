@@ -101,11 +101,12 @@ def load():
         L.lbm_destroy.argtypes = [vp]
         for name, args in (("lbm_batch_create", [vp, C.POINTER(vp)]), ("lbm_batch_add", [vp, vp]),
                            ("lbm_batch_remove", [vp, vp]), ("lbm_batch_set_mode", [vp, C.c_int32, C.c_int32]),
-                           ("lbm_batch_set_config", [vp, C.c_int32]),
-                           ("lbm_batch_tune", [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_float)]),
+                           ("lbm_batch_set_config", [vp, C.c_int32, C.c_int32]),
+                           ("lbm_batch_tune", [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                               C.POINTER(C.c_float)]),
                            ("lbm_batch_step", [vp, C.c_int64]), ("lbm_batch_sync", [vp]),
                            ("lbm_batch_info", [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
-                                               C.POINTER(C.c_int32), C.POINTER(C.c_int64)])):
+                                               C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)])):
             getattr(L, name).restype = C.c_int
             getattr(L, name).argtypes = args
         L.lbm_batch_last_error.restype = C.c_char_p
@@ -326,15 +327,17 @@ class Batch:
     def set_mode(self, steps_per_launch: int = 1, graph_steps: int = 32):
         self._check(load().lbm_batch_set_mode(self._h, int(steps_per_launch), int(graph_steps)))
 
-    def set_config(self, config: int):
-        self._check(load().lbm_batch_set_config(self._h, int(config)))
+    def set_config(self, config: int, rows_per_unit: int = 4):
+        self._check(load().lbm_batch_set_config(self._h, int(config), int(rows_per_unit)))
 
     def tune(self, trial_launches: int = 5):
-        """Autotune the kernel shape; returns (best config, ms per launch of each config)."""
-        best = C.c_int32()
-        ms = (C.c_float * 5)()
-        self._check(load().lbm_batch_tune(self._h, int(trial_launches), C.byref(best), ms))
-        return best.value, list(ms)
+        """Autotune the kernel shape; returns (best config, best rows per unit,
+        {(rows, config): ms per launch})."""
+        best, rows = C.c_int32(), C.c_int32()
+        ms = (C.c_float * 15)()
+        self._check(load().lbm_batch_tune(self._h, int(trial_launches), C.byref(best), C.byref(rows), ms))
+        table = {(r, c): ms[i * 5 + c] for i, r in enumerate((1, 4, 16)) for c in range(5)}
+        return best.value, rows.value, table
 
     def step(self, n: int = 1):
         self._check(load().lbm_batch_step(self._h, int(n)))
@@ -343,11 +346,12 @@ class Batch:
         self._check(load().lbm_batch_sync(self._h))
 
     def info(self):
-        m, u, cfg = C.c_int32(), C.c_int32(), C.c_int32()
+        m, u, cfg, rows = C.c_int32(), C.c_int32(), C.c_int32(), C.c_int32()
         cells, steps = C.c_int64(), C.c_int64()
         self._check(load().lbm_batch_info(self._h, C.byref(m), C.byref(cells), C.byref(u), C.byref(cfg),
-                                          C.byref(steps)))
-        return dict(members=m.value, cells=cells.value, units=u.value, config=cfg.value, steps=steps.value)
+                                          C.byref(rows), C.byref(steps)))
+        return dict(members=m.value, cells=cells.value, units=u.value, config=cfg.value, rows_per_unit=rows.value,
+                    steps=steps.value)
 
     def close(self):
         h = getattr(self, "_h", None)

@@ -35,14 +35,15 @@ def _alone(P, case, storage, nsteps, seed):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-@pytest.mark.parametrize("mode", [(1, 0), (1, 4), (3, 0), (3, 6)])
+@pytest.mark.parametrize("mode", [(1, 0, 1), (1, 4, 4), (3, 0, 16), (3, 6, 3)])
 def test_batch_equals_alone(storage, mode):
     P = _P()
     cases = _mix()
     total = 11
     ref = [_alone(P, c, storage, total, 30 + i) for i, c in enumerate(cases)]
     b = P.Batch()
-    b.set_mode(*mode)
+    b.set_mode(*mode[:2])
+    b.set_config(-1, mode[2])
     lats = []
     for i, c in enumerate(cases):
         lat = P.Lattice(c, storage=storage)
@@ -85,8 +86,8 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
     b.step(5)
     b.sync()
     before = [lat.populations() for lat in lats]
-    best, ms = b.tune(trial_launches=3)
-    assert 0 <= best < 5 and all(m > 0 for m in ms)
+    best, rows, ms = b.tune(trial_launches=3)
+    assert 0 <= best < 5 and rows in (1, 4, 16) and all(m > 0 for m in ms.values())
     after = [lat.populations() for lat in lats]
     for (f0, g0), (f1, g1) in zip(before, after):
         assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
@@ -98,7 +99,7 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
         f, g = lat.populations()
         fr, gr = ref.populations()
         assert np.array_equal(f, fr) and np.array_equal(g, gr)
-    assert b.info()["config"] == best
+    assert b.info()["config"] == best and b.info()["rows_per_unit"] == rows
 
 
 def test_batched_lattice_rejects_lbm_step_and_fp64():
