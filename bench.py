@@ -279,7 +279,10 @@ def run_batched(args):
         return e0.elapsed_time(e1)
 
     res = {}
-    for name, mode in (("graph", (1, 32)), ("launch_per_step", (1, 0)), ("persistent_8", (8, 0))):
+    tuned_kind = b.info()["config"]
+    for name, mode, kind in (("fused_graph", (1, 32), "fused"), ("fused_launch_per_step", (1, 0), "fused"),
+                             ("fused_persistent_8", (8, 0), "fused"), ("concurrent_graph", (1, 32), "concurrent")):
+        b.set_kind(kind)
         b.set_mode(*mode)
         ms = timed(b.step, args.steps)
         res[name] = {"MLUPS": round(cells * args.steps / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms / args.steps, 4)}
@@ -302,7 +305,8 @@ def run_batched(args):
         "config": {"workload": f"batched_cavities_{args.count}", "lattices": args.count, "fluid_cells": cells,
                    "sides": "uniform 128..1024", "Ra": "log-uniform [1e3, 1e6]", "storage": STORAGE_NAME[args.storage],
                    "tuned_config": best, "tuned_rows_per_unit": best_rows,
-                   "tune_ms_per_launch": {f"rows{r}_cfg{c}": round(m, 4) for (r, c), m in ms_cfg.items()}},
+                   "tune_ms_per_launch": {(f"rows{k[0]}_cfg{k[1]}" if isinstance(k, tuple) else k): round(m, 4)
+                                          for k, m in ms_cfg.items()}},
         "modes": res,
         "serial_per_lattice": {"MLUPS": round(cells * k_serial / (ms_serial * 1e-3) / 1e6, 1),
                                "ms_per_step": round(ms_serial / k_serial, 4), "launches_per_step": args.count},

@@ -227,6 +227,11 @@ struct lbm_batch {
     int steps_per_launch = 1;
     int graph_steps = 32;
     int rows_per_unit = 4;
+    int kind = LBM_BATCH_FUSED;
+    // concurrent kind: one stream per member for the fork/join of the graph
+    std::vector<cudaStream_t> lstreams;
+    std::vector<cudaEvent_t> levents;
+    cudaEvent_t fork = nullptr;
     cudaGraphExec_t graph = nullptr;
     std::string err;
 
@@ -332,7 +337,51 @@ lbm_status rebuild(lbm_batch *b) {
     return LBM_OK;
 }
 
+cudaError_t ensure_streams(lbm_batch *b) {
+    cudaError_t e = cudaSuccess;
+    if (!b->fork) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+    while (e == cudaSuccess && b->lstreams.size() < b->members.size()) {
+        cudaStream_t s = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) {
+            b->lstreams.push_back(s);
+            b->levents.push_back(ev);
+        }
+    }
+    return e;
+}
+
+// n steps of every member with each member's own step kernel (its AUTO or
+// chosen variant), each member on its own stream between a fork and a join on
+// `st`, so the members' kernels can run concurrently. src_fixed >= 0 re-runs
+// the current step n times without advancing (tuning).
+cudaError_t launch_concurrent(lbm_batch *b, int n, cudaStream_t st, bool advance) {
+    cudaError_t e = ensure_streams(b);
+    if (e != cudaSuccess) return e;
+    e = cudaEventRecord(b->fork, st);
+    if (e != cudaSuccess) return e;
+    for (size_t l = 0; l < b->members.size(); ++l) {
+        lbm_lattice *h = b->members[l];
+        cudaStream_t ls = b->lstreams[l];
+        e = cudaStreamWaitEvent(ls, b->fork, 0);
+        if (e != cudaSuccess) return e;
+        int cur = h->cur;
+        for (int k = 0; k < n; ++k) {
+            e = h->L->step(h->kp, cur, ls);
+            if (e != cudaSuccess) return e;
+            if (advance) cur ^= 1;
+        }
+        e = cudaEventRecord(b->levents[l], ls);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->levents[l], 0);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
+    if (b->kind == LBM_BATCH_CONCURRENT) return launch_concurrent(b, n, st, true);
     // n steps starting at parity: one launch per step, or persistent launches of steps_per_launch
     while (n > 0) {
         cudaError_t e;
@@ -441,6 +490,14 @@ lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t gr
     return LBM_OK;
 }
 
+lbm_status lbm_batch_set_kind(lbm_batch *b, int32_t kind) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (kind != LBM_BATCH_FUSED && kind != LBM_BATCH_CONCURRENT) return bfail(b, LBM_EINVAL, "unknown batch kind");
+    b->kind = kind;
+    drop_graph(b);
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_unit) {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     if (config < -1 || config >= nomrt::kBatchConfigs) return bfail(b, LBM_EINVAL, "config out of range");
@@ -461,6 +518,14 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps) {
     lbm_status st = rebuild(b);
     if (st != LBM_OK) return st;
     int64_t left = nsteps;
+    auto advance = [&](int64_t k) {
+        b->s += k;
+        left -= k;
+        for (lbm_lattice *h : b->members) {
+            h->cur = (int)((h->cur + k) & 1);
+            h->steps += k;
+        }
+    };
     while (left > 0) {
         const int parity = (int)(b->s & 1);
         if (b->graph_steps > 0 && parity == 0 && left >= b->graph_steps) {
@@ -468,8 +533,7 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps) {
             if (st != LBM_OK) return st;
             cudaError_t e = cudaGraphLaunch(b->graph, b->stream);
             if (e != cudaSuccess) return bcuda(b, e, "graph launch");
-            b->s += b->graph_steps;
-            left -= b->graph_steps;
+            advance(b->graph_steps);
             continue;
         }
         // direct launches: one step to reach even parity, or the remainder
@@ -477,12 +541,7 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps) {
         k = std::min<int64_t>(k, 1 << 20);
         cudaError_t e = launch_steps(b, parity, (int)k, b->stream);
         if (e != cudaSuccess) return bcuda(b, e, "batch step launch");
-        b->s += k;
-        left -= k;
-    }
-    for (lbm_lattice *h : b->members) {
-        h->cur = (int)((h->cur + nsteps) & 1);
-        h->steps += nsteps;
+        advance(k);
     }
     return LBM_OK;
 }
@@ -554,14 +613,28 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_co
             }
         }
     }
+    // the concurrent kind: every member's own kernel, members in parallel
+    float conc_ms = 1e30f;
+    if (out == LBM_OK) {
+        cudaError_t e = launch_concurrent(b, 1, b->stream, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = launch_concurrent(b, trial_launches, b->stream, false);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&conc_ms, e0, e1);
+        if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (concurrent)");
+        conc_ms /= (float)trial_launches;
+        if (ms_per_launch) ms_per_launch[kTuneRowCount * nomrt::kBatchConfigs] = conc_ms;
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (out != LBM_OK) return out;
+    b->kind = conc_ms < best_ms ? LBM_BATCH_CONCURRENT : LBM_BATCH_FUSED;
     b->config = best;
     b->rows_per_unit = best_r;
     b->dirty = true;
     drop_graph(b);
-    if (best_config) *best_config = best;
+    if (best_config) *best_config = b->kind == LBM_BATCH_CONCURRENT ? -2 : best;
     if (best_rows) *best_rows = best_r;
     return LBM_OK;
 }
@@ -576,7 +649,7 @@ lbm_status lbm_batch_info(const lbm_batch *b, int32_t *members, int64_t *cells, 
         *cells = c;
     }
     if (units) *units = b->nunits;
-    if (config) *config = b->cfg();
+    if (config) *config = b->kind == LBM_BATCH_CONCURRENT ? -2 : b->cfg();
     if (rows_per_unit) *rows_per_unit = b->rows_per_unit;
     if (steps_done) *steps_done = b->s;
     return LBM_OK;
@@ -592,6 +665,9 @@ void lbm_batch_destroy(lbm_batch *b) {
     cudaStreamSynchronize(b->stream);
     for (lbm_lattice *h : b->members) h->batch = nullptr;
     drop_graph(b);
+    for (cudaStream_t ls : b->lstreams) cudaStreamDestroy(ls);
+    for (cudaEvent_t ev : b->levents) cudaEventDestroy(ev);
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
     if (b->d_lats) cudaFree(b->d_lats);
     if (b->d_units) cudaFree(b->d_units);

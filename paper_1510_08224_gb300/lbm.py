@@ -26,7 +26,7 @@ EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_st
             "lbm_nusselt",
             "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
             "lbm_destroy", "lbm_residual_fields_noalloc", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
-            "lbm_batch_set_mode", "lbm_batch_set_config", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
+            "lbm_batch_set_mode", "lbm_batch_set_kind", "lbm_batch_set_config", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
             "lbm_batch_info", "lbm_batch_last_error", "lbm_batch_destroy")
 
 
@@ -101,7 +101,7 @@ def load():
         L.lbm_destroy.argtypes = [vp]
         for name, args in (("lbm_batch_create", [vp, C.POINTER(vp)]), ("lbm_batch_add", [vp, vp]),
                            ("lbm_batch_remove", [vp, vp]), ("lbm_batch_set_mode", [vp, C.c_int32, C.c_int32]),
-                           ("lbm_batch_set_config", [vp, C.c_int32, C.c_int32]),
+                           ("lbm_batch_set_config", [vp, C.c_int32, C.c_int32]), ("lbm_batch_set_kind", [vp, C.c_int32]),
                            ("lbm_batch_tune", [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                                C.POINTER(C.c_float)]),
                            ("lbm_batch_step", [vp, C.c_int64]), ("lbm_batch_sync", [vp]),
@@ -327,6 +327,12 @@ class Batch:
     def set_mode(self, steps_per_launch: int = 1, graph_steps: int = 32):
         self._check(load().lbm_batch_set_mode(self._h, int(steps_per_launch), int(graph_steps)))
 
+    def set_kind(self, kind):
+        """'fused' (one kernel over every member's work) or 'concurrent' (each
+        member's own kernel, members side by side)."""
+        k = {"fused": 0, "concurrent": 1}[kind] if isinstance(kind, str) else int(kind)
+        self._check(load().lbm_batch_set_kind(self._h, k))
+
     def set_config(self, config: int, rows_per_unit: int = 4):
         self._check(load().lbm_batch_set_config(self._h, int(config), int(rows_per_unit)))
 
@@ -334,9 +340,10 @@ class Batch:
         """Autotune the kernel shape; returns (best config, best rows per unit,
         {(rows, config): ms per launch})."""
         best, rows = C.c_int32(), C.c_int32()
-        ms = (C.c_float * 15)()
+        ms = (C.c_float * 16)()
         self._check(load().lbm_batch_tune(self._h, int(trial_launches), C.byref(best), C.byref(rows), ms))
         table = {(r, c): ms[i * 5 + c] for i, r in enumerate((1, 4, 16)) for c in range(5)}
+        table["concurrent"] = ms[15]
         return best.value, rows.value, table
 
     def step(self, n: int = 1):

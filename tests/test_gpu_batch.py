@@ -35,7 +35,8 @@ def _alone(P, case, storage, nsteps, seed):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-@pytest.mark.parametrize("mode", [(1, 0, 1), (1, 4, 4), (3, 0, 16), (3, 6, 3)])
+@pytest.mark.parametrize("mode", [(1, 0, 1, "fused"), (1, 4, 4, "fused"), (3, 0, 16, "fused"), (3, 6, 3, "fused"),
+                                  (1, 0, 4, "concurrent"), (1, 4, 4, "concurrent")])
 def test_batch_equals_alone(storage, mode):
     P = _P()
     cases = _mix()
@@ -44,6 +45,7 @@ def test_batch_equals_alone(storage, mode):
     b = P.Batch()
     b.set_mode(*mode[:2])
     b.set_config(-1, mode[2])
+    b.set_kind(mode[3])
     lats = []
     for i, c in enumerate(cases):
         lat = P.Lattice(c, storage=storage)
@@ -87,7 +89,7 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
     b.sync()
     before = [lat.populations() for lat in lats]
     best, rows, ms = b.tune(trial_launches=3)
-    assert 0 <= best < 5 and rows in (1, 4, 16) and all(m > 0 for m in ms.values())
+    assert (best == -2 or 0 <= best < 5) and rows in (1, 4, 16) and all(m > 0 for m in ms.values())
     after = [lat.populations() for lat in lats]
     for (f0, g0), (f1, g1) in zip(before, after):
         assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
