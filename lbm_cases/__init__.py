@@ -293,3 +293,28 @@ def batched_cavities(count: int = 64, side_lo: int = 128, side_hi: int = 1024, r
     ras = np.exp(np.log(ra_lo) + u[1::2] * (np.log(ra_hi) - np.log(ra_lo)))
     return [cavity(n=int(n), Ra=float(ra), Pr=Pr, Ma=Ma, seed=seed + 1 + k) for k, (n, ra) in
             enumerate(zip(sides, ras))]
+
+
+def serving_stream(n: int = 40, rate: float = 20.0, seed: int = 0, side_lo: int = 64, side_hi: int = 2048,
+                   ra_lo: float = 1e3, ra_hi: float = 1e6, Pr: float = 0.71, Ma: float = 0.1):
+    """n requests with Poisson arrivals (exponential gaps of mean 1/rate from
+    SplitMix64(seed)); each is a cavity (side s) or a Rayleigh-Benard cell
+    (s x s/2, periodic in x) with equal odds, s log-uniform over
+    [side_lo, side_hi], Ra log-uniform over [ra_lo, ra_hi].
+    Returns [(arrival seconds, kind, case)]."""
+    u = uniform01(seed, 4 * n)
+    gaps = -np.log(1.0 - u[0::4]) / rate
+    arrivals = np.cumsum(gaps) - gaps[0]
+    sides = np.exp(np.log(side_lo) + u[1::4] * (np.log(side_hi) - np.log(side_lo)))
+    ras = np.exp(np.log(ra_lo) + u[2::4] * (np.log(ra_hi) - np.log(ra_lo)))
+    out = []
+    for k in range(n):
+        s = max(8, int(round(sides[k])))
+        if u[4 * k + 3] < 0.5:
+            case = cavity(n=s, Ra=float(ras[k]), Pr=Pr, Ma=Ma, seed=seed + 100 + k)
+            kind = "cavity"
+        else:
+            case = rayleigh_benard(nx=s, H=max(4, s // 2), Ra=float(ras[k]), Pr=Pr, Ma=Ma, seed=seed + 100 + k)
+            kind = "rayleigh_benard"
+        out.append((float(arrivals[k]), kind, case))
+    return out
