@@ -160,6 +160,21 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max_time(ms: float, dist, device) -> float:
+    """Max over ranks of a per-rank time (the slowest rank bounds the job)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_mlups(fluid_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Cells all ranks updated (each rank advances its own replica) / slowest time."""
+    return world * fluid_per_rank * steps / (ms_max * 1e-3) / 1e6
+
+
 def time_steps(P, torch, case, storage, steps, warmup):
     """Device-timed K steps of one lattice. Returns (elapsed_ms, lattice)."""
     lat = P.Lattice(case, storage=storage)
@@ -430,18 +445,14 @@ def main():
     if dist:
         dist.barrier()
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
+    ms_max = reduce_max_time(ms, dist, "cuda")
     sampler.stop()
     clocks = sampler.summary(t_start, t_end)
     r = lat.residual()  # finite-state check of the run (first call: snapshot)
     lat.close()
     del lat
 
-    value = world * fluid * args.steps / (ms_max * 1e-3) / 1e6
+    value = whole_job_mlups(fluid, args.steps, world, ms_max)
     ms_step = ms_max / args.steps
     peak, peak_src = measured_peak()
     achieved = BYTES_PER_NODE[args.storage] * fluid / (ms / args.steps * 1e-3) / 1e9
