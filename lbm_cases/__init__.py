@@ -22,6 +22,11 @@ import numpy as np
 
 DIRICHLET = 0
 ADIABATIC = 1
+# wall schemes: halfway walls between a fluid cell and a frame of solid cells, or
+# node-based walls whose boundary nodes are reconstructed by non-equilibrium
+# extrapolation (the paper's default, Sec. 3)
+HALFWAY = 0
+NEE = 1
 
 # kinetic rates used for the convection problems of Sec. 3.4 of the paper
 KINETIC_CONVECTION = dict(s_e=1.6, s_q=1.2, s_eps=1.8, zeta_e=1.9, zeta_nu=1.9)
@@ -37,6 +42,7 @@ class Wall:
     uy: float = 0.0
     kind: int = ADIABATIC
     T: float = 0.0
+    scheme: int = HALFWAY
 
 
 @dataclass
@@ -318,3 +324,82 @@ def serving_stream(n: int = 40, rate: float = 20.0, seed: int = 0, side_lo: int 
             kind = "rayleigh_benard"
         out.append((float(arrivals[k]), kind, case))
     return out
+
+
+# --------------------------------------------------- node-based (NEE) walls --
+
+def node_y(H: int) -> np.ndarray:
+    """Wall-normal positions of the nodes 0..H of a node-based channel, in units of H."""
+    return np.arange(H + 1) / H
+
+
+def poiseuille_nee(H: int = 60, nx: int = 6, ax: float = 2e-6, s_nu: float = 1.754, kinetic=None) -> Case:
+    """Sec. 3.1 as the paper sets it up: walls on the nodes y = 0 and y = H
+    (H + 1 rows of nodes, non-equilibrium extrapolation), periodic x, body
+    force a = (ax, 0), s_nu given, the other rates 1. Exact profile (Eq. 34):
+    u_x = ax y (H - y) / (2 nu)."""
+    kin = dict(KINETIC_ONE if kinetic is None else kinetic)
+    nu = (1.0 / s_nu - 0.5) * CS2
+    walls = [Wall(0.0, 0.0, ADIABATIC, 0.0, NEE), Wall(0.0, 0.0, ADIABATIC, 0.0, NEE)]
+    flags = np.zeros((H + 1, nx), np.uint8)
+    flags[0, :] = 1
+    flags[-1, :] = 2
+    return Case("poiseuille_nee", nx, H + 1, True, False, flags, walls, nu=nu, alpha=0.1, ax=ax, L=float(H),
+                meta=dict(H=H, ax=ax, nodes=True), **kin)
+
+
+def porous_couette_nee(H: int = 60, nx: int = 6, Re: float = 10.0, Pr: float = 0.71, U0: float = 0.01,
+                       v0: float = 0.01, s_nu: float | None = None, T_h: float = 1.0, T_c: float = 0.0) -> Case:
+    """Sec. 3.3 as the paper sets it up: node-based walls at y = 0 (static,
+    cold, injecting v0) and y = H (moving at U0, hot, sucking v0), periodic x,
+    no buoyancy, kinetic rates 1. Re = H v0 / nu unless s_nu is given, in
+    which case v0 = Re nu / H and U0 = v0 (the convergence study fixes Re and
+    s_nu and keeps the paper's u0 = v0)."""
+    if s_nu is None:
+        nu = H * v0 / Re
+    else:
+        nu = (1.0 / s_nu - 0.5) * CS2
+        v0 = Re * nu / H
+        U0 = v0
+    alpha = nu / Pr
+    walls = [Wall(0.0, v0, DIRICHLET, T_c, NEE), Wall(U0, v0, DIRICHLET, T_h, NEE)]
+    flags = np.zeros((H + 1, nx), np.uint8)
+    flags[0, :] = 1
+    flags[-1, :] = 2
+    return Case("porous_couette_nee", nx, H + 1, True, False, flags, walls, nu=nu, alpha=alpha,
+                T0=0.5 * (T_h + T_c), delta_T=T_h - T_c, L=float(H),
+                meta=dict(Re=Re, Pr=Pr, U0=U0, v0=v0, T_h=T_h, T_c=T_c, H=H, nodes=True), **KINETIC_ONE)
+
+
+def porous_couette_nee_exact(case: Case):
+    """Eqs. 36-37 on the nodes 0..H."""
+    m = case.meta
+    y = node_y(m["H"])
+    Re, Pr = m["Re"], m["Pr"]
+    ux = m["U0"] * np.expm1(Re * y) / np.expm1(Re)
+    T = m["T_c"] + (m["T_h"] - m["T_c"]) * np.expm1(Pr * Re * y) / np.expm1(Pr * Re)
+    return ux, T
+
+
+def cavity_nee(n: int = 64, Ra: float = 1e3, Pr: float = 0.71, Ma: float = 0.1, T_h: float = 1.0, T_c: float = 0.0,
+               noise: float = 0.0, seed: int = 0, kinetic=None) -> Case:
+    """Sec. 3.4 as the paper sets it up: (n + 1) x (n + 1) nodes, walls on the
+    boundary nodes (non-equilibrium extrapolation): left hot, right cold, top
+    and bottom adiabatic, all static; L = n. Corner nodes belong to the side
+    walls."""
+    dT = T_h - T_c
+    nu, alpha, g_beta = convection_params(float(n), Ra, Pr, Ma, dT)
+    walls = [Wall(0, 0, DIRICHLET, T_h, NEE), Wall(0, 0, DIRICHLET, T_c, NEE), Wall(0, 0, ADIABATIC, 0.0, NEE),
+             Wall(0, 0, ADIABATIC, 0.0, NEE)]
+    flags = np.zeros((n + 1, n + 1), np.uint8)
+    flags[0, :] = 3
+    flags[-1, :] = 4
+    flags[:, 0] = 1
+    flags[:, -1] = 2
+    T0 = 0.5 * (T_h + T_c)
+    Ti = np.full(flags.shape, T0)
+    if noise:
+        Ti += noise * (2.0 * uniform01(seed, Ti.size).reshape(Ti.shape) - 1.0)
+    kin = dict(KINETIC_CONVECTION if kinetic is None else kinetic)
+    return Case("cavity_nee", n + 1, n + 1, False, False, flags, walls, nu=nu, alpha=alpha, g_beta=g_beta, T0=T0,
+                delta_T=dT, T_init=Ti, L=float(n), meta=dict(Ra=Ra, Pr=Pr, Ma=Ma, nodes=True), **kin)

@@ -57,6 +57,7 @@ class OrcParams(C.Structure):
         ("zeta_e", C.c_double), ("zeta_nu", C.c_double), ("varpi", C.c_double),
         ("s8_literal", C.c_int32),
         ("T_init", C.c_void_p),
+        ("wall_scheme", C.c_void_p),
     ]
 
 
@@ -142,8 +143,9 @@ class OracleLattice:
         wu = np.ascontiguousarray([[w.ux, w.uy] for w in case.walls] or [[0.0, 0.0]], dtype=np.float64)
         wk = np.ascontiguousarray([w.kind for w in case.walls] or [0], dtype=np.int32)
         wT = np.ascontiguousarray([w.T for w in case.walls] or [0.0], dtype=np.float64)
+        ws = np.ascontiguousarray([getattr(w, "scheme", 0) for w in case.walls] or [0], dtype=np.int32)
         Ti = None if case.T_init is None else np.ascontiguousarray(case.T_init, dtype=np.float64)
-        self._keep = (flags, wu, wk, wT, Ti)
+        self._keep = (flags, wu, wk, wT, Ti, ws)
         p = OrcParams()
         p.nx, p.ny = case.nx, case.ny
         p.periodic_x, p.periodic_y = int(case.periodic_x), int(case.periodic_y)
@@ -156,6 +158,7 @@ class OracleLattice:
         p.zeta_e, p.zeta_nu, p.varpi = case.zeta_e, case.zeta_nu, case.varpi
         p.s8_literal = int(bool(s8_literal))
         p.T_init = Ti.ctypes.data if Ti is not None else None
+        p.wall_scheme = ws.ctypes.data
         self._p = p
         h = lib().orc_create(C.byref(p))
         if not h:

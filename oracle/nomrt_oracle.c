@@ -128,6 +128,7 @@ typedef struct {
     double varpi;              /* model parameter of Eq. 28 */
     int32_t s8_literal;        /* 1: the printed S~_8 of Eq. 17 (reading A2) */
     const double *T_init;      /* ny*nx or NULL (T0 everywhere) */
+    const int32_t *wall_scheme; /* n_walls or NULL: 0 halfway (solid cells), 1 non-equilibrium extrapolation */
 } orc_params;
 
 /* Per-node collision inputs. s[9] is Lambda of Eq. 20, z[5] is Q of Eq. 29. */
@@ -144,6 +145,8 @@ typedef struct {
     int n_walls;
     double *wall_u, *wall_T;
     int *wall_kind;
+    int *wall_scheme;
+    uint8_t *nee_dir; /* per cell: 0, or i in 1..8 with the fluid node x_f = x + e_i of a boundary node */
     orc_rates r;
     double *f[2]; /* [9][ny*nx] */
     double *g[2]; /* [5][ny*nx] */
@@ -269,6 +272,19 @@ static int wrap(int v, int n, int periodic) {
     return v;
 }
 
+/* A cell is updated every step if it is fluid or a boundary node of a wall
+ * treated by non-equilibrium extrapolation; the cells of halfway walls are
+ * solid and never updated. */
+static int is_solid(const orc_lattice *L, int c) {
+    int k = L->flags[c];
+    return k != 0 && L->wall_scheme[k - 1] == 0;
+}
+
+static int is_nee(const orc_lattice *L, int c) {
+    int k = L->flags[c];
+    return k != 0 && L->wall_scheme[k - 1] == 1;
+}
+
 /* Post-streaming populations at fluid node (x, y), pulled from the
  * post-collision state (fsrc, gsrc) by Eqs. 9 and 25, with the wall rules of
  * reading A5 on links whose source cell is solid. */
@@ -280,7 +296,7 @@ static void gather(const orc_lattice *L, const double *fsrc, const double *gsrc,
         int sx = wrap(x - EX[i], L->nx, L->px);
         int sy = wrap(y - EY[i], L->ny, L->py);
         int src = sy * L->nx + sx;
-        int k = L->flags[src];
+        int k = is_solid(L, src) ? L->flags[src] : 0;
         if (k == 0) {
             fin[i] = fsrc[i * nxy + src];
         } else {
@@ -297,6 +313,58 @@ static void gather(const orc_lattice *L, const double *fsrc, const double *gsrc,
             }
         }
     }
+}
+
+/* Incompressible equilibrium (Eq. 22 under reading A1) and the D2Q5
+ * temperature equilibrium (Eq. 30) of direction i. */
+static double feq_i(int i, double rho, double ux, double uy) {
+    double eu = EX[i] * ux + EY[i] * uy;
+    return W9[i] * (rho + RHO0 * (eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - (ux * ux + uy * uy) / (2.0 * CS2)));
+}
+
+static double geq_i(int i, double T, double ux, double uy, double varpi) {
+    if (i == 0) return (1.0 - varpi) * T;
+    return 0.25 * varpi * T + 0.5 * (EX[i] * ux + EY[i] * uy) * T;
+}
+
+/* Non-equilibrium extrapolation (Z. Guo, C. Zheng, B. Shi, Chin. Phys. 11 (2002)
+ * 366), the paper's default wall treatment (Sec. 3): at boundary node x_b of a
+ * node-based wall, every population is the equilibrium at the wall state plus
+ * the non-equilibrium part at the nearest fluid node x_f, both after streaming:
+ *   f_b = f_eq(rho_f, u_w) + [f(x_f) - f_eq(rho_f, u_f)]
+ *   g_b = g_eq(T_b, u_w)   + [g(x_f) - g_eq(T_f, u_f)]
+ * with rho_b = rho_f, T_b = T_w for a fixed temperature and T_b = T_f for an
+ * adiabatic wall; rho_f, u_f, T_f by Eqs. 18, 19, 27 with the force of Eq. 4. */
+static void nee_gather(const orc_lattice *L, const double *fsrc, const double *gsrc, int x, int y,
+                       double fin[9], double gin[5]) {
+    int c = y * L->nx + x;
+    int d = L->nee_dir[c];
+    int xf = wrap(x + EX[d], L->nx, L->px), yf = wrap(y + EY[d], L->ny, L->py);
+    double ff[9], gf[5];
+    gather(L, fsrc, gsrc, xf, yf, ff, gf);
+    double rho = 0.0, T = 0.0, jx = 0.0, jy = 0.0;
+    for (int i = 0; i < 9; ++i) {
+        rho += ff[i];
+        jx += EX[i] * ff[i];
+        jy += EY[i] * ff[i];
+    }
+    for (int i = 0; i < 5; ++i) T += gf[i];
+    double Fx = L->r.ax, Fy = L->r.ay + L->r.g_beta * (T - L->r.T0);
+    double ux = (jx + 0.5 * RHO0 * Fx) / RHO0, uy = (jy + 0.5 * RHO0 * Fy) / RHO0;
+    int k = L->flags[c];
+    double uwx = L->wall_u[2 * (k - 1)], uwy = L->wall_u[2 * (k - 1) + 1];
+    double Tb = L->wall_kind[k - 1] == 0 ? L->wall_T[k - 1] : T;
+    for (int i = 0; i < 9; ++i) fin[i] = feq_i(i, rho, uwx, uwy) + (ff[i] - feq_i(i, rho, ux, uy));
+    for (int i = 0; i < 5; ++i)
+        gin[i] = geq_i(i, Tb, uwx, uwy, L->r.varpi) + (gf[i] - geq_i(i, T, ux, uy, L->r.varpi));
+}
+
+/* The populations an updated cell collides: pulled for fluid, extrapolated for
+ * boundary nodes. */
+static void pre_collision(const orc_lattice *L, const double *fsrc, const double *gsrc, int x, int y,
+                          double fin[9], double gin[5]) {
+    if (L->nee_dir[y * L->nx + x]) nee_gather(L, fsrc, gsrc, x, y, fin, gin);
+    else gather(L, fsrc, gsrc, x, y, fin, gin);
 }
 
 void orc_destroy(orc_lattice *L);
@@ -319,21 +387,36 @@ orc_lattice *orc_create(const orc_params *p) {
     L->wall_u = (double *)calloc(2 * (size_t)(p->n_walls + 1), sizeof(double));
     L->wall_T = (double *)calloc((size_t)p->n_walls + 1, sizeof(double));
     L->wall_kind = (int *)calloc((size_t)p->n_walls + 1, sizeof(int));
+    L->wall_scheme = (int *)calloc((size_t)p->n_walls + 1, sizeof(int));
+    L->nee_dir = (uint8_t *)calloc(nxy, 1);
     for (int k = 0; k < p->n_walls; ++k) {
         L->wall_u[2 * k] = p->wall_u[2 * k];
         L->wall_u[2 * k + 1] = p->wall_u[2 * k + 1];
         L->wall_T[k] = p->wall_T[k];
         L->wall_kind[k] = p->wall_kind[k];
+        L->wall_scheme[k] = p->wall_scheme ? p->wall_scheme[k] : 0;
     }
     orc_rates_from_params(p, &L->r);
     for (size_t c = 0; c < nxy; ++c)
         if (L->flags[c] > p->n_walls) { orc_destroy(L); return NULL; }
     for (int y = 0; y < L->ny; ++y)
         for (int x = 0; x < L->nx; ++x) {
-            if (L->flags[y * L->nx + x]) continue;
-            for (int i = 1; i < 9; ++i) {
-                int sx = wrap(x - EX[i], L->nx, L->px), sy = wrap(y - EY[i], L->ny, L->py);
-                if (sx < 0 || sx >= L->nx || sy < 0 || sy >= L->ny) { orc_destroy(L); return NULL; }
+            int c = y * L->nx + x;
+            if (L->flags[c] == 0) {
+                for (int i = 1; i < 9; ++i) {
+                    int sx = wrap(x - EX[i], L->nx, L->px), sy = wrap(y - EY[i], L->ny, L->py);
+                    if (sx < 0 || sx >= L->nx || sy < 0 || sy >= L->ny) { orc_destroy(L); return NULL; }
+                }
+            } else if (is_nee(L, c)) {
+                /* the nearest fluid node: an axis neighbour if there is one, else a diagonal */
+                int d = 0;
+                for (int i = 1; i < 9 && !d; ++i) {
+                    int sx = wrap(x + EX[i], L->nx, L->px), sy = wrap(y + EY[i], L->ny, L->py);
+                    if (sx < 0 || sx >= L->nx || sy < 0 || sy >= L->ny) continue;
+                    if (L->flags[sy * L->nx + sx] == 0) d = i;
+                }
+                if (!d) { orc_destroy(L); return NULL; }
+                L->nee_dir[c] = (uint8_t)d;
             }
         }
     for (int b = 0; b < 2; ++b) {
@@ -342,7 +425,7 @@ orc_lattice *orc_create(const orc_params *p) {
     }
     /* Reading A4: rest equilibrium, f_bar_i = w_i rho0, g_i = g_eq_i(T_init, 0) (Eqs. 22, 30). */
     for (size_t c = 0; c < nxy; ++c) {
-        if (L->flags[c]) continue;
+        if (is_solid(L, (int)c)) continue;
         double T = p->T_init ? p->T_init[c] : p->T0;
         for (int i = 0; i < 9; ++i) L->f[0][i * nxy + c] = W9[i] * RHO0;
         L->g[0][0 * nxy + c] = (1.0 - p->varpi) * T;
@@ -357,6 +440,8 @@ void orc_destroy(orc_lattice *L) {
     free(L->wall_u);
     free(L->wall_T);
     free(L->wall_kind);
+    free(L->wall_scheme);
+    free(L->nee_dir);
     for (int b = 0; b < 2; ++b) { free(L->f[b]); free(L->g[b]); }
     free(L->snap);
     free(L);
@@ -376,9 +461,9 @@ void orc_step(orc_lattice *L, int64_t nsteps) {
         for (int y = 0; y < L->ny; ++y) {
             for (int x = 0; x < L->nx; ++x) {
                 int c = y * L->nx + x;
-                if (L->flags[c]) continue;
+                if (is_solid(L, c)) continue;
                 double fin[9], gin[5], fo[9], go[5];
-                gather(L, fs, gs, x, y, fin, gin);
+                pre_collision(L, fs, gs, x, y, fin, gin);
                 orc_collide_node(&L->r, fin, gin, fo, go, NULL);
                 for (int i = 0; i < 9; ++i) fd[i * nxy + c] = fo[i];
                 for (int i = 0; i < 5; ++i) gd[i * nxy + c] = go[i];
@@ -388,16 +473,17 @@ void orc_step(orc_lattice *L, int64_t nsteps) {
     }
 }
 
-/* Reading A6: macroscopics at every node (solid nodes give zeros). */
+/* Reading A6: macroscopics at every node (solid nodes give zeros; boundary
+ * nodes of extrapolated walls give their reconstructed state). */
 void orc_macro(const orc_lattice *L, double *rho, double *ux, double *uy, double *T) {
     const int nxy = L->nx * L->ny;
     for (int y = 0; y < L->ny; ++y)
         for (int x = 0; x < L->nx; ++x) {
             int c = y * L->nx + x;
             double mac[4] = {0, 0, 0, 0};
-            if (!L->flags[c]) {
+            if (!is_solid(L, c)) {
                 double fin[9], gin[5], fo[9], go[5];
-                gather(L, L->f[L->cur], L->g[L->cur], x, y, fin, gin);
+                pre_collision(L, L->f[L->cur], L->g[L->cur], x, y, fin, gin);
                 orc_collide_node(&L->r, fin, gin, fo, go, mac);
             }
             if (rho) rho[c] = mac[0];
@@ -420,7 +506,7 @@ void orc_set_populations(orc_lattice *L, const double *f, const double *g) {
     if (f) memcpy(L->f[L->cur], f, 9 * nxy * sizeof(double));
     if (g) memcpy(L->g[L->cur], g, 5 * nxy * sizeof(double));
     for (size_t c = 0; c < nxy; ++c)
-        if (L->flags[c]) {
+        if (is_solid(L, (int)c)) {
             for (int i = 0; i < 9; ++i) L->f[L->cur][i * nxy + c] = 0.0;
             for (int i = 0; i < 5; ++i) L->g[L->cur][i * nxy + c] = 0.0;
         }
@@ -432,15 +518,15 @@ void orc_set_populations(orc_lattice *L, const double *f, const double *g) {
  * node is solid. */
 int orc_update_node(const orc_lattice *L, const double *fsrc, const double *gsrc, int x, int y,
                     double fout[9], double gout[5]) {
-    if (L->flags[y * L->nx + x]) return -1;
+    if (is_solid(L, y * L->nx + x)) return -1;
     double fin[9], gin[5];
-    gather(L, fsrc, gsrc, x, y, fin, gin);
+    pre_collision(L, fsrc, gsrc, x, y, fin, gin);
     orc_collide_node(&L->r, fin, gin, fout, gout, NULL);
     return 0;
 }
 
 /* Eq. 39 with reading A8. side: 0 left (x min), 1 right, 2 bottom (y min), 3 top.
- * The wall is the frame line of solid cells on that side; the average runs over
+ * The wall is the frame line of wall cells on that side; the average runs over
  * the lines where the two nearest cells are fluid and the wall cell has a fixed
  * temperature. Nu = -L (dT/dx_axis) / dT where x_axis is x for the side walls
  * and y for the bottom and top. Returns NaN if no such line exists. */
@@ -458,8 +544,12 @@ double orc_nusselt(const orc_lattice *L, int side, double Lref, double dT) {
         else { cw = (L->ny - 1) * L->nx + s; c1 = cw - L->nx; c2 = cw - 2 * L->nx; }
         int k = L->flags[cw];
         if (k == 0 || L->flags[c1] || L->flags[c2] || L->wall_kind[k - 1] != 0) continue;
-        /* dT/ds, s measured from the wall into the fluid. */
-        double dTds = (9.0 * T[c1] - T[c2] - 8.0 * L->wall_T[k - 1]) / 3.0;
+        /* dT/ds, s measured from the wall into the fluid: a halfway wall sits half a
+         * cell before c1 (reading A8); a node-based wall is the node cw itself, and
+         * the one-sided second-order difference uses the nodes at 0, 1, 2. */
+        double Tw = L->wall_T[k - 1];
+        double dTds = L->wall_scheme[k - 1] == 1 ? (-3.0 * Tw + 4.0 * T[c1] - T[c2]) / 2.0
+                                                 : (9.0 * T[c1] - T[c2] - 8.0 * Tw) / 3.0;
         double dTdaxis = (side == 0 || side == 2) ? dTds : -dTds;
         sum += -Lref * dTdaxis / dT;
         ++count;
