@@ -18,8 +18,9 @@
  *    are [9][ny][nx] (f, directions of Eq. 5) and [5][ny][nx] (g).
  *  - Lengths are lattice units (delta_x = delta_t = 1, c = 1, rho0 = 1: Sec. 3).
  *  - Walls are half-way between a fluid cell and a solid cell (halfway
- *    bounce-back). A fluid cell at a non-periodic edge is an error: the flag map
- *    must carry a frame of solid cells there.
+ *    bounce-back), or on boundary nodes (non-equilibrium extrapolation), per
+ *    wall. A fluid cell at a non-periodic edge is an error: the flag map must
+ *    carry a frame of wall cells there.
  */
 #ifndef NOMRT_LBM_H
 #define NOMRT_LBM_H
@@ -50,18 +51,30 @@ typedef enum { LBM_T_DIRICHLET = 0, LBM_T_ADIABATIC = 1 } lbm_thermal_kind;
 
 typedef enum { LBM_SIDE_LEFT = 0, LBM_SIDE_RIGHT = 1, LBM_SIDE_BOTTOM = 2, LBM_SIDE_TOP = 3 } lbm_side;
 
-/* One wall. Wall id k (the flag value of its solid cells) is walls[k-1].
- * Flow: halfway bounce-back with Ladd's moving-wall term,
+/* Wall schemes. HALFWAY: the wall lies half-way between a fluid cell and the
+ * wall's cells, which are solid and never updated. NEE: the wall's cells are
+ * boundary nodes on the wall itself (node-based wall, the paper's setting in
+ * Sec. 3), rebuilt every step by non-equilibrium extrapolation (Z. Guo,
+ * C. Zheng, B. Shi, Chin. Phys. 11 (2002) 366) and then collided like fluid. */
+typedef enum { LBM_WALL_HALFWAY = 0, LBM_WALL_NEE = 1 } lbm_wall_scheme;
+
+/* One wall. Wall id k (the flag value of its cells) is walls[k-1].
+ * HALFWAY flow: bounce-back with Ladd's moving-wall term,
  *   f_i(x) = f*_opp(i)(x) + 2 w_i rho0 (e_i . u_w) / c_s^2
- * for a direction i arriving at fluid cell x from a solid cell of this wall;
+ * for a direction i arriving at fluid cell x from a cell of this wall;
  * u_w may be tangential (a lid) or normal (a porous wall injecting fluid).
- * Temperature: LBM_T_DIRICHLET holds T = T by anti-bounce-back,
+ * HALFWAY temperature: LBM_T_DIRICHLET holds T = T by anti-bounce-back,
  *   g_i(x) = -g*_opp(i)(x) + 2 (varpi/4) T;
- * LBM_T_ADIABATIC is a zero-flux wall, g_i(x) = g*_opp(i)(x). */
+ * LBM_T_ADIABATIC is a zero-flux wall, g_i(x) = g*_opp(i)(x).
+ * NEE: at boundary node x_b with nearest fluid node x_f (an axis neighbour if
+ * one is fluid, else a diagonal one), after streaming,
+ *   f_b = f_eq(rho_f, u_w) + [f(x_f) - f_eq(rho_f, u_f)]
+ *   g_b = g_eq(T_b, u_w) + [g(x_f) - g_eq(T_f, u_f)]
+ * with T_b = T for LBM_T_DIRICHLET and T_b = T_f for LBM_T_ADIABATIC. */
 typedef struct {
     double ux, uy;
-    int32_t kind; /* lbm_thermal_kind */
-    int32_t reserved;
+    int32_t kind;   /* lbm_thermal_kind */
+    int32_t scheme; /* lbm_wall_scheme */
     double T;
 } lbm_wall;
 
@@ -144,8 +157,9 @@ lbm_status lbm_read_macro(lbm_lattice *h, double *rho, double *ux, double *uy, d
 /* Mean Nusselt number on a frame wall (Eq. 39): Nu = -L (dT/dx_n) / delta_T,
  * x_n = x for LEFT/RIGHT and y for BOTTOM/TOP, with the wall gradient
  * (9 T_1/2 - T_3/2 - 8 T_w) / 3 from the two nearest fluid cells and the wall's
- * fixed temperature, averaged over the lines where both cells are fluid and
- * the frame cell is a fixed-temperature wall. L <= 0 means the number of
+ * fixed temperature (HALFWAY walls), or (-3 T_w + 4 T_1 - T_2) / 2 from the
+ * wall node and the next two nodes (NEE walls), averaged over the lines where
+ * both cells are fluid and the frame cell is a fixed-temperature wall. L <= 0 means the number of
  * fluid cells across the lattice along x_n. FP64 reduction. Synchronises.
  * LBM_EINVAL if no such line exists. */
 lbm_status lbm_nusselt(lbm_lattice *h, int32_t side, double L, double delta_T, double *nu_mean);

@@ -25,7 +25,7 @@ struct Layout {
     size_t pop_bytes = 0;       // one buffer
     size_t off_pop[2] = {0, 0};
     size_t off_mask = 0, off_flags = 0, off_walls = 0, off_snap = 0, off_stage = 0, off_part = 0, off_res = 0,
-           off_status = 0;
+           off_status = 0, off_nee_dir = 0, off_nee = 0;
     int stage_rows = 0;
     size_t total = 0;
 };

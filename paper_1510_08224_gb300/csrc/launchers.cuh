@@ -94,7 +94,27 @@ template <typename S>
 cudaError_t launch_step_variant(const KParams &p, int variant, int src, cudaStream_t st);
 
 template <typename S>
+cudaError_t launch_nee(const KParams &p, int src, cudaStream_t st) {
+    using C = typename Store<S>::C;
+    if (p.n_nee == 0) return cudaSuccess;
+    k_nee<S><<<(p.n_nee + 127) / 128, 128, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p), p.nee,
+                                                    p.n_nee);
+    return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st);
+
+// One step: the main kernel over fluid cells, then the boundary nodes of NEE walls.
+template <typename S>
 cudaError_t launch_step(const KParams &p, int src, cudaStream_t st) {
+    cudaError_t e = launch_step_main<S>(p, src, st);
+    if (e != cudaSuccess) return e;
+    return launch_nee<S>(p, src, st);
+}
+
+template <typename S>
+cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
     int variant = p.variant;
     KParams q = p;
     if constexpr (Store<S>::kShifted) {
@@ -208,6 +228,7 @@ template <typename S>
 Launchers make_launchers() {
     Launchers L;
     L.step = &launch_step<S>;
+    L.nee = &launch_nee<S>;
     L.init_rows = &launch_init_rows<S>;
     L.macro_rows = &launch_macro_rows<S>;
     L.export_rows = &launch_export_rows<S>;

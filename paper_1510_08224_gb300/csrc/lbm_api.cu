@@ -38,7 +38,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 size_t elem_bytes(int storage) { return storage == LBM_F64 ? 8 : storage == LBM_F32_SHIFTED ? 4 : 2; }
 
-Layout make_layout(int nx, int ny, int storage, int n_walls) {
+Layout make_layout(int nx, int ny, int storage, int n_walls, int n_nee) {
     Layout L;
     const size_t eb = elem_bytes(storage);
     L.pitch = (int)align_up((size_t)nx, 128 / eb);
@@ -58,6 +58,8 @@ Layout make_layout(int nx, int ny, int storage, int n_walls) {
     L.off_part = o; o += align_up(sizeof(double) * nomrt::kRedBlocks * 8, kAlign);
     L.off_res = o; o += align_up(sizeof(double) * 8, kAlign);
     L.off_status = o; o += kAlign;
+    L.off_nee_dir = o; o += align_up(L.plane, kAlign);
+    L.off_nee = o; o += align_up(sizeof(int2) * (size_t)std::max(1, n_nee), kAlign);
     L.total = o;
     return L;
 }
@@ -76,6 +78,36 @@ Derived derive(const lbm_params *p) {
 }
 
 bool in_open_02(double v) { return std::isfinite(v) && v > 0.0 && v < 2.0; }
+
+// Cells of HALFWAY walls are solid; cells of NEE walls are boundary nodes.
+bool solid_cell(const lbm_params *p, size_t c) {
+    const uint8_t k = p->flags[c];
+    return k != 0 && p->walls[k - 1].scheme == LBM_WALL_HALFWAY;
+}
+
+bool nee_cell(const lbm_params *p, size_t c) {
+    const uint8_t k = p->flags[c];
+    return k != 0 && p->walls[k - 1].scheme == LBM_WALL_NEE;
+}
+
+// Direction i of a boundary node's nearest fluid node x + e_i: an axis
+// neighbour if one is fluid, else a diagonal one; 0 if there is none.
+int nee_direction(const lbm_params *p, int x, int y) {
+    for (int i = 1; i < 9; ++i) {
+        int sx = x + kEx[i], sy = y + kEy[i];
+        if (p->periodic_x) sx = (sx + p->nx) % p->nx;
+        if (p->periodic_y) sy = (sy + p->ny) % p->ny;
+        if (sx < 0 || sx >= p->nx || sy < 0 || sy >= p->ny) continue;
+        if (p->flags[(size_t)sy * p->nx + sx] == 0) return i;
+    }
+    return 0;
+}
+
+int count_nee(const lbm_params *p) {
+    int n = 0;
+    for (size_t c = 0; c < (size_t)p->nx * p->ny; ++c) n += nee_cell(p, c);
+    return n;
+}
 
 // Returns an empty string if p is valid, else the reason.
 std::string validate(const lbm_params *p) {
@@ -104,6 +136,7 @@ std::string validate(const lbm_params *p) {
         const lbm_wall &w = p->walls[k];
         if (!std::isfinite(w.ux) || !std::isfinite(w.uy) || !std::isfinite(w.T)) return "wall values must be finite";
         if (w.kind != LBM_T_DIRICHLET && w.kind != LBM_T_ADIABATIC) return "unknown wall thermal kind";
+        if (w.scheme != LBM_WALL_HALFWAY && w.scheme != LBM_WALL_NEE) return "unknown wall scheme";
     }
     const size_t eb = elem_bytes(p->storage);
     const size_t pitch = align_up((size_t)p->nx, 128 / eb);
@@ -114,6 +147,11 @@ std::string validate(const lbm_params *p) {
             const uint8_t k = p->flags[(size_t)y * nx + x];
             if (k > p->n_walls) {
                 snprintf(buf, sizeof buf, "cell (%d, %d) has wall id %d > n_walls", x, y, (int)k);
+                return buf;
+            }
+            if (k && p->walls[k - 1].scheme == LBM_WALL_NEE && nee_direction(p, x, y) == 0) {
+                snprintf(buf, sizeof buf, "boundary node (%d, %d) of an extrapolated wall has no fluid neighbour", x,
+                         y);
                 return buf;
             }
             if (k) continue;
@@ -127,7 +165,7 @@ std::string validate(const lbm_params *p) {
                              "fluid cell (%d, %d) touches a non-periodic edge; add a frame of solid cells", x, y);
                     return buf;
                 }
-                solid += p->flags[(size_t)sy * nx + sx] != 0;
+                solid += solid_cell(p, (size_t)sy * nx + sx);
             }
             if (solid == 8) {
                 snprintf(buf, sizeof buf, "fluid cell (%d, %d) has no fluid neighbour", x, y);
@@ -197,7 +235,7 @@ size_t lbm_footprint_bytes(const lbm_params *p) {
         g_create_error = why;
         return 0;
     }
-    return make_layout(p->nx, p->ny, p->storage, p->n_walls).total;
+    return make_layout(p->nx, p->ny, p->storage, p->n_walls, count_nee(p)).total;
 }
 
 lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, size_t device_bytes,
@@ -215,7 +253,8 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     h->storage = p->storage;
     h->n_walls = p->n_walls;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
-    h->lay = make_layout(p->nx, p->ny, p->storage, p->n_walls);
+    const int n_nee = count_nee(p);
+    h->lay = make_layout(p->nx, p->ny, p->storage, p->n_walls, n_nee);
     h->L = &launchers_for(p->storage);
     const size_t need = h->lay.total;
     auto bail = [&](lbm_status st, const std::string &m) {
@@ -242,19 +281,29 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     // host-side maps: wall ids and the link map (bit i-1: direction i pulls from a solid cell)
     const int nx = p->nx, ny = p->ny, pitch = h->lay.pitch;
     h->flags.assign(p->flags, p->flags + (size_t)nx * ny);
-    std::vector<uint8_t> hmask((size_t)ny * pitch, kSolid), hflags((size_t)ny * pitch, 0);
+    std::vector<uint8_t> hmask((size_t)ny * pitch, kSolid), hflags((size_t)ny * pitch, 0),
+        hdir((size_t)ny * pitch, 0);
+    std::vector<int2> hnee;
     for (int y = 0; y < ny; ++y)
         for (int x = 0; x < nx; ++x) {
-            const uint8_t k = p->flags[(size_t)y * nx + x];
+            const size_t c = (size_t)y * nx + x;
+            const uint8_t k = p->flags[c];
             hflags[(size_t)y * pitch + x] = k;
-            if (k) continue;
+            if (k) {
+                if (nee_cell(p, c)) {
+                    const int d = nee_direction(p, x, y);
+                    hdir[(size_t)y * pitch + x] = (uint8_t)d;
+                    hnee.push_back(make_int2(y * pitch + x, d | ((int)k << 8)));
+                }
+                continue;
+            }
             ++h->fluid;
             unsigned m = 0;
             for (int i = 1; i < 9; ++i) {
                 int sx = x - kEx[i], sy = y - kEy[i];
                 if (h->px) sx = (sx + nx) % nx;
                 if (h->py) sy = (sy + ny) % ny;
-                if (p->flags[(size_t)sy * nx + sx]) m |= 1u << (i - 1);
+                if (solid_cell(p, (size_t)sy * nx + sx)) m |= 1u << (i - 1);
             }
             hmask[(size_t)y * pitch + x] = (uint8_t)m;
         }
@@ -272,6 +321,10 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
             hw[k].tb = 0.0;
         }
         hw[k].Tw = w.T;
+        hw[k].uwx = w.ux;
+        hw[k].uwy = w.uy;
+        hw[k].nee = w.scheme == LBM_WALL_NEE ? 1.0 : 0.0;
+        hw[k].adiabatic = w.kind == LBM_T_ADIABATIC ? 1.0 : 0.0;
     }
 
     KParams &kp = h->kp;
@@ -301,6 +354,9 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     kp.varpi = p->varpi;
     kp.rho_ref = p->storage == LBM_F64 ? 0.0 : 1.0;
     kp.T_ref = T_ref;
+    kp.nee = reinterpret_cast<const int2 *>(h->mem + h->lay.off_nee);
+    kp.n_nee = (int)hnee.size();
+    kp.nee_dir = reinterpret_cast<const uint8_t *>(h->mem + h->lay.off_nee_dir);
     kp.variant = nomrt::kStepAuto;
     kp.config = 0;
     kp.status = reinterpret_cast<int *>(h->mem + h->lay.off_status);
@@ -320,6 +376,12 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     if ((e = cudaMemcpyAsync(h->mem + h->lay.off_walls, hw.data(), sizeof(WallDev) * hw.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_bail(e, "upload walls");
+    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_nee_dir, hdir.data(), hdir.size(), cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
+        return cuda_bail(e, "upload boundary-node directions");
+    if (!hnee.empty() && (e = cudaMemcpyAsync(h->mem + h->lay.off_nee, hnee.data(), hnee.size() * sizeof(int2),
+                                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_bail(e, "upload boundary nodes");
     // initial state, row chunks of T through the staging area
     std::vector<double> Trow((size_t)h->lay.stage_rows * nx);
     for (int r0 = 0; r0 < ny; r0 += h->lay.stage_rows) {

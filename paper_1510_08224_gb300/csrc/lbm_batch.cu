@@ -380,12 +380,32 @@ cudaError_t launch_concurrent(lbm_batch *b, int n, cudaStream_t st, bool advance
     return cudaSuccess;
 }
 
+// The boundary nodes of NEE walls of every member, for the batch step at
+// `parity` (after the fused kernel, which skips them).
+cudaError_t launch_nee_passes(lbm_batch *b, int parity, cudaStream_t st) {
+    for (size_t l = 0; l < b->members.size(); ++l) {
+        lbm_lattice *h = b->members[l];
+        if (h->kp.n_nee == 0) continue;
+        cudaError_t e = h->L->nee(h->kp, (parity + b->flip[l]) & 1, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+bool any_nee(const lbm_batch *b) {
+    for (const lbm_lattice *h : b->members)
+        if (h->kp.n_nee > 0) return true;
+    return false;
+}
+
 cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
     if (b->kind == LBM_BATCH_CONCURRENT) return launch_concurrent(b, n, st, true);
+    const bool nee = any_nee(b);
     // n steps starting at parity: one launch per step, or persistent launches of steps_per_launch
+    // (members with NEE walls need a pass between steps, so they force one launch per step)
     while (n > 0) {
         cudaError_t e;
-        if (b->steps_per_launch > 1) {
+        if (b->steps_per_launch > 1 && !nee) {
             const int k = std::min(n, b->steps_per_launch);
             e = b->storage == LBM_F16_SHIFTED
                     ? nomrt::launch_batch_persistent<__half>(b->cfg(), b->d_lats, b->d_units, b->nunits, parity, k,
@@ -398,6 +418,7 @@ cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
             e = b->storage == LBM_F16_SHIFTED
                     ? nomrt::launch_batch_step<__half>(b->cfg(), b->d_lats, b->d_units, b->nunits, parity, st)
                     : nomrt::launch_batch_step<float>(b->cfg(), b->d_lats, b->d_units, b->nunits, parity, st);
+            if (e == cudaSuccess && nee) e = launch_nee_passes(b, parity, st);
             parity ^= 1;
             n -= 1;
         }

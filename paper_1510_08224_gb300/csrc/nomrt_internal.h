@@ -38,7 +38,9 @@ struct WallDev {
     double tsgn;
     double tb;
     double Tw;
-    double pad[4];
+    double uwx, uwy;  // wall velocity
+    double nee;       // 1: node-based wall (non-equilibrium extrapolation), 0: halfway
+    double adiabatic; // 1: adiabatic, 0: fixed temperature
 };
 
 // Everything a kernel needs to know about one lattice, in FP64; each kernel
@@ -56,6 +58,9 @@ struct KParams {
     double z_a, z_e, z_nu;            // Eq. 29
     double g_beta, T0, ax, ay, varpi; // Eq. 4, Eq. 28
     double rho_ref, T_ref;            // storage shift (0 for FP64 storage)
+    const int2 *nee;                  // boundary nodes of NEE walls: (cell offset, dir | wall id << 8)
+    int n_nee;
+    const uint8_t *nee_dir;           // per cell: 0, or the direction i of the nearest fluid node x + e_i
     int variant;                      // step kernel variant (kStep*)
     int config;                       // shape index within the variant (TMA: 0..kTmaConfigs-1)
     int *status;                      // device status word
@@ -65,7 +70,10 @@ struct KParams {
 // All are asynchronous on `st` and return the launch error.
 struct Launchers {
     // one fused stream-and-collide step reading buffer `src`, writing 1 - src
+    // (boundary nodes of NEE walls included)
     cudaError_t (*step)(const KParams &, int src, cudaStream_t st);
+    // the boundary nodes of NEE walls alone (after a step kernel that skipped them)
+    cudaError_t (*nee)(const KParams &, int src, cudaStream_t st);
     // initial state into buffer `buf`, rows [r0, r1); T rows in `T` (device, (r1-r0)*nx)
     cudaError_t (*init_rows)(const KParams &, int buf, int r0, int r1, const double *T, cudaStream_t st);
     // macroscopics of rows [r0, r1) into out[4][(r1-r0)*nx] (rho, ux, uy, T)

@@ -94,6 +94,7 @@ struct RatesC {
     C T_ref;
     C hx;                         // ax / 2
     C h2e, h2nu, h23eps;          // 2 (1 - s_e/2), 2 (1 - s_nu/2), (2/3)(1 - s_eps/2)
+    C varpi;                      // Eq. 28
 };
 
 template <typename C>
@@ -123,6 +124,7 @@ inline RatesC<C> make_rates(const KParams &p) {
     r.h2e = (C)(2.0 * (1.0 - 0.5 * p.s_e));
     r.h2nu = (C)(2.0 * (1.0 - 0.5 * p.s_nu));
     r.h23eps = (C)(2.0 / 3.0 * (1.0 - 0.5 * p.s_eps));
+    r.varpi = (C)p.varpi;
     return r;
 }
 
@@ -163,10 +165,16 @@ struct Geom {
     const uint8_t *mask;
     const uint8_t *flags;
     const WallDev *walls;
+    const uint8_t *nee_dir;  // per cell: 0, or the direction of a boundary node's nearest fluid node
 };
 
 inline Geom make_geom(const KParams &p) {
-    return Geom{p.nx, p.ny, p.pitch, p.px, p.py, p.mask, p.flags, p.walls};
+    return Geom{p.nx, p.ny, p.pitch, p.px, p.py, p.mask, p.flags, p.walls, p.nee_dir};
+}
+
+// A cell whose populations are kept: fluid, or a boundary node of an NEE wall.
+__device__ __forceinline__ bool kept_cell(const Geom &g, int off) {
+    return g.mask[off] != kSolid || g.nee_dir[off] != 0;
 }
 
 // --------------------------------------------------------------- pull step
@@ -238,6 +246,47 @@ __device__ __forceinline__ Macro<C> macro_of(const RatesC<C> &r, const C f[9], c
     M.ux = jx + C(0.5) * M.Fx;
     M.uy = jy + C(0.5) * M.Fy;
     return M;
+}
+
+// Non-equilibrium extrapolation at boundary node (x, y) of wall w whose nearest
+// fluid node is x + e_d: the fluid node's post-streaming populations plus the
+// difference of the equilibria at the wall state and at the fluid node's
+// state (Eq. 22 under the incompressible reading; Eq. 30), which is
+//   f_b = f_eq(rho_f, u_w) + [f(x_f) - f_eq(rho_f, u_f)]
+//   g_b = g_eq(T_b, u_w)   + [g(x_f) - g_eq(T_f, u_f)]
+// in the storage frame (the shift cancels in the differences).
+template <typename S>
+__device__ __forceinline__ void nee_rebuild(const S *const *src, const Geom &g,
+                                            const RatesC<typename Store<S>::C> &r, int x, int y, int d,
+                                            const WallDev *w, typename Store<S>::C f[9],
+                                            typename Store<S>::C t[5]) {
+    using C = typename Store<S>::C;
+    const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+    const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+    const C w9[9] = {C(4.0 / 9), C(1.0 / 9), C(1.0 / 9), C(1.0 / 9), C(1.0 / 9),
+                     C(1.0 / 36), C(1.0 / 36), C(1.0 / 36), C(1.0 / 36)};
+    int xf = x + ex[d], yf = y + ey[d];
+    if (g.px) xf = (xf < 0) ? xf + g.nx : (xf >= g.nx ? xf - g.nx : xf);
+    if (g.py) yf = (yf < 0) ? yf + g.ny : (yf >= g.ny ? yf - g.ny : yf);
+    const unsigned mf = g.mask[yf * g.pitch + xf];
+    pull<S>(src, g, xf, yf, mf, f, t);
+    const Macro<C> M = macro_of<C>(r, f, t);
+    const C uwx = (C)w->uwx, uwy = (C)w->uwy;
+    const C Tf = r.T_ref + M.dT;
+    const C Tb = w->adiabatic != 0.0 ? Tf : (C)w->Tw;
+    const C uf2 = M.ux * M.ux + M.uy * M.uy, uw2 = uwx * uwx + uwy * uwy;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const C euw = ex[i] * uwx + ey[i] * uwy, euf = ex[i] * M.ux + ey[i] * M.uy;
+        f[i] += w9[i] * ((C(3) * euw + C(4.5) * euw * euw - C(1.5) * uw2) -
+                         (C(3) * euf + C(4.5) * euf * euf - C(1.5) * uf2));
+    }
+    t[0] += (C(1) - r.varpi) * (Tb - Tf);
+#pragma unroll
+    for (int i = 1; i < 5; ++i) {
+        const C euw = ex[i] * uwx + ey[i] * uwy, euf = ex[i] * M.ux + ey[i] * M.uy;
+        t[i] += C(0.25) * r.varpi * (Tb - Tf) + C(0.5) * (euw * Tb - euf * Tf);
+    }
 }
 
 // Flow collision (Eq. 8 with Eqs. 16, 17, 20 under the incompressible reading,
@@ -513,6 +562,28 @@ __global__ void __launch_bounds__(256) k_step(const Planes<S> pl, const Geom g, 
     }
 }
 
+// Boundary nodes of NEE walls: rebuild (non-equilibrium extrapolation), collide,
+// store. Runs after a step kernel that skipped them (their link-map byte is
+// kSolid), reading the same source buffer.
+template <typename S>
+__global__ void __launch_bounds__(128) k_nee(const Planes<S> pl, const Geom g, const RatesC<typename Store<S>::C> r,
+                                             const int2 *nee, int n) {
+    using C = typename Store<S>::C;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int2 e = nee[i];
+    const int off = e.x, d = e.y & 0xFF, k = e.y >> 8;
+    const int y = off / g.pitch, x = off - y * g.pitch;
+    C f[9], t[5];
+    nee_rebuild<S>(pl.src, g, r, x, y, d, g.walls + k, f, t);
+    if constexpr (Store<S>::kShifted) collide_x<float>(r, f, t);
+    else collide<C>(r, f, t);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Store<S>::st(pl.dst[q] + off, f[q]);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) Store<S>::st(pl.dst[9 + q] + off, t[q]);
+}
+
 // Initial state (rest equilibrium, Eqs. 22, 30 at u = 0) in the storage frame.
 template <typename S>
 __global__ void k_init_rows(const Planes<S> pl, const Geom g, int r0, int r1, const double *T, double T_ref,
@@ -521,7 +592,7 @@ __global__ void k_init_rows(const Planes<S> pl, const Geom g, int r0, int r1, co
     const int y = r0 + blockIdx.y;
     if (x >= g.pitch || y >= r1) return;
     const int off = y * g.pitch + x;
-    const bool fluid = x < g.nx && g.mask[off] != kSolid;
+    const bool fluid = x < g.nx && kept_cell(g, off);
     const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
     const double Tn = fluid ? T[(size_t)(y - r0) * g.nx + x] : 0.0;
     for (int q = 0; q < 9; ++q) {
@@ -545,10 +616,12 @@ __global__ void k_macro_rows(const Planes<S> pl, const Geom g, const RatesC<type
     const size_t n = (size_t)(r1 - r0) * g.nx;
     const size_t o = (size_t)(y - r0) * g.nx + x;
     const unsigned m = g.mask[y * g.pitch + x];
+    const unsigned d = g.nee_dir[y * g.pitch + x];
     double v[4] = {0, 0, 0, 0};
-    if (m != kSolid) {
+    if (m != kSolid || d != 0) {
         C f[9], t[5];
-        pull<S>(pl.src, g, x, y, m, f, t);
+        if (m != kSolid) pull<S>(pl.src, g, x, y, m, f, t);
+        else nee_rebuild<S>(pl.src, g, r, x, y, (int)d, g.walls + g.flags[y * g.pitch + x], f, t);
         Macro<C> M = macro_of<C>(r, f, t);
         v[0] = rho_ref + (double)M.drho;
         v[1] = (double)M.ux;
@@ -567,7 +640,7 @@ __global__ void k_export_rows(const Planes<S> pl, const Geom g, int r0, int r1, 
     const size_t n = (size_t)(r1 - r0) * g.nx;
     const size_t o = (size_t)(y - r0) * g.nx + x;
     const int off = y * g.pitch + x;
-    const bool fluid = g.mask[off] != kSolid;
+    const bool fluid = kept_cell(g, off);
     const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
     for (int q = 0; q < kQ; ++q) {
         double v = 0.0;
@@ -589,7 +662,7 @@ __global__ void k_import_rows(const Planes<S> pl, const Geom g, int r0, int r1, 
     const size_t n = (size_t)(r1 - r0) * g.nx;
     const size_t o = (size_t)(y - r0) * g.nx + x;
     const int off = y * g.pitch + x;
-    const bool fluid = g.mask[off] != kSolid;
+    const bool fluid = kept_cell(g, off);
     const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
     for (int q = 0; q < kQ; ++q) {
         if (q < 9 && !(which & 1)) continue;
@@ -654,7 +727,8 @@ __global__ void __launch_bounds__(kRedThreads) k_nusselt(const Planes<S> pl, con
         const double Tw = w->Tw;
         const double T1 = temperature_at<S>(pl, g, x1, y1, T_ref);
         const double T2 = temperature_at<S>(pl, g, x2, y2, T_ref);
-        const double dTds = (9.0 * T1 - T2 - 8.0 * Tw) / 3.0;
+        // halfway wall half a cell before c1; node-based wall on the wall node itself
+        const double dTds = w->nee != 0.0 ? (-3.0 * Tw + 4.0 * T1 - T2) / 2.0 : (9.0 * T1 - T2 - 8.0 * Tw) / 3.0;
         const double dTdn = (side == 0 || side == 2) ? dTds : -dTds;
         v[0] += -L * dTdn / dT;
         v[1] += 1.0;

@@ -37,7 +37,7 @@ class LBMError(RuntimeError):
 
 
 class lbm_wall(C.Structure):
-    _fields_ = [("ux", C.c_double), ("uy", C.c_double), ("kind", C.c_int32), ("reserved", C.c_int32),
+    _fields_ = [("ux", C.c_double), ("uy", C.c_double), ("kind", C.c_int32), ("scheme", C.c_int32),
                 ("T", C.c_double)]
 
 
@@ -140,7 +140,7 @@ def make_params(case, storage: str = "f32"):
     assert flags.shape == (case.ny, case.nx)
     walls = (lbm_wall * max(1, len(case.walls)))()
     for k, w in enumerate(case.walls):
-        walls[k] = lbm_wall(float(w.ux), float(w.uy), int(w.kind), 0, float(w.T))
+        walls[k] = lbm_wall(float(w.ux), float(w.uy), int(w.kind), int(getattr(w, "scheme", 0)), float(w.T))
     Ti = None
     if getattr(case, "T_init", None) is not None:
         Ti = np.ascontiguousarray(case.T_init, dtype=np.float64)

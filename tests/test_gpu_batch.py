@@ -23,6 +23,7 @@ def _mix():
         lc.periodic_box(37, 9, nu=0.02, alpha=0.03, T0=0.2,
                         T_init=0.2 + 0.1 * lc.uniform01(4, 333).reshape(9, 37)),
         lc.cavity(n=130, Ra=1e5, noise=1e-3),
+        lc.cavity_nee(n=45, Ra=1e4, noise=1e-3),  # node-based walls: the fused kind adds their pass
     ]
 
 

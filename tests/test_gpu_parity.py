@@ -38,10 +38,12 @@ def _cases_small():
         lc.obstacle_channel(nx=261, H=9, frac=0.15, seed=4),  # scattered solid cells, moving lid
         lc.periodic_box(6, 9, nu=0.02, alpha=0.03, T0=0.2,
                         T_init=0.2 + 0.1 * lc.uniform01(9, 54).reshape(9, 6)),  # periodic in x and y
+        lc.cavity_nee(n=19, Ra=1e4, noise=1e-3),                 # node-based walls on all four sides
+        lc.porous_couette_nee(H=13, nx=5, Re=10, s_nu=0.8),       # node-based moving, injecting walls
     ]
 
 
-N_SMALL = 8
+N_SMALL = 10
 
 
 @pytest.mark.parametrize("idx", range(N_SMALL))
@@ -51,7 +53,7 @@ def test_fp64_populations_match_oracle(idx, nsteps):
     case = _cases_small()[idx]
     g = P.Lattice(case, storage="f64")
     o = oracle.OracleLattice(case)
-    if idx in (0, 6, 7):  # start off-equilibrium
+    if idx in (0, 6, 7, 8):  # start off-equilibrium
         f0, g0 = lc.random_state(case, seed=11)
         g.set_populations(f0, g0)
         o.set_populations(f0, g0)
@@ -307,3 +309,27 @@ def test_nan_state_is_reported_as_diverged():
     with pytest.raises(P.LBMError) as e:
         g.residual()
     assert e.value.status == 4  # LBM_EDIVERGED
+
+
+def test_nee_cavity_nusselt_against_table3_on_gpu():
+    """Node-based cavity (the paper's walls), Ra = 1e3, 64 x 64 intervals,
+    FP64 storage, run to steady state: Nu within 0.5 % of Table 3 (1.1161)
+    and equal to the oracle's value after the same steps."""
+    import os
+    P = _P()
+    row = np.loadtxt(os.path.join(os.path.dirname(__file__), "golden", "table3_cavity.txt"))[0]
+    case = lc.cavity_nee(n=64, Ra=1e3)
+    g = P.Lattice(case, storage="f64")
+    g.residual()
+    for _ in range(200):
+        g.step(1000)
+        if g.residual() < 1e-9:
+            break
+    nu = [g.nusselt(s, L=64.0) for s in (0, 1)]
+    for v in nu:
+        assert abs(v - row[5]) / row[5] < 5e-3
+    steps = g.info()["steps"]
+    o = oracle.OracleLattice(case, threads=8)
+    o.step(steps)
+    for side, v in zip((0, 1), nu):
+        assert abs(v - o.nusselt(side, L=64.0)) < 1e-10
