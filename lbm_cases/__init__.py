@@ -70,6 +70,10 @@ class Case:
     T_init: np.ndarray | None = None  # (ny, nx) float64
     L: float = 1.0                  # characteristic length for Nu
     meta: dict = field(default_factory=dict)
+    thermal_q: int = 5              # 5: D2Q5 temperature (Sec. 2.2); 9: the D2Q9 model (Eqs. 31-33)
+    theta: float = 1.0              # the switch of Eq. 31 (D2Q9 model)
+    zeta_q: float = 1.0             # kinetic rates of Eq. 32 (D2Q9 model)
+    zeta_eps: float = 1.0
 
     @property
     def fluid_nodes(self) -> int:
@@ -253,16 +257,19 @@ def periodic_box(nx: int, ny: int, nu: float = 0.05, alpha: float = 0.05, g_beta
 def random_state(case: Case, seed: int, amp_f: float = 0.02, amp_g: float = 0.05):
     """A seeded non-equilibrium population state for parity checks: rest
     weights w_i plus uniform noise for the flow, T0 shares plus noise for the
-    temperature; zeros on solid cells. Layout (9, ny, nx) and (5, ny, nx)."""
+    temperature; zeros on solid cells (cells of halfway walls). Layout
+    (9, ny, nx) and (thermal_q, ny, nx)."""
     w9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
-    wT = np.array([1 - case.varpi] + [case.varpi / 4] * 4)
+    tq = getattr(case, "thermal_q", 5)
+    wT = w9 if tq == 9 else np.array([1 - case.varpi] + [case.varpi / 4] * 4)
     n = case.nx * case.ny
     f = w9[:, None] + amp_f * (2 * uniform01(seed, 9 * n).reshape(9, n) - 1)
-    g = (case.T0 + 0.3) * wT[:, None] + amp_g * (2 * uniform01(seed + 1, 5 * n).reshape(5, n) - 1)
-    solid = (case.flags.reshape(-1) != 0)
+    g = (case.T0 + 0.3) * wT[:, None] + amp_g * (2 * uniform01(seed + 1, tq * n).reshape(tq, n) - 1)
+    flags = case.flags.reshape(-1)
+    solid = np.array([k != 0 and case.walls[k - 1].scheme == HALFWAY for k in flags], dtype=bool)
     f[:, solid] = 0.0
     g[:, solid] = 0.0
-    return f.reshape(9, case.ny, case.nx), g.reshape(5, case.ny, case.nx)
+    return f.reshape(9, case.ny, case.nx), g.reshape(tq, case.ny, case.nx)
 
 
 def obstacle_channel(nx: int = 37, H: int = 11, frac: float = 0.12, seed: int = 1, U0: float = 0.04,
@@ -403,3 +410,12 @@ def cavity_nee(n: int = 64, Ra: float = 1e3, Pr: float = 0.71, Ma: float = 0.1, 
     kin = dict(KINETIC_CONVECTION if kinetic is None else kinetic)
     return Case("cavity_nee", n + 1, n + 1, False, False, flags, walls, nu=nu, alpha=alpha, g_beta=g_beta, T0=T0,
                 delta_T=dT, T_init=Ti, L=float(n), meta=dict(Ra=Ra, Pr=Pr, Ma=Ma, nodes=True), **kin)
+
+
+def with_d2q9_temperature(case: Case, theta: float = 1.0, zeta_q: float | None = None,
+                          zeta_eps: float | None = None) -> Case:
+    """The same problem solved with the D2Q9 temperature model of Eqs. 31-33
+    (same alpha; zeta_e and zeta_nu kept; zeta_q, zeta_eps default to them)."""
+    return replace(case, thermal_q=9, theta=float(theta),
+                   zeta_q=case.zeta_e if zeta_q is None else zeta_q,
+                   zeta_eps=case.zeta_e if zeta_eps is None else zeta_eps)

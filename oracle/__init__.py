@@ -58,15 +58,18 @@ class OrcParams(C.Structure):
         ("s8_literal", C.c_int32),
         ("T_init", C.c_void_p),
         ("wall_scheme", C.c_void_p),
+        ("thermal_q", C.c_int32),
+        ("theta", C.c_double),
+        ("zeta_q", C.c_double), ("zeta_eps", C.c_double),
     ]
 
 
 class OrcRates(C.Structure):
     _fields_ = [
-        ("s", C.c_double * 9), ("z", C.c_double * 5),
+        ("s", C.c_double * 9), ("z", C.c_double * 9),
         ("g_beta", C.c_double), ("T0", C.c_double),
         ("ax", C.c_double), ("ay", C.c_double), ("varpi", C.c_double),
-        ("s8_literal", C.c_int32),
+        ("s8_literal", C.c_int32), ("tq", C.c_int32), ("theta", C.c_double),
     ]
 
 
@@ -95,6 +98,8 @@ def lib():
             L.orc_get_rates.argtypes = [C.c_void_p, C.POINTER(OrcRates)]
             L.orc_tables.argtypes = [dp, dp, dp, dp, C.POINTER(C.c_int), C.POINTER(C.c_int), dp]
             L.orc_threads_available.restype = C.c_int
+            L.orc_thermal_q.restype = C.c_int
+            L.orc_thermal_q.argtypes = [C.c_void_p]
             _lib = L
     return _lib
 
@@ -113,24 +118,30 @@ def tables():
     return dict(M=M, Minv=Mi, N=N, Ninv=Ni, ex=np.array(ex[:]), ey=np.array(ey[:]), w=w)
 
 
-def make_rates(s, z, g_beta=0.0, T0=0.0, ax=0.0, ay=0.0, varpi=0.5, s8_literal=False) -> OrcRates:
+def make_rates(s, z, g_beta=0.0, T0=0.0, ax=0.0, ay=0.0, varpi=0.5, s8_literal=False, theta=1.0) -> OrcRates:
+    """z has 5 entries (D2Q5 temperature, Eq. 29) or 9 (the D2Q9 model, Eq. 32)."""
     r = OrcRates()
     for k in range(9):
         r.s[k] = float(s[k])
-    for k in range(5):
+    for k in range(len(z)):
         r.z[k] = float(z[k])
     r.g_beta, r.T0, r.ax, r.ay, r.varpi = g_beta, T0, ax, ay, varpi
     r.s8_literal = int(bool(s8_literal))
+    r.tq = 9 if len(z) == 9 else 5
+    r.theta = float(theta)
     return r
 
 
 def collide_node(rates: OrcRates, fbar, g):
-    """One collision (Eq. 8 then Eq. 24) at one node. Returns (f*, g*, (rho, ux, uy, T))."""
+    """One collision (Eq. 8, then Eq. 24 or the D2Q9 model) at one node.
+    Returns (f*, g*, (rho, ux, uy, T))."""
+    tq = rates.tq
     fbar = np.ascontiguousarray(fbar, dtype=np.float64)
-    g = np.ascontiguousarray(g, dtype=np.float64)
-    fo = np.zeros(9); go = np.zeros(5); mac = np.zeros(4)
-    lib().orc_collide_node(C.byref(rates), _dptr(fbar), _dptr(g), _dptr(fo), _dptr(go), _dptr(mac))
-    return fo, go, mac
+    gin = np.zeros(9)
+    gin[:tq] = np.asarray(g, dtype=np.float64)[:tq]
+    fo = np.zeros(9); go = np.zeros(9); mac = np.zeros(4)
+    lib().orc_collide_node(C.byref(rates), _dptr(fbar), _dptr(gin), _dptr(fo), _dptr(go), _dptr(mac))
+    return fo, go[:tq], mac
 
 
 class OracleLattice:
@@ -159,6 +170,10 @@ class OracleLattice:
         p.s8_literal = int(bool(s8_literal))
         p.T_init = Ti.ctypes.data if Ti is not None else None
         p.wall_scheme = ws.ctypes.data
+        p.thermal_q = int(getattr(case, "thermal_q", 5))
+        p.theta = float(getattr(case, "theta", 1.0))
+        p.zeta_q = float(getattr(case, "zeta_q", 1.0))
+        p.zeta_eps = float(getattr(case, "zeta_eps", 1.0))
         self._p = p
         h = lib().orc_create(C.byref(p))
         if not h:
@@ -166,6 +181,7 @@ class OracleLattice:
         self._h = h
         if threads != 1:
             lib().orc_set_threads(h, threads)
+        self.tq = lib().orc_thermal_q(h)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -188,22 +204,22 @@ class OracleLattice:
         return tuple(out)
 
     def populations(self):
-        f = np.zeros((9, self.ny, self.nx)); g = np.zeros((5, self.ny, self.nx))
+        f = np.zeros((9, self.ny, self.nx)); g = np.zeros((self.tq, self.ny, self.nx))
         lib().orc_get_populations(self._h, _dptr(f), _dptr(g))
         return f, g
 
     def set_populations(self, f, g):
         f = np.ascontiguousarray(f, dtype=np.float64); g = np.ascontiguousarray(g, dtype=np.float64)
-        assert f.size == 9 * self.nx * self.ny and g.size == 5 * self.nx * self.ny
+        assert f.size == 9 * self.nx * self.ny and g.size == self.tq * self.nx * self.ny
         lib().orc_set_populations(self._h, _dptr(f), _dptr(g))
 
     def update_node(self, f_src, g_src, x: int, y: int):
         """One step at node (x, y) reading the external state (f_src, g_src)."""
-        fo = np.zeros(9); go = np.zeros(5)
+        fo = np.zeros(9); go = np.zeros(9)
         rc = lib().orc_update_node(self._h, _dptr(f_src), _dptr(g_src), int(x), int(y), _dptr(fo), _dptr(go))
         if rc != 0:
             raise ValueError("solid node")
-        return fo, go
+        return fo, go[:self.tq]
 
     def nusselt(self, side: int, L: float | None = None, dT: float | None = None) -> float:
         """Mean Nusselt number on a frame wall (Eq. 39, reading A8).

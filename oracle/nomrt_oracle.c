@@ -17,6 +17,9 @@
  *            streaming f_bar_i(x + e_i, t + 1) = f_bar*_i(x, t) (Eq. 9).
  *   heat   : D2Q5, n* = n - Q (n - n_eq) (Eq. 24), n = N g (Eq. 26),
  *            n_eq from Eq. 28, Q from Eq. 29, N^-1 from Eq. A2; streaming Eq. 25.
+ *            Or the D2Q9 temperature model of Eqs. 31-33: n = M g with the
+ *            D2Q9 basis (reading A13), n_eq = M g_eq with g_eq of Eq. 31, Q of
+ *            Eq. 32, alpha = c_s^2 (1/zeta_alpha - 1/2).
  *   force  : F = g beta (T - T0) j + a (Eq. 4).
  *   macro  : rho = sum f_bar (Eq. 18), rho0 u = sum e f_bar + rho0 F / 2
  *            (Eq. 19 under the incompressible approximation, Sec. 2.1),
@@ -41,6 +44,9 @@
  *       macroscopics the (N+1)-th collision would use.
  *   A8  Nusselt (Eq. 39): second-order one-sided gradient at the halfway wall,
  *       dT/dn = (9 T_1/2 - T_3/2 - 8 T_w) / 3, midpoint average along the wall.
+ *   A13 the D2Q9 temperature model's transformation (not printed): the D2Q9
+ *       non-orthogonal basis M of Eq. 13. Its walls: anti-bounce-back with the
+ *       even part of Eq. 31 at (T_w, u_w), bounce-back when adiabatic.
  *   A9  residual: max(|u - u_prev|_2 / |u|_2, |T - T_prev|_2 / |T|_2) over
  *       fluid nodes (u as a vector field), against the previous call's snapshot.
  */
@@ -129,14 +135,20 @@ typedef struct {
     int32_t s8_literal;        /* 1: the printed S~_8 of Eq. 17 (reading A2) */
     const double *T_init;      /* ny*nx or NULL (T0 everywhere) */
     const int32_t *wall_scheme; /* n_walls or NULL: 0 halfway (solid cells), 1 non-equilibrium extrapolation */
+    int32_t thermal_q;         /* 5: D2Q5 (Sec. 2.2); 9: the D2Q9 model of Eqs. 31-33 */
+    double theta;              /* the switch of Eq. 31, 0 or 1 (D2Q9 model) */
+    double zeta_q, zeta_eps;   /* kinetic rates of Eq. 32 (D2Q9 model) */
 } orc_params;
 
-/* Per-node collision inputs. s[9] is Lambda of Eq. 20, z[5] is Q of Eq. 29. */
+/* Per-node collision inputs. s[9] is Lambda of Eq. 20; z is Q of Eq. 29 (its
+ * first 5 entries, tq = 5) or of Eq. 32 (9 entries, tq = 9). */
 typedef struct {
     double s[9];
-    double z[5];
+    double z[9];
     double g_beta, T0, ax, ay, varpi;
     int32_t s8_literal;
+    int32_t tq;
+    double theta;
 } orc_rates;
 
 typedef struct {
@@ -149,7 +161,8 @@ typedef struct {
     uint8_t *nee_dir; /* per cell: 0, or i in 1..8 with the fluid node x_f = x + e_i of a boundary node */
     orc_rates r;
     double *f[2]; /* [9][ny*nx] */
-    double *g[2]; /* [5][ny*nx] */
+    double *g[2]; /* [tq][ny*nx] */
+    int tq;
     int cur;
     double *snap; /* residual snapshot [3][ny*nx], NULL until first call */
     int nthreads;
@@ -160,11 +173,12 @@ typedef struct {
 /* The flow collision of Sec. 2.1 at one node, followed by the heat collision of
  * Sec. 2.2. fbar and g are the post-streaming populations; the outputs are the
  * post-collision populations and (rho, ux, uy, T). */
-void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[5],
-                      double fstar[9], double gstar[5], double macro[4]) {
-    /* Eq. 27: temperature. */
+void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[9],
+                      double fstar[9], double gstar[9], double macro[4]) {
+    const int tq = r->tq == 9 ? 9 : 5;
+    /* Eq. 27: temperature (the sum over the thermal lattice). */
     double T = 0.0;
-    for (int i = 0; i < 5; ++i) T += g[i];
+    for (int i = 0; i < tq; ++i) T += g[i];
     /* Eq. 4: Boussinesq buoyancy plus the external acceleration. */
     double Fx = r->ax;
     double Fy = r->ay + r->g_beta * (T - r->T0);
@@ -220,21 +234,44 @@ void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[5
         for (int k = 0; k < 9; ++k) fstar[i] += MINV9[i][k] * ms[k];
     }
 
-    /* Eq. 26: n = N g. */
-    double n[5];
-    for (int k = 0; k < 5; ++k) {
-        n[k] = 0.0;
-        for (int i = 0; i < 5; ++i) n[k] += N5[k][i] * g[i];
-    }
-    /* Eq. 28. */
-    double neq[5] = {T, ux * T, uy * T, r->varpi * T, 0.0};
-    /* Eq. 24 with Q of Eq. 29. */
-    double ns[5];
-    for (int k = 0; k < 5; ++k) ns[k] = n[k] - r->z[k] * (n[k] - neq[k]);
-    /* g* = N^-1 n* (Eq. A2). */
-    for (int i = 0; i < 5; ++i) {
-        gstar[i] = 0.0;
-        for (int k = 0; k < 5; ++k) gstar[i] += NINV5[i][k] * ns[k];
+    if (tq == 9) {
+        /* D2Q9 temperature model: g_eq of Eq. 31, n = M g and n_eq = M g_eq
+         * (reading A13), n* = n - Q (n - n_eq) with Q of Eq. 32, g* = M^-1 n*. */
+        double geq[9], n[9], neq[9], ns[9];
+        for (int i = 0; i < 9; ++i) {
+            double eu = EX[i] * ux + EY[i] * uy;
+            geq[i] = W9[i] * T * (1.0 + eu / CS2 + r->theta * (eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2)));
+        }
+        for (int k = 0; k < 9; ++k) {
+            n[k] = 0.0;
+            neq[k] = 0.0;
+            for (int i = 0; i < 9; ++i) {
+                n[k] += M9[k][i] * g[i];
+                neq[k] += M9[k][i] * geq[i];
+            }
+        }
+        for (int k = 0; k < 9; ++k) ns[k] = n[k] - r->z[k] * (n[k] - neq[k]);
+        for (int i = 0; i < 9; ++i) {
+            gstar[i] = 0.0;
+            for (int k = 0; k < 9; ++k) gstar[i] += MINV9[i][k] * ns[k];
+        }
+    } else {
+        /* Eq. 26: n = N g. */
+        double n[5];
+        for (int k = 0; k < 5; ++k) {
+            n[k] = 0.0;
+            for (int i = 0; i < 5; ++i) n[k] += N5[k][i] * g[i];
+        }
+        /* Eq. 28. */
+        double neq[5] = {T, ux * T, uy * T, r->varpi * T, 0.0};
+        /* Eq. 24 with Q of Eq. 29. */
+        double ns[5];
+        for (int k = 0; k < 5; ++k) ns[k] = n[k] - r->z[k] * (n[k] - neq[k]);
+        /* g* = N^-1 n* (Eq. A2). */
+        for (int i = 0; i < 5; ++i) {
+            gstar[i] = 0.0;
+            for (int k = 0; k < 5; ++k) gstar[i] += NINV5[i][k] * ns[k];
+        }
     }
     if (macro) {
         macro[0] = rho;
@@ -246,15 +283,26 @@ void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[5
 
 /* Fill the rate vectors from the transport coefficients:
  * nu = cs^2 (1/s_nu - 1/2) (Sec. 2.1), alpha = cs_T^2 (1/zeta_alpha - 1/2) with
- * cs_T^2 = varpi / 2 (Sec. 2.2). s0 = s1 = s2 = 1 and zeta0 = 1 as in Eqs. 20, 29. */
+ * cs_T^2 = varpi / 2 (Sec. 2.2) or cs^2 for the D2Q9 model (Eq. 33 text).
+ * s0 = s1 = s2 = 1 and zeta0 = 1 as in Eqs. 20, 29, 32. */
 void orc_rates_from_params(const orc_params *p, orc_rates *r) {
     double s_nu = 1.0 / (0.5 + p->nu / CS2);
-    double csT2 = 0.5 * p->varpi;
-    double z_alpha = 1.0 / (0.5 + p->alpha / csT2);
     double s[9] = {1.0, 1.0, 1.0, p->s_e, s_nu, s_nu, p->s_q, p->s_q, p->s_eps};
-    double z[5] = {1.0, z_alpha, z_alpha, p->zeta_e, p->zeta_nu};
     memcpy(r->s, s, sizeof s);
-    memcpy(r->z, z, sizeof z);
+    r->tq = p->thermal_q == 9 ? 9 : 5;
+    r->theta = p->theta;
+    if (r->tq == 9) {
+        /* Eq. 32 with alpha = c_s^2 (1/zeta_alpha - 1/2) */
+        double z_alpha = 1.0 / (0.5 + p->alpha / CS2);
+        double z[9] = {1.0, z_alpha, z_alpha, p->zeta_e, p->zeta_nu, p->zeta_nu, p->zeta_q, p->zeta_q, p->zeta_eps};
+        memcpy(r->z, z, sizeof z);
+    } else {
+        /* Eq. 29 with alpha = c_sT^2 (1/zeta_alpha - 1/2), c_sT^2 = varpi/2 */
+        double csT2 = 0.5 * p->varpi;
+        double z_alpha = 1.0 / (0.5 + p->alpha / csT2);
+        double z[9] = {1.0, z_alpha, z_alpha, p->zeta_e, p->zeta_nu, 0, 0, 0, 0};
+        memcpy(r->z, z, sizeof z);
+    }
     r->g_beta = p->g_beta;
     r->T0 = p->T0;
     r->ax = p->ax;
@@ -289,7 +337,7 @@ static int is_nee(const orc_lattice *L, int c) {
  * post-collision state (fsrc, gsrc) by Eqs. 9 and 25, with the wall rules of
  * reading A5 on links whose source cell is solid. */
 static void gather(const orc_lattice *L, const double *fsrc, const double *gsrc, int x, int y,
-                   double fin[9], double gin[5]) {
+                   double fin[9], double gin[9]) {
     const int nxy = L->nx * L->ny;
     const int self = y * L->nx + x;
     for (int i = 0; i < 9; ++i) {
@@ -303,11 +351,22 @@ static void gather(const orc_lattice *L, const double *fsrc, const double *gsrc,
             double uwx = L->wall_u[2 * (k - 1)], uwy = L->wall_u[2 * (k - 1) + 1];
             fin[i] = fsrc[OPP[i] * nxy + self] + 2.0 * W9[i] * RHO0 * (EX[i] * uwx + EY[i] * uwy) / CS2;
         }
-        if (i < 5) {
+        if (i < L->tq) {
             if (k == 0) {
                 gin[i] = gsrc[i * nxy + src];
             } else if (L->wall_kind[k - 1] == 0) {
-                gin[i] = -gsrc[OPP[i] * nxy + self] + 2.0 * (L->r.varpi / 4.0) * L->wall_T[k - 1];
+                /* anti-bounce-back with the even part of the equilibrium at the wall:
+                 * (varpi/4) T_w for Eq. 30; w_i T_w [1 + theta((e.u)^2/(2cs^4) - u^2/(2cs^2))] for Eq. 31 */
+                double even;
+                if (L->tq == 9) {
+                    double uwx = L->wall_u[2 * (k - 1)], uwy = L->wall_u[2 * (k - 1) + 1];
+                    double eu = EX[i] * uwx + EY[i] * uwy;
+                    even = W9[i] * L->wall_T[k - 1] *
+                           (1.0 + L->r.theta * (eu * eu / (2.0 * CS2 * CS2) - (uwx * uwx + uwy * uwy) / (2.0 * CS2)));
+                } else {
+                    even = (L->r.varpi / 4.0) * L->wall_T[k - 1];
+                }
+                gin[i] = -gsrc[OPP[i] * nxy + self] + 2.0 * even;
             } else {
                 gin[i] = gsrc[OPP[i] * nxy + self];
             }
@@ -322,9 +381,13 @@ static double feq_i(int i, double rho, double ux, double uy) {
     return W9[i] * (rho + RHO0 * (eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - (ux * ux + uy * uy) / (2.0 * CS2)));
 }
 
-static double geq_i(int i, double T, double ux, double uy, double varpi) {
-    if (i == 0) return (1.0 - varpi) * T;
-    return 0.25 * varpi * T + 0.5 * (EX[i] * ux + EY[i] * uy) * T;
+static double geq_i(const orc_lattice *L, int i, double T, double ux, double uy) {
+    if (L->tq == 9) { /* Eq. 31 */
+        double eu = EX[i] * ux + EY[i] * uy;
+        return W9[i] * T * (1.0 + eu / CS2 + L->r.theta * (eu * eu / (2.0 * CS2 * CS2) - (ux * ux + uy * uy) / (2.0 * CS2)));
+    }
+    if (i == 0) return (1.0 - L->r.varpi) * T; /* Eq. 30 */
+    return 0.25 * L->r.varpi * T + 0.5 * (EX[i] * ux + EY[i] * uy) * T;
 }
 
 /* Non-equilibrium extrapolation (Z. Guo, C. Zheng, B. Shi, Chin. Phys. 11 (2002)
@@ -336,11 +399,11 @@ static double geq_i(int i, double T, double ux, double uy, double varpi) {
  * with rho_b = rho_f, T_b = T_w for a fixed temperature and T_b = T_f for an
  * adiabatic wall; rho_f, u_f, T_f by Eqs. 18, 19, 27 with the force of Eq. 4. */
 static void nee_gather(const orc_lattice *L, const double *fsrc, const double *gsrc, int x, int y,
-                       double fin[9], double gin[5]) {
+                       double fin[9], double gin[9]) {
     int c = y * L->nx + x;
     int d = L->nee_dir[c];
     int xf = wrap(x + EX[d], L->nx, L->px), yf = wrap(y + EY[d], L->ny, L->py);
-    double ff[9], gf[5];
+    double ff[9], gf[9];
     gather(L, fsrc, gsrc, xf, yf, ff, gf);
     double rho = 0.0, T = 0.0, jx = 0.0, jy = 0.0;
     for (int i = 0; i < 9; ++i) {
@@ -348,21 +411,20 @@ static void nee_gather(const orc_lattice *L, const double *fsrc, const double *g
         jx += EX[i] * ff[i];
         jy += EY[i] * ff[i];
     }
-    for (int i = 0; i < 5; ++i) T += gf[i];
+    for (int i = 0; i < L->tq; ++i) T += gf[i];
     double Fx = L->r.ax, Fy = L->r.ay + L->r.g_beta * (T - L->r.T0);
     double ux = (jx + 0.5 * RHO0 * Fx) / RHO0, uy = (jy + 0.5 * RHO0 * Fy) / RHO0;
     int k = L->flags[c];
     double uwx = L->wall_u[2 * (k - 1)], uwy = L->wall_u[2 * (k - 1) + 1];
     double Tb = L->wall_kind[k - 1] == 0 ? L->wall_T[k - 1] : T;
     for (int i = 0; i < 9; ++i) fin[i] = feq_i(i, rho, uwx, uwy) + (ff[i] - feq_i(i, rho, ux, uy));
-    for (int i = 0; i < 5; ++i)
-        gin[i] = geq_i(i, Tb, uwx, uwy, L->r.varpi) + (gf[i] - geq_i(i, T, ux, uy, L->r.varpi));
+    for (int i = 0; i < L->tq; ++i) gin[i] = geq_i(L, i, Tb, uwx, uwy) + (gf[i] - geq_i(L, i, T, ux, uy));
 }
 
 /* The populations an updated cell collides: pulled for fluid, extrapolated for
  * boundary nodes. */
 static void pre_collision(const orc_lattice *L, const double *fsrc, const double *gsrc, int x, int y,
-                          double fin[9], double gin[5]) {
+                          double fin[9], double gin[9]) {
     if (L->nee_dir[y * L->nx + x]) nee_gather(L, fsrc, gsrc, x, y, fin, gin);
     else gather(L, fsrc, gsrc, x, y, fin, gin);
 }
@@ -397,6 +459,7 @@ orc_lattice *orc_create(const orc_params *p) {
         L->wall_scheme[k] = p->wall_scheme ? p->wall_scheme[k] : 0;
     }
     orc_rates_from_params(p, &L->r);
+    L->tq = L->r.tq;
     for (size_t c = 0; c < nxy; ++c)
         if (L->flags[c] > p->n_walls) { orc_destroy(L); return NULL; }
     for (int y = 0; y < L->ny; ++y)
@@ -421,15 +484,14 @@ orc_lattice *orc_create(const orc_params *p) {
         }
     for (int b = 0; b < 2; ++b) {
         L->f[b] = (double *)calloc(9 * nxy, sizeof(double));
-        L->g[b] = (double *)calloc(5 * nxy, sizeof(double));
+        L->g[b] = (double *)calloc((size_t)L->tq * nxy, sizeof(double));
     }
     /* Reading A4: rest equilibrium, f_bar_i = w_i rho0, g_i = g_eq_i(T_init, 0) (Eqs. 22, 30). */
     for (size_t c = 0; c < nxy; ++c) {
         if (is_solid(L, (int)c)) continue;
         double T = p->T_init ? p->T_init[c] : p->T0;
         for (int i = 0; i < 9; ++i) L->f[0][i * nxy + c] = W9[i] * RHO0;
-        L->g[0][0 * nxy + c] = (1.0 - p->varpi) * T;
-        for (int i = 1; i < 5; ++i) L->g[0][i * nxy + c] = 0.25 * p->varpi * T;
+        for (int i = 0; i < L->tq; ++i) L->g[0][i * nxy + c] = geq_i(L, i, T, 0.0, 0.0);
     }
     return L;
 }
@@ -462,11 +524,11 @@ void orc_step(orc_lattice *L, int64_t nsteps) {
             for (int x = 0; x < L->nx; ++x) {
                 int c = y * L->nx + x;
                 if (is_solid(L, c)) continue;
-                double fin[9], gin[5], fo[9], go[5];
+                double fin[9], gin[9], fo[9], go[9];
                 pre_collision(L, fs, gs, x, y, fin, gin);
                 orc_collide_node(&L->r, fin, gin, fo, go, NULL);
                 for (int i = 0; i < 9; ++i) fd[i * nxy + c] = fo[i];
-                for (int i = 0; i < 5; ++i) gd[i * nxy + c] = go[i];
+                for (int i = 0; i < L->tq; ++i) gd[i * nxy + c] = go[i];
             }
         }
         L->cur = 1 - L->cur;
@@ -482,7 +544,7 @@ void orc_macro(const orc_lattice *L, double *rho, double *ux, double *uy, double
             int c = y * L->nx + x;
             double mac[4] = {0, 0, 0, 0};
             if (!is_solid(L, c)) {
-                double fin[9], gin[5], fo[9], go[5];
+                double fin[9], gin[9], fo[9], go[9];
                 pre_collision(L, L->f[L->cur], L->g[L->cur], x, y, fin, gin);
                 orc_collide_node(&L->r, fin, gin, fo, go, mac);
             }
@@ -498,28 +560,28 @@ void orc_macro(const orc_lattice *L, double *rho, double *ux, double *uy, double
 void orc_get_populations(const orc_lattice *L, double *f, double *g) {
     size_t nxy = (size_t)L->nx * L->ny;
     if (f) memcpy(f, L->f[L->cur], 9 * nxy * sizeof(double));
-    if (g) memcpy(g, L->g[L->cur], 5 * nxy * sizeof(double));
+    if (g) memcpy(g, L->g[L->cur], (size_t)L->tq * nxy * sizeof(double));
 }
 
 void orc_set_populations(orc_lattice *L, const double *f, const double *g) {
     size_t nxy = (size_t)L->nx * L->ny;
     if (f) memcpy(L->f[L->cur], f, 9 * nxy * sizeof(double));
-    if (g) memcpy(L->g[L->cur], g, 5 * nxy * sizeof(double));
+    if (g) memcpy(L->g[L->cur], g, (size_t)L->tq * nxy * sizeof(double));
     for (size_t c = 0; c < nxy; ++c)
         if (is_solid(L, (int)c)) {
             for (int i = 0; i < 9; ++i) L->f[L->cur][i * nxy + c] = 0.0;
-            for (int i = 0; i < 5; ++i) L->g[L->cur][i * nxy + c] = 0.0;
+            for (int i = 0; i < L->tq; ++i) L->g[L->cur][i * nxy + c] = 0.0;
         }
 }
 
 /* One step at a single fluid node, reading an external post-collision state
  * (fsrc [9][ny*nx], gsrc [5][ny*nx]) through this lattice's flags and walls.
- * Used to check single sampled nodes of very large lattices. Returns -1 if the
+ * Used to check single sampled nodes of very large lattices. gsrc: [tq][ny*nx]. Returns -1 if the
  * node is solid. */
 int orc_update_node(const orc_lattice *L, const double *fsrc, const double *gsrc, int x, int y,
-                    double fout[9], double gout[5]) {
+                    double fout[9], double gout[9]) {
     if (is_solid(L, y * L->nx + x)) return -1;
-    double fin[9], gin[5];
+    double fin[9], gin[9];
     pre_collision(L, fsrc, gsrc, x, y, fin, gin);
     orc_collide_node(&L->r, fin, gin, fout, gout, NULL);
     return 0;
@@ -609,3 +671,5 @@ int orc_threads_available(void) {
     return 1;
 #endif
 }
+
+int orc_thermal_q(const orc_lattice *L) { return L->tq; }
