@@ -42,7 +42,8 @@ typedef enum {
 } lbm_status;
 
 /* Population storage. The FP32/FP16 forms store deviations from the rest state,
- * f_bar_i - w_i rho0 and g_i - w^T_i T0 (w^T = (1 - varpi, varpi/4 x4)), and
+ * f_bar_i - w_i rho0 and g_i - w^T_i T0 (w^T = (1 - varpi, varpi/4 x4) for
+ * D2Q5, w^T = w of the D2Q9 lattice for the model of Eqs. 31-33), and
  * compute moments and collision in FP32. LBM_F64 stores f_bar and g as they are
  * and computes in FP64. */
 typedef enum { LBM_F64 = 0, LBM_F32_SHIFTED = 1, LBM_F16_SHIFTED = 2 } lbm_storage;
@@ -95,6 +96,16 @@ typedef struct {
     double zeta_e, zeta_nu;       /* kinetic rates of Eq. 29, each in (0, 2) */
     double varpi;                 /* Eq. 28 parameter, in (0, 1); the paper uses 1/2 */
     const double *T_init;         /* optional ny*nx initial temperature; NULL = T0 */
+    /* Temperature lattice. 0 or 5: D2Q5 (Sec. 2.2, Eqs. 24-30). 9: the D2Q9
+     * model of Eqs. 31-33, whose moments come from M of Eq. 13, with
+     *   g_eq_i = w_i T [1 + e_i.u / c_s^2 + theta ((e_i.u)^2 / (2 c_s^4) - u^2 / (2 c_s^2))],
+     * zeta_alpha = 1 / (1/2 + alpha / c_s^2), c_s^2 = 1/3, and varpi unused
+     * (it must still lie in (0, 1)). Its halfway Dirichlet wall is
+     *   g_i(x) = -g*_opp(i)(x) + 2 w_i T [1 + theta ((e_i.u_w)^2 / (2 c_s^4) - u_w^2 / (2 c_s^2))].
+     * The step variants TMA and VEC8 and fused batches take D2Q5 lattices only. */
+    int32_t thermal_q;
+    double theta;                 /* Eq. 31: 1 keeps the second-order terms, 0 drops them (thermal_q = 9) */
+    double zeta_q, zeta_eps;      /* Eq. 32 rates of the q and epsilon moments (thermal_q = 9), in (0, 2) */
 } lbm_params;
 
 typedef struct lbm_lattice lbm_lattice; /* opaque; owned by the library */
@@ -172,8 +183,9 @@ lbm_status lbm_nusselt(lbm_lattice *h, int32_t side, double L, double delta_T, d
 lbm_status lbm_residual(lbm_lattice *h, double *r);
 
 /* Export / import the post-collision state as FP64 f_bar [9][ny][nx] and
- * g [5][ny][nx] host arrays (shift added back or removed; solid cells read 0
- * and are forced to 0 on import). Either pointer may be NULL. Synchronises. */
+ * g [TQ][ny][nx] host arrays, TQ = 5 or 9 (thermal_q) (shift added back or
+ * removed; solid cells read 0 and are forced to 0 on import). Either pointer
+ * may be NULL. Synchronises. */
 lbm_status lbm_get_populations(lbm_lattice *h, double *f9, double *g5);
 lbm_status lbm_set_populations(lbm_lattice *h, const double *f9, const double *g5);
 

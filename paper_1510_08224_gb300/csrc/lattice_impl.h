@@ -20,6 +20,7 @@ void batch_detach(lbm_batch *b, lbm_lattice *h);
 
 // Device layout of one lattice, all offsets from the block base.
 struct Layout {
+    int nq = 14;                // population planes per buffer: 9 + 5 or 9 + 9
     int pitch = 0;
     size_t plane = 0;           // elements per plane
     size_t pop_bytes = 0;       // one buffer

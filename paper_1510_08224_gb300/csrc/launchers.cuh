@@ -97,8 +97,11 @@ template <typename S>
 cudaError_t launch_nee(const KParams &p, int src, cudaStream_t st) {
     using C = typename Store<S>::C;
     if (p.n_nee == 0) return cudaSuccess;
-    k_nee<S><<<(p.n_nee + 127) / 128, 128, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p), p.nee,
-                                                    p.n_nee);
+    const dim3 grid((p.n_nee + 127) / 128);
+    if (p.tq == 9)
+        k_nee<S, 9><<<grid, 128, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p), p.nee, p.n_nee);
+    else
+        k_nee<S, 5><<<grid, 128, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p), p.nee, p.n_nee);
     return cudaGetLastError();
 }
 
@@ -122,7 +125,8 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
         // five (FP32) or seven (FP16) resident blocks per SM
         if (variant == kStepAuto) {
             variant = kStepVec4;
-            q.config = sizeof(S) == 4 ? 1 : 3;
+            // the D2Q9 temperature model keeps nine more values per cell in registers: four blocks per SM
+            q.config = p.tq == 9 ? 0 : (sizeof(S) == 4 ? 1 : 3);
         }
     } else {
         variant = kStepScalar;
@@ -130,11 +134,16 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
     return launch_step_variant<S>(q, variant, src, st);
 }
 
-template <typename S>
-cudaError_t launch_step_variant(const KParams &p, int variant, int src, cudaStream_t st) {
+// TQ: temperature populations per node (5: D2Q5; 9: the D2Q9 model, which
+// has the scalar and four-cell kernels only).
+template <typename S, int TQ>
+cudaError_t launch_step_tq(const KParams &p, int variant, int src, cudaStream_t st) {
     using C = typename Store<S>::C;
     if constexpr (Store<S>::kShifted) {
-        if (variant == kStepTma) return launch_tma<S>(p, src, st);
+        if (variant == kStepTma) {
+            if constexpr (TQ == 5) return launch_tma<S>(p, src, st);
+            else return cudaErrorInvalidValue;
+        }
         if (variant == kStepVec4) {
             // four cells per thread, 128 threads per block, one row per block row; the
             // config asks ptxas for 4, 5, 6, 7 or 8 resident blocks per SM
@@ -144,15 +153,15 @@ cudaError_t launch_step_variant(const KParams &p, int variant, int src, cudaStre
             const Geom g = make_geom(p);
             const RatesC<float> r = make_rates<float>(p);
             switch (p.config) {
-                case 1: k_step4<S, 5><<<grid, 128, 0, st>>>(pl, g, r); break;
-                case 2: k_step4<S, 6><<<grid, 128, 0, st>>>(pl, g, r); break;
-                case 3: k_step4<S, 7><<<grid, 128, 0, st>>>(pl, g, r); break;
-                case 4: k_step4<S, 8><<<grid, 128, 0, st>>>(pl, g, r); break;
-                default: k_step4<S, 4><<<grid, 128, 0, st>>>(pl, g, r); break;
+                case 1: k_step4<S, 5, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
+                case 2: k_step4<S, 6, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
+                case 3: k_step4<S, 7, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
+                case 4: k_step4<S, 8, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
+                default: k_step4<S, 4, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
             }
             return cudaGetLastError();
         }
-        if constexpr (sizeof(S) == 2) {
+        if constexpr (sizeof(S) == 2 && TQ == 5) {
             if (variant == kStepVec8) {
                 // eight cells per thread (FP16 only)
                 const int threads_x = p.pitch / 8;
@@ -169,15 +178,21 @@ cudaError_t launch_step_variant(const KParams &p, int variant, int src, cudaStre
     const dim3 b = step_block();
     const int gy = (p.ny + (int)b.y - 1) / (int)b.y;
     const dim3 grid((p.nx + b.x - 1) / b.x, gy < 65535 ? gy : 65535);
-    k_step<S><<<grid, b, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p));
+    if (variant != kStepScalar && variant != kStepAuto) return cudaErrorInvalidValue;
+    k_step<S, TQ><<<grid, b, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p));
     return cudaGetLastError();
+}
+
+template <typename S>
+cudaError_t launch_step_variant(const KParams &p, int variant, int src, cudaStream_t st) {
+    return p.tq == 9 ? launch_step_tq<S, 9>(p, variant, src, st) : launch_step_tq<S, 5>(p, variant, src, st);
 }
 
 template <typename S>
 cudaError_t launch_init_rows(const KParams &p, int buf, int r0, int r1, const double *T, cudaStream_t st) {
     const dim3 grid((p.pitch + 127) / 128, r1 - r0);
     k_init_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, T, p.T_ref, p.varpi,
-                                         Store<S>::kShifted ? 1 : 0);
+                                         Store<S>::kShifted ? 1 : 0, p.tq);
     return cudaGetLastError();
 }
 
@@ -185,8 +200,12 @@ template <typename S>
 cudaError_t launch_macro_rows(const KParams &p, int buf, int r0, int r1, double *out, cudaStream_t st) {
     using C = typename Store<S>::C;
     const dim3 grid((p.nx + 127) / 128, r1 - r0);
-    k_macro_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p), r0, r1,
-                                          p.rho_ref, p.T_ref, out);
+    if (p.tq == 9)
+        k_macro_rows<S, 9><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p), r0, r1,
+                                                 p.rho_ref, p.T_ref, out);
+    else
+        k_macro_rows<S, 5><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p), r0, r1,
+                                                 p.rho_ref, p.T_ref, out);
     return cudaGetLastError();
 }
 
@@ -194,7 +213,7 @@ template <typename S>
 cudaError_t launch_export_rows(const KParams &p, int buf, int r0, int r1, double *out, cudaStream_t st) {
     const dim3 grid((p.nx + 127) / 128, r1 - r0);
     k_export_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, p.rho_ref, p.T_ref,
-                                           p.varpi, out);
+                                           p.varpi, p.tq, out);
     return cudaGetLastError();
 }
 
@@ -203,15 +222,19 @@ cudaError_t launch_import_rows(const KParams &p, int buf, int r0, int r1, const 
                                cudaStream_t st) {
     const dim3 grid((p.nx + 127) / 128, r1 - r0);
     k_import_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, p.rho_ref, p.T_ref,
-                                           p.varpi, in, which);
+                                           p.varpi, p.tq, in, which);
     return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_nusselt(const KParams &p, int buf, int side, double L, double dT, double *partials,
                            cudaStream_t st) {
-    k_nusselt<S><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), side, L, dT, p.T_ref,
-                                                    partials);
+    if (p.tq == 9)
+        k_nusselt<S, 9><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), side, L, dT,
+                                                           p.T_ref, partials);
+    else
+        k_nusselt<S, 5><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), side, L, dT,
+                                                           p.T_ref, partials);
     return cudaGetLastError();
 }
 
@@ -219,8 +242,12 @@ template <typename S>
 cudaError_t launch_residual(const KParams &p, int buf, double *snap, int have_snap, double *partials,
                             cudaStream_t st) {
     using C = typename Store<S>::C;
-    k_residual<S><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p),
-                                                     p.T_ref, snap, p.plane, have_snap, partials);
+    if (p.tq == 9)
+        k_residual<S, 9><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p),
+                                                            p.T_ref, snap, p.plane, have_snap, partials);
+    else
+        k_residual<S, 5><<<kRedBlocks, kRedThreads, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p),
+                                                            p.T_ref, snap, p.plane, have_snap, partials);
     return cudaGetLastError();
 }
 

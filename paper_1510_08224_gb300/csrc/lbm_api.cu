@@ -18,7 +18,6 @@
 
 using nomrt::KParams;
 using nomrt::Layout;
-using nomrt::kQ;
 using nomrt::kSolid;
 using nomrt::WallDev;
 
@@ -38,12 +37,15 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 size_t elem_bytes(int storage) { return storage == LBM_F64 ? 8 : storage == LBM_F32_SHIFTED ? 4 : 2; }
 
-Layout make_layout(int nx, int ny, int storage, int n_walls, int n_nee) {
+int thermal_q(const lbm_params *p) { return p->thermal_q == 9 ? 9 : 5; }
+
+Layout make_layout(int nx, int ny, int storage, int n_walls, int n_nee, int tq) {
     Layout L;
     const size_t eb = elem_bytes(storage);
+    L.nq = 9 + tq;
     L.pitch = (int)align_up((size_t)nx, 128 / eb);
     L.plane = (size_t)ny * L.pitch;
-    L.pop_bytes = align_up(L.plane * eb * kQ, kAlign);
+    L.pop_bytes = align_up(L.plane * eb * L.nq, kAlign);
     size_t o = 0;
     L.off_pop[0] = o; o += L.pop_bytes;
     L.off_pop[1] = o; o += L.pop_bytes;
@@ -51,7 +53,7 @@ Layout make_layout(int nx, int ny, int storage, int n_walls, int n_nee) {
     L.off_flags = o; o += align_up(L.plane, kAlign);
     L.off_walls = o; o += align_up(sizeof(WallDev) * (size_t)(n_walls + 1), kAlign);
     L.off_snap = o; o += align_up(3 * L.plane * sizeof(double), kAlign);
-    const size_t row_bytes = (size_t)kQ * nx * sizeof(double);
+    const size_t row_bytes = (size_t)L.nq * nx * sizeof(double);
     // at most 8192 rows per chunk keeps every chunked launch under the 65535 grid-y limit
     L.stage_rows = (int)std::max<size_t>(1, std::min<size_t>({(size_t)ny, kStageBytes / row_bytes, (size_t)8192}));
     L.off_stage = o; o += align_up(row_bytes * L.stage_rows, kAlign);
@@ -69,11 +71,13 @@ struct Derived {
 };
 
 // Rates from the transport coefficients: nu = c_s^2 (1/s_nu - 1/2) (Sec. 2.1),
-// alpha = c_sT^2 (1/zeta_alpha - 1/2) with c_sT^2 = varpi/2 (Sec. 2.2).
+// alpha = c_sT^2 (1/zeta_alpha - 1/2) with c_sT^2 = varpi/2 (Sec. 2.2), or
+// c_sT^2 = c_s^2 for the D2Q9 temperature model (Eq. 33).
 Derived derive(const lbm_params *p) {
     Derived d;
     d.s_nu = 1.0 / (0.5 + p->nu / kCs2);
-    d.z_a = 1.0 / (0.5 + p->alpha / (0.5 * p->varpi));
+    const double csT2 = thermal_q(p) == 9 ? kCs2 : 0.5 * p->varpi;
+    d.z_a = 1.0 / (0.5 + p->alpha / csT2);
     return d;
 }
 
@@ -121,6 +125,11 @@ std::string validate(const lbm_params *p) {
     if (!(std::isfinite(p->varpi) && p->varpi > 0.0 && p->varpi < 1.0)) return "varpi must be in (0, 1)";
     if (!(std::isfinite(p->nu) && p->nu > 0.0)) return "nu must be > 0";
     if (!(std::isfinite(p->alpha) && p->alpha > 0.0)) return "alpha must be > 0";
+    if (p->thermal_q != 0 && p->thermal_q != 5 && p->thermal_q != 9) return "thermal_q must be 0, 5 or 9";
+    if (thermal_q(p) == 9) {
+        if (!in_open_02(p->zeta_q) || !in_open_02(p->zeta_eps)) return "zeta_q and zeta_eps must be in (0, 2)";
+        if (!std::isfinite(p->theta)) return "theta must be finite";
+    }
     Derived d = derive(p);
     const double rates[7] = {d.s_nu, p->s_e, p->s_q, p->s_eps, d.z_a, p->zeta_e, p->zeta_nu};
     const char *names[7] = {"s_nu", "s_e", "s_q", "s_eps", "zeta_alpha", "zeta_e", "zeta_nu"};
@@ -235,7 +244,7 @@ size_t lbm_footprint_bytes(const lbm_params *p) {
         g_create_error = why;
         return 0;
     }
-    return make_layout(p->nx, p->ny, p->storage, p->n_walls, count_nee(p)).total;
+    return make_layout(p->nx, p->ny, p->storage, p->n_walls, count_nee(p), thermal_q(p)).total;
 }
 
 lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, size_t device_bytes,
@@ -254,7 +263,7 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     h->n_walls = p->n_walls;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
     const int n_nee = count_nee(p);
-    h->lay = make_layout(p->nx, p->ny, p->storage, p->n_walls, n_nee);
+    h->lay = make_layout(p->nx, p->ny, p->storage, p->n_walls, n_nee, thermal_q(p));
     h->L = &launchers_for(p->storage);
     const size_t need = h->lay.total;
     auto bail = [&](lbm_status st, const std::string &m) {
@@ -310,12 +319,20 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     std::vector<WallDev> hw((size_t)p->n_walls + 1);
     std::memset(hw.data(), 0, sizeof(WallDev) * hw.size());
     const double T_ref = p->storage == LBM_F64 ? 0.0 : p->T0;
+    const int tq = thermal_q(p);
     for (int k = 1; k <= p->n_walls; ++k) {
         const lbm_wall &w = p->walls[k - 1];
         for (int i = 0; i < 9; ++i) hw[k].cf[i] = 2.0 * kW[i] * 1.0 * (kEx[i] * w.ux + kEy[i] * w.uy) / kCs2;
         if (w.kind == LBM_T_DIRICHLET) {
             hw[k].tsgn = -1.0;
             hw[k].tb = 0.5 * p->varpi * (w.T - T_ref);
+            // D2Q9 model: twice the even part of Eq. 31 at the wall, less the storage shift
+            const double uw2 = w.ux * w.ux + w.uy * w.uy;
+            for (int i = 0; i < 9; ++i) {
+                const double eu = kEx[i] * w.ux + kEy[i] * w.uy;
+                const double even = kW[i] * w.T * (1.0 + p->theta * (eu * eu / (2.0 * kCs2 * kCs2) - uw2 / (2.0 * kCs2)));
+                hw[k].tb9[i] = 2.0 * (even - kW[i] * T_ref);
+            }
         } else {
             hw[k].tsgn = 1.0;
             hw[k].tb = 0.0;
@@ -354,6 +371,10 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     kp.varpi = p->varpi;
     kp.rho_ref = p->storage == LBM_F64 ? 0.0 : 1.0;
     kp.T_ref = T_ref;
+    kp.tq = tq;
+    kp.theta = tq == 9 ? p->theta : 0.0;
+    kp.z_q = tq == 9 ? p->zeta_q : 0.0;
+    kp.z_eps = tq == 9 ? p->zeta_eps : 0.0;
     kp.nee = reinterpret_cast<const int2 *>(h->mem + h->lay.off_nee);
     kp.n_nee = (int)hnee.size();
     kp.nee_dir = reinterpret_cast<const uint8_t *>(h->mem + h->lay.off_nee_dir);
@@ -438,6 +459,8 @@ lbm_status lbm_set_step_kernel(lbm_lattice *h, int32_t variant, int32_t config) 
     const int32_t n = lbm_step_kernel_count(h->storage, variant);
     if (n == 0) return fail(h, LBM_EINVAL, "step variant not available for this storage");
     if (config < 0 || config >= n) return fail(h, LBM_EINVAL, "step kernel config out of range");
+    if (h->kp.tq == 9 && (variant == LBM_STEP_TMA || variant == LBM_STEP_VEC8))
+        return fail(h, LBM_EINVAL, "the D2Q9 temperature model has the SCALAR and VEC4 step kernels only");
     h->kp.variant = variant;
     h->kp.config = config;
     return LBM_OK;
@@ -447,7 +470,7 @@ lbm_status lbm_read_macro(lbm_lattice *h, double *rho, double *ux, double *uy, d
     if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
     double *outs[4] = {rho, ux, uy, T};
     const int nx = h->nx;
-    const int rows = std::max(1, h->lay.stage_rows * kQ / 4);
+    const int rows = std::max(1, h->lay.stage_rows * h->lay.nq / 4);
     for (int r0 = 0; r0 < h->ny; r0 += rows) {
         const int r1 = std::min(h->ny, r0 + rows);
         const size_t n = (size_t)(r1 - r0) * nx;
@@ -527,7 +550,7 @@ lbm_status lbm_get_populations(lbm_lattice *h, double *f9, double *g5) {
         const int r1 = std::min(h->ny, r0 + h->lay.stage_rows);
         const size_t n = (size_t)(r1 - r0) * nx;
         LBM_CUDA(h, h->L->export_rows(h->kp, h->cur, r0, r1, h->stage(), h->stream), "export kernel");
-        for (int q = 0; q < kQ; ++q) {
+        for (int q = 0; q < h->lay.nq; ++q) {
             double *dst = q < 9 ? (f9 ? f9 + q * nxy : nullptr) : (g5 ? g5 + (q - 9) * nxy : nullptr);
             if (dst)
                 LBM_CUDA(h,
@@ -550,7 +573,7 @@ lbm_status lbm_set_populations(lbm_lattice *h, const double *f9, const double *g
     for (int r0 = 0; r0 < h->ny; r0 += h->lay.stage_rows) {
         const int r1 = std::min(h->ny, r0 + h->lay.stage_rows);
         const size_t n = (size_t)(r1 - r0) * nx;
-        for (int q = 0; q < kQ; ++q) {
+        for (int q = 0; q < h->lay.nq; ++q) {
             const double *src = q < 9 ? (f9 ? f9 + q * nxy : nullptr) : (g5 ? g5 + (q - 9) * nxy : nullptr);
             if (src)
                 LBM_CUDA(h,

@@ -9,8 +9,10 @@
 
 namespace nomrt {
 
-// Number of populations per node: 9 (D2Q9 flow, Eq. 5) + 5 (D2Q5 temperature).
+// Number of populations per node: 9 (D2Q9 flow, Eq. 5) + 5 (D2Q5 temperature);
+// kQmax with the D2Q9 temperature model of Eqs. 31-33 (9 + 9).
 constexpr int kQ = 14;
+constexpr int kQmax = 18;
 // Link-map value of a solid cell (and of the row padding).
 constexpr uint8_t kSolid = 0xFF;
 // Fixed number of blocks of the reduction kernels (deterministic sums).
@@ -41,6 +43,7 @@ struct WallDev {
     double uwx, uwy;  // wall velocity
     double nee;       // 1: node-based wall (non-equilibrium extrapolation), 0: halfway
     double adiabatic; // 1: adiabatic, 0: fixed temperature
+    double tb9[9];    // D2Q9 temperature model: g_i = tsgn g*_opp(i) + tb9[i]
 };
 
 // Everything a kernel needs to know about one lattice, in FP64; each kernel
@@ -58,6 +61,8 @@ struct KParams {
     double z_a, z_e, z_nu;            // Eq. 29
     double g_beta, T0, ax, ay, varpi; // Eq. 4, Eq. 28
     double rho_ref, T_ref;            // storage shift (0 for FP64 storage)
+    int tq;                           // temperature lattice: 5 (D2Q5) or 9 (Eqs. 31-33)
+    double theta, z_q, z_eps;         // Eq. 31 switch, Eq. 32 rates (tq = 9)
     const int2 *nee;                  // boundary nodes of NEE walls: (cell offset, dir | wall id << 8)
     int n_nee;
     const uint8_t *nee_dir;           // per cell: 0, or the direction i of the nearest fluid node x + e_i
@@ -78,7 +83,7 @@ struct Launchers {
     cudaError_t (*init_rows)(const KParams &, int buf, int r0, int r1, const double *T, cudaStream_t st);
     // macroscopics of rows [r0, r1) into out[4][(r1-r0)*nx] (rho, ux, uy, T)
     cudaError_t (*macro_rows)(const KParams &, int buf, int r0, int r1, double *out, cudaStream_t st);
-    // FP64 export / import of rows [r0, r1): out/in [kQ][(r1-r0)*nx]
+    // FP64 export / import of rows [r0, r1): out/in [9 + tq][(r1-r0)*nx]
     cudaError_t (*export_rows)(const KParams &, int buf, int r0, int r1, double *out, cudaStream_t st);
     cudaError_t (*import_rows)(const KParams &, int buf, int r0, int r1, const double *in, int which,
                                cudaStream_t st);

@@ -95,6 +95,8 @@ struct RatesC {
     C hx;                         // ax / 2
     C h2e, h2nu, h23eps;          // 2 (1 - s_e/2), 2 (1 - s_nu/2), (2/3)(1 - s_eps/2)
     C varpi;                      // Eq. 28
+    // D2Q9 temperature model (Eqs. 31-33): zeta_e, zeta_nu, zeta_q, zeta_eps and theta
+    C z_e, z_nu, om_zq, z_q, om_zeps, z_eps, theta;
 };
 
 template <typename C>
@@ -125,14 +127,21 @@ inline RatesC<C> make_rates(const KParams &p) {
     r.h2nu = (C)(2.0 * (1.0 - 0.5 * p.s_nu));
     r.h23eps = (C)(2.0 / 3.0 * (1.0 - 0.5 * p.s_eps));
     r.varpi = (C)p.varpi;
+    r.z_e = (C)p.z_e;
+    r.z_nu = (C)p.z_nu;
+    r.om_zq = (C)(1.0 - p.z_q);
+    r.z_q = (C)p.z_q;
+    r.om_zeps = (C)(1.0 - p.z_eps);
+    r.z_eps = (C)p.z_eps;
+    r.theta = (C)p.theta;
     return r;
 }
 
 // Kernel arguments: typed plane pointers of both buffers.
 template <typename S>
 struct Planes {
-    const S *src[kQ];
-    S *dst[kQ];
+    const S *src[kQmax];
+    S *dst[kQmax];
     __device__ __forceinline__ const S *src_at(int q) const { return src[q]; }
     __device__ __forceinline__ S *dst_at(int q) const { return dst[q]; }
 };
@@ -153,7 +162,7 @@ inline Planes<S> make_planes(const KParams &p, int src) {
     Planes<S> pl;
     S *a = static_cast<S *>(p.pop[src]);
     S *b = static_cast<S *>(p.pop[1 - src]);
-    for (int q = 0; q < kQ; ++q) {
+    for (int q = 0; q < kQmax; ++q) {
         pl.src[q] = a + (size_t)q * p.plane;
         pl.dst[q] = b + (size_t)q * p.plane;
     }
@@ -181,9 +190,9 @@ __device__ __forceinline__ bool kept_cell(const Geom &g, int off) {
 
 // Post-streaming populations at fluid cell (x, y): Eq. 9 and Eq. 25 in pull
 // form, then the halfway wall rules on the links flagged in `m`.
-template <typename S>
+template <typename S, int TQ = 5>
 __device__ __forceinline__ void pull(const S *const *src, const Geom &g, int x, int y, unsigned m,
-                                     typename Store<S>::C f[9], typename Store<S>::C t[5]) {
+                                     typename Store<S>::C f[9], typename Store<S>::C t[TQ]) {
     using St = Store<S>;
     int xm = x - 1, xp = x + 1, ym = y - 1, yp = y + 1;
     if (g.px) {
@@ -210,6 +219,12 @@ __device__ __forceinline__ void pull(const S *const *src, const Geom &g, int x, 
     t[2] = St::ld(src[11] + rm + x);
     t[3] = St::ld(src[12] + r0 + xp);
     t[4] = St::ld(src[13] + rp + x);
+    if constexpr (TQ == 9) {
+        t[5] = St::ld(src[14] + rm + xm);
+        t[6] = St::ld(src[15] + rm + xp);
+        t[7] = St::ld(src[16] + rp + xp);
+        t[8] = St::ld(src[17] + rp + xm);
+    }
     if (m) {
         using C = typename St::C;
         const int sidx[9] = {r0 + x, r0 + xm, rm + x, r0 + xp, rp + x, rm + xm, rm + xp, rp + xp, rp + xm};
@@ -219,7 +234,9 @@ __device__ __forceinline__ void pull(const S *const *src, const Geom &g, int x, 
             if (m & (1u << (i - 1))) {
                 const WallDev *w = g.walls + g.flags[sidx[i]];
                 f[i] = St::ld(src[opp[i]] + r0 + x) + (C)__ldg(&w->cf[i]);
-                if (i < 5) t[i] = (C)__ldg(&w->tsgn) * St::ld(src[9 + opp[i]] + r0 + x) + (C)__ldg(&w->tb);
+                if (i < TQ)
+                    t[i] = (C)__ldg(&w->tsgn) * St::ld(src[9 + opp[i]] + r0 + x) +
+                           (C)__ldg(TQ == 9 ? &w->tb9[i] : &w->tb);
             }
         }
     }
@@ -234,10 +251,11 @@ struct Macro {
     C drho, ux, uy, dT, Fx, Fy;
 };
 
-template <typename C>
-__device__ __forceinline__ Macro<C> macro_of(const RatesC<C> &r, const C f[9], const C t[5]) {
+template <typename C, int TQ = 5>
+__device__ __forceinline__ Macro<C> macro_of(const RatesC<C> &r, const C f[9], const C t[TQ]) {
     Macro<C> M;
-    M.dT = ((t[0] + t[1]) + (t[2] + t[3])) + t[4];
+    if constexpr (TQ == 9) M.dT = (((t[0] + t[1]) + (t[2] + t[3])) + (t[4] + t[5])) + ((t[6] + t[7]) + t[8]);
+    else M.dT = ((t[0] + t[1]) + (t[2] + t[3])) + t[4];
     M.Fx = r.ax;
     M.Fy = r.Fy0 + r.g_beta * M.dT;
     M.drho = (((f[0] + f[1]) + (f[2] + f[3])) + (f[4] + f[5])) + ((f[6] + f[7]) + f[8]);
@@ -255,11 +273,11 @@ __device__ __forceinline__ Macro<C> macro_of(const RatesC<C> &r, const C f[9], c
 //   f_b = f_eq(rho_f, u_w) + [f(x_f) - f_eq(rho_f, u_f)]
 //   g_b = g_eq(T_b, u_w)   + [g(x_f) - g_eq(T_f, u_f)]
 // in the storage frame (the shift cancels in the differences).
-template <typename S>
+template <typename S, int TQ = 5>
 __device__ __forceinline__ void nee_rebuild(const S *const *src, const Geom &g,
                                             const RatesC<typename Store<S>::C> &r, int x, int y, int d,
                                             const WallDev *w, typename Store<S>::C f[9],
-                                            typename Store<S>::C t[5]) {
+                                            typename Store<S>::C t[TQ]) {
     using C = typename Store<S>::C;
     const int ex[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
     const int ey[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -269,8 +287,8 @@ __device__ __forceinline__ void nee_rebuild(const S *const *src, const Geom &g,
     if (g.px) xf = (xf < 0) ? xf + g.nx : (xf >= g.nx ? xf - g.nx : xf);
     if (g.py) yf = (yf < 0) ? yf + g.ny : (yf >= g.ny ? yf - g.ny : yf);
     const unsigned mf = g.mask[yf * g.pitch + xf];
-    pull<S>(src, g, xf, yf, mf, f, t);
-    const Macro<C> M = macro_of<C>(r, f, t);
+    pull<S, TQ>(src, g, xf, yf, mf, f, t);
+    const Macro<C> M = macro_of<C, TQ>(r, f, t);
     const C uwx = (C)w->uwx, uwy = (C)w->uwy;
     const C Tf = r.T_ref + M.dT;
     const C Tb = w->adiabatic != 0.0 ? Tf : (C)w->Tw;
@@ -281,24 +299,74 @@ __device__ __forceinline__ void nee_rebuild(const S *const *src, const Geom &g,
         f[i] += w9[i] * ((C(3) * euw + C(4.5) * euw * euw - C(1.5) * uw2) -
                          (C(3) * euf + C(4.5) * euf * euf - C(1.5) * uf2));
     }
-    t[0] += (C(1) - r.varpi) * (Tb - Tf);
+    if constexpr (TQ == 9) {
+        // Eq. 31 at (T_b, u_w) and (T_f, u_f)
 #pragma unroll
-    for (int i = 1; i < 5; ++i) {
-        const C euw = ex[i] * uwx + ey[i] * uwy, euf = ex[i] * M.ux + ey[i] * M.uy;
-        t[i] += C(0.25) * r.varpi * (Tb - Tf) + C(0.5) * (euw * Tb - euf * Tf);
+        for (int i = 0; i < 9; ++i) {
+            const C euw = ex[i] * uwx + ey[i] * uwy, euf = ex[i] * M.ux + ey[i] * M.uy;
+            t[i] += w9[i] * (Tb * (C(1) + C(3) * euw + r.theta * (C(4.5) * euw * euw - C(1.5) * uw2)) -
+                             Tf * (C(1) + C(3) * euf + r.theta * (C(4.5) * euf * euf - C(1.5) * uf2)));
+        }
+    } else {
+        t[0] += (C(1) - r.varpi) * (Tb - Tf);
+#pragma unroll
+        for (int i = 1; i < 5; ++i) {
+            const C euw = ex[i] * uwx + ey[i] * uwy, euf = ex[i] * M.ux + ey[i] * M.uy;
+            t[i] += C(0.25) * r.varpi * (Tb - Tf) + C(0.5) * (euw * Tb - euf * Tf);
+        }
     }
 }
 
 // Flow collision (Eq. 8 with Eqs. 16, 17, 20 under the incompressible reading,
 // rho0 = 1) and temperature collision (Eq. 24 with Eqs. 28, 29), in place.
+// D2Q9 temperature model (Eqs. 31-33, reading: the transformation is M of
+// Eq. 13): n = M g on pair sums, n* = n - Q (n - n_eq) with n_eq = M g_eq of
+// Eq. 31 in the storage frame, g = M^-1 n*. n0 = T - T_ref is given.
 template <typename C>
-__device__ __forceinline__ void collide(const RatesC<C> &r, C f[9], C t[5]) {
-    // ---- D2Q5: n = N g (Eq. 26), relax (Eq. 24), g = N^-1 n (Eq. A2)
-    const C n0 = ((t[0] + t[1]) + (t[2] + t[3])) + t[4];  // T - T_ref
-    const C n1 = t[1] - t[3];
-    const C n2 = t[2] - t[4];
-    const C n3 = (t[1] + t[3]) + (t[2] + t[4]);
-    const C n4 = (t[1] + t[3]) - (t[2] + t[4]);
+__device__ __forceinline__ void thermal_q9(const RatesC<C> &r, C t[9], C n0, C ux, C uy, C uu) {
+    const C b13 = t[1] + t[3], e13 = t[1] - t[3];
+    const C b24 = t[2] + t[4], e24 = t[2] - t[4];
+    const C b57 = t[5] + t[7], e57 = t[5] - t[7];
+    const C b68 = t[6] + t[8], e68 = t[6] - t[8];
+    const C Dt = b57 + b68;
+    const C n6 = e57 + e68, n7 = e57 - e68;
+    const C n1 = e13 + n7, n2 = e24 + n6;
+    const C n3 = (b13 + b24) + (Dt + Dt);
+    const C n4 = b13 - b24, n5 = b57 - b68, n8 = Dt;
+    const C T = r.T_ref + n0;
+    const C q1 = r.om_a * n1 + r.z_a * (T * ux);
+    const C q2 = r.om_a * n2 + r.z_a * (T * uy);
+    const C q3 = r.om_ze * n3 + r.z_e * (C(2.0 / 3.0) * n0 + r.theta * (T * uu));
+    const C q4 = r.om_zn * n4 + r.z_nu * (r.theta * (T * (ux * ux - uy * uy)));
+    const C q5 = r.om_zn * n5 + r.z_nu * (r.theta * (T * (ux * uy)));
+    const C q6 = r.om_zq * n6 + r.z_q * (C(1.0 / 3.0) * (T * uy));
+    const C q7 = r.om_zq * n7 + r.z_q * (C(1.0 / 3.0) * (T * ux));
+    const C q8 = r.om_zeps * n8 + r.z_eps * (C(1.0 / 9.0) * n0 + C(1.0 / 3.0) * (r.theta * (T * uu)));
+    const C A = C(0.25) * q3 - C(0.5) * q8;
+    const C B = C(0.25) * q4;
+    const C h1 = C(0.5) * (q1 - q7);
+    const C h2 = C(0.5) * (q2 - q6);
+    const C P = C(0.25) * (q8 + q5);
+    const C Q = C(0.25) * (q6 + q7);
+    const C R = C(0.25) * (q8 - q5);
+    const C Sx = C(0.25) * (q6 - q7);
+    t[0] = (n0 - q3) + q8;
+    t[1] = (A + B) + h1;
+    t[3] = (A + B) - h1;
+    t[2] = (A - B) + h2;
+    t[4] = (A - B) - h2;
+    t[5] = P + Q;
+    t[7] = P - Q;
+    t[6] = R + Sx;
+    t[8] = R - Sx;
+}
+
+template <typename C, int TQ = 5>
+__device__ __forceinline__ void collide(const RatesC<C> &r, C f[9], C t[TQ]) {
+    // temperature first: the buoyancy of Eq. 4 needs it
+    C n0;
+    if constexpr (TQ == 9) n0 = (((t[0] + t[1]) + (t[2] + t[3])) + (t[4] + t[5])) + ((t[6] + t[7]) + t[8]);
+    else n0 = ((t[0] + t[1]) + (t[2] + t[3])) + t[4];  // T - T_ref
     const C Fx = r.ax;
     const C Fy = r.Fy0 + r.g_beta * n0;  // Eq. 4
 
@@ -354,7 +422,16 @@ __device__ __forceinline__ void collide(const RatesC<C> &r, C f[9], C t[5]) {
     f[6] = R + Sx;
     f[8] = R - Sx;
 
-    // ---- D2Q5 relaxation with n_eq = (T, ux T, uy T, varpi T, 0)
+    if constexpr (TQ == 9) {
+        thermal_q9<C>(r, t, n0, ux, uy, uu);
+        return;
+    } else {
+    // ---- D2Q5: n = N g (Eq. 26), relaxation (Eq. 24) with n_eq = (T, ux T, uy T, varpi T, 0),
+    // g = N^-1 n* (Eq. A2)
+    const C n1 = t[1] - t[3];
+    const C n2 = t[2] - t[4];
+    const C n3 = (t[1] + t[3]) + (t[2] + t[4]);
+    const C n4 = (t[1] + t[3]) - (t[2] + t[4]);
     const C T = r.T_ref + n0;
     const C q1 = r.om_a * n1 + r.z_a * (ux * T);
     const C q2 = r.om_a * n2 + r.z_a * (uy * T);
@@ -366,6 +443,7 @@ __device__ __forceinline__ void collide(const RatesC<C> &r, C f[9], C t[5]) {
     t[3] = (c3 + c4) - C(0.5) * q1;
     t[2] = (c3 - c4) + C(0.5) * q2;
     t[4] = (c3 - c4) - C(0.5) * q2;
+    }
 }
 
 // ------------------------------------------- FP32 collision, explicit rounding
@@ -399,19 +477,63 @@ struct Ops<float2> {
     static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 };
 
+// thermal_q9 with every rounding explicit (T is float or float2).
+template <typename T>
+__device__ __forceinline__ void thermal_q9_x(const RatesC<float> &r, T t[9], T n0, T ux, T uy, T uu) {
+    using O = Ops<T>;
+    const T b13 = O::add(t[1], t[3]), e13 = O::sub(t[1], t[3]);
+    const T b24 = O::add(t[2], t[4]), e24 = O::sub(t[2], t[4]);
+    const T b57 = O::add(t[5], t[7]), e57 = O::sub(t[5], t[7]);
+    const T b68 = O::add(t[6], t[8]), e68 = O::sub(t[6], t[8]);
+    const T Dt = O::add(b57, b68);
+    const T n6 = O::add(e57, e68), n7 = O::sub(e57, e68);
+    const T n1 = O::add(e13, n7), n2 = O::add(e24, n6);
+    const T n3 = O::add(O::add(b13, b24), O::add(Dt, Dt));
+    const T n4 = O::sub(b13, b24), n5 = O::sub(b57, b68);
+    const T Tm = O::add(O::bc(r.T_ref), n0);
+    const T Tuu = O::mul(O::bc(r.theta), O::mul(Tm, uu));
+    const T q1 = O::fma(O::bc(r.om_a), n1, O::mul(O::bc(r.z_a), O::mul(Tm, ux)));
+    const T q2 = O::fma(O::bc(r.om_a), n2, O::mul(O::bc(r.z_a), O::mul(Tm, uy)));
+    const T q3 = O::fma(O::bc(r.om_ze), n3, O::mul(O::bc(r.z_e), O::fma(O::bc(2.0f / 3.0f), n0, Tuu)));
+    const T dxy = O::fma(ux, ux, O::mul(O::bc(-1.f), O::mul(uy, uy)));
+    const T q4 = O::fma(O::bc(r.om_zn), n4, O::mul(O::bc(r.z_nu), O::mul(O::bc(r.theta), O::mul(Tm, dxy))));
+    const T q5 = O::fma(O::bc(r.om_zn), n5, O::mul(O::bc(r.z_nu), O::mul(O::bc(r.theta), O::mul(Tm, O::mul(ux, uy)))));
+    const T q6 = O::fma(O::bc(r.om_zq), n6, O::mul(O::bc(r.z_q), O::mul(O::bc(1.0f / 3.0f), O::mul(Tm, uy))));
+    const T q7 = O::fma(O::bc(r.om_zq), n7, O::mul(O::bc(r.z_q), O::mul(O::bc(1.0f / 3.0f), O::mul(Tm, ux))));
+    const T q8 = O::fma(O::bc(r.om_zeps), Dt,
+                        O::mul(O::bc(r.z_eps), O::fma(O::bc(1.0f / 9.0f), n0, O::mul(O::bc(1.0f / 3.0f), Tuu))));
+    const T A = O::fma(O::bc(0.25f), q3, O::mul(O::bc(-0.5f), q8));
+    const T B = O::mul(O::bc(0.25f), q4);
+    const T h1 = O::mul(O::bc(0.5f), O::sub(q1, q7));
+    const T h2 = O::mul(O::bc(0.5f), O::sub(q2, q6));
+    const T P = O::mul(O::bc(0.25f), O::add(q8, q5));
+    const T Q = O::mul(O::bc(0.25f), O::add(q6, q7));
+    const T R = O::mul(O::bc(0.25f), O::sub(q8, q5));
+    const T Sx = O::mul(O::bc(0.25f), O::sub(q6, q7));
+    const T AB = O::add(A, B), AmB = O::sub(A, B);
+    t[0] = O::add(O::sub(n0, q3), q8);
+    t[1] = O::add(AB, h1);
+    t[3] = O::sub(AB, h1);
+    t[2] = O::add(AmB, h2);
+    t[4] = O::sub(AmB, h2);
+    t[5] = O::add(P, Q);
+    t[7] = O::sub(P, Q);
+    t[6] = O::add(R, Sx);
+    t[8] = O::sub(R, Sx);
+}
+
 // Same method as collide<float> (Eq. 8 with Eqs. 16, 17, 20; Eq. 24 with
 // Eqs. 28, 29; M and M^-1 of Eqs. 13 and A1 on pair sums), every rounding
 // explicit. T is float (one cell) or float2 (two cells).
-template <typename T>
-__device__ __forceinline__ void collide_x(const RatesC<float> &r, T f[9], T t[5]) {
+template <typename T, int TQ = 5>
+__device__ __forceinline__ void collide_x(const RatesC<float> &r, T f[9], T t[TQ]) {
     using O = Ops<T>;
-    // D2Q5 forward map (Eq. 26)
-    const T s13 = O::add(t[1], t[3]), s24 = O::add(t[2], t[4]);
-    const T n0 = O::add(O::add(O::add(t[0], t[1]), O::add(t[2], t[3])), t[4]);  // T - T_ref
-    const T n1 = O::sub(t[1], t[3]);
-    const T n2 = O::sub(t[2], t[4]);
-    const T n3 = O::add(s13, s24);
-    const T n4 = O::sub(s13, s24);
+    T n0;
+    if constexpr (TQ == 9)
+        n0 = O::add(O::add(O::add(O::add(t[0], t[1]), O::add(t[2], t[3])), O::add(t[4], t[5])),
+                    O::add(O::add(t[6], t[7]), t[8]));
+    else
+        n0 = O::add(O::add(O::add(t[0], t[1]), O::add(t[2], t[3])), t[4]);  // T - T_ref
     const T Fx = O::bc(r.ax);
     const T Fy = O::fma(O::bc(r.g_beta), n0, O::bc(r.Fy0));  // Eq. 4
     // D2Q9 forward map (Eq. 13)
@@ -469,7 +591,16 @@ __device__ __forceinline__ void collide_x(const RatesC<float> &r, T f[9], T t[5]
     f[7] = O::sub(P, Q);
     f[6] = O::add(R, Sx);
     f[8] = O::sub(R, Sx);
-    // D2Q5 relaxation (Eq. 24) and back map (Eq. A2)
+    if constexpr (TQ == 9) {
+        thermal_q9_x<T>(r, t, n0, ux, uy, uu);
+        return;
+    } else {
+    // D2Q5 forward map (Eq. 26), relaxation (Eq. 24) and back map (Eq. A2)
+    const T s13 = O::add(t[1], t[3]), s24 = O::add(t[2], t[4]);
+    const T n1 = O::sub(t[1], t[3]);
+    const T n2 = O::sub(t[2], t[4]);
+    const T n3 = O::add(s13, s24);
+    const T n4 = O::sub(s13, s24);
     const T Tm = O::add(O::bc(r.T_ref), n0);
     const T q1 = O::fma(O::bc(r.om_a), n1, O::mul(O::bc(r.z_a), O::mul(ux, Tm)));
     const T q2 = O::fma(O::bc(r.om_a), n2, O::mul(O::bc(r.z_a), O::mul(uy, Tm)));
@@ -482,33 +613,34 @@ __device__ __forceinline__ void collide_x(const RatesC<float> &r, T f[9], T t[5]
     t[3] = O::fma(O::bc(-0.5f), q1, c34);
     t[2] = O::fma(O::bc(0.5f), q2, c3m4);
     t[4] = O::fma(O::bc(-0.5f), q2, c3m4);
+    }
 }
 
 // Collide cells K and K + 1 of an N-cell group as one float2 pair, in place.
-template <int K, int N>
-__device__ __forceinline__ void collide_pair(const RatesC<float> &r, float f[9][N], float t[5][N]) {
-    float2 fp[9], tp[5];
+template <int K, int N, int TQ = 5>
+__device__ __forceinline__ void collide_pair(const RatesC<float> &r, float f[9][N], float t[TQ][N]) {
+    float2 fp[9], tp[TQ];
 #pragma unroll
     for (int i = 0; i < 9; ++i) fp[i] = make_float2(f[i][K], f[i][K + 1]);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) tp[i] = make_float2(t[i][K], t[i][K + 1]);
-    collide_x<float2>(r, fp, tp);
+    for (int i = 0; i < TQ; ++i) tp[i] = make_float2(t[i][K], t[i][K + 1]);
+    collide_x<float2, TQ>(r, fp, tp);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         f[i][K] = fp[i].x;
         f[i][K + 1] = fp[i].y;
     }
 #pragma unroll
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < TQ; ++i) {
         t[i][K] = tp[i].x;
         t[i][K + 1] = tp[i].y;
     }
 }
 
 // Halfway wall links of cell K of an N-cell group (link-map bytes mN), in place.
-template <typename S, int K, int N, typename PA, bool NC = true>
+template <typename S, int K, int N, typename PA, bool NC = true, int TQ = 5>
 __device__ __forceinline__ void wall_links(const PA &pl, const Geom &g, uint32_t mN, int x0, int r0, int rm,
-                                           int rp, float f[9][N], float t[5][N]) {
+                                           int rp, float f[9][N], float t[TQ][N]) {
     const unsigned m = (mN >> (8 * K)) & 0xFFu;
     if (m == 0 || m == kSolid) return;
     const int x = x0 + K;
@@ -524,25 +656,26 @@ __device__ __forceinline__ void wall_links(const PA &pl, const Geom &g, uint32_t
         if (m & (1u << (i - 1))) {
             const WallDev *w = g.walls + g.flags[sidx[i]];
             f[i][K] = Ld<S, NC>::one(pl.src_at(opp[i]) + r0 + x) + (float)__ldg(&w->cf[i]);
-            if (i < 5)
-                t[i][K] = (float)__ldg(&w->tsgn) * Ld<S, NC>::one(pl.src_at(9 + opp[i]) + r0 + x) + (float)__ldg(&w->tb);
+            if (i < TQ)
+                t[i][K] = (float)__ldg(&w->tsgn) * Ld<S, NC>::one(pl.src_at(9 + opp[i]) + r0 + x) +
+                          (float)__ldg(TQ == 9 ? &w->tb9[i] : &w->tb);
         }
     }
 }
 
 // Solid cell K of a group: write zeros (solid cells hold zeros).
-template <int K, int N>
-__device__ __forceinline__ void zero_solid(uint32_t mN, float f[9][N], float t[5][N]) {
+template <int K, int N, int TQ = 5>
+__device__ __forceinline__ void zero_solid(uint32_t mN, float f[9][N], float t[TQ][N]) {
     if (((mN >> (8 * K)) & 0xFFu) != kSolid) return;
 #pragma unroll
     for (int i = 0; i < 9; ++i) f[i][K] = 0.f;
 #pragma unroll
-    for (int i = 0; i < 5; ++i) t[i][K] = 0.f;
+    for (int i = 0; i < TQ; ++i) t[i][K] = 0.f;
 }
 
 // ------------------------------------------------------------------ kernels
 
-template <typename S>
+template <typename S, int TQ = 5>
 __global__ void __launch_bounds__(256) k_step(const Planes<S> pl, const Geom g, const RatesC<typename Store<S>::C> r) {
     using C = typename Store<S>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -551,21 +684,21 @@ __global__ void __launch_bounds__(256) k_step(const Planes<S> pl, const Geom g, 
         const int off = y * g.pitch + x;
         const unsigned m = __ldg(g.mask + off);
         if (m == kSolid) continue;
-        C f[9], t[5];
-        pull<S>(pl.src, g, x, y, m, f, t);
-        if constexpr (Store<S>::kShifted) collide_x<float>(r, f, t);
-        else collide<C>(r, f, t);
+        C f[9], t[TQ];
+        pull<S, TQ>(pl.src, g, x, y, m, f, t);
+        if constexpr (Store<S>::kShifted) collide_x<float, TQ>(r, f, t);
+        else collide<C, TQ>(r, f, t);
 #pragma unroll
         for (int q = 0; q < 9; ++q) Store<S>::st(pl.dst[q] + off, f[q]);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) Store<S>::st(pl.dst[9 + q] + off, t[q]);
+        for (int q = 0; q < TQ; ++q) Store<S>::st(pl.dst[9 + q] + off, t[q]);
     }
 }
 
 // Boundary nodes of NEE walls: rebuild (non-equilibrium extrapolation), collide,
 // store. Runs after a step kernel that skipped them (their link-map byte is
 // kSolid), reading the same source buffer.
-template <typename S>
+template <typename S, int TQ = 5>
 __global__ void __launch_bounds__(128) k_nee(const Planes<S> pl, const Geom g, const RatesC<typename Store<S>::C> r,
                                              const int2 *nee, int n) {
     using C = typename Store<S>::C;
@@ -574,20 +707,27 @@ __global__ void __launch_bounds__(128) k_nee(const Planes<S> pl, const Geom g, c
     const int2 e = nee[i];
     const int off = e.x, d = e.y & 0xFF, k = e.y >> 8;
     const int y = off / g.pitch, x = off - y * g.pitch;
-    C f[9], t[5];
-    nee_rebuild<S>(pl.src, g, r, x, y, d, g.walls + k, f, t);
-    if constexpr (Store<S>::kShifted) collide_x<float>(r, f, t);
-    else collide<C>(r, f, t);
+    C f[9], t[TQ];
+    nee_rebuild<S, TQ>(pl.src, g, r, x, y, d, g.walls + k, f, t);
+    if constexpr (Store<S>::kShifted) collide_x<float, TQ>(r, f, t);
+    else collide<C, TQ>(r, f, t);
 #pragma unroll
     for (int q = 0; q < 9; ++q) Store<S>::st(pl.dst[q] + off, f[q]);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) Store<S>::st(pl.dst[9 + q] + off, t[q]);
+    for (int q = 0; q < TQ; ++q) Store<S>::st(pl.dst[9 + q] + off, t[q]);
 }
 
 // Initial state (rest equilibrium, Eqs. 22, 30 at u = 0) in the storage frame.
+// The temperature weights of the storage frame: D2Q5 (Eq. 30 at u = 0, with
+// varpi of Eq. 28) or the D2Q9 weights (Eq. 31 at u = 0).
+__device__ __forceinline__ double thermal_weight(int q, int tq, double varpi) {
+    if (tq == 9) return q == 0 ? 4.0 / 9 : (q < 5 ? 1.0 / 9 : 1.0 / 36);
+    return q == 0 ? 1.0 - varpi : 0.25 * varpi;
+}
+
 template <typename S>
 __global__ void k_init_rows(const Planes<S> pl, const Geom g, int r0, int r1, const double *T, double T_ref,
-                            double varpi, int shifted) {
+                            double varpi, int shifted, int tq) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = r0 + blockIdx.y;
     if (x >= g.pitch || y >= r1) return;
@@ -599,14 +739,14 @@ __global__ void k_init_rows(const Planes<S> pl, const Geom g, int r0, int r1, co
         double v = fluid ? (shifted ? 0.0 : w9[q]) : 0.0;
         Store<S>::st(const_cast<S *>(pl.src[q]) + off, (typename Store<S>::C)v);
     }
-    for (int q = 0; q < 5; ++q) {
-        const double wT = q == 0 ? 1.0 - varpi : 0.25 * varpi;
+    for (int q = 0; q < tq; ++q) {
+        const double wT = thermal_weight(q, tq, varpi);
         double v = fluid ? wT * (Tn - T_ref) : 0.0;
         Store<S>::st(const_cast<S *>(pl.src[9 + q]) + off, (typename Store<S>::C)v);
     }
 }
 
-template <typename S>
+template <typename S, int TQ = 5>
 __global__ void k_macro_rows(const Planes<S> pl, const Geom g, const RatesC<typename Store<S>::C> r, int r0,
                              int r1, double rho_ref, double T_ref, double *out) {
     using C = typename Store<S>::C;
@@ -619,10 +759,10 @@ __global__ void k_macro_rows(const Planes<S> pl, const Geom g, const RatesC<type
     const unsigned d = g.nee_dir[y * g.pitch + x];
     double v[4] = {0, 0, 0, 0};
     if (m != kSolid || d != 0) {
-        C f[9], t[5];
-        if (m != kSolid) pull<S>(pl.src, g, x, y, m, f, t);
-        else nee_rebuild<S>(pl.src, g, r, x, y, (int)d, g.walls + g.flags[y * g.pitch + x], f, t);
-        Macro<C> M = macro_of<C>(r, f, t);
+        C f[9], t[TQ];
+        if (m != kSolid) pull<S, TQ>(pl.src, g, x, y, m, f, t);
+        else nee_rebuild<S, TQ>(pl.src, g, r, x, y, (int)d, g.walls + g.flags[y * g.pitch + x], f, t);
+        Macro<C> M = macro_of<C, TQ>(r, f, t);
         v[0] = rho_ref + (double)M.drho;
         v[1] = (double)M.ux;
         v[2] = (double)M.uy;
@@ -633,7 +773,7 @@ __global__ void k_macro_rows(const Planes<S> pl, const Geom g, const RatesC<type
 
 template <typename S>
 __global__ void k_export_rows(const Planes<S> pl, const Geom g, int r0, int r1, double rho_ref, double T_ref,
-                              double varpi, double *out) {
+                              double varpi, int tq, double *out) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = r0 + blockIdx.y;
     if (x >= g.nx || y >= r1) return;
@@ -642,10 +782,10 @@ __global__ void k_export_rows(const Planes<S> pl, const Geom g, int r0, int r1, 
     const int off = y * g.pitch + x;
     const bool fluid = kept_cell(g, off);
     const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-    for (int q = 0; q < kQ; ++q) {
+    for (int q = 0; q < 9 + tq; ++q) {
         double v = 0.0;
         if (fluid) {
-            double shift = q < 9 ? w9[q] * rho_ref : (q == 9 ? 1.0 - varpi : 0.25 * varpi) * T_ref;
+            double shift = q < 9 ? w9[q] * rho_ref : thermal_weight(q - 9, tq, varpi) * T_ref;
             v = (double)Store<S>::ld(pl.src[q] + off) + shift;
         }
         out[q * n + o] = v;
@@ -655,7 +795,7 @@ __global__ void k_export_rows(const Planes<S> pl, const Geom g, int r0, int r1, 
 // which: bit 0 = f planes present, bit 1 = g planes present
 template <typename S>
 __global__ void k_import_rows(const Planes<S> pl, const Geom g, int r0, int r1, double rho_ref, double T_ref,
-                              double varpi, const double *in, int which) {
+                              double varpi, int tq, const double *in, int which) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = r0 + blockIdx.y;
     if (x >= g.nx || y >= r1) return;
@@ -664,10 +804,10 @@ __global__ void k_import_rows(const Planes<S> pl, const Geom g, int r0, int r1, 
     const int off = y * g.pitch + x;
     const bool fluid = kept_cell(g, off);
     const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-    for (int q = 0; q < kQ; ++q) {
+    for (int q = 0; q < 9 + tq; ++q) {
         if (q < 9 && !(which & 1)) continue;
         if (q >= 9 && !(which & 2)) continue;
-        double shift = q < 9 ? w9[q] * rho_ref : (q == 9 ? 1.0 - varpi : 0.25 * varpi) * T_ref;
+        double shift = q < 9 ? w9[q] * rho_ref : thermal_weight(q - 9, tq, varpi) * T_ref;
         double v = fluid ? in[q * n + o] - shift : 0.0;
         Store<S>::st(const_cast<S *>(pl.src[q]) + off, (typename Store<S>::C)v);
     }
@@ -695,18 +835,21 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[W], double *parti
     }
 }
 
-// Temperature after the pull at one fluid cell (Eq. 27), FP64 accumulation.
-template <typename S>
+// Temperature after the pull at one fluid cell (Eq. 27; the zeroth moment of
+// the D2Q9 model), FP64 accumulation.
+template <typename S, int TQ>
 __device__ __forceinline__ double temperature_at(const Planes<S> &pl, const Geom &g, int x, int y, double T_ref) {
     using C = typename Store<S>::C;
     const unsigned m = g.mask[y * g.pitch + x];
-    C f[9], t[5];
-    pull<S>(pl.src, g, x, y, m, f, t);
-    return T_ref + ((((double)t[0] + (double)t[1]) + ((double)t[2] + (double)t[3])) + (double)t[4]);
+    C f[9], t[TQ];
+    pull<S, TQ>(pl.src, g, x, y, m, f, t);
+    double s = ((((double)t[0] + (double)t[1]) + ((double)t[2] + (double)t[3])) + (double)t[4]);
+    if constexpr (TQ == 9) s += (((double)t[5] + (double)t[6]) + ((double)t[7] + (double)t[8]));
+    return T_ref + s;
 }
 
 // Eq. 39 with the one-sided wall gradient; one thread per line along the wall.
-template <typename S>
+template <typename S, int TQ = 5>
 __global__ void __launch_bounds__(kRedThreads) k_nusselt(const Planes<S> pl, const Geom g, int side, double L,
                                                          double dT, double T_ref, double *partials) {
     const int along = side < 2 ? g.ny : g.nx;
@@ -725,8 +868,8 @@ __global__ void __launch_bounds__(kRedThreads) k_nusselt(const Planes<S> pl, con
         const WallDev *w = g.walls + k;
         if (w->tsgn > 0.0) continue;  // adiabatic: no wall temperature
         const double Tw = w->Tw;
-        const double T1 = temperature_at<S>(pl, g, x1, y1, T_ref);
-        const double T2 = temperature_at<S>(pl, g, x2, y2, T_ref);
+        const double T1 = temperature_at<S, TQ>(pl, g, x1, y1, T_ref);
+        const double T2 = temperature_at<S, TQ>(pl, g, x2, y2, T_ref);
         // halfway wall half a cell before c1; node-based wall on the wall node itself
         const double dTds = w->nee != 0.0 ? (-3.0 * Tw + 4.0 * T1 - T2) / 2.0 : (9.0 * T1 - T2 - 8.0 * Tw) / 3.0;
         const double dTdn = (side == 0 || side == 2) ? dTds : -dTds;
@@ -736,7 +879,7 @@ __global__ void __launch_bounds__(kRedThreads) k_nusselt(const Planes<S> pl, con
     block_reduce_store<2>(v, partials);
 }
 
-template <typename S>
+template <typename S, int TQ = 5>
 __global__ void __launch_bounds__(kRedThreads) k_residual(const Planes<S> pl, const Geom g,
                                                           const RatesC<typename Store<S>::C> r, double T_ref,
                                                           double *snap, size_t plane, int have_snap,
@@ -750,9 +893,9 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(const Planes<S> pl, co
         const int off = y * g.pitch + x;
         const unsigned m = g.mask[off];
         if (m == kSolid) continue;
-        C f[9], t[5];
-        pull<S>(pl.src, g, x, y, m, f, t);
-        Macro<C> M = macro_of<C>(r, f, t);
+        C f[9], t[TQ];
+        pull<S, TQ>(pl.src, g, x, y, m, f, t);
+        Macro<C> M = macro_of<C, TQ>(r, f, t);
         const double ux = (double)M.ux, uy = (double)M.uy, T = T_ref + (double)M.dT;
         if (have_snap) {
             const double a = ux - snap[off], b = uy - snap[plane + off], d = T - snap[2 * plane + off];
@@ -866,7 +1009,7 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
 // One warp's share of a row: cells x0..x0+3 of row y for each lane (x0 = base +
 // 4 lane). Every lane of the warp calls it with the same y. PA gives the plane
 // pointers (Planes or StridedPlanes).
-template <typename S, typename PA, bool NC = true>
+template <typename S, typename PA, bool NC = true, int TQ = 5>
 __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<float> &r, int x0, int y, int lane) {
     const int r0 = y * g.pitch;
     const bool inrow = x0 < g.pitch;
@@ -881,7 +1024,7 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
     }
     // rows of a non-periodic edge hold no fluid cell, so a warp that gets here has 0 < y < ny - 1
     const int rm = ym * g.pitch, rp = yp * g.pitch;
-    float f[9][4], t[5][4];
+    float f[9][4], t[TQ][4];
     ld_plane<S, 0, NC>(pl.src_at(0) + r0, g, x0, lane, inrow, f[0]);
     ld_plane<S, 1, NC>(pl.src_at(1) + r0, g, x0, lane, inrow, f[1]);
     ld_plane<S, 0, NC>(pl.src_at(2) + rm, g, x0, lane, inrow, f[2]);
@@ -896,32 +1039,38 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
     ld_plane<S, 0, NC>(pl.src_at(11) + rm, g, x0, lane, inrow, t[2]);
     ld_plane<S, -1, NC>(pl.src_at(12) + r0, g, x0, lane, inrow, t[3]);
     ld_plane<S, 0, NC>(pl.src_at(13) + rp, g, x0, lane, inrow, t[4]);
+    if constexpr (TQ == 9) {
+        ld_plane<S, 1, NC>(pl.src_at(14) + rm, g, x0, lane, inrow, t[5]);
+        ld_plane<S, -1, NC>(pl.src_at(15) + rm, g, x0, lane, inrow, t[6]);
+        ld_plane<S, -1, NC>(pl.src_at(16) + rp, g, x0, lane, inrow, t[7]);
+        ld_plane<S, 1, NC>(pl.src_at(17) + rp, g, x0, lane, inrow, t[8]);
+    }
     if (!any) return;
     if (m4 != 0u) {
-        wall_links<S, 0, 4, PA, NC>(pl, g, m4, x0, r0, rm, rp, f, t);
-        wall_links<S, 1, 4, PA, NC>(pl, g, m4, x0, r0, rm, rp, f, t);
-        wall_links<S, 2, 4, PA, NC>(pl, g, m4, x0, r0, rm, rp, f, t);
-        wall_links<S, 3, 4, PA, NC>(pl, g, m4, x0, r0, rm, rp, f, t);
+        wall_links<S, 0, 4, PA, NC, TQ>(pl, g, m4, x0, r0, rm, rp, f, t);
+        wall_links<S, 1, 4, PA, NC, TQ>(pl, g, m4, x0, r0, rm, rp, f, t);
+        wall_links<S, 2, 4, PA, NC, TQ>(pl, g, m4, x0, r0, rm, rp, f, t);
+        wall_links<S, 3, 4, PA, NC, TQ>(pl, g, m4, x0, r0, rm, rp, f, t);
     }
-    collide_pair<0, 4>(r, f, t);
-    collide_pair<2, 4>(r, f, t);
+    collide_pair<0, 4, TQ>(r, f, t);
+    collide_pair<2, 4, TQ>(r, f, t);
     if (m4 != 0u) {
-        zero_solid<0, 4>(m4, f, t);
-        zero_solid<1, 4>(m4, f, t);
-        zero_solid<2, 4>(m4, f, t);
-        zero_solid<3, 4>(m4, f, t);
+        zero_solid<0, 4, TQ>(m4, f, t);
+        zero_solid<1, 4, TQ>(m4, f, t);
+        zero_solid<2, 4, TQ>(m4, f, t);
+        zero_solid<3, 4, TQ>(m4, f, t);
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) Vec4<S>::st(pl.dst_at(i) + r0 + x0, f[i]);
 #pragma unroll
-    for (int i = 0; i < 5; ++i) Vec4<S>::st(pl.dst_at(9 + i) + r0 + x0, t[i]);
+    for (int i = 0; i < TQ; ++i) Vec4<S>::st(pl.dst_at(9 + i) + r0 + x0, t[i]);
 }
 
-template <typename S, int MINB>
+template <typename S, int MINB, int TQ = 5>
 __global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const Geom g, const RatesC<float> r) {
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    for (int y = blockIdx.y; y < g.ny; y += gridDim.y) row4<S>(pl, g, r, x0, y, lane);
+    for (int y = blockIdx.y; y < g.ny; y += gridDim.y) row4<S, Planes<S>, true, TQ>(pl, g, r, x0, y, lane);
 }
 
 }  // namespace nomrt

@@ -50,6 +50,8 @@ class lbm_params(C.Structure):
         ("s_e", C.c_double), ("s_q", C.c_double), ("s_eps", C.c_double),
         ("zeta_e", C.c_double), ("zeta_nu", C.c_double), ("varpi", C.c_double),
         ("T_init", C.c_void_p),
+        ("thermal_q", C.c_int32), ("theta", C.c_double),
+        ("zeta_q", C.c_double), ("zeta_eps", C.c_double),
     ]
 
 
@@ -135,7 +137,8 @@ def _check(status: int, handle=None):
 def make_params(case, storage: str = "f32"):
     """lbm_params from any object with the problem's attributes (nx, ny,
     periodic_x, periodic_y, flags, walls, nu, alpha, g_beta, T0, ax, ay, s_e,
-    s_q, s_eps, zeta_e, zeta_nu, varpi, T_init). Returns (params, keepalive)."""
+    s_q, s_eps, zeta_e, zeta_nu, varpi, T_init; optionally thermal_q, theta,
+    zeta_q, zeta_eps for the D2Q9 temperature model). Returns (params, keepalive)."""
     flags = np.ascontiguousarray(case.flags, dtype=np.uint8)
     assert flags.shape == (case.ny, case.nx)
     walls = (lbm_wall * max(1, len(case.walls)))()
@@ -155,6 +158,10 @@ def make_params(case, storage: str = "f32"):
     for name in ("nu", "alpha", "g_beta", "T0", "ax", "ay", "s_e", "s_q", "s_eps", "zeta_e", "zeta_nu", "varpi"):
         setattr(p, name, float(getattr(case, name)))
     p.T_init = Ti.ctypes.data if Ti is not None else None
+    p.thermal_q = int(getattr(case, "thermal_q", 5))
+    p.theta = float(getattr(case, "theta", 1.0))
+    p.zeta_q = float(getattr(case, "zeta_q", 1.0))
+    p.zeta_eps = float(getattr(case, "zeta_eps", 1.0))
     return p, (flags, walls, Ti)
 
 
@@ -204,6 +211,7 @@ class Lattice:
         self.case = case
         self.storage = storage
         self.nx, self.ny = int(case.nx), int(case.ny)
+        self.tq = 9 if int(getattr(case, "thermal_q", 5)) == 9 else 5
         p, keep = make_params(case, storage)
         need = L.lbm_footprint_bytes(C.byref(p))
         if need == 0:
@@ -276,13 +284,13 @@ class Lattice:
         return v.value
 
     def populations(self):
-        f = np.empty((9, self.ny, self.nx)); g = np.empty((5, self.ny, self.nx))
+        f = np.empty((9, self.ny, self.nx)); g = np.empty((self.tq, self.ny, self.nx))
         _check(load().lbm_get_populations(self._h, _dptr(f), _dptr(g)), self._h)
         return f, g
 
     def set_populations(self, f=None, g=None):
         f = None if f is None else np.ascontiguousarray(f, dtype=np.float64).reshape(9, self.ny, self.nx)
-        g = None if g is None else np.ascontiguousarray(g, dtype=np.float64).reshape(5, self.ny, self.nx)
+        g = None if g is None else np.ascontiguousarray(g, dtype=np.float64).reshape(self.tq, self.ny, self.nx)
         _check(load().lbm_set_populations(self._h, _dptr(f), _dptr(g)), self._h)
 
     def info(self):
