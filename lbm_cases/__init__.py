@@ -74,6 +74,7 @@ class Case:
     theta: float = 1.0              # the switch of Eq. 31 (D2Q9 model)
     zeta_q: float = 1.0             # kinetic rates of Eq. 32 (D2Q9 model)
     zeta_eps: float = 1.0
+    collision: int = 0              # 0: the MRT collisions; 1: BGK (one rate for f, one for g)
 
     @property
     def fluid_nodes(self) -> int:
@@ -419,3 +420,20 @@ def with_d2q9_temperature(case: Case, theta: float = 1.0, zeta_q: float | None =
     return replace(case, thermal_q=9, theta=float(theta),
                    zeta_q=case.zeta_e if zeta_q is None else zeta_q,
                    zeta_eps=case.zeta_e if zeta_eps is None else zeta_eps)
+
+
+def with_bgk(case: Case) -> Case:
+    """The same problem with single-relaxation-time (BGK) collisions: omega
+    from nu, zeta from alpha; the other kinetic rates are unused."""
+    return replace(case, collision=1)
+
+
+def with_equal_rates(case: Case) -> Case:
+    """MRT with every flow rate set to s_nu and every temperature rate set to
+    zeta_alpha (both from the transport coefficients): mathematically the BGK
+    collision of the same problem."""
+    s_nu = 1.0 / (0.5 + 3.0 * case.nu)
+    cs_T2 = 1.0 / 3.0 if case.thermal_q == 9 else 0.5 * case.varpi
+    z_a = 1.0 / (0.5 + case.alpha / cs_T2)
+    return replace(case, collision=0, s_e=s_nu, s_q=s_nu, s_eps=s_nu, zeta_e=z_a, zeta_nu=z_a, zeta_q=z_a,
+                   zeta_eps=z_a)

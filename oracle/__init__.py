@@ -61,6 +61,7 @@ class OrcParams(C.Structure):
         ("thermal_q", C.c_int32),
         ("theta", C.c_double),
         ("zeta_q", C.c_double), ("zeta_eps", C.c_double),
+        ("collision", C.c_int32),
     ]
 
 
@@ -70,6 +71,7 @@ class OrcRates(C.Structure):
         ("g_beta", C.c_double), ("T0", C.c_double),
         ("ax", C.c_double), ("ay", C.c_double), ("varpi", C.c_double),
         ("s8_literal", C.c_int32), ("tq", C.c_int32), ("theta", C.c_double),
+        ("bgk", C.c_int32),
     ]
 
 
@@ -118,8 +120,10 @@ def tables():
     return dict(M=M, Minv=Mi, N=N, Ninv=Ni, ex=np.array(ex[:]), ey=np.array(ey[:]), w=w)
 
 
-def make_rates(s, z, g_beta=0.0, T0=0.0, ax=0.0, ay=0.0, varpi=0.5, s8_literal=False, theta=1.0) -> OrcRates:
-    """z has 5 entries (D2Q5 temperature, Eq. 29) or 9 (the D2Q9 model, Eq. 32)."""
+def make_rates(s, z, g_beta=0.0, T0=0.0, ax=0.0, ay=0.0, varpi=0.5, s8_literal=False, theta=1.0,
+               bgk=False) -> OrcRates:
+    """z has 5 entries (D2Q5 temperature, Eq. 29) or 9 (the D2Q9 model, Eq. 32).
+    bgk: single-relaxation-time collisions at omega = s[4], zeta = z[1]."""
     r = OrcRates()
     for k in range(9):
         r.s[k] = float(s[k])
@@ -129,6 +133,7 @@ def make_rates(s, z, g_beta=0.0, T0=0.0, ax=0.0, ay=0.0, varpi=0.5, s8_literal=F
     r.s8_literal = int(bool(s8_literal))
     r.tq = 9 if len(z) == 9 else 5
     r.theta = float(theta)
+    r.bgk = int(bool(bgk))
     return r
 
 
@@ -174,6 +179,7 @@ class OracleLattice:
         p.theta = float(getattr(case, "theta", 1.0))
         p.zeta_q = float(getattr(case, "zeta_q", 1.0))
         p.zeta_eps = float(getattr(case, "zeta_eps", 1.0))
+        p.collision = int(getattr(case, "collision", 0))
         self._p = p
         h = lib().orc_create(C.byref(p))
         if not h:

@@ -20,6 +20,10 @@
  *            Or the D2Q9 temperature model of Eqs. 31-33: n = M g with the
  *            D2Q9 basis (reading A13), n_eq = M g_eq with g_eq of Eq. 31, Q of
  *            Eq. 32, alpha = c_s^2 (1/zeta_alpha - 1/2).
+ *   BGK    : the single-rate special case (every rate of Eq. 20 equal to s_nu,
+ *            every rate of Eq. 29 / Eq. 32 equal to zeta_alpha), selected by
+ *            `collision` and written in velocity space: incompressible
+ *            equilibrium, Guo-Zheng-Shi forcing, Eq. 30 or Eq. 31 for T.
  *   force  : F = g beta (T - T0) j + a (Eq. 4).
  *   macro  : rho = sum f_bar (Eq. 18), rho0 u = sum e f_bar + rho0 F / 2
  *            (Eq. 19 under the incompressible approximation, Sec. 2.1),
@@ -138,6 +142,7 @@ typedef struct {
     int32_t thermal_q;         /* 5: D2Q5 (Sec. 2.2); 9: the D2Q9 model of Eqs. 31-33 */
     double theta;              /* the switch of Eq. 31, 0 or 1 (D2Q9 model) */
     double zeta_q, zeta_eps;   /* kinetic rates of Eq. 32 (D2Q9 model) */
+    int32_t collision;         /* 0: the MRT collisions (Eq. 8, Eq. 24 or Eq. 32); 1: BGK (one rate each) */
 } orc_params;
 
 /* Per-node collision inputs. s[9] is Lambda of Eq. 20; z is Q of Eq. 29 (its
@@ -149,6 +154,7 @@ typedef struct {
     int32_t s8_literal;
     int32_t tq;
     double theta;
+    int32_t bgk;   /* 1: single-relaxation-time collisions with omega = s[4], zeta = z[1] */
 } orc_rates;
 
 typedef struct {
@@ -194,6 +200,40 @@ void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[9
     double ux = (jx + 0.5 * RHO0 * Fx) / RHO0;
     double uy = (jy + 0.5 * RHO0 * Fy) / RHO0;
     double uu = ux * ux + uy * uy;
+    if (macro) {
+        macro[0] = rho;
+        macro[1] = ux;
+        macro[2] = uy;
+        macro[3] = T;
+    }
+
+    if (r->bgk) {
+        /* BGK, the single-rate special case, written in velocity space: the
+         * flow relaxes to the incompressible equilibrium (reading A1) at
+         * omega = s_nu and takes the forcing term of Guo, Zheng and Shi
+         * (Phys. Rev. E 65, 046308, 2002),
+         *   F_i = w_i rho0 [(e_i - u) / c_s^2 + (e_i . u) e_i / c_s^4] . F,
+         * weighted by 1 - omega/2; the temperature relaxes to the equilibrium
+         * of Eq. 30 (D2Q5) or Eq. 31 (D2Q9) at zeta_alpha. */
+        const double om = r->s[4], zt = r->z[1];
+        for (int i = 0; i < 9; ++i) {
+            double eu = EX[i] * ux + EY[i] * uy;
+            double eF = EX[i] * Fx + EY[i] * Fy;
+            double feq = W9[i] * (rho + RHO0 * (eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2)));
+            double Fi = W9[i] * RHO0 * (((EX[i] - ux) * Fx + (EY[i] - uy) * Fy) / CS2 + eu * eF / (CS2 * CS2));
+            fstar[i] = fbar[i] - om * (fbar[i] - feq) + (1.0 - 0.5 * om) * Fi;
+        }
+        for (int i = 0; i < tq; ++i) {
+            double eu = EX[i] * ux + EY[i] * uy;
+            double geq;
+            if (tq == 9)
+                geq = W9[i] * T * (1.0 + eu / CS2 + r->theta * (eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2)));
+            else
+                geq = i == 0 ? (1.0 - r->varpi) * T : 0.25 * r->varpi * T + 0.5 * eu * T;
+            gstar[i] = g[i] - zt * (g[i] - geq);
+        }
+        return;
+    }
 
     /* Eq. 10: m_bar = M f_bar. */
     double m[9];
@@ -273,12 +313,6 @@ void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[9
             for (int k = 0; k < 5; ++k) gstar[i] += NINV5[i][k] * ns[k];
         }
     }
-    if (macro) {
-        macro[0] = rho;
-        macro[1] = ux;
-        macro[2] = uy;
-        macro[3] = T;
-    }
 }
 
 /* Fill the rate vectors from the transport coefficients:
@@ -291,6 +325,7 @@ void orc_rates_from_params(const orc_params *p, orc_rates *r) {
     memcpy(r->s, s, sizeof s);
     r->tq = p->thermal_q == 9 ? 9 : 5;
     r->theta = p->theta;
+    r->bgk = p->collision == 1;
     if (r->tq == 9) {
         /* Eq. 32 with alpha = c_s^2 (1/zeta_alpha - 1/2) */
         double z_alpha = 1.0 / (0.5 + p->alpha / CS2);

@@ -1,0 +1,100 @@
+"""Pins of the oracle's BGK switch (single-relaxation-time collisions written
+in velocity space). BGK is the special case of the MRT collisions with every
+rate equal (Sec. 2.1, Eq. 20; Sec. 2.2, Eq. 29; Eq. 32), and the equal-rate MRT
+collision is pinned against the textbook BGK update with Guo forcing in
+test_oracle_pins, so the BGK path is checked against that independent route:
+node by node, lattice by lattice, with either temperature lattice. The other
+kinetic rates must not reach it, and the conserved quantities stay conserved."""
+import numpy as np
+import pytest
+
+import lbm_cases as lc
+import oracle
+from test_oracle_pins import E, W
+
+
+def _node(rng, tq):
+    f = W * (1 + 0.2 * rng.standard_normal(9))
+    wT = W if tq == 9 else np.array([0.5, 0.125, 0.125, 0.125, 0.125])
+    g = wT * (0.6 + 0.2 * rng.standard_normal(tq))
+    return f, g
+
+
+@pytest.mark.parametrize("tq,theta", [(5, 1.0), (9, 1.0), (9, 0.0)])
+@pytest.mark.parametrize("omega,zeta", [(1.0, 1.0), (0.6, 1.3), (1.85, 0.9)])
+def test_bgk_equals_mrt_with_equal_rates(tq, theta, omega, zeta):
+    rng = np.random.default_rng(12)
+    kw = dict(g_beta=3e-3, T0=0.4, ax=2e-4, ay=-1e-4, theta=theta)
+    for _ in range(20):
+        f, g = _node(rng, tq)
+        mrt = oracle.make_rates([omega] * 9, [zeta] * tq, **kw)
+        # BGK takes omega from s_nu (s[4]) and zeta from zeta_alpha (z[1]); the rest are noise
+        s = rng.uniform(0.2, 1.9, 9); s[4] = omega
+        z = rng.uniform(0.2, 1.9, tq); z[1] = zeta
+        bgk = oracle.make_rates(s, z, bgk=True, **kw)
+        fm, gm, mm = oracle.collide_node(mrt, f, g)
+        fb, gb, mb = oracle.collide_node(bgk, f, g)
+        assert np.abs(fm - fb).max() < 2e-15
+        assert np.abs(gm - gb).max() < 2e-15
+        assert np.abs(np.asarray(mm) - np.asarray(mb)).max() == 0.0
+
+
+@pytest.mark.parametrize("tq", [5, 9])
+def test_bgk_conserves_mass_temperature_and_adds_the_force(tq):
+    rng = np.random.default_rng(13)
+    for _ in range(20):
+        f, g = _node(rng, tq)
+        gb, T0, ax, ay = 5e-3, 0.3, 1e-3, -2e-3
+        r = oracle.make_rates(rng.uniform(0.2, 1.9, 9), rng.uniform(0.2, 1.9, tq), g_beta=gb, T0=T0, ax=ax,
+                              ay=ay, bgk=True)
+        fs, gs, _ = oracle.collide_node(r, f, g)
+        Fy = ay + gb * (g.sum() - T0)
+        assert abs(fs.sum() - f.sum()) < 1e-15
+        assert abs(E[:, 0] @ fs - E[:, 0] @ f - ax) < 1e-15
+        assert abs(E[:, 1] @ fs - E[:, 1] @ f - Fy) < 1e-15
+        assert abs(gs.sum() - g.sum()) < 1e-15
+
+
+def test_bgk_differs_from_mrt_with_unequal_rates():
+    """The switch changes the method: with s_e != s_nu the two collisions differ
+    by O(s_e - s_nu) times the non-equilibrium part."""
+    rng = np.random.default_rng(14)
+    f, g = _node(rng, 5)
+    s = [1, 1, 1, 1.6, 1.1, 1.1, 1.2, 1.2, 1.8]
+    z = [1, 0.9, 0.9, 1.3, 1.4]
+    fm, gm, _ = oracle.collide_node(oracle.make_rates(s, z), f, g)
+    fb, gb, _ = oracle.collide_node(oracle.make_rates(s, z, bgk=True), f, g)
+    assert np.abs(fm - fb).max() > 1e-4 and np.abs(gm - gb).max() > 1e-4
+
+
+def _lattice_cases():
+    q = lc.with_d2q9_temperature
+    return [
+        lc.cavity(n=20, Ra=1e4, n_y=13, noise=1e-3),
+        lc.couette(H=9, nx=5, U0=0.05),
+        lc.obstacle_channel(nx=37, H=9, frac=0.15, seed=4),
+        lc.cavity_nee(n=19, Ra=1e4, noise=1e-3),
+        lc.porous_couette_nee(H=13, nx=5, Re=10, s_nu=0.8),
+        q(lc.cavity(n=20, Ra=1e4, n_y=13, noise=1e-3)),
+        q(lc.obstacle_channel(nx=37, H=9, frac=0.15, seed=4), theta=0.0),
+    ]
+
+
+@pytest.mark.parametrize("idx", range(7))
+def test_bgk_lattice_equals_equal_rate_mrt_lattice(idx):
+    """Whole lattices, walls of both schemes included, 30 steps from a random
+    state: the BGK run and the equal-rate MRT run agree to rounding."""
+    case = _lattice_cases()[idx]
+    a = oracle.OracleLattice(lc.with_bgk(case))
+    b = oracle.OracleLattice(lc.with_equal_rates(case))
+    f0, g0 = lc.random_state(case, seed=60 + idx)
+    a.set_populations(f0, g0)
+    b.set_populations(f0, g0)
+    a.step(30)
+    b.step(30)
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert np.abs(fa - fb).max() <= 1e-13 * np.abs(fb).max()
+    assert np.abs(ga - gb).max() <= 1e-13 * np.abs(gb).max()
+    for x, y in zip(a.macro(), b.macro()):
+        assert np.abs(x - y).max() <= 1e-13 * max(1.0, np.abs(y).max())
