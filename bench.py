@@ -333,6 +333,92 @@ def run_batched(args):
     return 0
 
 
+def run_cost(args):
+    """Cost of the collision operators and temperature lattices on the same
+    workload (Rayleigh-Benard, --nx x --H): MRT (Eq. 8 + Eq. 24) against BGK,
+    with D2Q5 (Sec. 2.2) or the D2Q9 temperature model (Eqs. 31-33), in each
+    storage. Per model: the AUTO kernel and every step kernel of the storage
+    (scalar, VEC4 configs), device-timed; the line's value is the MRT D2Q5
+    MLUPS of --storage."""
+    import torch
+    import paper_1510_08224_gb300 as P
+    torch.cuda.set_device(0)
+    base = workload(args.nx, args.H)
+    fluid = base.fluid_nodes
+    peak, peak_src = measured_peak()
+    models = {"mrt_d2q5": base, "bgk_d2q5": lc.with_bgk(base),
+              "mrt_d2q9t": lc.with_d2q9_temperature(base), "bgk_d2q9t": lc.with_bgk(lc.with_d2q9_temperature(base))}
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(0).start()
+    t_start = time.perf_counter()
+    table = {}
+    launches = 0
+    for st in ("f64", "f32", "f16"):
+        eb = {"f64": 8, "f32": 4, "f16": 2}[st]
+        k = args.steps if st != "f64" else max(10, args.steps // 8)
+        for name, case in models.items():
+            planes = 9 + (9 if case.thermal_q == 9 else 5)
+            bpn = planes * eb * 2 + 1
+            lat = P.Lattice(case, storage=st)
+            kernels = [("auto", 0)]
+            if st != "f64" and args.sweep:
+                kernels += [("scalar", 0)] + [("vec4", c) for c in range(P.step_kernel_count(st, "vec4"))]
+            row = {}
+            for v in kernels:
+                lat.set_step_kernel(*v)
+                lat.step(args.warmup)
+                lat.sync()
+                e0.record(stream)
+                lat.step(k)
+                e1.record(stream)
+                e1.synchronize()
+                launches += k
+                ms = e0.elapsed_time(e1) / k
+                gbs = bpn * fluid / (ms * 1e-3) / 1e9
+                row[f"{v[0]}{v[1] if v[0] == 'vec4' else ''}"] = {
+                    "MLUPS": round(fluid / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 5),
+                    "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4)}
+            try:  # the timing does not depend on it, but say whether the run stayed finite
+                lat.residual()
+                finite = True
+            except P.LBMError:
+                finite = False
+            lat.close()
+            table[f"{st}/{name}"] = {"bytes_per_node": bpn, "steps": k, "finite": finite, "kernels": row}
+    t_end = time.perf_counter()
+    sampler.stop()
+
+    def best_ms(key):
+        return min(v["ms_per_step"] for v in table[key]["kernels"].values())
+
+    ratios = {}
+    for st in ("f64", "f32", "f16"):
+        m5, b5 = best_ms(f"{st}/mrt_d2q5"), best_ms(f"{st}/bgk_d2q5")
+        m9, b9 = best_ms(f"{st}/mrt_d2q9t"), best_ms(f"{st}/bgk_d2q9t")
+        ratios[st] = {"mrt_over_bgk_d2q5": round(m5 / b5, 4), "mrt_over_bgk_d2q9t": round(m9 / b9, 4),
+                      "d2q9t_over_d2q5_mrt": round(m9 / m5, 4)}
+    key = f"{args.storage}/mrt_d2q5"
+    ms = table[key]["kernels"]["auto"]["ms_per_step"]
+    line = {
+        "metric": METRIC, "value": round(fluid / (ms * 1e-3) / 1e6, 1), "unit": "MLUPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": COMPUTE_DTYPE[args.storage], "data": "synthetic",
+        "config": {"workload": f"collision_cost_rayleigh_benard_{args.nx}x{args.H}", "fluid_cells": fluid,
+                   "storage": STORAGE_NAME[args.storage],
+                   "models": "MRT or BGK collisions; D2Q5 or D2Q9 temperature lattice",
+                   "l2": "no flush: working set > L2"},
+        "models": table,
+        "time_ratios_best_kernel": ratios,
+        "gpu_launches": launches,
+        "clocks": sampler.summary(t_start, t_end),
+        "peak": {"hbm_gbs": peak, "source": peak_src},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     """Continuous-batching serving: Poisson arrivals (20 per second, seed 0) of
     cavity and Rayleigh-Benard requests, sides log-uniform in [64, 2048], Ra
@@ -393,7 +479,8 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="rb", choices=["rb", "batch", "serve"],
+    ap.add_argument("--sweep", action="store_true", help="cost workload: time every step kernel of each model")
+    ap.add_argument("--workload", default="rb", choices=["rb", "batch", "serve", "cost"],
                     help="rb: the 4096 x 2048 Rayleigh-Benard step (default); batch: uneven cavities advanced together")
     ap.add_argument("--count", type=int, default=64, help="lattices (batch) or requests (serve)")
     ap.add_argument("--side-hi", type=int, default=2048, help="largest side of a served request")
@@ -408,6 +495,8 @@ def main():
         return run_batched(args)
     if args.workload == "serve":
         return run_serving(args)
+    if args.workload == "cost":
+        return run_cost(args)
 
     import torch
     import paper_1510_08224_gb300 as P

@@ -79,6 +79,18 @@ typedef struct {
     double T;
 } lbm_wall;
 
+/* Collision operator. MRT: Eq. 8 for the flow, Eq. 24 (or the D2Q9 model's
+ * Eq. 32) for temperature. BGK: the special case with one rate each, computed in
+ * velocity space,
+ *   f*_i = f_i - s_nu (f_i - f_eq_i) + (1 - s_nu/2) w_i [3 (e_i - u).F + 9 (e_i.u)(e_i.F)]
+ *   g*_i = g_i - zeta_alpha (g_i - g_eq_i)
+ * with the incompressible f_eq (rho0 = 1), the forcing of Guo, Zheng and Shi
+ * (Phys. Rev. E 65, 046308, 2002), and g_eq of Eq. 30 or Eq. 31; s_e, s_q,
+ * s_eps, zeta_e, zeta_nu, zeta_q and zeta_eps are then unused (but still
+ * validated). BGK lattices have the SCALAR and VEC4 step kernels only and do not
+ * join fused batches. */
+typedef enum { LBM_COLLISION_MRT = 0, LBM_COLLISION_BGK = 1 } lbm_collision;
+
 /* Problem statement (Sec. 2, Eqs. 1-4) and the model's rates. */
 typedef struct {
     int32_t nx, ny;               /* cells, frame included, x fastest */
@@ -106,6 +118,7 @@ typedef struct {
     int32_t thermal_q;
     double theta;                 /* Eq. 31: 1 keeps the second-order terms, 0 drops them (thermal_q = 9) */
     double zeta_q, zeta_eps;      /* Eq. 32 rates of the q and epsilon moments (thermal_q = 9), in (0, 2) */
+    int32_t collision;            /* lbm_collision */
 } lbm_params;
 
 typedef struct lbm_lattice lbm_lattice; /* opaque; owned by the library */
@@ -134,8 +147,9 @@ lbm_status lbm_step(lbm_lattice *h, int64_t nsteps);
 lbm_status lbm_sync(lbm_lattice *h);
 
 /* Step kernel variants. All compute the same arithmetic and give the same
- * bits for a given storage. AUTO picks the fastest measured on GB300: VEC4
- * config 1 for FP32, VEC4 config 3 for FP16, the scalar kernel for FP64.
+ * bits for a given storage. AUTO picks the fastest measured on GB300: the
+ * scalar kernel for FP64; VEC4 for FP32 / FP16 with config 1 / 3 (MRT, D2Q5),
+ * 1 / 2 (BGK, D2Q5) or 0 / 1 (the D2Q9 temperature model).
  * SCALAR: one cell per thread. VEC4: four cells per thread with 128-bit (FP32)
  * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls; configs 0-4 ask
  * for 4, 5, 6, 7 or 8 resident blocks per SM. VEC8 (FP16 only): eight cells per

@@ -98,10 +98,16 @@ cudaError_t launch_nee(const KParams &p, int src, cudaStream_t st) {
     using C = typename Store<S>::C;
     if (p.n_nee == 0) return cudaSuccess;
     const dim3 grid((p.n_nee + 127) / 128);
-    if (p.tq == 9)
-        k_nee<S, 9><<<grid, 128, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p), p.nee, p.n_nee);
-    else
-        k_nee<S, 5><<<grid, 128, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p), p.nee, p.n_nee);
+    const Planes<S> pl = make_planes<S>(p, src);
+    const Geom g = make_geom(p);
+    const RatesC<C> r = make_rates<C>(p);
+    if (p.tq == 9) {
+        if (p.bgk) k_nee<S, 9, true><<<grid, 128, 0, st>>>(pl, g, r, p.nee, p.n_nee);
+        else k_nee<S, 9, false><<<grid, 128, 0, st>>>(pl, g, r, p.nee, p.n_nee);
+    } else {
+        if (p.bgk) k_nee<S, 5, true><<<grid, 128, 0, st>>>(pl, g, r, p.nee, p.n_nee);
+        else k_nee<S, 5, false><<<grid, 128, 0, st>>>(pl, g, r, p.nee, p.n_nee);
+    }
     return cudaGetLastError();
 }
 
@@ -125,8 +131,12 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
         // five (FP32) or seven (FP16) resident blocks per SM
         if (variant == kStepAuto) {
             variant = kStepVec4;
-            // the D2Q9 temperature model keeps nine more values per cell in registers: four blocks per SM
-            q.config = p.tq == 9 ? 0 : (sizeof(S) == 4 ? 1 : 3);
+            // VEC4 configs measured fastest on GB300 (4096 x 2048 cells): MRT D2Q5 5 (FP32) or
+            // 7 (FP16) blocks per SM; BGK D2Q5 5 or 6; the D2Q9 temperature model, which keeps
+            // nine more values per cell in registers, 4 or 5
+            if (p.tq == 9) q.config = sizeof(S) == 4 ? 0 : 1;
+            else if (p.bgk) q.config = sizeof(S) == 4 ? 1 : 2;
+            else q.config = sizeof(S) == 4 ? 1 : 3;
         }
     } else {
         variant = kStepScalar;
@@ -134,14 +144,16 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
     return launch_step_variant<S>(q, variant, src, st);
 }
 
-// TQ: temperature populations per node (5: D2Q5; 9: the D2Q9 model, which
-// has the scalar and four-cell kernels only).
-template <typename S, int TQ>
-cudaError_t launch_step_tq(const KParams &p, int variant, int src, cudaStream_t st) {
+// TQ: temperature populations per node (5: D2Q5; 9: the D2Q9 model). BGK:
+// single-rate collisions. The D2Q9 model and BGK have the scalar and
+// four-cell kernels only.
+template <typename S, int TQ, bool BGK>
+cudaError_t launch_step_m(const KParams &p, int variant, int src, cudaStream_t st) {
     using C = typename Store<S>::C;
+    constexpr bool kBase = TQ == 5 && !BGK;
     if constexpr (Store<S>::kShifted) {
         if (variant == kStepTma) {
-            if constexpr (TQ == 5) return launch_tma<S>(p, src, st);
+            if constexpr (kBase) return launch_tma<S>(p, src, st);
             else return cudaErrorInvalidValue;
         }
         if (variant == kStepVec4) {
@@ -153,15 +165,15 @@ cudaError_t launch_step_tq(const KParams &p, int variant, int src, cudaStream_t 
             const Geom g = make_geom(p);
             const RatesC<float> r = make_rates<float>(p);
             switch (p.config) {
-                case 1: k_step4<S, 5, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
-                case 2: k_step4<S, 6, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
-                case 3: k_step4<S, 7, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
-                case 4: k_step4<S, 8, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
-                default: k_step4<S, 4, TQ><<<grid, 128, 0, st>>>(pl, g, r); break;
+                case 1: k_step4<S, 5, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
+                case 2: k_step4<S, 6, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
+                case 3: k_step4<S, 7, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
+                case 4: k_step4<S, 8, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
+                default: k_step4<S, 4, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
             }
             return cudaGetLastError();
         }
-        if constexpr (sizeof(S) == 2 && TQ == 5) {
+        if constexpr (sizeof(S) == 2 && kBase) {
             if (variant == kStepVec8) {
                 // eight cells per thread (FP16 only)
                 const int threads_x = p.pitch / 8;
@@ -179,13 +191,15 @@ cudaError_t launch_step_tq(const KParams &p, int variant, int src, cudaStream_t 
     const int gy = (p.ny + (int)b.y - 1) / (int)b.y;
     const dim3 grid((p.nx + b.x - 1) / b.x, gy < 65535 ? gy : 65535);
     if (variant != kStepScalar && variant != kStepAuto) return cudaErrorInvalidValue;
-    k_step<S, TQ><<<grid, b, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p));
+    k_step<S, TQ, BGK><<<grid, b, 0, st>>>(make_planes<S>(p, src), make_geom(p), make_rates<C>(p));
     return cudaGetLastError();
 }
 
 template <typename S>
 cudaError_t launch_step_variant(const KParams &p, int variant, int src, cudaStream_t st) {
-    return p.tq == 9 ? launch_step_tq<S, 9>(p, variant, src, st) : launch_step_tq<S, 5>(p, variant, src, st);
+    if (p.tq == 9)
+        return p.bgk ? launch_step_m<S, 9, true>(p, variant, src, st) : launch_step_m<S, 9, false>(p, variant, src, st);
+    return p.bgk ? launch_step_m<S, 5, true>(p, variant, src, st) : launch_step_m<S, 5, false>(p, variant, src, st);
 }
 
 template <typename S>

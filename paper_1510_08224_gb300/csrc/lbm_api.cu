@@ -126,6 +126,7 @@ std::string validate(const lbm_params *p) {
     if (!(std::isfinite(p->nu) && p->nu > 0.0)) return "nu must be > 0";
     if (!(std::isfinite(p->alpha) && p->alpha > 0.0)) return "alpha must be > 0";
     if (p->thermal_q != 0 && p->thermal_q != 5 && p->thermal_q != 9) return "thermal_q must be 0, 5 or 9";
+    if (p->collision != LBM_COLLISION_MRT && p->collision != LBM_COLLISION_BGK) return "unknown collision operator";
     if (thermal_q(p) == 9) {
         if (!in_open_02(p->zeta_q) || !in_open_02(p->zeta_eps)) return "zeta_q and zeta_eps must be in (0, 2)";
         if (!std::isfinite(p->theta)) return "theta must be finite";
@@ -375,6 +376,7 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     kp.theta = tq == 9 ? p->theta : 0.0;
     kp.z_q = tq == 9 ? p->zeta_q : 0.0;
     kp.z_eps = tq == 9 ? p->zeta_eps : 0.0;
+    kp.bgk = p->collision == LBM_COLLISION_BGK ? 1 : 0;
     kp.nee = reinterpret_cast<const int2 *>(h->mem + h->lay.off_nee);
     kp.n_nee = (int)hnee.size();
     kp.nee_dir = reinterpret_cast<const uint8_t *>(h->mem + h->lay.off_nee_dir);
@@ -459,8 +461,8 @@ lbm_status lbm_set_step_kernel(lbm_lattice *h, int32_t variant, int32_t config) 
     const int32_t n = lbm_step_kernel_count(h->storage, variant);
     if (n == 0) return fail(h, LBM_EINVAL, "step variant not available for this storage");
     if (config < 0 || config >= n) return fail(h, LBM_EINVAL, "step kernel config out of range");
-    if (h->kp.tq == 9 && (variant == LBM_STEP_TMA || variant == LBM_STEP_VEC8))
-        return fail(h, LBM_EINVAL, "the D2Q9 temperature model has the SCALAR and VEC4 step kernels only");
+    if ((h->kp.tq == 9 || h->kp.bgk) && (variant == LBM_STEP_TMA || variant == LBM_STEP_VEC8))
+        return fail(h, LBM_EINVAL, "the D2Q9 temperature model and BGK have the SCALAR and VEC4 step kernels only");
     h->kp.variant = variant;
     h->kp.config = config;
     return LBM_OK;

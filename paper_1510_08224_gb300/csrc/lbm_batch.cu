@@ -478,7 +478,8 @@ lbm_status lbm_batch_add(lbm_batch *b, lbm_lattice *h) {
     if (!b || !h) return bfail(b, LBM_EINVAL, "batch or lattice is NULL");
     if (h->batch) return bfail(b, LBM_EINVAL, "lattice already belongs to a batch");
     if (h->storage == LBM_F64) return bfail(b, LBM_EINVAL, "batches hold FP32 or FP16 storage only");
-    if (h->kp.tq != 5) return bfail(b, LBM_EINVAL, "batches hold lattices with the D2Q5 temperature model only");
+    if (h->kp.tq != 5 || h->kp.bgk)
+        return bfail(b, LBM_EINVAL, "batches hold MRT lattices with the D2Q5 temperature model only");
     if (b->storage >= 0 && h->storage != b->storage) return bfail(b, LBM_EINVAL, "batch members share one storage");
     if (h->stream != b->stream) return bfail(b, LBM_EINVAL, "a member must use the batch's stream");
     b->storage = h->storage;

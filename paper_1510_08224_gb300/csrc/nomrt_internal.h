@@ -63,6 +63,7 @@ struct KParams {
     double rho_ref, T_ref;            // storage shift (0 for FP64 storage)
     int tq;                           // temperature lattice: 5 (D2Q5) or 9 (Eqs. 31-33)
     double theta, z_q, z_eps;         // Eq. 31 switch, Eq. 32 rates (tq = 9)
+    int bgk;                          // 1: single-rate (BGK) collisions
     const int2 *nee;                  // boundary nodes of NEE walls: (cell offset, dir | wall id << 8)
     int n_nee;
     const uint8_t *nee_dir;           // per cell: 0, or the direction i of the nearest fluid node x + e_i

@@ -458,6 +458,7 @@ struct Ops;
 
 template <>
 struct Ops<float> {
+    using V = float;
     static __device__ __forceinline__ float bc(float c) { return c; }
     static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
     static __device__ __forceinline__ float sub(float a, float b) { return __fadd_rn(a, -b); }
@@ -467,6 +468,7 @@ struct Ops<float> {
 
 template <>
 struct Ops<float2> {
+    using V = float;
     static __device__ __forceinline__ float2 bc(float c) { return make_float2(c, c); }
     static __device__ __forceinline__ float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
     // a - b as fma(b, -1, a): one rounding of the exact difference
@@ -475,6 +477,16 @@ struct Ops<float2> {
     }
     static __device__ __forceinline__ float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
     static __device__ __forceinline__ float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+};
+
+template <>
+struct Ops<double> {
+    using V = double;
+    static __device__ __forceinline__ double bc(double c) { return c; }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
 
 // thermal_q9 with every rounding explicit (T is float or float2).
@@ -616,15 +628,128 @@ __device__ __forceinline__ void collide_x(const RatesC<float> &r, T f[9], T t[TQ
     }
 }
 
+// ------------------------------------------------------------ BGK collision
+
+// e_I . (x, y) for the D2Q9 velocities of Eq. 5 (I >= 1), exactly.
+template <int I, typename O, typename T>
+__device__ __forceinline__ T edot(T x, T y) {
+    if constexpr (I == 1) return x;
+    else if constexpr (I == 2) return y;
+    else if constexpr (I == 3) return O::mul(O::bc(-1), x);
+    else if constexpr (I == 4) return O::mul(O::bc(-1), y);
+    else if constexpr (I == 5) return O::add(x, y);
+    else if constexpr (I == 6) return O::sub(y, x);
+    else if constexpr (I == 7) return O::mul(O::bc(-1), O::add(x, y));
+    else return O::sub(x, y);
+}
+
+// Directions I and J = opp(I) of the BGK collision (see collide_bgk_x). Both
+// equilibria and forcing terms split into a part even in e (shared) and a part
+// odd in e (sign flipped): with eu = e_I.u, eF = e_I.F and C0 = s base - 3 h u.F,
+//   f*_I,J = (1 - s) f_I,J + w [C0 + eu (4.5 s eu + 9 h eF)] +- 3 w (s eu + h eF).
+template <int I, int J, typename T, typename R, int TQ>
+__device__ __forceinline__ void bgk_pair(const R &r, T f[9], T t[TQ], T C0, T ux, T uy, T Fx, T Fy, T uu, T zn0,
+                                         T zT) {
+    using O = Ops<T>;
+    using V = typename O::V;
+    constexpr double w = I < 5 ? 1.0 / 9 : 1.0 / 36;
+    const T W = O::bc((V)w), W3 = O::bc((V)(3.0 * w));
+    const T eu = edot<I, O>(ux, uy), eF = edot<I, O>(Fx, Fy);
+    const T hF = O::mul(O::bc(r.h_nu), eF);
+    const T ev = O::mul(W, O::fma(eu, O::fma(O::mul(O::bc((V)4.5), O::bc(r.s_nu)), eu, O::mul(O::bc(9), hF)), C0));
+    const T od = O::mul(W3, O::fma(O::bc(r.s_nu), eu, hF));
+    f[I] = O::fma(O::bc(r.om_nu), f[I], O::add(ev, od));
+    f[J] = O::fma(O::bc(r.om_nu), f[J], O::sub(ev, od));
+    if constexpr (TQ == 9 || J < 5) {
+        T evT, odT;
+        if constexpr (TQ == 9) {
+            // zeta w [(T - T_ref) + T theta (4.5 eu^2 - 1.5 u^2)] +- 3 zeta w T eu  (Eq. 31, storage frame)
+            const T q2 = O::fma(O::mul(O::bc((V)4.5), eu), eu, O::mul(O::bc((V)-1.5), uu));
+            evT = O::mul(W, O::fma(O::mul(zT, O::bc(r.theta)), q2, zn0));
+            odT = O::mul(W3, O::mul(zT, eu));
+        } else {
+            // zeta [(varpi/4)(T - T_ref)] +- zeta (1/2) T eu  (Eq. 30, storage frame)
+            evT = O::mul(O::mul(O::bc((V)0.25), O::bc(r.varpi)), zn0);
+            odT = O::mul(O::bc((V)0.5), O::mul(zT, eu));
+        }
+        t[I] = O::fma(O::bc(r.om_a), t[I], O::add(evT, odT));
+        t[J] = O::fma(O::bc(r.om_a), t[J], O::sub(evT, odT));
+    }
+}
+
+// BGK: the special case of Eqs. 8 and 24 (or Eq. 32) with one rate for the
+// flow (s = s_nu, h = 1 - s/2) and one for temperature (zeta = zeta_alpha),
+// written in velocity space, every rounding explicit (T = double, float or
+// float2; R = RatesC of its scalar type):
+//   f*_i = f_i - s (f_i - f_eq_i) + h w_i [3 (e_i - u) . F + 9 (e_i . u)(e_i . F)]
+//   g*_i = g_i - zeta (g_i - g_eq_i)
+// with the incompressible equilibrium f_eq_i = w_i [rho + 3 e_i.u + 4.5 (e_i.u)^2
+// - 1.5 u^2] (rho0 = 1), the forcing term of Guo, Zheng and Shi (Phys. Rev. E 65,
+// 046308, 2002), and g_eq of Eq. 30 (D2Q5) or Eq. 31 (D2Q9). In the storage frame
+// every equilibrium is shifted like the populations. Opposite directions are
+// updated together (bgk_pair).
+template <typename T, typename R, int TQ>
+__device__ __forceinline__ void collide_bgk_x(const R &r, T f[9], T t[TQ]) {
+    using O = Ops<T>;
+    using V = typename O::V;
+    T n0;
+    if constexpr (TQ == 9)
+        n0 = O::add(O::add(O::add(O::add(t[0], t[1]), O::add(t[2], t[3])), O::add(t[4], t[5])),
+                    O::add(O::add(t[6], t[7]), t[8]));
+    else
+        n0 = O::add(O::add(O::add(t[0], t[1]), O::add(t[2], t[3])), t[4]);
+    const T Fx = O::bc(r.ax);
+    const T Fy = O::fma(O::bc(r.g_beta), n0, O::bc(r.Fy0));  // Eq. 4
+    const T a13 = O::add(f[1], f[3]), d13 = O::sub(f[1], f[3]);
+    const T a24 = O::add(f[2], f[4]), d24 = O::sub(f[2], f[4]);
+    const T a57 = O::add(f[5], f[7]), d57 = O::sub(f[5], f[7]);
+    const T a68 = O::add(f[6], f[8]), d68 = O::sub(f[6], f[8]);
+    const T m0 = O::add(O::add(f[0], O::add(a13, a24)), O::add(a57, a68));  // Eq. 18
+    const T jx = O::add(d13, O::sub(d57, d68));
+    const T jy = O::add(d24, O::add(d57, d68));
+    const T ux = O::add(jx, O::bc(r.hx));  // Eq. 19, rho0 = 1
+    const T uy = O::fma(O::bc((V)0.5), Fy, jy);
+    const T uu = O::fma(ux, ux, O::mul(uy, uy));
+    const T uF = O::fma(ux, Fx, O::mul(uy, Fy));
+    // C0 = s (rho - 1.5 u^2) - 3 h u.F, the isotropic part of s f_eq / w + h F / w
+    const T C0 = O::fma(O::bc(r.s_nu), O::fma(O::bc((V)-1.5), uu, m0), O::mul(O::mul(O::bc(-3), O::bc(r.h_nu)), uF));
+    const T Tm = O::add(O::bc(r.T_ref), n0);
+    const T zn0 = O::mul(O::bc(r.z_a), n0), zT = O::mul(O::bc(r.z_a), Tm);
+    f[0] = O::fma(O::bc(r.om_nu), f[0], O::mul(O::bc((V)(4.0 / 9)), C0));
+    if constexpr (TQ == 9) {
+        // zeta (4/9) [(T - T_ref) - 1.5 theta T u^2]
+        const T q2 = O::mul(O::bc((V)-1.5), uu);
+        t[0] = O::fma(O::bc(r.om_a), t[0], O::mul(O::bc((V)(4.0 / 9)), O::fma(O::mul(zT, O::bc(r.theta)), q2, zn0)));
+    } else {
+        t[0] = O::fma(O::bc(r.om_a), t[0], O::mul(O::sub(O::bc(1), O::bc(r.varpi)), zn0));
+    }
+    bgk_pair<1, 3, T, R, TQ>(r, f, t, C0, ux, uy, Fx, Fy, uu, zn0, zT);
+    bgk_pair<2, 4, T, R, TQ>(r, f, t, C0, ux, uy, Fx, Fy, uu, zn0, zT);
+    bgk_pair<5, 7, T, R, TQ>(r, f, t, C0, ux, uy, Fx, Fy, uu, zn0, zT);
+    bgk_pair<6, 8, T, R, TQ>(r, f, t, C0, ux, uy, Fx, Fy, uu, zn0, zT);
+}
+
+// The collision of one cell in the storage's compute type: MRT (exact FP64
+// operators, or explicit FP32 rounding for shifted storage) or BGK.
+template <typename S, int TQ, bool BGK>
+__device__ __forceinline__ void collide_cell(const RatesC<typename Store<S>::C> &r, typename Store<S>::C f[9],
+                                             typename Store<S>::C t[TQ]) {
+    using C = typename Store<S>::C;
+    if constexpr (BGK) collide_bgk_x<C, RatesC<C>, TQ>(r, f, t);
+    else if constexpr (Store<S>::kShifted) collide_x<float, TQ>(r, f, t);
+    else collide<C, TQ>(r, f, t);
+}
+
 // Collide cells K and K + 1 of an N-cell group as one float2 pair, in place.
-template <int K, int N, int TQ = 5>
+template <int K, int N, int TQ = 5, bool BGK = false>
 __device__ __forceinline__ void collide_pair(const RatesC<float> &r, float f[9][N], float t[TQ][N]) {
     float2 fp[9], tp[TQ];
 #pragma unroll
     for (int i = 0; i < 9; ++i) fp[i] = make_float2(f[i][K], f[i][K + 1]);
 #pragma unroll
     for (int i = 0; i < TQ; ++i) tp[i] = make_float2(t[i][K], t[i][K + 1]);
-    collide_x<float2, TQ>(r, fp, tp);
+    if constexpr (BGK) collide_bgk_x<float2, RatesC<float>, TQ>(r, fp, tp);
+    else collide_x<float2, TQ>(r, fp, tp);
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         f[i][K] = fp[i].x;
@@ -675,7 +800,7 @@ __device__ __forceinline__ void zero_solid(uint32_t mN, float f[9][N], float t[T
 
 // ------------------------------------------------------------------ kernels
 
-template <typename S, int TQ = 5>
+template <typename S, int TQ = 5, bool BGK = false>
 __global__ void __launch_bounds__(256) k_step(const Planes<S> pl, const Geom g, const RatesC<typename Store<S>::C> r) {
     using C = typename Store<S>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
@@ -686,8 +811,7 @@ __global__ void __launch_bounds__(256) k_step(const Planes<S> pl, const Geom g, 
         if (m == kSolid) continue;
         C f[9], t[TQ];
         pull<S, TQ>(pl.src, g, x, y, m, f, t);
-        if constexpr (Store<S>::kShifted) collide_x<float, TQ>(r, f, t);
-        else collide<C, TQ>(r, f, t);
+        collide_cell<S, TQ, BGK>(r, f, t);
 #pragma unroll
         for (int q = 0; q < 9; ++q) Store<S>::st(pl.dst[q] + off, f[q]);
 #pragma unroll
@@ -698,7 +822,7 @@ __global__ void __launch_bounds__(256) k_step(const Planes<S> pl, const Geom g, 
 // Boundary nodes of NEE walls: rebuild (non-equilibrium extrapolation), collide,
 // store. Runs after a step kernel that skipped them (their link-map byte is
 // kSolid), reading the same source buffer.
-template <typename S, int TQ = 5>
+template <typename S, int TQ = 5, bool BGK = false>
 __global__ void __launch_bounds__(128) k_nee(const Planes<S> pl, const Geom g, const RatesC<typename Store<S>::C> r,
                                              const int2 *nee, int n) {
     using C = typename Store<S>::C;
@@ -709,8 +833,7 @@ __global__ void __launch_bounds__(128) k_nee(const Planes<S> pl, const Geom g, c
     const int y = off / g.pitch, x = off - y * g.pitch;
     C f[9], t[TQ];
     nee_rebuild<S, TQ>(pl.src, g, r, x, y, d, g.walls + k, f, t);
-    if constexpr (Store<S>::kShifted) collide_x<float, TQ>(r, f, t);
-    else collide<C, TQ>(r, f, t);
+    collide_cell<S, TQ, BGK>(r, f, t);
 #pragma unroll
     for (int q = 0; q < 9; ++q) Store<S>::st(pl.dst[q] + off, f[q]);
 #pragma unroll
@@ -1009,7 +1132,7 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
 // One warp's share of a row: cells x0..x0+3 of row y for each lane (x0 = base +
 // 4 lane). Every lane of the warp calls it with the same y. PA gives the plane
 // pointers (Planes or StridedPlanes).
-template <typename S, typename PA, bool NC = true, int TQ = 5>
+template <typename S, typename PA, bool NC = true, int TQ = 5, bool BGK = false>
 __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<float> &r, int x0, int y, int lane) {
     const int r0 = y * g.pitch;
     const bool inrow = x0 < g.pitch;
@@ -1052,8 +1175,8 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
         wall_links<S, 2, 4, PA, NC, TQ>(pl, g, m4, x0, r0, rm, rp, f, t);
         wall_links<S, 3, 4, PA, NC, TQ>(pl, g, m4, x0, r0, rm, rp, f, t);
     }
-    collide_pair<0, 4, TQ>(r, f, t);
-    collide_pair<2, 4, TQ>(r, f, t);
+    collide_pair<0, 4, TQ, BGK>(r, f, t);
+    collide_pair<2, 4, TQ, BGK>(r, f, t);
     if (m4 != 0u) {
         zero_solid<0, 4, TQ>(m4, f, t);
         zero_solid<1, 4, TQ>(m4, f, t);
@@ -1066,11 +1189,11 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
     for (int i = 0; i < TQ; ++i) Vec4<S>::st(pl.dst_at(9 + i) + r0 + x0, t[i]);
 }
 
-template <typename S, int MINB, int TQ = 5>
+template <typename S, int MINB, int TQ = 5, bool BGK = false>
 __global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const Geom g, const RatesC<float> r) {
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    for (int y = blockIdx.y; y < g.ny; y += gridDim.y) row4<S, Planes<S>, true, TQ>(pl, g, r, x0, y, lane);
+    for (int y = blockIdx.y; y < g.ny; y += gridDim.y) row4<S, Planes<S>, true, TQ, BGK>(pl, g, r, x0, y, lane);
 }
 
 }  // namespace nomrt

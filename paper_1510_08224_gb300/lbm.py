@@ -52,6 +52,7 @@ class lbm_params(C.Structure):
         ("T_init", C.c_void_p),
         ("thermal_q", C.c_int32), ("theta", C.c_double),
         ("zeta_q", C.c_double), ("zeta_eps", C.c_double),
+        ("collision", C.c_int32),
     ]
 
 
@@ -138,7 +139,8 @@ def make_params(case, storage: str = "f32"):
     """lbm_params from any object with the problem's attributes (nx, ny,
     periodic_x, periodic_y, flags, walls, nu, alpha, g_beta, T0, ax, ay, s_e,
     s_q, s_eps, zeta_e, zeta_nu, varpi, T_init; optionally thermal_q, theta,
-    zeta_q, zeta_eps for the D2Q9 temperature model). Returns (params, keepalive)."""
+    zeta_q, zeta_eps for the D2Q9 temperature model and collision, 1 for BGK).
+    Returns (params, keepalive)."""
     flags = np.ascontiguousarray(case.flags, dtype=np.uint8)
     assert flags.shape == (case.ny, case.nx)
     walls = (lbm_wall * max(1, len(case.walls)))()
@@ -162,6 +164,7 @@ def make_params(case, storage: str = "f32"):
     p.theta = float(getattr(case, "theta", 1.0))
     p.zeta_q = float(getattr(case, "zeta_q", 1.0))
     p.zeta_eps = float(getattr(case, "zeta_eps", 1.0))
+    p.collision = int(getattr(case, "collision", 0))
     return p, (flags, walls, Ti)
 
 

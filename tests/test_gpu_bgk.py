@@ -1,0 +1,168 @@
+"""Parity of the CUDA BGK switch (single-rate collisions in velocity space) with
+the oracle's BGK path, for both temperature lattices and both wall schemes:
+FP64 element by element (<= 1e-12 relative max-norm), FP32/FP16 one step from
+the same quantised state, every step kernel variant bit-identical, and the GPU
+BGK run equal to the GPU MRT run with equal rates (the same method by another
+route)."""
+import numpy as np
+import pytest
+
+import lbm_cases as lc
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+W9 = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)[:, None, None]
+
+
+def _P():
+    import paper_1510_08224_gb300 as P
+    return P
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def _cases():
+    b, q = lc.with_bgk, lc.with_d2q9_temperature
+    return [
+        b(lc.periodic_box(7, 5, nu=0.03, alpha=0.04, g_beta=2e-3, T0=0.5, ax=1e-5)),
+        b(lc.couette(H=9, nx=5, U0=0.05)),
+        b(lc.cavity(n=20, Ra=1e4, n_y=13, noise=1e-3)),
+        b(lc.rayleigh_benard(nx=133, H=7, Ra=1e5, sigma=1e-2)),
+        b(lc.obstacle_channel(nx=261, H=9, frac=0.15, seed=4)),
+        b(lc.cavity_nee(n=19, Ra=1e4, noise=1e-3)),
+        b(lc.porous_couette_nee(H=13, nx=5, Re=10, s_nu=0.8)),
+        b(q(lc.cavity(n=20, Ra=1e4, n_y=13, noise=1e-3))),
+        b(q(lc.obstacle_channel(nx=37, H=9, frac=0.15, seed=5), theta=0.0)),
+    ]
+
+
+N = 9
+RANDOM_START = (0, 2, 4, 5, 7, 8)
+
+
+def _wT(case):
+    if case.thermal_q == 9:
+        return W9
+    return np.array([1 - case.varpi] + [case.varpi / 4] * 4)[:, None, None]
+
+
+@pytest.mark.parametrize("idx", range(N))
+@pytest.mark.parametrize("nsteps", [0, 1, 2, 10])
+def test_bgk_fp64_matches_oracle(idx, nsteps):
+    P = _P()
+    case = _cases()[idx]
+    g = P.Lattice(case, storage="f64")
+    o = oracle.OracleLattice(case)
+    if idx in RANDOM_START:
+        f0, g0 = lc.random_state(case, seed=71 + idx)
+        g.set_populations(f0, g0)
+        o.set_populations(f0, g0)
+    g.step(nsteps)
+    o.step(nsteps)
+    fg, gg = g.populations()
+    fo, go = o.populations()
+    assert _rel(fg, fo) <= FP64_TOL
+    assert _rel(gg, go) <= FP64_TOL
+    for a, b in zip(g.macro(), o.macro()):
+        assert np.abs(a - b).max() <= FP64_TOL * max(np.abs(b).max(), 1.0)
+
+
+def test_bgk_fp64_cavity_1e4_steps():
+    P = _P()
+    case = lc.with_bgk(lc.cavity(n=32, Ra=1e4, noise=1e-3))
+    g = P.Lattice(case, storage="f64")
+    o = oracle.OracleLattice(case, threads=4)
+    g.step(10000)
+    o.step(10000)
+    for a, b in zip(g.macro()[1:], o.macro()[1:]):
+        assert _rel(a, b) <= FP64_TOL
+    for side in (0, 1):
+        assert abs(g.nusselt(side) - o.nusselt(side)) <= 1e-11
+
+
+ONE_STEP_TOL = {"f32": 2e-6, "f16": 2e-3}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("idx", range(N))
+def test_bgk_reduced_precision_one_step(storage, idx):
+    P = _P()
+    case = _cases()[idx]
+    g = P.Lattice(case, storage=storage)
+    f0, g0 = lc.random_state(case, seed=81 + idx)
+    g.set_populations(f0, g0)
+    fq, gq = g.populations()
+    o = oracle.OracleLattice(case)
+    o.set_populations(fq, gq)
+    g.step(1)
+    o.step(1)
+    fg, gg = g.populations()
+    fo, go = o.populations()
+    halfway = np.zeros(case.flags.shape, bool)
+    for k, w in enumerate(case.walls, start=1):
+        if w.scheme == lc.HALFWAY:
+            halfway |= case.flags == k
+    dev_f = np.where(halfway, 0.0, fo - W9)
+    dev_g = np.where(halfway, 0.0, go - _wT(case) * case.T0)
+    assert np.abs(fg - fo).max() <= ONE_STEP_TOL[storage] * np.abs(dev_f).max()
+    assert np.abs(gg - go).max() <= ONE_STEP_TOL[storage] * np.abs(dev_g).max()
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("idx", range(N))
+def test_bgk_step_variants_agree_bitwise(storage, idx):
+    P = _P()
+    case = _cases()[idx]
+    f0, g0 = lc.random_state(case, seed=91 + idx)
+    out = {}
+    variants = [("scalar", 0)] + [("vec4", c) for c in range(P.step_kernel_count(storage, "vec4"))] + [("auto", 0)]
+    for v in variants:
+        lat = P.Lattice(case, storage=storage)
+        lat.set_step_kernel(*v)
+        lat.set_populations(f0, g0)
+        lat.step(5)
+        out[v] = lat.populations()
+        lat.sync()
+    ref = out[("scalar", 0)]
+    for v, o in out.items():
+        assert np.array_equal(o[0], ref[0]) and np.array_equal(o[1], ref[1]), v
+
+
+@pytest.mark.parametrize("idx", [2, 5, 7])
+def test_bgk_equals_equal_rate_mrt_on_gpu(idx):
+    """FP64, 200 steps from a random state: the BGK kernel and the MRT kernel
+    with every rate equal give the same populations to rounding."""
+    P = _P()
+    case = _cases()[idx]
+    mrt = lc.with_equal_rates(case)
+    f0, g0 = lc.random_state(case, seed=101 + idx)
+    a = P.Lattice(case, storage="f64")
+    b = P.Lattice(mrt, storage="f64")
+    a.set_populations(f0, g0)
+    b.set_populations(f0, g0)
+    a.step(200)
+    b.step(200)
+    fa, ga = a.populations()
+    fb, gb = b.populations()
+    assert _rel(fa, fb) <= 1e-12 and _rel(ga, gb) <= 1e-12
+
+
+def test_bgk_rejects_tma_vec8_batches_and_bad_switch():
+    P = _P()
+    case = lc.with_bgk(lc.couette(H=6, nx=5))
+    lat = P.Lattice(case, storage="f16")
+    with pytest.raises(P.LBMError):
+        lat.set_step_kernel("tma", 0)
+    with pytest.raises(P.LBMError):
+        lat.set_step_kernel("vec8", 0)
+    b = P.Batch()
+    lat2 = P.Lattice(case, storage="f32", stream=b.stream)
+    with pytest.raises(P.LBMError):
+        b.add(lat2)
+    b.close()
+    with pytest.raises(P.LBMError):
+        P.Lattice(case.with_(collision=2))
