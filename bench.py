@@ -63,13 +63,12 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
-def profiled_traffic(storage: str, nx: int, ny: int):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, or None
-    if there is none for this storage and size, or the kernel sources changed
-    since it was taken."""
-    path = os.path.join(PROFILE_DIR, f"k_step_{storage}_rb{nx}x{ny - 2}.md")
+def profile_values(name: str):
+    """The key=value pairs of a committed ncu summary's header comment, or {}
+    if the file is missing or the kernel sources changed since it was taken."""
+    path = os.path.join(PROFILE_DIR, name)
     if not os.path.exists(path):
-        return None
+        return {}
     vals = {}
     with open(path) as f:
         for line in f:
@@ -79,11 +78,40 @@ def profiled_traffic(storage: str, nx: int, ny: int):
                         k, v = kv.split("=", 1)
                         vals[k] = v
     if vals.get("kernel_hash") != kernel_source_hash():
-        return None
+        return {}
+    return vals
+
+
+def profiled_traffic(storage: str, nx: int, ny: int):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, or None
+    if there is none for this storage and size, or the kernel sources changed
+    since it was taken."""
     try:
-        return float(vals["traffic_bytes_per_launch"])
+        return float(profile_values(f"k_step_{storage}_rb{nx}x{ny - 2}.md")["traffic_bytes_per_launch"])
     except (KeyError, ValueError):
         return None
+
+
+# GB300's nominal FP64 rate (no measured FP64 peak exists for this pool); an FMA counts twice
+FP64_PEAK_TFLOPS = 1.25
+
+
+def fp64_alu_roofline(mlups: float):
+    """The FP64 step kernel is bound by the FP64 pipe: achieved FP64 TFLOP/s from
+    the ncu-counted DADD + DMUL + 2 DFMA per cell, against the nominal rate; also
+    as FP64 instructions against half the nominal FLOP rate (the pipe's issue
+    limit when every instruction counts once)."""
+    v = profile_values("k_step_f64_rb1024x512.md")
+    try:
+        flops, inst = float(v["fp64_flops_per_cell"]), float(v["fp64_inst_per_cell"])
+    except (KeyError, ValueError):
+        return None
+    tf = flops * mlups * 1e6 / 1e12
+    ti = inst * mlups * 1e6 / 1e12
+    return {"bound": "alu", "achieved": round(tf, 4), "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": round(tf / FP64_PEAK_TFLOPS, 4), "fp64_flops_per_cell": flops, "fp64_inst_per_cell": inst,
+            "inst_frac": round(ti / (FP64_PEAK_TFLOPS / 2), 4),
+            "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak); counts from ncu"}
 
 
 class ClockSampler:
@@ -103,12 +131,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
             return self
         self.thread = threading.Thread(target=self._read, daemon=True)
         self.thread.start()
+        # the timed region is short: start it only once samples are flowing
+        t_end = time.perf_counter() + 5.0
+        while not self.samples and time.perf_counter() < t_end and self.proc.poll() is None:
+            time.sleep(0.01)
         return self
 
     def _read(self):
@@ -296,7 +328,8 @@ def run_batched(args):
     res = {}
     tuned_kind = b.info()["config"]
     for name, mode, kind in (("fused_graph", (1, 32), "fused"), ("fused_launch_per_step", (1, 0), "fused"),
-                             ("fused_persistent_8", (8, 0), "fused"), ("concurrent_graph", (1, 32), "concurrent")):
+                             ("fused_persistent_8", (8, 0), "fused"), ("concurrent_graph", (1, 32), "concurrent"),
+                             ("concurrent_graph_2", (1, 2), "concurrent")):
         b.set_kind(kind)
         b.set_mode(*mode)
         ms = timed(b.step, args.steps)
@@ -551,7 +584,11 @@ def main():
             "kernel": "k_step", "bytes_per_node": BYTES_PER_NODE[args.storage],
             "peak_source": f"{peak_src} HBM copy bandwidth (burst)"}
     if args.storage == "f64":
-        roof["note"] = "FP64 arithmetic bound; GB/s shown against the HBM peak for reference"
+        alu = fp64_alu_roofline(value / world)
+        if alu:
+            alu["hbm_GB/s"] = roof["achieved"]
+            alu["hbm_frac"] = roof["frac"]
+            roof = alu
 
     line = {
         "metric": METRIC, "value": round(value, 1), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -584,8 +621,11 @@ def main():
             vms, vl = time_steps(P, torch, case, st, k, args.warmup)
             vl.close()
             vach = BYTES_PER_NODE[st] * fluid / (vms / k * 1e-3) / 1e9
-            var[STORAGE_NAME[st]] = {"MLUPS": round(fluid * k / (vms * 1e-3) / 1e6, 1), "steps": k,
+            vm = fluid * k / (vms * 1e-3) / 1e6
+            var[STORAGE_NAME[st]] = {"MLUPS": round(vm, 1), "steps": k,
                                      "GB/s": round(vach, 1), "frac": round(vach / peak, 4)}
+            if st == "f64":
+                var[STORAGE_NAME[st]]["alu"] = fp64_alu_roofline(vm)
         line["variants"] = var
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case)
