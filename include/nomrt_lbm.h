@@ -259,8 +259,11 @@ lbm_status lbm_batch_remove(lbm_batch *b, lbm_lattice *h);
  * that many steps; 0 disables graphs. Defaults: 1 and 32. */
 lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t graph_steps);
 
-/* How a batch step runs. FUSED: one kernel over the work list of every
- * member (the default). CONCURRENT: each member's own single-lattice step
+/* How a batch step runs. FUSED: one kernel launch per step over every member
+ * (per 64 members), whose grid concatenates the members' own four-cell-kernel
+ * grids, with the members' descriptors in the launch's parameter space (the
+ * default); with steps_per_launch > 1, a cooperative persistent kernel over a
+ * work list of row segments instead. CONCURRENT: each member's own single-lattice step
  * kernel (its lbm_set_step_kernel choice), the members on separate streams
  * between a fork and a join, so their kernels run side by side; with
  * graph_steps > 0 the whole fork/join is one captured graph. */
@@ -269,17 +272,18 @@ lbm_status lbm_batch_set_kind(lbm_batch *b, int32_t kind);
 
 /* Kernel shape: config 0..4 asks for 4..8 resident 128-thread blocks per SM
  * (-1: the default, 1 for FP32 and 3 for FP16); rows_per_unit (1..1024) is the
- * number of consecutive rows of one 128-cell segment a warp takes per work
- * unit (default 4). */
+ * number of consecutive rows of one 128-cell segment a warp of the persistent
+ * kernel takes per work unit (default 1). */
 lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_unit);
 
-/* Autotuner: for rows_per_unit in {1, 4, 16} and each config of the FUSED
- * kind, and for the CONCURRENT kind, times trial_launches steps on the current
- * members (each trial recomputes the current step into the other buffer, so
- * the state is unchanged), selects the fastest, and returns the FUSED choice
- * in *best_config (-2 if CONCURRENT won) and *best_rows, and the mean ms per
- * step of every candidate in ms_per_launch[16] (15 FUSED entries, row-count
- * major, then CONCURRENT). Any output may be NULL. Synchronises. */
+/* Autotuner: for each config of the FUSED per-step kernel, and for the
+ * CONCURRENT kind, times trial_launches steps on the current members (each
+ * trial recomputes the current step into the other buffer, so the state is
+ * unchanged), selects the fastest kind and config, and returns the FUSED
+ * config in *best_config (-2 if CONCURRENT won), the unchanged rows_per_unit
+ * in *best_rows, and the mean ms per step of every candidate in
+ * ms_per_launch[6] (5 FUSED configs, then CONCURRENT). Any output may be NULL.
+ * Synchronises. */
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_config, int32_t *best_rows,
                           float *ms_per_launch);
 

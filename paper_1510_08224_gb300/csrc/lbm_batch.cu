@@ -2,12 +2,18 @@
 // storage): one kernel launch advances every member lattice by one time step
 // (or, in persistent mode, by k steps with a grid barrier between them).
 //
-// Work list: units of (lattice, first row, 128-cell segment, row count). A warp
-// takes a unit, reads its lattice's descriptor (buffers, geometry, rates) once
-// and runs the same row code as the single-lattice VEC4 kernel on each of the
-// unit's rows, so a lattice stepped in a batch produces the same bits as when
-// stepped alone. Launches are persistent: a grid of resident CTAs strides over
-// the units.
+// Per-step launch: the descriptors of up to kGroupLats members (buffers,
+// geometry, rates) travel as one large kernel parameter, so they sit in the
+// constant bank exactly as a single-lattice kernel's parameters do. The grid
+// is the concatenation of every member's own VEC4 grid (one 128-thread block
+// per 512-cell segment of a row); a block finds its member by a binary search
+// over the members' first block indices and runs the single-lattice row code,
+// so a lattice stepped in a batch produces the same bits as when stepped alone,
+// and the members' partial last waves fill each other.
+//
+// Persistent launch: a work list of units (lattice, first row, 128-cell
+// segment, row count) with the descriptors in device memory; a grid of
+// resident CTAs strides over the units, steps separated by a grid barrier.
 //
 // Ping-pong: member l reads buffer (s + flip_l) & 1 at batch step s, where
 // flip_l is fixed when the lattice joins, so lattices that joined at different
@@ -29,6 +35,7 @@ namespace nomrt {
 constexpr int kBatchWarps = 4;  // warps (units) per CTA
 constexpr int kBatchThreads = 32 * kBatchWarps;
 constexpr int kBatchConfigs = 5;  // resident blocks asked of ptxas: 4 + config
+constexpr int kGroupLats = 64;    // members per per-step launch (parameter space holds their descriptors)
 constexpr long long kBarrierBudgetCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 struct __align__(16) BatchLat {
@@ -64,13 +71,46 @@ __device__ __forceinline__ void batch_unit(const BatchLat *lats, const int4 u, i
     for (int k = 0; k < u.w; ++k) row4<S, StridedPlanes<S>, NC>(pa, g, r, u.z + 4 * lane, u.y + k, lane);
 }
 
-// One step of every member: warps stride over the units.
+// One member's descriptor in the per-step launch's parameter.
+struct GridLat {
+    Geom g;
+    const void *pop0;
+    const void *pop1;
+    long long plane;
+    int flip;
+    int xblocks;  // blocks per row: ceil(pitch / 512)
+    RatesC<float> r;
+};
+
+struct GroupParams {
+    int nlats;
+    int block0[kGroupLats + 1];  // first block of each member; block0[nlats] = grid size
+    GridLat lat[kGroupLats];
+};
+
+// One step of every member of a group: block b belongs to the member l with
+// block0[l] <= b < block0[l + 1] and covers cells 512 xb .. 512 xb + 511 of row
+// y of it, like block (xb, y) of the single-lattice VEC4 kernel.
 template <typename S, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
-    k_batch_step(const BatchLat *lats, const int4 *units, int nunits, int parity) {
-    const int stride = gridDim.x * kBatchWarps;
-    for (int w = blockIdx.x * kBatchWarps + (threadIdx.x >> 5); w < nunits; w += stride)
-        batch_unit<S, true>(lats, units[w], parity, threadIdx.x & 31);
+    k_batch_grid(const __grid_constant__ GroupParams P, int parity) {
+    const int b = blockIdx.x;
+    int lo = 0, hi = P.nlats - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.block0[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const GridLat &L = P.lat[lo];
+    const int lb = b - P.block0[lo];
+    const int y = lb / L.xblocks, xb = lb - y * L.xblocks;
+    const int sel = (parity + L.flip) & 1;
+    StridedPlanes<S> pa;
+    pa.src = static_cast<const S *>(sel ? L.pop1 : L.pop0);
+    pa.dst = static_cast<S *>(const_cast<void *>(sel ? L.pop0 : L.pop1));
+    pa.plane = L.plane;
+    row4<S, StridedPlanes<S>, true>(pa, L.g, L.r, (xb * kBatchThreads + (int)threadIdx.x) * 4, y,
+                                    threadIdx.x & 31);
 }
 
 template <typename S, int MINB, bool PERSISTENT>
@@ -144,27 +184,21 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
 }
 
 template <typename S, int MINB>
-cudaError_t launch_step_shape(const BatchLat *lats, const int4 *units, int nunits, int parity, cudaStream_t st) {
-    auto kern = k_batch_step<S, MINB>;
-    int blocks = 0;
-    cudaError_t e = resident_grid<GridTag<S, MINB, false>>(kern, &blocks);
-    if (e != cudaSuccess) return e;
-    const int need = (nunits + kBatchWarps - 1) / kBatchWarps;
-    if (blocks > need) blocks = need;
+cudaError_t launch_grid_shape(const GroupParams &G, int parity, cudaStream_t st) {
+    const int blocks = G.block0[G.nlats];
     if (blocks == 0) return cudaSuccess;
-    kern<<<blocks, kBatchThreads, 0, st>>>(lats, units, nunits, parity);
+    k_batch_grid<S, MINB><<<blocks, kBatchThreads, 0, st>>>(G, parity);
     return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t launch_batch_step(int config, const BatchLat *lats, const int4 *units, int nunits, int parity,
-                              cudaStream_t st) {
+cudaError_t launch_batch_grid(int config, const GroupParams &G, int parity, cudaStream_t st) {
     switch (config) {
-        case 1: return launch_step_shape<S, 5>(lats, units, nunits, parity, st);
-        case 2: return launch_step_shape<S, 6>(lats, units, nunits, parity, st);
-        case 3: return launch_step_shape<S, 7>(lats, units, nunits, parity, st);
-        case 4: return launch_step_shape<S, 8>(lats, units, nunits, parity, st);
-        default: return launch_step_shape<S, 4>(lats, units, nunits, parity, st);
+        case 1: return launch_grid_shape<S, 5>(G, parity, st);
+        case 2: return launch_grid_shape<S, 6>(G, parity, st);
+        case 3: return launch_grid_shape<S, 7>(G, parity, st);
+        case 4: return launch_grid_shape<S, 8>(G, parity, st);
+        default: return launch_grid_shape<S, 4>(G, parity, st);
     }
 }
 
@@ -221,12 +255,13 @@ struct lbm_batch {
     int *d_status = nullptr;
     size_t cap_lats = 0, cap_units = 0;
     int nunits = 0;
+    std::vector<nomrt::GroupParams> groups;  // per-step launch parameters, kGroupLats members each
     int64_t cells = 0;
     bool dirty = true;
     int config = -1;  // -1: default per storage
     int steps_per_launch = 1;
     int graph_steps = 32;
-    int rows_per_unit = 4;
+    int rows_per_unit = 1;
     int kind = LBM_BATCH_FUSED;
     // concurrent kind: one stream per member for the fork/join of the graph
     std::vector<cudaStream_t> lstreams;
@@ -239,10 +274,6 @@ struct lbm_batch {
 };
 
 namespace {
-
-// Rows per unit the tuner tries.
-constexpr int kTuneRows[] = {1, 4, 16};
-constexpr int kTuneRowCount = 3;
 
 lbm_status bfail(lbm_batch *b, lbm_status st, const std::string &m) {
     if (b) b->err = m;
@@ -268,6 +299,7 @@ lbm_status rebuild(lbm_batch *b) {
     std::vector<BatchLat> lats(b->members.size());
     std::vector<int4> units;
     b->cells = 0;
+    b->groups.clear();
     for (size_t l = 0; l < b->members.size(); ++l) {
         lbm_lattice *h = b->members[l];
         const nomrt::KParams &kp = h->kp;
@@ -286,6 +318,22 @@ lbm_status rebuild(lbm_batch *b) {
         d.flip = b->flip[l];
         d.r = nomrt::make_rates<float>(kp);
         b->cells += h->fluid;
+        // the per-step launch: member l joins group l / kGroupLats with its VEC4 grid
+        if (l % nomrt::kGroupLats == 0) {
+            b->groups.emplace_back();
+            std::memset(&b->groups.back(), 0, sizeof(nomrt::GroupParams));
+        }
+        nomrt::GroupParams &G = b->groups.back();
+        nomrt::GridLat &gl = G.lat[G.nlats];
+        gl.g = nomrt::make_geom(kp);
+        gl.pop0 = kp.pop[0];
+        gl.pop1 = kp.pop[1];
+        gl.plane = (long long)kp.plane;
+        gl.flip = b->flip[l];
+        gl.xblocks = (kp.pitch / 4 + nomrt::kBatchThreads - 1) / nomrt::kBatchThreads;
+        gl.r = d.r;
+        G.block0[G.nlats + 1] = G.block0[G.nlats] + kp.ny * gl.xblocks;
+        G.nlats += 1;
         // units: runs of up to rows_per_unit consecutive rows of a 128-cell segment,
         // skipping rows of the segment that hold no fluid cell
         const int R = b->rows_per_unit;
@@ -398,6 +446,16 @@ bool any_nee(const lbm_batch *b) {
     return false;
 }
 
+// One step of every member with the per-step fused kernel: one launch per group.
+cudaError_t launch_grid_step(lbm_batch *b, int config, int parity, cudaStream_t st) {
+    for (const nomrt::GroupParams &G : b->groups) {
+        cudaError_t e = b->storage == LBM_F16_SHIFTED ? nomrt::launch_batch_grid<__half>(config, G, parity, st)
+                                                      : nomrt::launch_batch_grid<float>(config, G, parity, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
     if (b->kind == LBM_BATCH_CONCURRENT) return launch_concurrent(b, n, st, true);
     const bool nee = any_nee(b);
@@ -415,9 +473,7 @@ cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
             parity = (parity + k) & 1;
             n -= k;
         } else {
-            e = b->storage == LBM_F16_SHIFTED
-                    ? nomrt::launch_batch_step<__half>(b->cfg(), b->d_lats, b->d_units, b->nunits, parity, st)
-                    : nomrt::launch_batch_step<float>(b->cfg(), b->d_lats, b->d_units, b->nunits, parity, st);
+            e = launch_grid_step(b, b->cfg(), parity, st);
             if (e == cudaSuccess && nee) e = launch_nee_passes(b, parity, st);
             parity ^= 1;
             n -= 1;
@@ -597,43 +653,33 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_co
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bfail(b, LBM_ECUDA, "event create");
-    int best = 0, best_r = b->rows_per_unit;
+    int best = 0;
     float best_ms = 1e30f;
-    lbm_status out = LBM_OK;
-    for (int ri = 0; ri < kTuneRowCount && out == LBM_OK; ++ri) {
-        b->rows_per_unit = kTuneRows[ri];
-        b->dirty = true;
-        out = rebuild(b);
-        for (int c = 0; c < nomrt::kBatchConfigs && out == LBM_OK; ++c) {
-            auto run = [&](int n) -> cudaError_t {
-                for (int k = 0; k < n; ++k) {
-                    cudaError_t e = b->storage == LBM_F16_SHIFTED
-                                        ? nomrt::launch_batch_step<__half>(c, b->d_lats, b->d_units, b->nunits,
-                                                                           parity, b->stream)
-                                        : nomrt::launch_batch_step<float>(c, b->d_lats, b->d_units, b->nunits,
-                                                                          parity, b->stream);
-                    if (e != cudaSuccess) return e;
-                }
-                return cudaSuccess;
-            };
-            cudaError_t e = run(1);  // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-            if (e == cudaSuccess) e = run(trial_launches);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                out = bcuda(b, e, "tuning launch");
-                break;
+    lbm_status out = rebuild(b);
+    for (int c = 0; c < nomrt::kBatchConfigs && out == LBM_OK; ++c) {
+        auto run = [&](int n) -> cudaError_t {
+            for (int k = 0; k < n; ++k) {
+                cudaError_t e = launch_grid_step(b, c, parity, b->stream);
+                if (e != cudaSuccess) return e;
             }
-            ms /= (float)trial_launches;
-            if (ms_per_launch) ms_per_launch[ri * nomrt::kBatchConfigs + c] = ms;
-            if (ms < best_ms) {
-                best_ms = ms;
-                best = c;
-                best_r = kTuneRows[ri];
-            }
+            return cudaSuccess;
+        };
+        cudaError_t e = run(1);  // warm-up
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = run(trial_launches);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            out = bcuda(b, e, "tuning launch");
+            break;
+        }
+        ms /= (float)trial_launches;
+        if (ms_per_launch) ms_per_launch[c] = ms;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = c;
         }
     }
     // the concurrent kind: every member's own kernel, members in parallel
@@ -647,18 +693,16 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_co
         if (e == cudaSuccess) e = cudaEventElapsedTime(&conc_ms, e0, e1);
         if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (concurrent)");
         conc_ms /= (float)trial_launches;
-        if (ms_per_launch) ms_per_launch[kTuneRowCount * nomrt::kBatchConfigs] = conc_ms;
+        if (ms_per_launch) ms_per_launch[nomrt::kBatchConfigs] = conc_ms;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (out != LBM_OK) return out;
     b->kind = conc_ms < best_ms ? LBM_BATCH_CONCURRENT : LBM_BATCH_FUSED;
     b->config = best;
-    b->rows_per_unit = best_r;
-    b->dirty = true;
     drop_graph(b);
     if (best_config) *best_config = b->kind == LBM_BATCH_CONCURRENT ? -2 : best;
-    if (best_rows) *best_rows = best_r;
+    if (best_rows) *best_rows = b->rows_per_unit;
     return LBM_OK;
 }
 

@@ -344,17 +344,18 @@ class Batch:
         k = {"fused": 0, "concurrent": 1}[kind] if isinstance(kind, str) else int(kind)
         self._check(load().lbm_batch_set_kind(self._h, k))
 
-    def set_config(self, config: int, rows_per_unit: int = 4):
+    def set_config(self, config: int, rows_per_unit: int = 1):
         self._check(load().lbm_batch_set_config(self._h, int(config), int(rows_per_unit)))
 
     def tune(self, trial_launches: int = 5):
-        """Autotune the kernel shape; returns (best config, best rows per unit,
-        {(rows, config): ms per launch})."""
+        """Autotune the kind and the fused kernel's config; returns (best config,
+        -2 if the concurrent kind won; rows per unit; {"fused_cfg<c>": ms per
+        step, "concurrent": ms per step})."""
         best, rows = C.c_int32(), C.c_int32()
-        ms = (C.c_float * 16)()
+        ms = (C.c_float * 6)()
         self._check(load().lbm_batch_tune(self._h, int(trial_launches), C.byref(best), C.byref(rows), ms))
-        table = {(r, c): ms[i * 5 + c] for i, r in enumerate((1, 4, 16)) for c in range(5)}
-        table["concurrent"] = ms[15]
+        table = {f"fused_cfg{c}": ms[c] for c in range(5)}
+        table["concurrent"] = ms[5]
         return best.value, rows.value, table
 
     def step(self, n: int = 1):

@@ -105,6 +105,29 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
     assert b.info()["config"] == best and b.info()["rows_per_unit"] == rows
 
 
+@pytest.mark.parametrize("graph_steps", [0, 4])
+def test_batch_of_more_than_64_members(graph_steps):
+    """70 small cavities of uneven size: the per-step fused kernel runs as two
+    launches (64 + 6 members) and each member still gets its bits alone."""
+    P = _P()
+    cases = [lc.cavity(n=6 + (k % 13), Ra=1e4, seed=k, noise=1e-3) for k in range(70)]
+    b = P.Batch()
+    b.set_kind("fused")
+    b.set_mode(1, graph_steps)
+    lats = [P.Lattice(c, storage="f32", stream=b.stream) for c in cases]
+    for lat in lats:
+        b.add(lat)
+    b.step(8)
+    b.sync()
+    for c, lat in zip(cases, lats):
+        ref = P.Lattice(c, storage="f32")
+        ref.step(8)
+        f, g = lat.populations()
+        fr, gr = ref.populations()
+        assert np.array_equal(f, fr) and np.array_equal(g, gr)
+    b.close()
+
+
 def test_batched_lattice_rejects_lbm_step_and_fp64():
     P = _P()
     b = P.Batch()

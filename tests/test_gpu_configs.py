@@ -7,6 +7,10 @@
 * Differentially heated cavity, 256 x 256, Ra = 1e5, Pr = 0.71, Ma = 0.1,
   2e5 steps in FP64 and FP32 storage: mean Nusselt number on the hot wall
   against the paper's Table 3 (cold wall 4.5273; equal at steady state).
+* Porous-plate thermal Couette, 8 x 64 fluid cells, Re = 5, Pr = 0.71,
+  Ra = 100, run to residual < 1e-10 in FP64: the profiles against the closed
+  forms of Eqs. 36-37 (Sec. 3.3) and against the oracle after the same steps;
+  FP32 after the same steps against the oracle.
 """
 import os
 
@@ -74,3 +78,59 @@ def test_cavity_ra1e5_256_nusselt_against_table3(storage):
     print(f"cavity 256^2 Ra 1e5 {storage}: Nu hot {nu_hot:.4f} cold {nu_cold:.4f} (Table 3: {row[5]})")
     assert abs(nu_hot - row[5]) / row[5] < 0.01
     assert abs(nu_cold - row[5]) / row[5] < 0.01
+
+
+def _eu_et(case, ux, uy, T):
+    """Eqs. 35 and 38 (relative errors of u and T) against Eqs. 36-37."""
+    ue, Te = lc.porous_couette_exact(case)
+    u_num = np.stack([ux[1:-1, :].mean(1), uy[1:-1, :].mean(1)], 1)
+    u_ex = np.stack([ue, np.full(ue.size, case.meta["v0"])], 1)
+    Eu = np.linalg.norm(u_num - u_ex, axis=1).sum() / np.linalg.norm(u_ex, axis=1).sum()
+    ET = np.sqrt(((T[1:-1, :].mean(1) - Te) ** 2).sum() / (Te ** 2).sum())
+    return Eu, ET
+
+
+@pytest.fixture(scope="module")
+def injection_channel_steady():
+    """FP64 GPU run of the 8 x 64 injection channel to residual < 1e-10
+    (checked every 1000 steps); the oracle advanced by the same steps."""
+    import paper_1510_08224_gb300 as P
+    case = lc.porous_couette(H=64, nx=8)
+    g = P.Lattice(case, storage="f64")
+    g.residual()
+    steps = 0
+    r = float("inf")
+    while r >= 1e-10 and steps < 400_000:
+        g.step(1000)
+        steps += 1000
+        r = g.residual()
+    o = oracle.OracleLattice(case)
+    o.step(steps)
+    return case, steps, r, g.macro(), o.macro()
+
+
+def test_injection_channel_fp64_steady_state(injection_channel_steady):
+    case, steps, r, gm, om = injection_channel_steady
+    assert r < 1e-10
+    for a, b in zip(gm, om):
+        assert np.abs(a - b).max() <= 1e-12 * max(1.0, np.abs(b).max())
+    Eu, ET = _eu_et(case, *gm[1:])
+    print(f"injection channel 8x64, FP64, {steps} steps, R {r:.1e}: E_u {Eu:.3e}, E_T {ET:.3e}")
+    # second-order error of the halfway walls at H = 64 (the oracle pin's bounds)
+    assert Eu < 2e-3 and ET < 1e-3
+    # the flow is uniform along the periodic x direction
+    assert np.abs(gm[1][1:-1] - gm[1][1:-1, :1]).max() < 1e-12
+
+
+def test_injection_channel_fp32_against_oracle(injection_channel_steady):
+    import paper_1510_08224_gb300 as P
+    case, steps, r, gm, om = injection_channel_steady
+    g = P.Lattice(case, storage="f32")
+    g.step(steps)
+    _, ux, uy, T = g.macro()
+    _, uxo, uyo, To = om
+    umax = max(np.abs(uxo).max(), np.abs(uyo).max())
+    eu = max(np.abs(ux - uxo).max(), np.abs(uy - uyo).max()) / umax
+    eT = np.abs(T - To).max() / case.delta_T
+    print(f"injection channel 8x64, FP32, {steps} steps: max-norm error u {eu:.2e} (of max|u|), T {eT:.2e}")
+    assert eu <= 1e-4 and eT <= 1e-4
