@@ -271,7 +271,8 @@ typedef enum { LBM_BATCH_FUSED = 0, LBM_BATCH_CONCURRENT = 1 } lbm_batch_kind;
 lbm_status lbm_batch_set_kind(lbm_batch *b, int32_t kind);
 
 /* Kernel shape: config 0..4 asks for 4..8 resident 128-thread blocks per SM
- * (-1: the default, 1 for FP32 and 3 for FP16); rows_per_unit (1..1024) is the
+ * of the per-step FUSED kernel (-1: the default, 1 for FP32 and 3 for FP16;
+ * the persistent kernel always takes 4 blocks per SM); rows_per_unit (1..1024) is the
  * number of consecutive rows of one 128-cell segment a warp of the persistent
  * kernel takes per work unit (default 1). */
 lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_unit);

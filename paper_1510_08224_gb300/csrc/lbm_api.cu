@@ -10,6 +10,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "lattice_impl.h"
@@ -83,17 +84,6 @@ Derived derive(const lbm_params *p) {
 
 bool in_open_02(double v) { return std::isfinite(v) && v > 0.0 && v < 2.0; }
 
-// Cells of HALFWAY walls are solid; cells of NEE walls are boundary nodes.
-bool solid_cell(const lbm_params *p, size_t c) {
-    const uint8_t k = p->flags[c];
-    return k != 0 && p->walls[k - 1].scheme == LBM_WALL_HALFWAY;
-}
-
-bool nee_cell(const lbm_params *p, size_t c) {
-    const uint8_t k = p->flags[c];
-    return k != 0 && p->walls[k - 1].scheme == LBM_WALL_NEE;
-}
-
 // Direction i of a boundary node's nearest fluid node x + e_i: an axis
 // neighbour if one is fluid, else a diagonal one; 0 if there is none.
 int nee_direction(const lbm_params *p, int x, int y) {
@@ -107,13 +97,112 @@ int nee_direction(const lbm_params *p, int x, int y) {
     return 0;
 }
 
-int count_nee(const lbm_params *p) {
-    int n = 0;
-    for (size_t c = 0; c < (size_t)p->nx * p->ny; ++c) n += nee_cell(p, c);
-    return n;
+// One pass over the cells: validates the flag map and, if `out` is given,
+// builds the device-side maps. Rows are split into bands scanned by host
+// threads; results are merged in row order, so they do not depend on the
+// thread count.
+struct CellScan {
+    int pitch = 0;
+    uint8_t *mask = nullptr;   // ny * pitch link map (bit i-1: direction i pulls from a solid cell)
+    uint8_t *flags = nullptr;  // ny * pitch wall ids
+    uint8_t *dir = nullptr;    // ny * pitch nearest-fluid direction of boundary nodes
+};
+
+struct ScanResult {
+    std::string err;  // empty if valid
+    int64_t fluid = 0;
+    std::vector<int2> nee;  // (cell offset in the pitched layout, direction | wall id << 8)
+};
+
+// Rows [y0, y1). Stops at the band's first invalid cell (row-major order).
+void scan_rows(const lbm_params *p, const uint8_t *halfway, int y0, int y1, const CellScan *out, ScanResult &r) {
+    const int nx = p->nx, ny = p->ny;
+    const bool px = p->periodic_x != 0, py = p->periodic_y != 0;
+    char buf[256];
+    for (int y = y0; y < y1; ++y) {
+        // source rows of directions with e_y = -1, 0, +1: y + 1, y, y - 1
+        const int ys[3] = {py ? (y + 1) % ny : y + 1, y, py ? (y - 1 + ny) % ny : y - 1};
+        const uint8_t *row = p->flags + (size_t)y * nx;
+        for (int x = 0; x < nx; ++x) {
+            const uint8_t k = row[x];
+            if (k > p->n_walls) {
+                snprintf(buf, sizeof buf, "cell (%d, %d) has wall id %d > n_walls", x, y, (int)k);
+                r.err = buf;
+                return;
+            }
+            const size_t off = (size_t)y * (out ? out->pitch : 0) + x;
+            if (out) out->flags[off] = k;
+            if (k) {
+                if (!halfway[k]) {  // boundary node of a node-based wall
+                    const int d = nee_direction(p, x, y);
+                    if (d == 0) {
+                        snprintf(buf, sizeof buf,
+                                 "boundary node (%d, %d) of an extrapolated wall has no fluid neighbour", x, y);
+                        r.err = buf;
+                        return;
+                    }
+                    if (out) {
+                        out->dir[off] = (uint8_t)d;
+                        r.nee.push_back(make_int2((int)off, d | ((int)k << 8)));
+                    } else {
+                        r.nee.push_back(make_int2(0, 0));
+                    }
+                }
+                continue;
+            }
+            unsigned m = 0;
+            for (int i = 1; i < 9; ++i) {
+                int sx = x - kEx[i];
+                if (px) sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+                const int sy = ys[kEy[i] + 1];
+                if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
+                    snprintf(buf, sizeof buf,
+                             "fluid cell (%d, %d) touches a non-periodic edge; add a frame of solid cells", x, y);
+                    r.err = buf;
+                    return;
+                }
+                if (halfway[p->flags[(size_t)sy * nx + sx]]) m |= 1u << (i - 1);
+            }
+            if (m == 0xFFu) {
+                snprintf(buf, sizeof buf, "fluid cell (%d, %d) has no fluid neighbour", x, y);
+                r.err = buf;
+                return;
+            }
+            ++r.fluid;
+            if (out) out->mask[off] = (uint8_t)m;
+        }
+    }
 }
 
-// Returns an empty string if p is valid, else the reason.
+ScanResult scan_cells(const lbm_params *p, const CellScan *out) {
+    uint8_t halfway[256] = {0};  // wall id -> its cells are solid (HALFWAY)
+    for (int k = 1; k <= p->n_walls; ++k) halfway[k] = p->walls[k - 1].scheme == LBM_WALL_HALFWAY;
+    const size_t cells = (size_t)p->nx * p->ny;
+    unsigned hw = std::thread::hardware_concurrency();
+    int nthreads = (int)std::min<size_t>(std::max(1u, std::min(hw, 16u)), std::max<size_t>(1, cells >> 18));
+    nthreads = std::min(nthreads, p->ny);
+    std::vector<ScanResult> part(nthreads);
+    std::vector<std::thread> pool;
+    const int band = (p->ny + nthreads - 1) / nthreads;
+    for (int t = 1; t < nthreads; ++t)
+        pool.emplace_back(scan_rows, p, halfway, std::min(p->ny, t * band), std::min(p->ny, (t + 1) * band), out,
+                          std::ref(part[t]));
+    scan_rows(p, halfway, 0, std::min(p->ny, band), out, part[0]);
+    for (auto &th : pool) th.join();
+    ScanResult r;
+    for (auto &q : part) {
+        if (!q.err.empty()) {
+            r.err = q.err;  // the first band with an error holds the first invalid cell
+            return r;
+        }
+        r.fluid += q.fluid;
+        r.nee.insert(r.nee.end(), q.nee.begin(), q.nee.end());
+    }
+    return r;
+}
+
+// Returns an empty string if p's scalar fields are valid, else the reason
+// (the flag map is checked by scan_cells).
 std::string validate(const lbm_params *p) {
     char buf[256];
     if (!p) return "params is NULL";
@@ -151,37 +240,6 @@ std::string validate(const lbm_params *p) {
     const size_t eb = elem_bytes(p->storage);
     const size_t pitch = align_up((size_t)p->nx, 128 / eb);
     if ((size_t)p->ny * pitch >= (size_t)INT32_MAX) return "lattice too large (ny * pitch must be < 2^31)";
-    const int nx = p->nx, ny = p->ny;
-    for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x) {
-            const uint8_t k = p->flags[(size_t)y * nx + x];
-            if (k > p->n_walls) {
-                snprintf(buf, sizeof buf, "cell (%d, %d) has wall id %d > n_walls", x, y, (int)k);
-                return buf;
-            }
-            if (k && p->walls[k - 1].scheme == LBM_WALL_NEE && nee_direction(p, x, y) == 0) {
-                snprintf(buf, sizeof buf, "boundary node (%d, %d) of an extrapolated wall has no fluid neighbour", x,
-                         y);
-                return buf;
-            }
-            if (k) continue;
-            int solid = 0;
-            for (int i = 1; i < 9; ++i) {
-                int sx = x - kEx[i], sy = y - kEy[i];
-                if (p->periodic_x) sx = (sx + nx) % nx;
-                if (p->periodic_y) sy = (sy + ny) % ny;
-                if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
-                    snprintf(buf, sizeof buf,
-                             "fluid cell (%d, %d) touches a non-periodic edge; add a frame of solid cells", x, y);
-                    return buf;
-                }
-                solid += solid_cell(p, (size_t)sy * nx + sx);
-            }
-            if (solid == 8) {
-                snprintf(buf, sizeof buf, "fluid cell (%d, %d) has no fluid neighbour", x, y);
-                return buf;
-            }
-        }
     return std::string();
 }
 
@@ -245,7 +303,12 @@ size_t lbm_footprint_bytes(const lbm_params *p) {
         g_create_error = why;
         return 0;
     }
-    return make_layout(p->nx, p->ny, p->storage, p->n_walls, count_nee(p), thermal_q(p)).total;
+    ScanResult sr = scan_cells(p, nullptr);
+    if (!sr.err.empty()) {
+        g_create_error = sr.err;
+        return 0;
+    }
+    return make_layout(p->nx, p->ny, p->storage, p->n_walls, (int)sr.nee.size(), thermal_q(p)).total;
 }
 
 lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, size_t device_bytes,
@@ -263,7 +326,25 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     h->storage = p->storage;
     h->n_walls = p->n_walls;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
-    const int n_nee = count_nee(p);
+    // host-side maps in one pass over the cells (which also validates them): wall ids, the
+    // link map (bit i-1: direction i pulls from a solid cell; padding and solid cells 0xFF)
+    // and the boundary nodes of node-based walls
+    const int pitch0 = (int)align_up((size_t)p->nx, 128 / elem_bytes(p->storage));
+    std::vector<uint8_t> hmask((size_t)p->ny * pitch0, kSolid), hflags((size_t)p->ny * pitch0, 0),
+        hdir((size_t)p->ny * pitch0, 0);
+    CellScan cs;
+    cs.pitch = pitch0;
+    cs.mask = hmask.data();
+    cs.flags = hflags.data();
+    cs.dir = hdir.data();
+    ScanResult sr = scan_cells(p, &cs);
+    if (!sr.err.empty()) {
+        lbm_destroy(h);
+        return fail(nullptr, LBM_EINVAL, sr.err);
+    }
+    std::vector<int2> &hnee = sr.nee;
+    const int n_nee = (int)hnee.size();
+    h->fluid = sr.fluid;
     h->lay = make_layout(p->nx, p->ny, p->storage, p->n_walls, n_nee, thermal_q(p));
     h->L = &launchers_for(p->storage);
     const size_t need = h->lay.total;
@@ -288,35 +369,8 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
         h->owns_mem = true;
     }
 
-    // host-side maps: wall ids and the link map (bit i-1: direction i pulls from a solid cell)
     const int nx = p->nx, ny = p->ny, pitch = h->lay.pitch;
     h->flags.assign(p->flags, p->flags + (size_t)nx * ny);
-    std::vector<uint8_t> hmask((size_t)ny * pitch, kSolid), hflags((size_t)ny * pitch, 0),
-        hdir((size_t)ny * pitch, 0);
-    std::vector<int2> hnee;
-    for (int y = 0; y < ny; ++y)
-        for (int x = 0; x < nx; ++x) {
-            const size_t c = (size_t)y * nx + x;
-            const uint8_t k = p->flags[c];
-            hflags[(size_t)y * pitch + x] = k;
-            if (k) {
-                if (nee_cell(p, c)) {
-                    const int d = nee_direction(p, x, y);
-                    hdir[(size_t)y * pitch + x] = (uint8_t)d;
-                    hnee.push_back(make_int2(y * pitch + x, d | ((int)k << 8)));
-                }
-                continue;
-            }
-            ++h->fluid;
-            unsigned m = 0;
-            for (int i = 1; i < 9; ++i) {
-                int sx = x - kEx[i], sy = y - kEy[i];
-                if (h->px) sx = (sx + nx) % nx;
-                if (h->py) sy = (sy + ny) % ny;
-                if (solid_cell(p, (size_t)sy * nx + sx)) m |= 1u << (i - 1);
-            }
-            hmask[(size_t)y * pitch + x] = (uint8_t)m;
-        }
     std::vector<WallDev> hw((size_t)p->n_walls + 1);
     std::memset(hw.data(), 0, sizeof(WallDev) * hw.size());
     const double T_ref = p->storage == LBM_F64 ? 0.0 : p->T0;

@@ -456,6 +456,10 @@ cudaError_t launch_grid_step(lbm_batch *b, int config, int parity, cudaStream_t 
     return cudaSuccess;
 }
 
+// The persistent kernel keeps its per-lattice descriptors in registers; four
+// resident blocks per SM is its only shape that does not spill.
+constexpr int kPersistentConfig = 0;
+
 cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
     if (b->kind == LBM_BATCH_CONCURRENT) return launch_concurrent(b, n, st, true);
     const bool nee = any_nee(b);
@@ -466,9 +470,9 @@ cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
         if (b->steps_per_launch > 1 && !nee) {
             const int k = std::min(n, b->steps_per_launch);
             e = b->storage == LBM_F16_SHIFTED
-                    ? nomrt::launch_batch_persistent<__half>(b->cfg(), b->d_lats, b->d_units, b->nunits, parity, k,
+                    ? nomrt::launch_batch_persistent<__half>(kPersistentConfig, b->d_lats, b->d_units, b->nunits, parity, k,
                                                              b->d_bar, b->d_status, st)
-                    : nomrt::launch_batch_persistent<float>(b->cfg(), b->d_lats, b->d_units, b->nunits, parity, k,
+                    : nomrt::launch_batch_persistent<float>(kPersistentConfig, b->d_lats, b->d_units, b->nunits, parity, k,
                                                             b->d_bar, b->d_status, st);
             parity = (parity + k) & 1;
             n -= k;
