@@ -76,10 +76,13 @@ class OrcRates(C.Structure):
 
 
 def lib():
+    """The compiled oracle. NOMRT_ORACLE_LIB, if set, names another build of
+    the same source to load instead (the mutation tests plant a mistake in a
+    copy of the source and check that the pins catch it)."""
     global _lib
     with _lock:
         if _lib is None:
-            L = C.CDLL(build())
+            L = C.CDLL(os.environ.get("NOMRT_ORACLE_LIB") or build())
             dp = C.POINTER(C.c_double)
             L.orc_create.restype = C.c_void_p
             L.orc_create.argtypes = [C.POINTER(OrcParams)]

@@ -42,6 +42,40 @@ def _poiseuille_error(H, s_nu, Re=49.4146):
     return np.abs(ux - ua).sum() / np.abs(ua).sum()  # Eq. 35
 
 
+def test_node_wall_rebuild_from_an_equilibrium_state():
+    """The scheme's definition on a state it must reproduce exactly: every node
+    at the same force-free equilibrium (rho = 1, u0, T0). After streaming, a
+    boundary node's fluid neighbour holds that equilibrium, so its
+    non-equilibrium part is zero and the rebuilt node is the equilibrium at the
+    wall state (1, u_w, T_w) of Eq. 22 and Eq. 30; collision keeps an
+    equilibrium, so that is what the node stores after one step, while every
+    fluid node keeps (1, u0, T0)."""
+    c = lc.porous_couette_nee(H=8, nx=3, Re=10.0, U0=0.02, v0=0.01)
+    E = np.array([[0, 0], [1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1]], float)
+    W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+    def feq(u):
+        eu = E @ u
+        return W * (1 + 3 * eu + 4.5 * eu**2 - 1.5 * (u @ u))
+
+    def geq(T, u):
+        return np.array([(1 - c.varpi) * T] + [c.varpi / 4 * T + 0.5 * (E[i] @ u) * T for i in range(1, 5)])
+
+    u0, T0 = np.array([0.013, -0.007]), 0.37
+    f = np.broadcast_to(feq(u0)[:, None, None], (9, c.ny, c.nx)).copy()
+    g = np.broadcast_to(geq(T0, u0)[:, None, None], (5, c.ny, c.nx)).copy()
+    o = oracle.OracleLattice(c)
+    o.set_populations(f, g)
+    o.step(1)
+    f1, g1 = o.populations()
+    for row, wall in ((0, c.walls[0]), (c.ny - 1, c.walls[1])):
+        uw = np.array([wall.ux, wall.uy])
+        assert np.abs(f1[:, row, :] - feq(uw)[:, None]).max() < 1e-15
+        assert np.abs(g1[:, row, :] - geq(wall.T, uw)[:, None]).max() < 1e-15
+    assert np.abs(f1[:, 1:-1, :] - feq(u0)[:, None, None]).max() < 1e-15
+    assert np.abs(g1[:, 1:-1, :] - geq(T0, u0)[:, None, None]).max() < 1e-15
+
+
 def test_poiseuille_errors_match_table2_in_magnitude_and_order():
     tab = np.loadtxt(os.path.join(GOLDEN, "table1_2_poiseuille.txt"))
     errs = []

@@ -429,6 +429,22 @@ def test_residual_of_a_rescaled_temperature():
     assert o.residual() == 0.0
 
 
+def test_residual_of_a_rescaled_velocity():
+    """Reading A9 for the velocity: with no force, u = sum e f, so replacing
+    f by w + c (f - w) scales u by c everywhere and leaves T alone; then
+    R = |c - 1| / c from the velocity part."""
+    c = lc.periodic_box(6, 5, T0=0.4)
+    o = oracle.OracleLattice(c)
+    f, g = lc.random_state(c, seed=4)
+    o.set_populations(f, g)
+    o.step(3)
+    assert np.isinf(o.residual())
+    f, g = o.populations()
+    w = W[:, None, None]
+    o.set_populations(w + 1.5 * (f - w), g)
+    assert abs(o.residual() - 0.5 / 1.5) < 1e-13
+
+
 def test_oracle_rejects_open_edges_and_unknown_walls():
     c = lc.couette(H=4, nx=3)
     with pytest.raises(ValueError):
