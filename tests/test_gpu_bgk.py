@@ -166,3 +166,19 @@ def test_bgk_rejects_tma_vec8_batches_and_bad_switch():
     b.close()
     with pytest.raises(P.LBMError):
         P.Lattice(case.with_(collision=2))
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("tq", [5, 9])
+def test_bgk_full_size_sampled_nodes(storage, tq):
+    """The benchmark lattice (4096 x 2048 fluid cells) with BGK collisions and
+    either temperature lattice, AUTO step kernel: one step from a seeded random
+    state against the oracle's single-node update at sampled nodes."""
+    from test_gpu_d2q9t import _full_size_sampled
+    base = lc.rayleigh_benard(nx=4096, H=2048, sigma=0.0)
+    case = lc.with_bgk(lc.with_d2q9_temperature(base) if tq == 9 else base)
+    ef, eg, sf, sg = _full_size_sampled(case, storage, seed=29 + tq)
+    if storage == "f64":
+        assert ef <= FP64_TOL * max(sf, 1.0) and eg <= FP64_TOL * max(sg, 1.0)
+    else:
+        assert ef <= ONE_STEP_TOL[storage] * sf and eg <= ONE_STEP_TOL[storage] * sg

@@ -194,3 +194,43 @@ def test_d2q9t_cavity_nusselt_close_to_d2q5():
                 break
         nus.append(g.nusselt(0))
     assert abs(nus[0] - nus[1]) / nus[0] < 1e-2
+
+
+def _full_size_sampled(case, storage, seed, nsample=2000):
+    """Rayleigh-Benard at the benchmark size (4096 x 2048 fluid cells), AUTO step
+    kernel: one step from a seeded random state, every population of sampled
+    nodes (the periodic seam and the wall rows included) against the oracle's
+    single-node update. Returns (max error f, max error g, scale f, scale g)."""
+    P = _P()
+    g = P.Lattice(case, storage=storage)
+    f0, g0 = lc.random_state(case, seed=seed)
+    g.set_populations(f0, g0)
+    fq, gq = g.populations()
+    g.step(1)
+    f1, g1 = g.populations()
+    o = oracle.OracleLattice(case.with_(T_init=None))
+    rng = np.random.default_rng(seed)
+    xs = rng.integers(0, case.nx, nsample)
+    ys = rng.integers(1, case.ny - 1, nsample)
+    xs[:4] = [0, case.nx - 1, 0, case.nx - 1]
+    ys[:4] = [1, 1, case.ny - 2, case.ny - 2]
+    fq = np.ascontiguousarray(fq); gq = np.ascontiguousarray(gq)
+    wT = W9[:, 0, 0] if case.thermal_q == 9 else np.array([0.5, 0.125, 0.125, 0.125, 0.125])
+    ef = eg = sf = sg = 0.0
+    for x, y in zip(xs, ys):
+        fo, go = o.update_node(fq, gq, int(x), int(y))
+        ef = max(ef, np.abs(f1[:, y, x] - fo).max())
+        eg = max(eg, np.abs(g1[:, y, x] - go).max())
+        sf = max(sf, np.abs(fo - W9[:, 0, 0]).max())
+        sg = max(sg, np.abs(go - wT * case.T0).max())
+    return ef, eg, sf, sg
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_d2q9t_full_size_sampled_nodes(storage):
+    case = lc.with_d2q9_temperature(lc.rayleigh_benard(nx=4096, H=2048, sigma=0.0))
+    ef, eg, sf, sg = _full_size_sampled(case, storage, seed=23)
+    if storage == "f64":
+        assert ef <= FP64_TOL * max(sf, 1.0) and eg <= FP64_TOL * max(sg, 1.0)
+    else:
+        assert ef <= ONE_STEP_TOL[storage] * sf and eg <= ONE_STEP_TOL[storage] * sg
