@@ -132,10 +132,10 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
         if (variant == kStepAuto) {
             variant = kStepVec4;
             // VEC4 configs measured fastest on GB300 (4096 x 2048 cells): MRT D2Q5 5 (FP32) or
-            // 7 (FP16) blocks per SM; BGK D2Q5 5 or 6; the D2Q9 temperature model, which keeps
-            // nine more values per cell in registers, 4 or 5
-            if (p.tq == 9) q.config = (sizeof(S) == 4 || p.bgk) ? 0 : 1;
-            else if (p.bgk) q.config = sizeof(S) == 4 ? 1 : 2;
+            // 7 (FP16) blocks per SM; BGK D2Q5 5 for both; the D2Q9 temperature model, which
+            // keeps nine more values per cell in registers, 4
+            if (p.tq == 9) q.config = 0;
+            else if (p.bgk) q.config = 1;
             else q.config = sizeof(S) == 4 ? 1 : 3;
         }
     } else {

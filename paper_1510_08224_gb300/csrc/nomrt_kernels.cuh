@@ -1189,11 +1189,36 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
     for (int i = 0; i < TQ; ++i) Vec4<S>::st(pl.dst_at(9 + i) + r0 + x0, t[i]);
 }
 
+// Bulk prefetch of `bytes` bytes at p into L2 (no registers, no completion to wait for).
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%1], %0;" ::"r"(bytes), "l"(p) : "memory");
+}
+
+// Rows ahead whose population segments a block of the four-cell kernel asks L2
+// to fetch: FP16 storage moves half the bytes per cell, so its loads alone keep
+// too few bytes in flight; a 16-row lead measured best on GB300 (FP32: none).
+template <typename S>
+struct PrefetchRows {
+    static constexpr int value = sizeof(S) == 2 ? 16 : 0;
+};
+
 template <typename S, int MINB, int TQ = 5, bool BGK = false>
 __global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const Geom g, const RatesC<float> r) {
+    constexpr int PF = PrefetchRows<S>::value;
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
-    for (int y = blockIdx.y; y < g.ny; y += gridDim.y) row4<S, Planes<S>, true, TQ, BGK>(pl, g, r, x0, y, lane);
+    for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {
+        if constexpr (PF > 0) {
+            // one thread per plane: this block's 512-cell segment of row y + PF (16-byte
+            // aligned: segments start at multiples of 512 elements, rows are 128-byte pitched)
+            if (threadIdx.x < 9 + TQ && y + PF < g.ny) {
+                const int xs = blockIdx.x * 512;
+                const int n = min(512, g.pitch - xs);
+                prefetch_l2_bulk(pl.src_at(threadIdx.x) + (size_t)(y + PF) * g.pitch + xs, (unsigned)(n * sizeof(S)));
+            }
+        }
+        row4<S, Planes<S>, true, TQ, BGK>(pl, g, r, x0, y, lane);
+    }
 }
 
 }  // namespace nomrt
