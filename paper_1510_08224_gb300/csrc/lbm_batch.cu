@@ -84,33 +84,38 @@ struct GridLat {
 
 struct GroupParams {
     int nlats;
-    int block0[kGroupLats + 1];  // first block of each member; block0[nlats] = grid size
+    int xblocks;                // the members' largest blocks per row (grid x)
+    int row0[kGroupLats + 1];   // first row of each member in the concatenation; row0[nlats] = rows
     GridLat lat[kGroupLats];
 };
 
-// One step of every member of a group: block b belongs to the member l with
-// block0[l] <= b < block0[l + 1] and covers cells 512 xb .. 512 xb + 511 of row
-// y of it, like block (xb, y) of the single-lattice VEC4 kernel.
+// One step of every member of a group. The members' rows are concatenated;
+// block (xb, b) takes concatenated rows b, b + gridDim.y, ...; row r belongs to
+// the member l with row0[l] <= r < row0[l + 1], and the block covers cells
+// 512 xb .. 512 xb + 511 of that row, like block (xb, y) of the single-lattice
+// VEC4 kernel (whose row loop this mirrors). Blocks past a member's row width
+// skip its rows.
 template <typename S, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     k_batch_grid(const __grid_constant__ GroupParams P, int parity) {
-    const int b = blockIdx.x;
-    int lo = 0, hi = P.nlats - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (P.block0[mid] <= b) lo = mid;
-        else hi = mid - 1;
+    const int lane = threadIdx.x & 31;
+    const int x0 = ((int)blockIdx.x * kBatchThreads + (int)threadIdx.x) * 4;
+    for (int row = blockIdx.y; row < P.row0[P.nlats]; row += gridDim.y) {
+        int lo = 0, hi = P.nlats - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.row0[mid] <= row) lo = mid;
+            else hi = mid - 1;
+        }
+        const GridLat &L = P.lat[lo];
+        if ((int)blockIdx.x >= L.xblocks) continue;
+        const int sel = (parity + L.flip) & 1;
+        StridedPlanes<S> pa;
+        pa.src = static_cast<const S *>(sel ? L.pop1 : L.pop0);
+        pa.dst = static_cast<S *>(const_cast<void *>(sel ? L.pop0 : L.pop1));
+        pa.plane = L.plane;
+        row4<S, StridedPlanes<S>, true>(pa, L.g, L.r, x0, row - P.row0[lo], lane);
     }
-    const GridLat &L = P.lat[lo];
-    const int lb = b - P.block0[lo];
-    const int y = lb / L.xblocks, xb = lb - y * L.xblocks;
-    const int sel = (parity + L.flip) & 1;
-    StridedPlanes<S> pa;
-    pa.src = static_cast<const S *>(sel ? L.pop1 : L.pop0);
-    pa.dst = static_cast<S *>(const_cast<void *>(sel ? L.pop0 : L.pop1));
-    pa.plane = L.plane;
-    row4<S, StridedPlanes<S>, true>(pa, L.g, L.r, (xb * kBatchThreads + (int)threadIdx.x) * 4, y,
-                                    threadIdx.x & 31);
 }
 
 template <typename S, int MINB, bool PERSISTENT>
@@ -185,9 +190,10 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
 
 template <typename S, int MINB>
 cudaError_t launch_grid_shape(const GroupParams &G, int parity, cudaStream_t st) {
-    const int blocks = G.block0[G.nlats];
-    if (blocks == 0) return cudaSuccess;
-    k_batch_grid<S, MINB><<<blocks, kBatchThreads, 0, st>>>(G, parity);
+    const int rows = G.row0[G.nlats];
+    if (rows == 0 || G.xblocks == 0) return cudaSuccess;
+    const dim3 grid(G.xblocks, rows < 65535 ? rows : 65535);
+    k_batch_grid<S, MINB><<<grid, kBatchThreads, 0, st>>>(G, parity);
     return cudaGetLastError();
 }
 
@@ -332,7 +338,8 @@ lbm_status rebuild(lbm_batch *b) {
         gl.flip = b->flip[l];
         gl.xblocks = (kp.pitch / 4 + nomrt::kBatchThreads - 1) / nomrt::kBatchThreads;
         gl.r = d.r;
-        G.block0[G.nlats + 1] = G.block0[G.nlats] + kp.ny * gl.xblocks;
+        G.row0[G.nlats + 1] = G.row0[G.nlats] + kp.ny;
+        G.xblocks = std::max(G.xblocks, gl.xblocks);
         G.nlats += 1;
         // units: runs of up to rows_per_unit consecutive rows of a 128-cell segment,
         // skipping rows of the segment that hold no fluid cell
