@@ -59,7 +59,7 @@ class Result:
 class GpuBackend:
     """The CUDA library: lattices in torch device memory, one Batch."""
 
-    def __init__(self, storage: str = "f32", graph_steps: int = 0, tune: bool = True):
+    def __init__(self, storage: str = "f32", graph_steps: int = 0):
         import torch
         from . import lbm
         self._lbm = lbm
@@ -68,7 +68,6 @@ class GpuBackend:
         self.batch = lbm.Batch()
         self.batch.set_kind("concurrent")
         self.batch.set_mode(1, graph_steps)
-        self.tune = tune
 
     def footprint(self, case) -> int:
         p, keep = self._lbm.make_params(case, self.storage)
