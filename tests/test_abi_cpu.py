@@ -73,3 +73,48 @@ def test_null_handles_are_errors():
     assert L.lbm_step(None, 1) == 1
     assert L.lbm_sync(None) == 1
     L.lbm_destroy(None)
+
+
+def test_validation_edge_cases_on_host():
+    """Parameter and flag-map checks that need no GPU (lbm_footprint_bytes runs
+    the same validation as lbm_create): size limit, degenerate lattices, the
+    D2Q9 temperature model's and BGK's parameters, and the first invalid cell
+    reported in row-major order whatever the number of scanning threads."""
+    import paper_1510_08224_gb300 as P
+    L = P.load()
+
+    def footprint(case, st="f32"):
+        p, keep = P.make_params(case, st)
+        return L.lbm_footprint_bytes(C.byref(p)), L.lbm_last_error(None).decode()
+
+    # ny * pitch must stay below 2^31: rejected before the flag map is read
+    small = lc.periodic_box(4, 4)
+    p, keep = P.make_params(small, "f32")
+    p.nx, p.ny = 65536, 40000
+    assert L.lbm_footprint_bytes(C.byref(p)) == 0
+    assert "too large" in L.lbm_last_error(None).decode()
+    # the smallest lattices: one periodic cell, one periodic column
+    assert footprint(lc.periodic_box(1, 1))[0] > 0
+    assert footprint(lc.periodic_box(1, 7))[0] > 0
+    # D2Q9 temperature model and BGK switch
+    q9 = lc.with_d2q9_temperature(lc.couette(H=6, nx=5))
+    n5, _ = footprint(lc.couette(H=6, nx=5))
+    n9, _ = footprint(q9)
+    assert n9 > n5  # four more planes per buffer
+    assert footprint(q9.with_(zeta_q=2.0))[0] == 0
+    assert footprint(q9.with_(thermal_q=7))[0] == 0
+    assert footprint(lc.with_bgk(q9))[0] == n9
+    assert footprint(q9.with_(collision=3))[0] == 0
+    # a boundary node of an extrapolated wall with no fluid neighbour
+    nee = lc.cavity_nee(n=8)
+    fl = nee.flags.copy(); fl[1:4, 1:4] = 1  # bury the corner node (0, 0) under wall cells
+    n, msg = footprint(nee.with_(flags=fl))
+    assert n == 0 and "boundary node" in msg
+    # the first invalid cell in row-major order, with errors in many row bands
+    big = lc.periodic_box(512, 1024)
+    fl = big.flags.copy()
+    fl[900, 17] = 5
+    fl[300, 400] = 9
+    fl[301, 2] = 6
+    n, msg = footprint(big.with_(flags=fl))
+    assert n == 0 and msg == "cell (400, 300) has wall id 9 > n_walls", msg
