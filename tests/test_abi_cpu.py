@@ -93,6 +93,9 @@ def test_validation_edge_cases_on_host():
     p.nx, p.ny = 65536, 40000
     assert L.lbm_footprint_bytes(C.byref(p)) == 0
     assert "too large" in L.lbm_last_error(None).decode()
+    # an empty lattice is rejected
+    p.nx, p.ny = 0, 4
+    assert L.lbm_footprint_bytes(C.byref(p)) == 0 and "nx and ny" in L.lbm_last_error(None).decode()
     # the smallest lattices: one periodic cell, one periodic column
     assert footprint(lc.periodic_box(1, 1))[0] > 0
     assert footprint(lc.periodic_box(1, 7))[0] > 0
