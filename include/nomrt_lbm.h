@@ -261,8 +261,8 @@ lbm_status lbm_batch_remove(lbm_batch *b, lbm_lattice *h);
 lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t graph_steps);
 
 /* How a batch step runs. FUSED: one kernel launch per step over every member
- * (per 64 members), whose grid concatenates the members' own four-cell-kernel
- * grids, with the members' descriptors in the launch's parameter space (the
+ * (per 64 members), whose grid covers the members' concatenated rows with
+ * the four-cell kernel's blocks, the members' descriptors in the launch's parameter space (the
  * default); with steps_per_launch > 1, a cooperative persistent kernel over a
  * work list of row segments instead. CONCURRENT: each member's own single-lattice step
  * kernel (its lbm_set_step_kernel choice), the members on separate streams
