@@ -417,7 +417,12 @@ cudaError_t launch_concurrent(lbm_batch *b, int n, cudaStream_t st, bool advance
     if (e != cudaSuccess) return e;
     e = cudaEventRecord(b->fork, st);
     if (e != cudaSuccess) return e;
-    for (size_t l = 0; l < b->members.size(); ++l) {
+    // largest members first, so the small ones fill in around them
+    std::vector<size_t> order(b->members.size());
+    for (size_t l = 0; l < order.size(); ++l) order[l] = l;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](size_t a, size_t c) { return b->members[a]->fluid > b->members[c]->fluid; });
+    for (size_t l : order) {
         lbm_lattice *h = b->members[l];
         cudaStream_t ls = b->lstreams[l];
         e = cudaStreamWaitEvent(ls, b->fork, 0);
