@@ -149,6 +149,15 @@ __global__ void __launch_bounds__(128, MINB) k_step8h(const Planes<__half> pl, c
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 8;
     for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {
+        // one thread per plane asks L2 for this block's 1024-cell segment of row y + 16
+        // (as the four-cell kernel does; 16-byte aligned: segments start at multiples of
+        // 1024 elements, rows are 128-byte pitched)
+        if (threadIdx.x < kQ && y + PrefetchRows<__half>::value < g.ny) {
+            const int xs = blockIdx.x * 1024;
+            const int n = min(1024, g.pitch - xs);
+            prefetch_l2_bulk(pl.src[threadIdx.x] + (size_t)(y + PrefetchRows<__half>::value) * g.pitch + xs,
+                             (unsigned)(n * sizeof(__half)));
+        }
         const int r0 = y * g.pitch;
         const bool inrow = x0 < g.pitch;
         uint2 m8 = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
