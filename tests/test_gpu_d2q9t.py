@@ -234,3 +234,26 @@ def test_d2q9t_full_size_sampled_nodes(storage):
         assert ef <= FP64_TOL * max(sf, 1.0) and eg <= FP64_TOL * max(sg, 1.0)
     else:
         assert ef <= ONE_STEP_TOL[storage] * sf and eg <= ONE_STEP_TOL[storage] * sg
+
+
+# Accumulated max-norm error after 4000 steps against the FP64 oracle (cavity
+# 32 x 32, Ra = 1e4, from rest): measured FP32 u 3.0e-7 (of max |u|), T 1.9e-7
+# (of delta T); FP16 u 3.8e-3, T 1.2e-3; bounded with margin.
+D2Q9T_MANY_STEP_TOL = {"f32": {"u": 1e-6, "T": 1e-6}, "f16": {"u": 1.5e-2, "T": 5e-3}}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_d2q9t_reduced_precision_cavity_error(storage):
+    P = _P()
+    case = lc.with_d2q9_temperature(lc.cavity(n=32, Ra=1e4, noise=1e-3))
+    g = P.Lattice(case, storage=storage)
+    o = oracle.OracleLattice(case, threads=4)
+    g.step(4000)
+    o.step(4000)
+    _, uxg, uyg, Tg = g.macro()
+    _, uxo, uyo, To = o.macro()
+    umax = max(np.abs(uxo).max(), np.abs(uyo).max())
+    eu = max(np.abs(uxg - uxo).max(), np.abs(uyg - uyo).max()) / umax
+    eT = np.abs(Tg - To).max() / case.delta_T
+    print(f"D2Q9 T {storage}: max-norm error u {eu:.3e} (of max|u|), T {eT:.3e} (of dT)")
+    assert eu <= D2Q9T_MANY_STEP_TOL[storage]["u"] and eT <= D2Q9T_MANY_STEP_TOL[storage]["T"]
