@@ -7,7 +7,9 @@
  * f_bar (Eqs. 7-9: pull streaming, raw-moment map with the non-orthogonal M of
  * Eq. 13, relaxation Eq. 8 with Eqs. 16, 17, 20, back map with M^-1 of Eq. A1)
  * and the D2Q5 temperature populations g (Eqs. 24-29, N^-1 of Eq. A2), with the
- * Boussinesq force of Eq. 4, in one fused CUDA kernel.
+ * Boussinesq force of Eq. 4, in one fused CUDA kernel. Options: the D2Q9
+ * temperature model of Eqs. 31-33 instead of D2Q5, and the single-rate (BGK)
+ * special case of both collisions.
  *
  * Conventions common to every call:
  *  - Every call returns an lbm_status and never throws or aborts.
@@ -15,7 +17,8 @@
  *  - A lattice is bound to one CUDA stream; its calls are not thread-safe.
  *    Different lattices are independent.
  *  - Host arrays are row-major [ny][nx] planes (x fastest); population exports
- *    are [9][ny][nx] (f, directions of Eq. 5) and [5][ny][nx] (g).
+ *    are [9][ny][nx] (f, directions of Eq. 5) and [5][ny][nx] (g; [9][ny][nx]
+ *    with the D2Q9 temperature model).
  *  - Lengths are lattice units (delta_x = delta_t = 1, c = 1, rho0 = 1: Sec. 3).
  *  - Walls are half-way between a fluid cell and a solid cell (halfway
  *    bounce-back), or on boundary nodes (non-equilibrium extrapolation), per
