@@ -477,6 +477,66 @@ def run_cost(args):
     return 0
 
 
+def cavity_table3_quantities(case, rho, ux, uy, T):
+    """The quantities of Table 3 (Sec. 3.4) from the steady fields of a
+    node-based cavity (walls on the boundary nodes, n intervals, L = n):
+    u_x max on the vertical midline and u_y max on the horizontal midline in
+    units of alpha / L, with their positions; the local Nusselt number on the
+    cold wall, -L (dT/dx)_wall / dT with the second-order one-sided gradient
+    (3 T_w - 4 T_1 + T_2) / 2 taken toward the wall, its maximum and position,
+    and its mean by the trapezoidal rule over the wall."""
+    n = case.nx - 1
+    scale = n / case.alpha
+    mid = n // 2
+    col = ux[:, mid] * scale
+    row = uy[mid, :] * scale
+    jy, ix = int(np.argmax(col)), int(np.argmax(row))
+    Tw = T[:, n]
+    grad = (3.0 * Tw - 4.0 * T[:, n - 1] + T[:, n - 2]) / 2.0   # dT/dx at x = L
+    nu_loc = -n * grad / case.delta_T
+    jn = int(np.argmax(nu_loc))
+    nu_mean = float(np.sum((nu_loc[1:] + nu_loc[:-1]) / 2.0) / n)
+    return {"ux_max": float(col[jy]), "y_max": jy / n, "uy_max": float(row[ix]), "x_max": ix / n,
+            "Nu_max": float(nu_loc[jn]), "y_Nu": jn / n, "Nu_mean": nu_mean}
+
+
+def run_table3(args):
+    """Table 3 of the paper (natural convection in a square cavity, Pr = 0.71,
+    Ma = 0.1, the paper's node-based walls and grids), each Ra run to a
+    steady-state residual below 1e-10, FP64 storage."""
+    import torch
+    import paper_1510_08224_gb300 as P
+    torch.cuda.set_device(0)
+    table = np.loadtxt(os.path.join(ROOT, "tests", "golden", "table3_cavity.txt"))
+    rows = {}
+    t0 = time.perf_counter()
+    for Ra, grid, uxp, uyp, nmaxp, nmeanp in table:
+        case = lc.cavity_nee(n=int(grid), Ra=float(Ra))
+        lat = P.Lattice(case, storage=args.storage)
+        lat.residual()
+        steps, r = 0, float("inf")
+        while r >= 1e-10 and steps < 3_000_000:
+            lat.step(2000)
+            steps += 2000
+            r = lat.residual()
+        q = cavity_table3_quantities(case, *lat.macro())
+        q["Nu_mean_hot_library"] = lat.nusselt("left", L=float(grid))
+        q.update(steps=steps, residual=r)
+        q["paper"] = {"ux_max": uxp, "uy_max": uyp, "Nu_max": nmaxp, "Nu_mean": nmeanp}
+        q["rel_dev"] = {k: round((q[k] - v) / v, 5) for k, v in q["paper"].items()}
+        rows[f"{Ra:g}"] = q
+        lat.close()
+    line = {"metric": METRIC, "value": max(abs(v) for q in rows.values() for v in q["rel_dev"].values()),
+            "unit": "max relative deviation from Table 3", "n_gpus": 1, "higher_is_better": False,
+            "dtype": COMPUTE_DTYPE[args.storage], "data": "synthetic",
+            "config": {"workload": "table3_cavity_nee", "storage": STORAGE_NAME[args.storage],
+                       "walls": "node-based, non-equilibrium extrapolation", "Pr": 0.71, "Ma": 0.1,
+                       "steady": "residual < 1e-10, checked every 2000 steps"},
+            "rows": rows, "seconds": round(time.perf_counter() - t0, 1)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     """Continuous-batching serving: Poisson arrivals (20 per second, seed 0) of
     cavity and Rayleigh-Benard requests, sides log-uniform in [64, 2048], Ra
@@ -538,8 +598,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--sweep", action="store_true", help="cost workload: time every step kernel of each model")
-    ap.add_argument("--workload", default="rb", choices=["rb", "batch", "serve", "cost"],
-                    help="rb: the 4096 x 2048 Rayleigh-Benard step (default); batch: uneven cavities advanced together")
+    ap.add_argument("--workload", default="rb", choices=["rb", "batch", "serve", "cost", "table3"],
+                    help="rb: the 4096 x 2048 Rayleigh-Benard step (default); batch: uneven cavities advanced together; serve: the serving stream; cost: collision operators; table3: the cavity of Table 3")
     ap.add_argument("--count", type=int, default=64, help="lattices (batch) or requests (serve)")
     ap.add_argument("--side-hi", type=int, default=2048, help="largest side of a served request")
     ap.add_argument("--step-cap", type=int, default=20000, help="step cap of a served request")
@@ -555,6 +615,8 @@ def main():
         return run_serving(args)
     if args.workload == "cost":
         return run_cost(args)
+    if args.workload == "table3":
+        return run_table3(args)
 
     import torch
     import paper_1510_08224_gb300 as P
