@@ -550,7 +550,7 @@ def run_serving(args):
     reqs = [serve.Request(k, c, t, nusselt_sides=((0,) if kind == "cavity" else (2,))) for k, (t, kind, c) in
             enumerate(stream)]
     cells = sum(int((r.case.flags == 0).sum()) for r in reqs)
-    be = serve.GpuBackend(args.storage)
+    be = serve.GpuBackend(args.storage, graph_steps=args.graph_steps)
     srv = serve.Server(be, budget_bytes=150e9, check_every=args.check_every, tol=1e-6, step_cap=args.step_cap)
     t0 = time.perf_counter()
     res = srv.run(reqs, realtime=True)
@@ -570,7 +570,7 @@ def run_serving(args):
                    "sides": f"log-uniform [64, {args.side_hi}]", "Ra": "log-uniform [1e3, 1e6]",
                    "types": "cavity | rayleigh_benard", "tol": 1e-6, "step_cap": srv.step_cap,
                    "check_every": args.check_every, "hbm_budget_bytes": 150e9, "storage": STORAGE_NAME[args.storage],
-                   "requests": len(reqs), "fluid_cells_total": cells},
+                   "requests": len(reqs), "fluid_cells_total": cells, "graph_steps": args.graph_steps},
         "served": {**s_ours, "makespan_s": round(span, 3), "peak_hbm_bytes": srv.peak_in_use,
                    "max_concurrent": srv.max_active,
                    "MLUPS": round(s_ours["cell_steps"] / span / 1e6, 1)},
@@ -604,6 +604,8 @@ def main():
     ap.add_argument("--side-hi", type=int, default=2048, help="largest side of a served request")
     ap.add_argument("--step-cap", type=int, default=20000, help="step cap of a served request")
     ap.add_argument("--check-every", type=int, default=500, help="steps between residual checks (serve)")
+    ap.add_argument("--graph-steps", type=int, default=20,
+                    help="serve: steps per captured CUDA graph of the served batch (0: launches from the host)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
