@@ -19,8 +19,8 @@ STORAGE = {"f64": 0, "f32": 1, "f16": 2}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 SIDES = {"left": 0, "right": 1, "bottom": 2, "top": 3}
 
-# Every symbol include/nomrt_lbm.h declares.
 STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3, "vec8": 4}
+# Every symbol include/nomrt_lbm.h declares.
 EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_step_kernel_count",
             "lbm_set_step_kernel", "lbm_read_macro",
             "lbm_nusselt",
@@ -263,8 +263,8 @@ class Lattice:
         _check(load().lbm_sync(self._h), self._h)
 
     def set_step_kernel(self, variant, config: int = 0):
-        """variant 'auto', 'scalar', 'vec4' or 'tma' and a config index (see
-        lbm_set_step_kernel)."""
+        """variant 'auto', 'scalar', 'vec4', 'vec8' or 'tma' and a config index
+        (see lbm_set_step_kernel)."""
         v = STEP_VARIANTS[variant] if isinstance(variant, str) else int(variant)
         _check(load().lbm_set_step_kernel(self._h, v, int(config)), self._h)
         self.kernel = (variant, int(config))
