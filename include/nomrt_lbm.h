@@ -299,6 +299,14 @@ lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
  * grid barrier (the members' state is then undefined). */
 lbm_status lbm_batch_sync(lbm_batch *b);
 
+/* Test hook for the timeout path. With extra = 1 the persistent kernel's grid
+ * barrier waits for one more arrival than the grid has, so its bounded wait
+ * (about 2 s) expires on purpose: the kernel records the timeout in the batch's
+ * status word and returns, and the next lbm_batch_sync reports LBM_ETIMEOUT
+ * (the members' state is then undefined). No fault and no hang are involved.
+ * extra = 0 restores normal operation. LBM_EINVAL for other values. */
+lbm_status lbm_batch_debug_barrier_extra(lbm_batch *b, int32_t extra);
+
 /* Members, their fluid cells, work units, active config (-2 for the
  * CONCURRENT kind) and rows per unit, batch steps taken. Any pointer may be
  * NULL. */

@@ -143,7 +143,9 @@ cudaError_t resident_grid(K kern, int *blocks) {
 
 // Grid-wide barrier of a cooperative launch. Clock-bounded: on expiry it
 // records kStatusTimeout and returns false (the caller then returns).
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status) {
+// `expected` is the number of arrivals that completes it: the grid size (a
+// larger value is the test hook lbm_batch_debug_barrier_extra).
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status, unsigned expected) {
     __shared__ int ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -152,7 +154,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status) {
         const unsigned gen = *vgen;
         __threadfence();
         const unsigned arrived = atomicAdd(bar, 1u) + 1u;
-        if (arrived == gridDim.x) {
+        if (arrived == expected) {
             atomicExch(bar, 0u);
             __threadfence();
             atomicAdd(bar + 1, 1u);
@@ -177,14 +179,15 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status) {
 // L2-coherent path because step s + 1 reads what step s wrote.
 template <typename S, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
-    k_batch_persistent(const BatchLat *lats, const int4 *units, int nunits, int parity0, int nsteps, unsigned *bar,
+    k_batch_persistent(const BatchLat *lats, const int4 *units, int nunits, int parity0, int nsteps, unsigned expected,
+                       unsigned *bar,
                        int *status) {
     const int lane = threadIdx.x & 31;
     const int stride = gridDim.x * kBatchWarps;
     for (int s = 0; s < nsteps; ++s) {
         for (int w = blockIdx.x * kBatchWarps + (threadIdx.x >> 5); w < nunits; w += stride)
             batch_unit<S, false>(lats, units[w], parity0 + s, lane);
-        if (s + 1 < nsteps && !grid_barrier(bar, status)) return;
+        if (s + 1 < nsteps && !grid_barrier(bar, status, expected)) return;
     }
 }
 
@@ -210,7 +213,7 @@ cudaError_t launch_batch_grid(int config, const GroupParams &G, int parity, cuda
 
 template <typename S, int MINB>
 cudaError_t launch_persistent_shape(const BatchLat *lats, const int4 *units, int nunits, int parity, int nsteps,
-                                    unsigned *bar, int *status, cudaStream_t st) {
+                                    int barrier_extra, unsigned *bar, int *status, cudaStream_t st) {
     auto kern = k_batch_persistent<S, MINB>;
     int blocks = 0;
     cudaError_t e = resident_grid<GridTag<S, MINB, true>>(kern, &blocks);
@@ -227,19 +230,20 @@ cudaError_t launch_persistent_shape(const BatchLat *lats, const int4 *units, int
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, kern, lats, units, nunits, parity, nsteps, bar, status);
+    const unsigned expected = (unsigned)(blocks + barrier_extra);
+    return cudaLaunchKernelEx(&cfg, kern, lats, units, nunits, parity, nsteps, expected, bar, status);
 }
 
 template <typename S>
 cudaError_t launch_batch_persistent(int config, const BatchLat *lats, const int4 *units, int nunits, int parity,
-                                    int nsteps, unsigned *bar, int *status, cudaStream_t st) {
+                                    int nsteps, int barrier_extra, unsigned *bar, int *status, cudaStream_t st) {
     if (nunits == 0) return cudaSuccess;
     switch (config) {
-        case 1: return launch_persistent_shape<S, 5>(lats, units, nunits, parity, nsteps, bar, status, st);
-        case 2: return launch_persistent_shape<S, 6>(lats, units, nunits, parity, nsteps, bar, status, st);
-        case 3: return launch_persistent_shape<S, 7>(lats, units, nunits, parity, nsteps, bar, status, st);
-        case 4: return launch_persistent_shape<S, 8>(lats, units, nunits, parity, nsteps, bar, status, st);
-        default: return launch_persistent_shape<S, 4>(lats, units, nunits, parity, nsteps, bar, status, st);
+        case 1: return launch_persistent_shape<S, 5>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
+        case 2: return launch_persistent_shape<S, 6>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
+        case 3: return launch_persistent_shape<S, 7>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
+        case 4: return launch_persistent_shape<S, 8>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
+        default: return launch_persistent_shape<S, 4>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
     }
 }
 
@@ -268,6 +272,7 @@ struct lbm_batch {
     int steps_per_launch = 1;
     int graph_steps = 32;
     int rows_per_unit = 1;
+    int barrier_extra = 0;  // test hook: grid-barrier arrivals that never come
     int kind = LBM_BATCH_FUSED;
     // concurrent kind: one stream per member for the fork/join of the graph
     std::vector<cudaStream_t> lstreams;
@@ -483,9 +488,9 @@ cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
             const int k = std::min(n, b->steps_per_launch);
             e = b->storage == LBM_F16_SHIFTED
                     ? nomrt::launch_batch_persistent<__half>(kPersistentConfig, b->d_lats, b->d_units, b->nunits, parity, k,
-                                                             b->d_bar, b->d_status, st)
+                                                             b->barrier_extra, b->d_bar, b->d_status, st)
                     : nomrt::launch_batch_persistent<float>(kPersistentConfig, b->d_lats, b->d_units, b->nunits, parity, k,
-                                                            b->d_bar, b->d_status, st);
+                                                            b->barrier_extra, b->d_bar, b->d_status, st);
             parity = (parity + k) & 1;
             n -= k;
         } else {
@@ -654,6 +659,14 @@ lbm_status lbm_batch_sync(lbm_batch *b) {
         cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned));
         return bfail(b, LBM_ETIMEOUT, "the persistent batch kernel gave up a grid barrier");
     }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_debug_barrier_extra(lbm_batch *b, int32_t extra) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    if (extra < 0 || extra > 1) return bfail(b, LBM_EINVAL, "extra must be 0 or 1");
+    b->barrier_extra = extra;
+    drop_graph(b);
     return LBM_OK;
 }
 

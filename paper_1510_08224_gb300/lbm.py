@@ -27,7 +27,7 @@ EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_st
             "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
             "lbm_destroy", "lbm_residual_fields_noalloc", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
             "lbm_batch_set_mode", "lbm_batch_set_kind", "lbm_batch_set_config", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
-            "lbm_batch_info", "lbm_batch_last_error", "lbm_batch_destroy")
+            "lbm_batch_info", "lbm_batch_last_error", "lbm_batch_destroy", "lbm_batch_debug_barrier_extra")
 
 
 class LBMError(RuntimeError):
@@ -108,6 +108,7 @@ def load():
                            ("lbm_batch_tune", [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                                C.POINTER(C.c_float)]),
                            ("lbm_batch_step", [vp, C.c_int64]), ("lbm_batch_sync", [vp]),
+                           ("lbm_batch_debug_barrier_extra", [vp, C.c_int32]),
                            ("lbm_batch_info", [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                                C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)])):
             getattr(L, name).restype = C.c_int
@@ -360,6 +361,11 @@ class Batch:
 
     def step(self, n: int = 1):
         self._check(load().lbm_batch_step(self._h, int(n)))
+
+    def debug_barrier_extra(self, extra: int):
+        """Test hook: make the persistent kernel's grid barrier time out (see
+        lbm_batch_debug_barrier_extra)."""
+        self._check(load().lbm_batch_debug_barrier_extra(self._h, int(extra)))
 
     def sync(self):
         self._check(load().lbm_batch_sync(self._h))

@@ -141,3 +141,39 @@ def test_batched_lattice_rejects_lbm_step_and_fp64():
         b.add(P.Lattice(lc.couette(H=4, nx=3), storage="f16"))  # storage mix
     b.remove(lat)
     lat.step(1)
+
+
+def test_persistent_barrier_timeout_is_reported_and_recoverable():
+    """The failure path of the cooperative persistent kernel, without a fault:
+    the test hook makes its grid barrier wait for an arrival that never comes,
+    the bounded wait (about 2 s) expires, lbm_batch_sync reports LBM_ETIMEOUT,
+    and after the hook is cleared the batch works again, bit for bit."""
+    import time
+    P = _P()
+    cases = _mix()[:5]  # no node-based walls: those force one launch per step
+    b = P.Batch()
+    lats = [P.Lattice(c, storage="f32", stream=b.stream) for c in cases]
+    for lat in lats:
+        b.add(lat)
+    b.set_kind("fused")
+    b.set_mode(4, 0)
+    b.debug_barrier_extra(1)
+    t0 = time.perf_counter()
+    b.step(4)
+    with pytest.raises(P.LBMError) as e:
+        b.sync()
+    assert e.value.status == 5  # LBM_ETIMEOUT
+    assert time.perf_counter() - t0 < 60
+    with pytest.raises(P.LBMError):
+        b.debug_barrier_extra(2)
+    b.debug_barrier_extra(0)
+    for i, (c, lat) in enumerate(zip(cases, lats)):
+        f0, g0 = lc.random_state(c, seed=70 + i)
+        lat.set_populations(f0, g0)
+    b.step(8)
+    b.sync()
+    for i, (c, lat) in enumerate(zip(cases, lats)):
+        f, g = lat.populations()
+        fr, gr = _alone(P, c, "f32", 8, 70 + i)
+        assert np.array_equal(f, fr) and np.array_equal(g, gr), i
+    b.close()
