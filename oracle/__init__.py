@@ -62,6 +62,7 @@ class OrcParams(C.Structure):
         ("theta", C.c_double),
         ("zeta_q", C.c_double), ("zeta_eps", C.c_double),
         ("collision", C.c_int32),
+        ("rho_in_u_terms", C.c_int32),
     ]
 
 
@@ -71,7 +72,7 @@ class OrcRates(C.Structure):
         ("g_beta", C.c_double), ("T0", C.c_double),
         ("ax", C.c_double), ("ay", C.c_double), ("varpi", C.c_double),
         ("s8_literal", C.c_int32), ("tq", C.c_int32), ("theta", C.c_double),
-        ("bgk", C.c_int32),
+        ("bgk", C.c_int32), ("rho_in_u", C.c_int32),
     ]
 
 
@@ -124,9 +125,11 @@ def tables():
 
 
 def make_rates(s, z, g_beta=0.0, T0=0.0, ax=0.0, ay=0.0, varpi=0.5, s8_literal=False, theta=1.0,
-               bgk=False) -> OrcRates:
+               bgk=False, rho_in_u=False) -> OrcRates:
     """z has 5 entries (D2Q5 temperature, Eq. 29) or 9 (the D2Q9 model, Eq. 32).
-    bgk: single-relaxation-time collisions at omega = s[4], zeta = z[1]."""
+    bgk: single-relaxation-time collisions at omega = s[4], zeta = z[1].
+    rho_in_u: the ablation of reading A1 (rho, not rho0, in the velocity-bearing
+    terms of the flow collision)."""
     r = OrcRates()
     for k in range(9):
         r.s[k] = float(s[k])
@@ -137,6 +140,7 @@ def make_rates(s, z, g_beta=0.0, T0=0.0, ax=0.0, ay=0.0, varpi=0.5, s8_literal=F
     r.tq = 9 if len(z) == 9 else 5
     r.theta = float(theta)
     r.bgk = int(bool(bgk))
+    r.rho_in_u = int(bool(rho_in_u))
     return r
 
 
@@ -155,7 +159,7 @@ def collide_node(rates: OrcRates, fbar, g):
 class OracleLattice:
     """A lattice advanced by the oracle. ``case`` is an ``lbm_cases.Case``."""
 
-    def __init__(self, case, s8_literal: bool = False, threads: int = 1):
+    def __init__(self, case, s8_literal: bool = False, threads: int = 1, rho_in_u: bool = False):
         self.case = case
         self.nx, self.ny = case.nx, case.ny
         flags = np.ascontiguousarray(case.flags, dtype=np.uint8)
@@ -183,6 +187,7 @@ class OracleLattice:
         p.zeta_q = float(getattr(case, "zeta_q", 1.0))
         p.zeta_eps = float(getattr(case, "zeta_eps", 1.0))
         p.collision = int(getattr(case, "collision", 0))
+        p.rho_in_u_terms = int(bool(rho_in_u))
         self._p = p
         h = lib().orc_create(C.byref(p))
         if not h:

@@ -143,6 +143,7 @@ typedef struct {
     double theta;              /* the switch of Eq. 31, 0 or 1 (D2Q9 model) */
     double zeta_q, zeta_eps;   /* kinetic rates of Eq. 32 (D2Q9 model) */
     int32_t collision;         /* 0: the MRT collisions (Eq. 8, Eq. 24 or Eq. 32); 1: BGK (one rate each) */
+    int32_t rho_in_u_terms;    /* 1: the alternative to reading A1 (rho, not rho0, in every term; ablation) */
 } orc_params;
 
 /* Per-node collision inputs. s[9] is Lambda of Eq. 20; z is Q of Eq. 29 (its
@@ -155,6 +156,7 @@ typedef struct {
     int32_t tq;
     double theta;
     int32_t bgk;   /* 1: single-relaxation-time collisions with omega = s[4], zeta = z[1] */
+    int32_t rho_in_u; /* 1: rho instead of rho0 in the velocity-bearing terms of the flow collision */
 } orc_rates;
 
 typedef struct {
@@ -191,14 +193,17 @@ void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[9
     /* Eq. 18: density. */
     double rho = 0.0;
     for (int i = 0; i < 9; ++i) rho += fbar[i];
-    /* Eq. 19 with j = rho0 u (incompressible approximation, reading A1). */
+    /* Eq. 19 with j = rho0 u (incompressible approximation, reading A1); the
+     * ablation rho_in_u keeps rho there and in every term below, as Eqs. 16,
+     * 17 and 19 are printed. */
+    const double R0 = r->rho_in_u ? rho : RHO0;
     double jx = 0.0, jy = 0.0;
     for (int i = 0; i < 9; ++i) {
         jx += EX[i] * fbar[i];
         jy += EY[i] * fbar[i];
     }
-    double ux = (jx + 0.5 * RHO0 * Fx) / RHO0;
-    double uy = (jy + 0.5 * RHO0 * Fy) / RHO0;
+    double ux = (jx + 0.5 * R0 * Fx) / R0;
+    double uy = (jy + 0.5 * R0 * Fy) / R0;
     double uu = ux * ux + uy * uy;
     if (macro) {
         macro[0] = rho;
@@ -219,8 +224,8 @@ void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[9
         for (int i = 0; i < 9; ++i) {
             double eu = EX[i] * ux + EY[i] * uy;
             double eF = EX[i] * Fx + EY[i] * Fy;
-            double feq = W9[i] * (rho + RHO0 * (eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2)));
-            double Fi = W9[i] * RHO0 * (((EX[i] - ux) * Fx + (EY[i] - uy) * Fy) / CS2 + eu * eF / (CS2 * CS2));
+            double feq = W9[i] * (rho + R0 * (eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2)));
+            double Fi = W9[i] * R0 * (((EX[i] - ux) * Fx + (EY[i] - uy) * Fy) / CS2 + eu * eF / (CS2 * CS2));
             fstar[i] = fbar[i] - om * (fbar[i] - feq) + (1.0 - 0.5 * om) * Fi;
         }
         for (int i = 0; i < tq; ++i) {
@@ -244,26 +249,26 @@ void orc_collide_node(const orc_rates *r, const double fbar[9], const double g[9
     /* Eq. 16 under reading A1. */
     double meq[9];
     meq[0] = rho;
-    meq[1] = RHO0 * ux;
-    meq[2] = RHO0 * uy;
-    meq[3] = 2.0 / 3.0 * rho + RHO0 * uu;
-    meq[4] = RHO0 * (ux * ux - uy * uy);
-    meq[5] = RHO0 * ux * uy;
-    meq[6] = 1.0 / 3.0 * RHO0 * uy;
-    meq[7] = 1.0 / 3.0 * RHO0 * ux;
-    meq[8] = 1.0 / 9.0 * rho + 1.0 / 3.0 * RHO0 * uu;
+    meq[1] = R0 * ux;
+    meq[2] = R0 * uy;
+    meq[3] = 2.0 / 3.0 * rho + R0 * uu;
+    meq[4] = R0 * (ux * ux - uy * uy);
+    meq[5] = R0 * ux * uy;
+    meq[6] = 1.0 / 3.0 * R0 * uy;
+    meq[7] = 1.0 / 3.0 * R0 * ux;
+    meq[8] = 1.0 / 9.0 * rho + 1.0 / 3.0 * R0 * uu;
     /* Eq. 17 under readings A1 and A2. */
     double S[9];
     S[0] = 0.0;
-    S[1] = RHO0 * Fx;
-    S[2] = RHO0 * Fy;
-    S[3] = 2.0 * RHO0 * (ux * Fx + uy * Fy);
-    S[4] = 2.0 * RHO0 * (ux * Fx - uy * Fy);
-    S[5] = RHO0 * (ux * Fy + uy * Fx);
-    S[6] = 1.0 / 3.0 * RHO0 * Fy;
-    S[7] = 1.0 / 3.0 * RHO0 * Fx;
-    S[8] = r->s8_literal ? 2.0 / 3.0 * RHO0 * (ux * Fy + uy * Fx)
-                         : 2.0 / 3.0 * RHO0 * (ux * Fx + uy * Fy);
+    S[1] = R0 * Fx;
+    S[2] = R0 * Fy;
+    S[3] = 2.0 * R0 * (ux * Fx + uy * Fy);
+    S[4] = 2.0 * R0 * (ux * Fx - uy * Fy);
+    S[5] = R0 * (ux * Fy + uy * Fx);
+    S[6] = 1.0 / 3.0 * R0 * Fy;
+    S[7] = 1.0 / 3.0 * R0 * Fx;
+    S[8] = r->s8_literal ? 2.0 / 3.0 * R0 * (ux * Fy + uy * Fx)
+                         : 2.0 / 3.0 * R0 * (ux * Fx + uy * Fy);
     /* Eq. 8 with the diagonal Lambda of Eq. 20 (delta_t = 1). */
     double ms[9];
     for (int k = 0; k < 9; ++k)
@@ -326,6 +331,7 @@ void orc_rates_from_params(const orc_params *p, orc_rates *r) {
     r->tq = p->thermal_q == 9 ? 9 : 5;
     r->theta = p->theta;
     r->bgk = p->collision == 1;
+    r->rho_in_u = p->rho_in_u_terms != 0;
     if (r->tq == 9) {
         /* Eq. 32 with alpha = c_s^2 (1/zeta_alpha - 1/2) */
         double z_alpha = 1.0 / (0.5 + p->alpha / CS2);

@@ -48,23 +48,23 @@ MUTANTS = [
      "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};",
      "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 9.0};"),
     ("half-force sign in u (Eq. 19)",
-     "double uy = (jy + 0.5 * RHO0 * Fy) / RHO0;",
-     "double uy = (jy - 0.5 * RHO0 * Fy) / RHO0;"),
+     "double uy = (jy + 0.5 * R0 * Fy) / R0;",
+     "double uy = (jy - 0.5 * R0 * Fy) / R0;"),
     ("m3_eq density coefficient (Eq. 16)",
-     "meq[3] = 2.0 / 3.0 * rho + RHO0 * uu;",
-     "meq[3] = 1.0 / 3.0 * rho + RHO0 * uu;"),
+     "meq[3] = 2.0 / 3.0 * rho + R0 * uu;",
+     "meq[3] = 1.0 / 3.0 * rho + R0 * uu;"),
     ("m8_eq density coefficient (Eq. 16)",
-     "meq[8] = 1.0 / 9.0 * rho + 1.0 / 3.0 * RHO0 * uu;",
-     "meq[8] = 1.0 / 3.0 * rho + 1.0 / 3.0 * RHO0 * uu;"),
+     "meq[8] = 1.0 / 9.0 * rho + 1.0 / 3.0 * R0 * uu;",
+     "meq[8] = 1.0 / 3.0 * rho + 1.0 / 3.0 * R0 * uu;"),
     ("m6_eq transposed operand (Eq. 16)",
-     "meq[6] = 1.0 / 3.0 * RHO0 * uy;",
-     "meq[6] = 1.0 / 3.0 * RHO0 * ux;"),
+     "meq[6] = 1.0 / 3.0 * R0 * uy;",
+     "meq[6] = 1.0 / 3.0 * R0 * ux;"),
     ("S3 factor (Eq. 17)",
-     "S[3] = 2.0 * RHO0 * (ux * Fx + uy * Fy);",
-     "S[3] = RHO0 * (ux * Fx + uy * Fy);"),
+     "S[3] = 2.0 * R0 * (ux * Fx + uy * Fy);",
+     "S[3] = R0 * (ux * Fx + uy * Fy);"),
     ("S7 operand (Eq. 17)",
-     "S[7] = 1.0 / 3.0 * RHO0 * Fx;",
-     "S[7] = 1.0 / 3.0 * RHO0 * Fy;"),
+     "S[7] = 1.0 / 3.0 * R0 * Fx;",
+     "S[7] = 1.0 / 3.0 * R0 * Fy;"),
     ("forcing weight sign (Eq. 8)",
      "(1.0 - 0.5 * r->s[k]) * S[k];",
      "(1.0 + 0.5 * r->s[k]) * S[k];"),

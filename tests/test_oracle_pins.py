@@ -452,3 +452,58 @@ def test_oracle_rejects_open_edges_and_unknown_walls():
     bad = c.flags.copy(); bad[0, 0] = 9
     with pytest.raises(ValueError):
         oracle.OracleLattice(c.with_(flags=bad))
+
+
+def _bgk_guo_compressible(f, g, omega, gb, T0, ax, ay):
+    """Textbook single-relaxation-time update with the standard (compressible)
+    equilibrium w_i rho [1 + 3 e.u + 4.5 (e.u)^2 - 1.5 u^2], u = (sum e f + F rho/2) / rho,
+    and the Guo-Zheng-Shi forcing term with rho."""
+    T = g.sum()
+    F = np.array([ax, ay + gb * (T - T0)])
+    rho = f.sum()
+    u = (E.T @ f + 0.5 * rho * F) / rho
+    eu = E @ u
+    feq = W * rho * (1 + 3 * eu + 4.5 * eu**2 - 1.5 * (u @ u))
+    S = W * rho * (3 * (E - u) @ F + 9 * eu * (E @ F))
+    return f - omega * (f - feq) + (1 - 0.5 * omega) * S
+
+
+@pytest.mark.parametrize("omega", [0.7, 1.0, 1.6])
+def test_rho_in_u_ablation_reduces_to_the_standard_equilibrium(omega):
+    """The alternative to reading A1 (rho everywhere, as Eqs. 16-17 and 19 are
+    printed): with equal rates it is BGK with the standard compressible
+    equilibrium and Guo forcing with rho (not the incompressible one), so
+    the two readings differ by O((rho - rho0) u) on states with rho != 1."""
+    rng = np.random.default_rng(9)
+    kw = dict(g_beta=4e-3, T0=0.3, ax=3e-4, ay=-2e-4)
+    for _ in range(20):
+        f = W * (1.0 + 0.1 * rng.standard_normal()) * (1 + 0.2 * rng.standard_normal(9))
+        g = np.array([0.5, 0.125, 0.125, 0.125, 0.125]) * (0.6 + 0.2 * rng.standard_normal(5))
+        alt = oracle.make_rates([omega] * 9, [1.0] * 5, rho_in_u=True, **kw)
+        fs, _, (rho, ux, uy, T) = oracle.collide_node(alt, f, g)
+        want = _bgk_guo_compressible(f, g, omega, kw["g_beta"], kw["T0"], kw["ax"], kw["ay"])
+        assert np.abs(fs - want).max() < 1e-15
+        # momentum changes by rho F under this reading
+        Fy = kw["ay"] + kw["g_beta"] * (g.sum() - kw["T0"])
+        assert abs(E[:, 0] @ fs - E[:, 0] @ f - f.sum() * kw["ax"]) < 1e-15
+        assert abs(E[:, 1] @ fs - E[:, 1] @ f - f.sum() * Fy) < 1e-15
+        base = oracle.make_rates([omega] * 9, [1.0] * 5, **kw)
+        fb, _, _ = oracle.collide_node(base, f, g)
+        if abs(f.sum() - 1.0) > 1e-3:
+            assert np.abs(fs - fb).max() > 1e-9
+
+
+def test_rho_in_u_ablation_changes_the_cavity_little():
+    """On the Sec. 3.4 cavity (Ra = 1e4, 24^2, 3000 steps) the two readings
+    agree to O(Ma^2): density stays within about 1e-3 of rho0, and u and T
+    differ by 3.5e-4 (of max |u|) and 1.9e-4 (of delta T)."""
+    c = lc.cavity(n=24, Ra=1e4, noise=1e-3)
+    a = oracle.OracleLattice(c)
+    b = oracle.OracleLattice(c, rho_in_u=True)
+    a.step(3000)
+    b.step(3000)
+    ra, uxa, uya, Ta = a.macro()
+    rb, uxb, uyb, Tb = b.macro()
+    umax = max(np.abs(uxa).max(), np.abs(uya).max())
+    du = max(np.abs(uxa - uxb).max(), np.abs(uya - uyb).max()) / umax
+    assert 0 < du < 5e-3 and np.abs(Ta - Tb).max() < 5e-3
