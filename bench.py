@@ -496,8 +496,14 @@ def cavity_table3_quantities(case, rho, ux, uy, T):
     nu_loc = -n * grad / case.delta_T
     jn = int(np.argmax(nu_loc))
     nu_mean = float(np.sum((nu_loc[1:] + nu_loc[:-1]) / 2.0) / n)
+    # the volume form, a diagnostic: Nu = 1 + L <u_x T> / (alpha dT), trapezoidal average
+    # over the node grid (conduction carries alpha dT / L on average, advection the rest)
+    wts = np.ones(n + 1)
+    wts[0] = wts[-1] = 0.5
+    avg = float(wts @ (ux * T) @ wts) / (n * n)
+    nu_vol = 1.0 + n * avg / (case.alpha * case.delta_T)
     return {"ux_max": float(col[jy]), "y_max": jy / n, "uy_max": float(row[ix]), "x_max": ix / n,
-            "Nu_max": float(nu_loc[jn]), "y_Nu": jn / n, "Nu_mean": nu_mean}
+            "Nu_max": float(nu_loc[jn]), "y_Nu": jn / n, "Nu_mean": nu_mean, "Nu_vol": nu_vol}
 
 
 def run_table3(args):

@@ -164,3 +164,5 @@ def test_table3_with_the_papers_node_walls(row):
         assert abs(q[k] - v) / v < 5e-3, (k, q[k], v)
     for k, v in zip(("y_max", "x_max", "y_Nu"), pos[2:]):
         assert abs(q[k] - v) <= 1.0 / grid + 1e-4, (k, q[k], v)
+    # the volume form of the Nusselt number agrees with the wall form at steady state
+    assert abs(q["Nu_vol"] - q["Nu_mean"]) / q["Nu_mean"] < 1e-2
