@@ -249,3 +249,18 @@ class OracleLattice:
 
 def threads_available() -> int:
     return lib().orc_threads_available()
+
+
+def relative_global_error(num, exact) -> float:
+    """Relative global error of Eq. 35 (velocity) and Eq. 38 (temperature).
+
+    Eq. 38 is printed as the root of the summed squared deviations over the
+    domain divided by the root of the summed squared analytical values; Eq. 35
+    names the same L2 norm for the velocity vector. Reading: both are that
+    global norm, with the sums over every node and every component of ``num``
+    and ``exact`` (arrays of one shape). The alternative reading of Eq. 35 (a
+    per-node Euclidean norm summed over the nodes) is kept by the tests for
+    comparison."""
+    num = np.asarray(num, np.float64)
+    exact = np.asarray(exact, np.float64)
+    return float(np.sqrt(((num - exact) ** 2).sum() / (exact ** 2).sum()))

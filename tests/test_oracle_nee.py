@@ -5,9 +5,11 @@ The paper cites the scheme without its formulas; this code reconstructs the
 boundary node's pre-collision populations as the equilibrium at the wall
 state plus the nearest fluid node's non-equilibrium part, then collides the
 node like a fluid node. The paper's error tables therefore pin magnitudes and
-trends, not digits: E_u within 15 % of Table 2 at every rate, the ordering in
-s_nu, second-order slopes close to the printed ones, and the cavity Nusselt
-number of Table 3."""
+trends, not digits: E_u (Eq. 35 as the global L2 norm) within 6 % of Table 2
+at every rate and within 15 % in the per-node reading, the ordering in s_nu,
+the two-point slope of Table 2 within 0.01, the velocity slope of Sec. 3.3
+within 0.02, the near independence of E_u from a_x of Table 1, and the cavity
+Nusselt number of Table 3."""
 import os
 
 import numpy as np
@@ -30,16 +32,20 @@ def _steady(o, chunk=2000, tol=1e-12, max_chunks=3000):
     return r
 
 
-def _poiseuille_error(H, s_nu, Re=49.4146):
+def _poiseuille_error(H, s_nu, Re=49.4146, ax=None):
+    """(E_u as the global L2 norm, E_u as summed per-node norms) of the
+    channel at steady state; ax follows from Re unless given."""
     nu = (1 / s_nu - 0.5) / 3
-    ax = 2 * Re * nu**2 / (H / 2) ** 3  # Re = u0 l_c / nu with u0 = ax l_c^2 / (2 nu), l_c = H / 2
+    if ax is None:
+        ax = 2 * Re * nu**2 / (H / 2) ** 3  # Re = u0 l_c / nu with u0 = ax l_c^2 / (2 nu), l_c = H / 2
     c = lc.poiseuille_nee(H=H, nx=2, ax=ax, s_nu=s_nu)
     o = oracle.OracleLattice(c)
     _steady(o)
     ux = o.macro()[1][:, 0]
     y = np.arange(H + 1)
     ua = ax / (2 * nu) * y * (H - y)  # Eq. 34 on the nodes, walls at y = 0 and y = H
-    return np.abs(ux - ua).sum() / np.abs(ua).sum()  # Eq. 35
+    # Eq. 35 (u_y is zero in both, so the per-node norm is |u_x - u_A|)
+    return oracle.relative_global_error(ux, ua), np.abs(ux - ua).sum() / np.abs(ua).sum()
 
 
 def test_node_wall_rebuild_from_an_equilibrium_state():
@@ -77,17 +83,30 @@ def test_node_wall_rebuild_from_an_equilibrium_state():
 
 
 def test_poiseuille_errors_match_table2_in_magnitude_and_order():
+    """Measured at dx = 1/30: global-L2 E_u 1.055 / 1.032 / 1.013 x Table 2 for
+    s_nu = 1.60 / 1.754 / 1.90, per-node form 1.137 / 1.113 / 1.092 x."""
     tab = np.loadtxt(os.path.join(GOLDEN, "table1_2_poiseuille.txt"))
     errs = []
     for row in tab:
-        e30 = _poiseuille_error(30, row[0])
-        assert abs(e30 - row[1]) / row[1] < 0.15, (row[0], e30, row[1])
+        e30, e30_node = _poiseuille_error(30, row[0])
+        assert abs(e30 - row[1]) / row[1] < 0.06, (row[0], e30, row[1])
+        assert abs(e30_node - row[1]) / row[1] < 0.15, (row[0], e30_node, row[1])
         errs.append(e30)
     assert errs[0] < errs[1] < errs[2]  # E_u grows with s_nu at fixed Re, as in Table 2
-    e60 = _poiseuille_error(60, 1.754)
-    assert abs(e60 - tab[1, 2]) / tab[1, 2] < 0.15
+    e60, _ = _poiseuille_error(60, 1.754)
+    assert abs(e60 - tab[1, 2]) / tab[1, 2] < 0.06
+    # two-point slope between dx = 1/30 and 1/60: Table 2's own is 1.9859, ours 1.9891
     slope = np.log(errs[1] / e60) / np.log(2.0)
-    assert 1.9 < slope < 2.1  # the paper reports 1.9902 for s_nu = 1.754
+    assert abs(slope - np.log(tab[1, 1] / tab[1, 2]) / np.log(2.0)) < 0.01
+
+
+def test_poiseuille_error_nearly_independent_of_body_force():
+    """Table 1: at s_nu = 1.754 and dx = 1/60, E_u moves by 0.6 % as a_x goes
+    from 2e-6 to 8e-6 (Re from 49 to 198): the error is a property of the
+    walls and the resolution, not of the flow speed. Ours moves by 0.5 %."""
+    e2, _ = _poiseuille_error(60, 1.754, ax=2e-6)
+    e8, _ = _poiseuille_error(60, 1.754, ax=8e-6)
+    assert abs(e8 / e2 - 1) < 0.01 and abs(e2 - 1.2600e-3) / 1.2600e-3 < 0.06
 
 
 def test_injection_channel_slopes_match_sec33():
@@ -102,12 +121,14 @@ def test_injection_channel_slopes_match_sec33():
         ue, Te = lc.porous_couette_nee_exact(c)
         u_num = np.stack([ux[:, 0], uy[:, 0]], 1)
         u_ex = np.stack([ue, np.full(H + 1, c.meta["v0"])], 1)
-        eu.append(np.linalg.norm(u_num - u_ex, axis=1).sum() / np.linalg.norm(u_ex, axis=1).sum())  # Eq. 35
-        eT.append(np.sqrt(((T[:, 0] - Te) ** 2).sum() / (Te**2).sum()))  # Eq. 38
+        eu.append(oracle.relative_global_error(u_num, u_ex))  # Eq. 35
+        eT.append(oracle.relative_global_error(T[:, 0], Te))  # Eq. 38
         assert np.abs(uy[:, 0] - c.meta["v0"]).max() < 1e-12  # the normal velocity is exact
     su = np.polyfit(np.log(1.0 / np.array(Hs)), np.log(eu), 1)[0]
     sT = np.polyfit(np.log(1.0 / np.array(Hs)), np.log(eT), 1)[0]
-    assert abs(su - float(golden["u"])) < 0.1 and abs(sT - float(golden["T"])) < 0.05, (su, sT)
+    # over dx = 1/30..1/90: 1.957 (1.939 with the per-node form of Eq. 35); over
+    # the paper's 1/30..1/150: 1.965 (per-node 1.951) against the printed 1.967
+    assert abs(su - float(golden["u"])) < 0.02 and abs(sT - float(golden["T"])) < 0.05, (su, sT)
 
 
 def test_conduction_cavity_nusselt_is_one_with_node_walls():

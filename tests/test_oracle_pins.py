@@ -351,9 +351,8 @@ def _porous_errors(H):
     ue, Te = lc.porous_couette_exact(c)
     u_num = np.stack([ux[1:-1, 0], uy[1:-1, 0]], 1)
     u_ex = np.stack([ue, np.full(H, c.meta["v0"])], 1)
-    # Eq. 35 and Eq. 38
-    Eu = np.linalg.norm(u_num - u_ex, axis=1).sum() / np.linalg.norm(u_ex, axis=1).sum()
-    ET = np.sqrt(((T[1:-1, 0] - Te) ** 2).sum() / (Te**2).sum())
+    Eu = oracle.relative_global_error(u_num, u_ex)  # Eq. 35
+    ET = oracle.relative_global_error(T[1:-1, 0], Te)  # Eq. 38
     return Eu, ET, o, c
 
 
@@ -507,3 +506,19 @@ def test_rho_in_u_ablation_changes_the_cavity_little():
     umax = max(np.abs(uxa).max(), np.abs(uya).max())
     du = max(np.abs(uxa - uxb).max(), np.abs(uya - uyb).max()) / umax
     assert 0 < du < 5e-3 and np.abs(Ta - Tb).max() < 5e-3
+
+
+def test_relative_global_error_closed_forms():
+    """Eqs. 35/38 read as the global L2 norm: a uniform relative deviation eps
+    gives eps; a constant offset c on a field with values v gives
+    c sqrt(n) / ||v||; a velocity field is measured over both components; a
+    permutation of the nodes changes nothing."""
+    rng = np.random.default_rng(5)
+    v = rng.uniform(0.5, 2.0, (40, 2))
+    assert abs(oracle.relative_global_error(v * 1.003, v) - 0.003) < 1e-15
+    assert abs(oracle.relative_global_error(v[:, 0] + 1e-3, v[:, 0]) - 1e-3 * np.sqrt(40) / np.linalg.norm(v[:, 0])) < 1e-15
+    d = np.zeros_like(v)
+    d[7, 1] = 0.02  # one component of one node
+    assert abs(oracle.relative_global_error(v + d, v) - 0.02 / np.linalg.norm(v)) < 1e-15
+    p = rng.permutation(40)
+    assert oracle.relative_global_error((v + d)[p], v[p]) == oracle.relative_global_error(v + d, v)
