@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <string>
 #include <thread>
@@ -103,9 +104,9 @@ int nee_direction(const lbm_params *p, int x, int y) {
 // thread count.
 struct CellScan {
     int pitch = 0;
-    uint8_t *mask = nullptr;   // ny * pitch link map (bit i-1: direction i pulls from a solid cell)
-    uint8_t *flags = nullptr;  // ny * pitch wall ids
-    uint8_t *dir = nullptr;    // ny * pitch nearest-fluid direction of boundary nodes
+    uint8_t *mask = nullptr;   // ny * pitch link map (bit i-1: direction i pulls from a solid cell; 0xFF
+                               // for solid cells and the padding columns)
+    uint8_t *flags = nullptr;  // ny * pitch wall ids (0 in the padding columns)
 };
 
 struct ScanResult {
@@ -114,69 +115,169 @@ struct ScanResult {
     std::vector<int2> nee;  // (cell offset in the pitched layout, direction | wall id << 8)
 };
 
-// Rows [y0, y1). Stops at the band's first invalid cell (row-major order).
-void scan_rows(const lbm_params *p, const uint8_t *halfway, int y0, int y1, const CellScan *out, ScanResult &r) {
+// Row y, cell by cell, in row-major order: the exact reference for the fast
+// path below, and the path that produces the error message of a row holding
+// an invalid cell. Returns false at the row's first invalid cell.
+bool scan_row_exact(const lbm_params *p, const uint8_t *halfway, int y, const CellScan *out, ScanResult &r) {
     const int nx = p->nx, ny = p->ny;
     const bool px = p->periodic_x != 0, py = p->periodic_y != 0;
     char buf[256];
-    for (int y = y0; y < y1; ++y) {
-        // source rows of directions with e_y = -1, 0, +1: y + 1, y, y - 1
-        const int ys[3] = {py ? (y + 1) % ny : y + 1, y, py ? (y - 1 + ny) % ny : y - 1};
-        const uint8_t *row = p->flags + (size_t)y * nx;
-        for (int x = 0; x < nx; ++x) {
-            const uint8_t k = row[x];
-            if (k > p->n_walls) {
-                snprintf(buf, sizeof buf, "cell (%d, %d) has wall id %d > n_walls", x, y, (int)k);
-                r.err = buf;
-                return;
-            }
-            const size_t off = (size_t)y * (out ? out->pitch : 0) + x;
-            if (out) out->flags[off] = k;
-            if (k) {
-                if (!halfway[k]) {  // boundary node of a node-based wall
-                    const int d = nee_direction(p, x, y);
-                    if (d == 0) {
-                        snprintf(buf, sizeof buf,
-                                 "boundary node (%d, %d) of an extrapolated wall has no fluid neighbour", x, y);
-                        r.err = buf;
-                        return;
-                    }
-                    if (out) {
-                        out->dir[off] = (uint8_t)d;
-                        r.nee.push_back(make_int2((int)off, d | ((int)k << 8)));
-                    } else {
-                        r.nee.push_back(make_int2(0, 0));
-                    }
-                }
-                continue;
-            }
-            unsigned m = 0;
-            for (int i = 1; i < 9; ++i) {
-                int sx = x - kEx[i];
-                if (px) sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
-                const int sy = ys[kEy[i] + 1];
-                if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
-                    snprintf(buf, sizeof buf,
-                             "fluid cell (%d, %d) touches a non-periodic edge; add a frame of solid cells", x, y);
-                    r.err = buf;
-                    return;
-                }
-                if (halfway[p->flags[(size_t)sy * nx + sx]]) m |= 1u << (i - 1);
-            }
-            if (m == 0xFFu) {
-                snprintf(buf, sizeof buf, "fluid cell (%d, %d) has no fluid neighbour", x, y);
-                r.err = buf;
-                return;
-            }
-            ++r.fluid;
-            if (out) out->mask[off] = (uint8_t)m;
+    // source rows of directions with e_y = -1, 0, +1: y + 1, y, y - 1
+    const int ys[3] = {py ? (y + 1) % ny : y + 1, y, py ? (y - 1 + ny) % ny : y - 1};
+    const uint8_t *row = p->flags + (size_t)y * nx;
+    for (int x = 0; x < nx; ++x) {
+        const uint8_t k = row[x];
+        if (k > p->n_walls) {
+            snprintf(buf, sizeof buf, "cell (%d, %d) has wall id %d > n_walls", x, y, (int)k);
+            r.err = buf;
+            return false;
         }
+        const size_t off = (size_t)y * (out ? out->pitch : 0) + x;
+        if (out) out->flags[off] = k;
+        if (k) {
+            if (!halfway[k]) {  // boundary node of a node-based wall
+                const int d = nee_direction(p, x, y);
+                if (d == 0) {
+                    snprintf(buf, sizeof buf,
+                             "boundary node (%d, %d) of an extrapolated wall has no fluid neighbour", x, y);
+                    r.err = buf;
+                    return false;
+                }
+                r.nee.push_back(out ? make_int2((int)off, d | ((int)k << 8)) : make_int2(0, 0));
+            }
+            continue;
+        }
+        unsigned m = 0;
+        for (int i = 1; i < 9; ++i) {
+            int sx = x - kEx[i];
+            if (px) sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+            const int sy = ys[kEy[i] + 1];
+            if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
+                snprintf(buf, sizeof buf,
+                         "fluid cell (%d, %d) touches a non-periodic edge; add a frame of solid cells", x, y);
+                r.err = buf;
+                return false;
+            }
+            if (halfway[p->flags[(size_t)sy * nx + sx]]) m |= 1u << (i - 1);
+        }
+        if (m == 0xFFu) {
+            snprintf(buf, sizeof buf, "fluid cell (%d, %d) has no fluid neighbour", x, y);
+            r.err = buf;
+            return false;
+        }
+        ++r.fluid;
+        if (out) out->mask[off] = (uint8_t)m;
+    }
+    return true;
+}
+
+// Cell kinds of row y, padded by one cell on each side: 1 = solid (a
+// bounce-back wall), 0 = fluid or a boundary node, 2 = outside the domain
+// (a non-periodic edge), 4 = a wall id above n_walls.
+void kinds_row(const lbm_params *p, const uint8_t *halfway, bool all_halfway, int y, uint8_t *pad) {
+    const int nx = p->nx, ny = p->ny;
+    if (y < 0 || y >= ny) {
+        if (!p->periodic_y) {
+            std::memset(pad, 2, (size_t)nx + 2);
+            return;
+        }
+        y = (y + ny) % ny;
+    }
+    const uint8_t *__restrict row = p->flags + (size_t)y * nx;
+    uint8_t *__restrict out = pad + 1;
+    const uint8_t nw = (uint8_t)p->n_walls;
+    if (all_halfway) {  // every wall bounces back: no table lookup, so the loop vectorises
+        for (int x = 0; x < nx; ++x) out[x] = row[x] > nw ? 4 : (row[x] != 0 ? 1 : 0);
+    } else {
+        for (int x = 0; x < nx; ++x) out[x] = row[x] > nw ? 4 : halfway[row[x]];
+    }
+    pad[0] = p->periodic_x ? pad[nx] : 2;
+    pad[nx + 1] = p->periodic_x ? pad[1] : 2;
+}
+
+// Rows [y0, y1). Stops at the band's first invalid cell (row-major order).
+// Each row is scanned from three padded rows of cell kinds in a loop without
+// branches (it vectorises); a row holding an invalid cell (a bad wall id, a
+// fluid cell at a non-periodic edge or without a fluid neighbour, a boundary
+// node without a fluid neighbour) is rescanned by scan_row_exact, which names
+// the first one.
+void scan_rows(const lbm_params *p, const uint8_t *halfway, bool all_halfway, int y0, int y1, const CellScan *out,
+               ScanResult &r) {
+    const int nx = p->nx;
+    std::vector<uint8_t> buf(4 * ((size_t)nx + 2));
+    uint8_t *up = buf.data(), *mid = up + nx + 2, *dn = mid + nx + 2;  // rows y + 1, y, y - 1
+    uint8_t *const mrow = dn + nx + 2;
+    if (y0 < y1) {
+        kinds_row(p, halfway, all_halfway, y0 - 1, dn);
+        kinds_row(p, halfway, all_halfway, y0, mid);
+    }
+    for (int y = y0; y < y1; ++y) {
+        kinds_row(p, halfway, all_halfway, y + 1, up);
+        const uint8_t *__restrict row = p->flags + (size_t)y * nx;
+        const uint8_t *__restrict U = up;
+        const uint8_t *__restrict C = mid;
+        const uint8_t *__restrict D = dn;
+        uint8_t *__restrict M = mrow;
+        // bit 1: a fluid cell pulls from outside; bit 2: a bad wall id; bit 3: a fluid
+        // cell without a fluid neighbour; bit 4: a boundary node of a node-based wall
+        uint8_t odd = 0;
+        int fluid = 0;
+        for (int x = 0; x < nx; ++x) {
+            const uint8_t w = C[x], c = C[x + 1], e = C[x + 2];
+            const uint8_t sw = D[x], s = D[x + 1], se = D[x + 2];
+            const uint8_t nw = U[x], n = U[x + 1], ne = U[x + 2];
+            // bit i-1: the source x - e_i of direction i is not fluid
+            const uint8_t m = (uint8_t)((w ? 1 : 0) | (s ? 2 : 0) | (e ? 4 : 0) | (n ? 8 : 0) | (sw ? 16 : 0) |
+                                        (se ? 32 : 0) | (ne ? 64 : 0) | (nw ? 128 : 0));
+            const uint8_t fm = row[x] == 0 ? 0xFF : 0;  // all ones for a fluid cell
+            const uint8_t all = (uint8_t)(w | s | e | n | sw | se | ne | nw);
+            const uint8_t full = m == 0xFF ? 8 : 0;
+            const uint8_t node = (row[x] != 0 && c == 0) ? 16 : 0;
+            odd |= (uint8_t)((c & 4) | ((all & 2) & fm) | (full & fm) | node);
+            fluid += fm & 1;
+            M[x] = (uint8_t)(m | ~fm);  // kSolid for every cell that is not fluid
+        }
+        const bool nodes = (odd & 16) != 0;
+        odd &= 15;
+        const size_t base = (size_t)y * (out ? out->pitch : 0);
+        if (out) {
+            std::memcpy(out->flags + base, row, (size_t)nx);
+            std::memcpy(out->mask + base, mrow, (size_t)nx);
+            std::memset(out->flags + base + nx, 0, (size_t)(out->pitch - nx));
+            std::memset(out->mask + base + nx, kSolid, (size_t)(out->pitch - nx));
+        }
+        const size_t nee0 = r.nee.size();
+        if (nodes && !odd) {
+            for (int x = 0; x < nx; ++x) {
+                if (row[x] == 0 || mid[x + 1] != 0) continue;
+                const int d = nee_direction(p, x, y);
+                if (d == 0) {
+                    odd = 8;
+                    break;
+                }
+                r.nee.push_back(out ? make_int2((int)(base + x), d | ((int)row[x] << 8)) : make_int2(0, 0));
+            }
+        }
+        if (odd) {
+            r.nee.resize(nee0);
+            if (!scan_row_exact(p, halfway, y, out, r)) return;
+        } else {
+            r.fluid += fluid;
+        }
+        uint8_t *t = dn;
+        dn = mid;
+        mid = up;
+        up = t;
     }
 }
 
 ScanResult scan_cells(const lbm_params *p, const CellScan *out) {
     uint8_t halfway[256] = {0};  // wall id -> its cells are solid (HALFWAY)
-    for (int k = 1; k <= p->n_walls; ++k) halfway[k] = p->walls[k - 1].scheme == LBM_WALL_HALFWAY;
+    bool all_halfway = true;
+    for (int k = 1; k <= p->n_walls; ++k) {
+        halfway[k] = p->walls[k - 1].scheme == LBM_WALL_HALFWAY;
+        all_halfway = all_halfway && halfway[k];
+    }
     const size_t cells = (size_t)p->nx * p->ny;
     unsigned hw = std::thread::hardware_concurrency();
     int nthreads = (int)std::min<size_t>(std::max(1u, std::min(hw, 16u)), std::max<size_t>(1, cells >> 18));
@@ -185,9 +286,9 @@ ScanResult scan_cells(const lbm_params *p, const CellScan *out) {
     std::vector<std::thread> pool;
     const int band = (p->ny + nthreads - 1) / nthreads;
     for (int t = 1; t < nthreads; ++t)
-        pool.emplace_back(scan_rows, p, halfway, std::min(p->ny, t * band), std::min(p->ny, (t + 1) * band), out,
-                          std::ref(part[t]));
-    scan_rows(p, halfway, 0, std::min(p->ny, band), out, part[0]);
+        pool.emplace_back(scan_rows, p, halfway, all_halfway, std::min(p->ny, t * band),
+                          std::min(p->ny, (t + 1) * band), out, std::ref(part[t]));
+    scan_rows(p, halfway, all_halfway, 0, std::min(p->ny, band), out, part[0]);
     for (auto &th : pool) th.join();
     ScanResult r;
     for (auto &q : part) {
@@ -330,13 +431,18 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     // link map (bit i-1: direction i pulls from a solid cell; padding and solid cells 0xFF)
     // and the boundary nodes of node-based walls
     const int pitch0 = (int)align_up((size_t)p->nx, 128 / elem_bytes(p->storage));
-    std::vector<uint8_t> hmask((size_t)p->ny * pitch0, kSolid), hflags((size_t)p->ny * pitch0, 0),
-        hdir((size_t)p->ny * pitch0, 0);
+    const size_t map_bytes = (size_t)p->ny * pitch0;
+    // written in full by the scan (padding columns included), so left uninitialised here
+    std::unique_ptr<uint8_t[]> hmask(new (std::nothrow) uint8_t[map_bytes]),
+        hflags(new (std::nothrow) uint8_t[map_bytes]);
+    if (!hmask || !hflags) {
+        lbm_destroy(h);
+        return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    }
     CellScan cs;
     cs.pitch = pitch0;
-    cs.mask = hmask.data();
-    cs.flags = hflags.data();
-    cs.dir = hdir.data();
+    cs.mask = hmask.get();
+    cs.flags = hflags.get();
     ScanResult sr = scan_cells(p, &cs);
     if (!sr.err.empty()) {
         lbm_destroy(h);
@@ -444,37 +550,46 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     };
     cudaError_t e;
     if ((e = cudaMemsetAsync(h->mem, 0, need, st)) != cudaSuccess) return cuda_bail(e, "memset");
-    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_mask, hmask.data(), hmask.size(), cudaMemcpyHostToDevice, st)) !=
+    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_mask, hmask.get(), map_bytes, cudaMemcpyHostToDevice, st)) !=
         cudaSuccess)
         return cuda_bail(e, "upload link map");
-    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_flags, hflags.data(), hflags.size(), cudaMemcpyHostToDevice,
-                             st)) != cudaSuccess)
+    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_flags, hflags.get(), map_bytes, cudaMemcpyHostToDevice, st)) !=
+        cudaSuccess)
         return cuda_bail(e, "upload flags");
     if ((e = cudaMemcpyAsync(h->mem + h->lay.off_walls, hw.data(), sizeof(WallDev) * hw.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_bail(e, "upload walls");
-    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_nee_dir, hdir.data(), hdir.size(), cudaMemcpyHostToDevice, st)) !=
-        cudaSuccess)
-        return cuda_bail(e, "upload boundary-node directions");
-    if (!hnee.empty() && (e = cudaMemcpyAsync(h->mem + h->lay.off_nee, hnee.data(), hnee.size() * sizeof(int2),
-                                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
-        return cuda_bail(e, "upload boundary nodes");
-    // initial state, row chunks of T through the staging area
-    std::vector<double> Trow((size_t)h->lay.stage_rows * nx);
-    for (int r0 = 0; r0 < ny; r0 += h->lay.stage_rows) {
-        const int r1 = std::min(ny, r0 + h->lay.stage_rows);
-        const size_t n = (size_t)(r1 - r0) * nx;
-        if (p->T_init)
-            std::memcpy(Trow.data(), p->T_init + (size_t)r0 * nx, n * sizeof(double));
-        else
-            std::fill(Trow.begin(), Trow.begin() + n, p->T0);
-        if ((e = cudaMemcpyAsync(h->stage(), Trow.data(), n * sizeof(double), cudaMemcpyHostToDevice, st)) !=
+    std::vector<uint8_t> hdir;  // nearest-fluid directions of boundary nodes (the device plane is zeroed)
+    if (!hnee.empty()) {
+        hdir.assign(map_bytes, 0);
+        for (const int2 &b : hnee) hdir[(size_t)b.x] = (uint8_t)(b.y & 0xFF);
+        if ((e = cudaMemcpyAsync(h->mem + h->lay.off_nee_dir, hdir.data(), map_bytes, cudaMemcpyHostToDevice, st)) !=
             cudaSuccess)
+            return cuda_bail(e, "upload boundary-node directions");
+        if ((e = cudaMemcpyAsync(h->mem + h->lay.off_nee, hnee.data(), hnee.size() * sizeof(int2),
+                                 cudaMemcpyHostToDevice, st)) != cudaSuccess)
+            return cuda_bail(e, "upload boundary nodes");
+    }
+    // initial state from T in row chunks through the staging area, which holds nq rows of
+    // populations and so stage_rows * nq rows of T. Stream order keeps a chunk's upload
+    // behind the previous chunk's init kernel; one wait at the end covers the host buffers.
+    const int t_rows = (int)std::min<size_t>({(size_t)ny, (size_t)h->lay.stage_rows * h->lay.nq, (size_t)65535});
+    std::vector<double> Tconst;
+    if (!p->T_init) {
+        Tconst.assign((size_t)t_rows * nx, p->T0);
+        if ((e = cudaMemcpyAsync(h->stage(), Tconst.data(), Tconst.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                 st)) != cudaSuccess)
+            return cuda_bail(e, "upload T0");
+    }
+    for (int r0 = 0; r0 < ny; r0 += t_rows) {
+        const int r1 = std::min(ny, r0 + t_rows);
+        if (p->T_init && (e = cudaMemcpyAsync(h->stage(), p->T_init + (size_t)r0 * nx,
+                                              (size_t)(r1 - r0) * nx * sizeof(double), cudaMemcpyHostToDevice, st)) !=
+                             cudaSuccess)
             return cuda_bail(e, "upload T_init");
         if ((e = h->L->init_rows(kp, 0, r0, r1, h->stage(), st)) != cudaSuccess) return cuda_bail(e, "init kernel");
-        // the staging buffer is reused by the next chunk: wait for this one
-        if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_bail(e, "init sync");
     }
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_bail(e, "init sync");
     h->cur = 0;
     *out = h;
     return LBM_OK;

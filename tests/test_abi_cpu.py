@@ -121,3 +121,42 @@ def test_validation_edge_cases_on_host():
     fl[301, 2] = 6
     n, msg = footprint(big.with_(flags=fl))
     assert n == 0 and msg == "cell (400, 300) has wall id 9 > n_walls", msg
+
+
+def test_flag_map_errors_each_named_at_their_cell():
+    """Each kind of invalid flag map is rejected with the cell that makes it
+    invalid, on lattices large enough to be scanned by several host threads:
+    a fluid cell on a non-periodic edge, a fluid cell whose eight neighbours
+    are all bounce-back walls, a wall id above n_walls seen first as a
+    neighbour of valid rows."""
+    import paper_1510_08224_gb300 as P
+    L = P.load()
+
+    def footprint(case):
+        p, keep = P.make_params(case, "f32")
+        return L.lbm_footprint_bytes(C.byref(p)), L.lbm_last_error(None).decode()
+
+    big = lc.periodic_box(600, 900)
+    assert footprint(big)[0] > 0
+    # a non-periodic y edge: the first fluid cell of row 0 pulls from outside
+    n, msg = footprint(big.with_(periodic_y=False))
+    assert n == 0 and msg.startswith("fluid cell (0, 0) touches a non-periodic edge"), msg
+    # a channel with walls on both sides is valid
+    ch = lc.couette(H=900, nx=600)
+    assert footprint(ch)[0] > 0
+    # an isolated fluid cell inside a block of bounce-back cells
+    fl = ch.flags.copy()
+    fl[700:703, 100:103] = 1
+    fl[701, 101] = 0
+    n, msg = footprint(ch.with_(flags=fl))
+    assert n == 0 and msg == "fluid cell (101, 701) has no fluid neighbour", msg
+    # a bad id in row 451 is the neighbour of fluid cells in rows 450 and 452
+    fl = ch.flags.copy()
+    fl[451, 333] = 7
+    n, msg = footprint(ch.with_(flags=fl))
+    assert n == 0 and msg == "cell (333, 451) has wall id 7 > n_walls", msg
+    # removing the top wall row leaves fluid cells on a non-periodic edge
+    fl = ch.flags.copy()
+    fl[-1, :] = 0
+    n, msg = footprint(ch.with_(flags=fl))
+    assert n == 0 and msg.startswith(f"fluid cell (0, {ch.ny - 1}) touches a non-periodic edge"), msg
