@@ -166,3 +166,24 @@ def test_table3_with_the_papers_node_walls(row):
         assert abs(q[k] - v) <= 1.0 / grid + 1e-4, (k, q[k], v)
     # the volume form of the Nusselt number agrees with the wall form at steady state
     assert abs(q["Nu_vol"] - q["Nu_mean"]) / q["Nu_mean"] < 1e-2
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+@pytest.mark.parametrize("with_T", [True, False])
+def test_initial_state_of_a_lattice_taller_than_one_upload_chunk(storage, with_T):
+    """lbm_create uploads T_init in chunks of the staging area (252 rows of an
+    8192-wide lattice): a 8192 x 600 periodic box starts at rest with T equal
+    to T_init (a seeded field) or to T0 everywhere, across the chunk seams.
+    The initial populations are the equilibria at (rho0, 0, T), so the
+    read-out T is T_init to rounding of the storage (reading A4)."""
+    import paper_1510_08224_gb300 as P
+    nx, ny = 8192, 600
+    T = 0.5 + 0.25 * (2 * lc.uniform01(17, nx * ny).reshape(ny, nx) - 1) if with_T else None
+    case = lc.periodic_box(nx, ny, T0=0.5, T_init=T)
+    lat = P.Lattice(case, storage=storage)
+    rho, ux, uy, Tg = lat.macro()
+    Te = T if with_T else np.full((ny, nx), 0.5)
+    tol = {"f64": 1e-15, "f32": 1e-7, "f16": 1e-3}[storage]
+    assert np.abs(Tg - Te).max() <= tol
+    assert np.abs(rho - 1).max() <= tol and np.abs(ux).max() <= 1e-15 and np.abs(uy).max() <= 1e-15
+    lat.close()
