@@ -172,17 +172,23 @@ def test_table3_with_the_papers_node_walls(row):
 @pytest.mark.parametrize("with_T", [True, False])
 def test_initial_state_of_a_lattice_taller_than_one_upload_chunk(storage, with_T):
     """lbm_create uploads T_init in chunks of the staging area (252 rows of an
-    8192-wide lattice): a 8192 x 600 periodic box starts at rest with T equal
-    to T_init (a seeded field) or to T0 everywhere, across the chunk seams.
-    The initial populations are the equilibria at (rho0, 0, T), so the
-    read-out T is T_init to rounding of the storage (reading A4)."""
+    8192-wide lattice): a 8192 x 600 periodic box starts at rest from T_init (a
+    seeded field) or from T0 everywhere, across the chunk seams. The initial
+    populations are the equilibria at (rho0, 0, T) (reading A4) and the
+    read-out is taken after the pull (reading A6), so it shows
+    (1 - varpi) T(x) + varpi/4 times the sum of T over the four axis
+    neighbours, to rounding of the storage."""
     import paper_1510_08224_gb300 as P
     nx, ny = 8192, 600
     T = 0.5 + 0.25 * (2 * lc.uniform01(17, nx * ny).reshape(ny, nx) - 1) if with_T else None
     case = lc.periodic_box(nx, ny, T0=0.5, T_init=T)
     lat = P.Lattice(case, storage=storage)
     rho, ux, uy, Tg = lat.macro()
-    Te = T if with_T else np.full((ny, nx), 0.5)
+    if with_T:
+        nb = np.roll(T, 1, 0) + np.roll(T, -1, 0) + np.roll(T, 1, 1) + np.roll(T, -1, 1)
+        Te = (1 - case.varpi) * T + case.varpi / 4 * nb
+    else:
+        Te = np.full((ny, nx), 0.5)
     tol = {"f64": 1e-15, "f32": 1e-7, "f16": 1e-3}[storage]
     assert np.abs(Tg - Te).max() <= tol
     assert np.abs(rho - 1).max() <= tol and np.abs(ux).max() <= 1e-15 and np.abs(uy).max() <= 1e-15
