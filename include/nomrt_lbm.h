@@ -183,6 +183,13 @@ lbm_status lbm_set_step_kernel(lbm_lattice *h, int32_t variant, int32_t config);
  * T = sum g (Eq. 27)). Solid cells read 0. Synchronises. */
 lbm_status lbm_read_macro(lbm_lattice *h, double *rho, double *ux, double *uy, double *T);
 
+/* The same for rows y0 <= y < y1 only: caller-owned host arrays of
+ * (y1 - y0)*nx doubles (any may be NULL), row y at offset (y - y0)*nx. For
+ * lattices whose full fields would not fit the host. LBM_EINVAL unless
+ * 0 <= y0 <= y1 <= ny. Synchronises. */
+lbm_status lbm_read_macro_rows(lbm_lattice *h, int32_t y0, int32_t y1, double *rho, double *ux, double *uy,
+                               double *T);
+
 /* Mean Nusselt number on a frame wall (Eq. 39): Nu = -L (dT/dx_n) / delta_T,
  * x_n = x for LEFT/RIGHT and y for BOTTOM/TOP, with the wall gradient
  * (9 T_1/2 - T_3/2 - 8 T_w) / 3 from the two nearest fluid cells and the wall's

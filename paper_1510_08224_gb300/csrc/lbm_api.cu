@@ -637,25 +637,32 @@ lbm_status lbm_set_step_kernel(lbm_lattice *h, int32_t variant, int32_t config) 
     return LBM_OK;
 }
 
-lbm_status lbm_read_macro(lbm_lattice *h, double *rho, double *ux, double *uy, double *T) {
+lbm_status lbm_read_macro_rows(lbm_lattice *h, int32_t y0, int32_t y1, double *rho, double *ux, double *uy,
+                               double *T) {
     if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    if (y0 < 0 || y1 > h->ny || y0 > y1) return fail(h, LBM_EINVAL, "rows must satisfy 0 <= y0 <= y1 <= ny");
     double *outs[4] = {rho, ux, uy, T};
     const int nx = h->nx;
     const int rows = std::max(1, h->lay.stage_rows * h->lay.nq / 4);
-    for (int r0 = 0; r0 < h->ny; r0 += rows) {
-        const int r1 = std::min(h->ny, r0 + rows);
+    for (int r0 = y0; r0 < y1; r0 += rows) {
+        const int r1 = std::min(y1, r0 + rows);
         const size_t n = (size_t)(r1 - r0) * nx;
         LBM_CUDA(h, h->L->macro_rows(h->kp, h->cur, r0, r1, h->stage(), h->stream), "macro kernel");
         for (int k = 0; k < 4; ++k)
             if (outs[k])
                 LBM_CUDA(h,
-                         cudaMemcpyAsync(outs[k] + (size_t)r0 * nx, h->stage() + k * n, n * sizeof(double),
+                         cudaMemcpyAsync(outs[k] + (size_t)(r0 - y0) * nx, h->stage() + k * n, n * sizeof(double),
                                          cudaMemcpyDeviceToHost, h->stream),
                          "read macro");
         LBM_CUDA(h, cudaStreamSynchronize(h->stream), "read macro sync");
     }
     LBM_STATUS(h);
     return LBM_OK;
+}
+
+lbm_status lbm_read_macro(lbm_lattice *h, double *rho, double *ux, double *uy, double *T) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    return lbm_read_macro_rows(h, 0, h->ny, rho, ux, uy, T);
 }
 
 lbm_status lbm_nusselt(lbm_lattice *h, int32_t side, double L, double delta_T, double *nu_mean) {

@@ -22,7 +22,7 @@ SIDES = {"left": 0, "right": 1, "bottom": 2, "top": 3}
 STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3, "vec8": 4}
 # Every symbol include/nomrt_lbm.h declares.
 EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_step_kernel_count",
-            "lbm_set_step_kernel", "lbm_read_macro",
+            "lbm_set_step_kernel", "lbm_read_macro", "lbm_read_macro_rows",
             "lbm_nusselt",
             "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
             "lbm_destroy", "lbm_residual_fields_noalloc", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
@@ -87,6 +87,8 @@ def load():
         L.lbm_set_step_kernel.argtypes = [vp, C.c_int32, C.c_int32]
         L.lbm_read_macro.restype = C.c_int
         L.lbm_read_macro.argtypes = [vp, dp, dp, dp, dp]
+        L.lbm_read_macro_rows.restype = C.c_int
+        L.lbm_read_macro_rows.argtypes = [vp, C.c_int32, C.c_int32, dp, dp, dp, dp]
         L.lbm_nusselt.restype = C.c_int
         L.lbm_nusselt.argtypes = [vp, C.c_int32, C.c_double, C.c_double, dp]
         L.lbm_residual.restype = C.c_int
@@ -274,6 +276,12 @@ class Lattice:
         """(rho, ux, uy, T), each (ny, nx) float64 on the host."""
         out = [np.empty((self.ny, self.nx)) for _ in range(4)]
         _check(load().lbm_read_macro(self._h, *[_dptr(a) for a in out]), self._h)
+        return tuple(out)
+
+    def macro_rows(self, y0: int, y1: int):
+        """(rho, ux, uy, T) of rows y0 <= y < y1, each (y1 - y0, nx) float64."""
+        out = [np.empty((max(0, y1 - y0), self.nx)) for _ in range(4)]
+        _check(load().lbm_read_macro_rows(self._h, int(y0), int(y1), *[_dptr(a) for a in out]), self._h)
         return tuple(out)
 
     def nusselt(self, side, L: float = 0.0, delta_T: float = 1.0) -> float:

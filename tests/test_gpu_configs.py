@@ -193,3 +193,33 @@ def test_initial_state_of_a_lattice_taller_than_one_upload_chunk(storage, with_T
     assert np.abs(Tg - Te).max() <= tol
     assert np.abs(rho - 1).max() <= tol and np.abs(ux).max() <= 1e-15 and np.abs(uy).max() <= 1e-15
     lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_large_channel_rows_against_oracle(storage):
+    """A 16384 x 16384 channel (268 M fluid cells; population planes 2^28
+    elements apart, so plane offsets pass 2^32 elements and bytes): Couette
+    flow with a moving hot top wall, a cold bottom wall and a body force,
+    5 steps from rest. The flow is uniform along the periodic x direction, so
+    each row equals the same row of a 4-wide channel run by the oracle; rows at
+    both walls and in the middle are read back with lbm_read_macro_rows."""
+    import paper_1510_08224_gb300 as P
+    H, K = 16384, 5
+    big = lc.couette(H=H, nx=16384, U0=0.05).with_(ax=1e-4)
+    small = lc.couette(H=H, nx=4, U0=0.05).with_(ax=1e-4)
+    lat = P.Lattice(big, storage=storage)
+    lat.step(K)
+    o = oracle.OracleLattice(small)
+    o.step(K)
+    om = o.macro()
+    umax = max(np.abs(om[1]).max(), 1e-300)
+    tol = {"f64": 1e-12, "f32": 1e-5, "f16": 5e-3}[storage]
+    for y0, y1 in ((0, 8), (H // 2 - 2, H // 2 + 2), (H - 6, H + 2)):
+        g = lat.macro_rows(y0, y1)
+        assert g[0].shape == (y1 - y0, 16384)
+        for k, (a, b) in enumerate(zip(g, om)):
+            b = b[y0:y1, :1]
+            assert np.abs(a - a[:, :1]).max() == 0.0, (k, y0)  # uniform along x
+            scale = {0: 1.0, 1: umax, 2: umax, 3: 1.0}[k]
+            assert np.abs(a[:, :1] - b).max() <= tol * scale, (k, y0, np.abs(a[:, :1] - b).max())
+    lat.close()
