@@ -223,3 +223,23 @@ def test_large_channel_rows_against_oracle(storage):
             scale = {0: 1.0, 1: umax, 2: umax, 3: 1.0}[k]
             assert np.abs(a[:, :1] - b).max() <= tol * scale, (k, y0, np.abs(a[:, :1] - b).max())
     lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_tall_column_beyond_the_grid_y_limit(storage):
+    """A 4-wide, 200,000-row channel: more rows than one launch's grid can
+    cover in y (65,535 block rows), so every step kernel walks the rows. The
+    whole field after 5 steps from rest equals the oracle's."""
+    import paper_1510_08224_gb300 as P
+    case = lc.couette(H=200_000, nx=4, U0=0.05).with_(ax=1e-4)
+    lat = P.Lattice(case, storage=storage)
+    lat.step(5)
+    o = oracle.OracleLattice(case)
+    o.step(5)
+    om = o.macro()
+    umax = np.abs(om[1]).max()
+    tol = {"f64": 1e-12, "f32": 1e-5, "f16": 5e-3}[storage]
+    for k, (a, b) in enumerate(zip(lat.macro(), om)):
+        scale = umax if k in (1, 2) else 1.0
+        assert np.abs(a - b).max() <= tol * scale, (k, np.abs(a - b).max())
+    lat.close()
