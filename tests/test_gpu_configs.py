@@ -243,3 +243,39 @@ def test_tall_column_beyond_the_grid_y_limit(storage):
         scale = umax if k in (1, 2) else 1.0
         assert np.abs(a - b).max() <= tol * scale, (k, np.abs(a - b).max())
     lat.close()
+
+
+def test_largest_lattice_fp16_rows_against_oracle():
+    """The largest lattice the ABI accepts in FP16 storage: 32768 x 65535 rows,
+    ny * pitch = 2,147,450,880 cells, just below the 2^31 limit on cell
+    offsets (178 GB on the device with the residual snapshot). Couette flow
+    with a body force, 5 steps from rest; rows at both walls and in the middle
+    against the oracle's 4-wide channel, as for the 16384 x 16384 channel.
+    Skipped where the GPU or the host has too little free memory."""
+    import torch
+    import paper_1510_08224_gb300 as P
+    H, nx, K = 65533, 32768, 5
+    big = lc.couette(H=H, nx=nx, U0=0.05).with_(ax=1e-4)
+    p, keep = P.make_params(big, "f16")
+    need = P.lbm_footprint_bytes(p)
+    assert need > 0, P.load().lbm_last_error(None).decode()
+    free_dev, _ = torch.cuda.mem_get_info()
+    free_host = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE")
+    if free_dev < need + (4 << 30) or free_host < (24 << 30):
+        pytest.skip(f"needs {need / 2**30:.0f} GiB on the device and 24 GiB on the host")
+    lat = P.Lattice(big, storage="f16")
+    lat.step(K)
+    o = oracle.OracleLattice(lc.couette(H=H, nx=4, U0=0.05).with_(ax=1e-4))
+    o.step(K)
+    om = o.macro()
+    umax = np.abs(om[1]).max()
+    for y0, y1 in ((0, 8), (H // 2 - 2, H // 2 + 2), (H - 6, H + 2)):
+        g = lat.macro_rows(y0, y1)
+        for k, (a, b) in enumerate(zip(g, om)):
+            b = b[y0:y1, :1]
+            assert np.abs(a - a[:, :1]).max() == 0.0, (k, y0)
+            scale = umax if k in (1, 2) else 1.0
+            assert np.abs(a[:, :1] - b).max() <= 5e-3 * scale, (k, y0)
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
