@@ -46,12 +46,15 @@ cudaError_t launch_tma_shape(const KParams &p, int src, cudaStream_t st) {
     constexpr int W = N * T;
     constexpr size_t smem = tma_smem_bytes<S, N, T, STAGES>();
     auto kern = k_step_tma<S, N, T, STAGES, MB>;
-    // persistent grid: resident CTAs per SM x SMs, computed once per device
-    static int cached_dev = -1, cached_blocks = 0;
+    // persistent grid: resident CTAs per SM x SMs, computed once per device (0: not yet;
+    // threads that race here compute and store the same value)
+    static std::atomic<int> cached[kMaxDevices];
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev != cached_dev) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    int cached_blocks = cached[dev].load(std::memory_order_acquire);
+    if (cached_blocks == 0) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0, sms = 0;
@@ -60,7 +63,7 @@ cudaError_t launch_tma_shape(const KParams &p, int src, cudaStream_t st) {
         e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
         cached_blocks = (per_sm > 0 ? per_sm : 1) * sms;
-        cached_dev = dev;
+        cached[dev].store(cached_blocks, std::memory_order_release);
     }
     TmaUnits U;
     U.y_lo = p.py ? 0 : 1;

@@ -125,19 +125,21 @@ struct GridTag {};
 // per kernel instantiation: TAG distinguishes kernels of the same signature).
 template <typename TAG, typename K>
 cudaError_t resident_grid(K kern, int *blocks) {
-    static int cached_dev = -1, cached = 0;
+    static std::atomic<int> cached[kMaxDevices];  // 0: not yet computed for that device
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev != cached_dev) {
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    int n = cached[dev].load(std::memory_order_acquire);
+    if (n == 0) {
         int per_sm = 0, sms = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchThreads, 0);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return e;
-        cached = (per_sm > 0 ? per_sm : 1) * sms;
-        cached_dev = dev;
+        n = (per_sm > 0 ? per_sm : 1) * sms;
+        cached[dev].store(n, std::memory_order_release);
     }
-    *blocks = cached;
+    *blocks = n;
     return cudaSuccess;
 }
 

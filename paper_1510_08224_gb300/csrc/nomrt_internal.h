@@ -5,6 +5,8 @@
 
 #include <cuda_runtime.h>
 #include <stddef.h>
+
+#include <atomic>
 #include <stdint.h>
 
 namespace nomrt {
@@ -13,6 +15,8 @@ namespace nomrt {
 // kQmax with the D2Q9 temperature model of Eqs. 31-33 (9 + 9).
 constexpr int kQ = 14;
 constexpr int kQmax = 18;
+// Devices a process may use; per-device launch caches hold one slot each.
+constexpr int kMaxDevices = 64;
 // Link-map value of a solid cell (and of the row padding).
 constexpr uint8_t kSolid = 0xFF;
 // Fixed number of blocks of the reduction kernels (deterministic sums).
