@@ -67,8 +67,9 @@ typedef enum { LBM_WALL_HALFWAY = 0, LBM_WALL_NEE = 1 } lbm_wall_scheme;
  *   f_i(x) = f*_opp(i)(x) + 2 w_i rho0 (e_i . u_w) / c_s^2
  * for a direction i arriving at fluid cell x from a cell of this wall;
  * u_w may be tangential (a lid) or normal (a porous wall injecting fluid).
- * HALFWAY temperature: LBM_T_DIRICHLET holds T = T by anti-bounce-back,
- *   g_i(x) = -g*_opp(i)(x) + 2 (varpi/4) T;
+ * HALFWAY temperature: LBM_T_DIRICHLET holds the wall at its temperature T by
+ * anti-bounce-back, g_i(x) = -g*_opp(i)(x) + 2 (varpi/4) T (D2Q5; the D2Q9
+ * model uses twice the even part of Eq. 31 at (T, u_w));
  * LBM_T_ADIABATIC is a zero-flux wall, g_i(x) = g*_opp(i)(x).
  * NEE: at boundary node x_b with nearest fluid node x_f (an axis neighbour if
  * one is fluid, else a diagonal one), after streaming,
@@ -128,7 +129,11 @@ typedef struct lbm_lattice lbm_lattice; /* opaque; owned by the library */
 
 /* Device bytes lbm_create needs for these parameters (populations in two
  * buffers, flag and link maps, residual snapshot, staging and reduction
- * scratch), or 0 if the parameters are invalid. Admission control uses it. */
+ * scratch), or 0 if the parameters are invalid (lbm_last_error(NULL) says why).
+ * Admission control uses it. Rows are padded to a pitch of 128 bytes of
+ * storage (nx rounded up to a multiple of 16 / 32 / 64 for FP64 / FP32 / FP16);
+ * ny * pitch must stay below 2^31, so the largest FP16 lattice is about
+ * 2.1e9 cells (178 GB with the residual snapshot). */
 size_t lbm_footprint_bytes(const lbm_params *p);
 
 /* Validate p, upload flags, walls and T_init, and set the initial state
