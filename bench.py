@@ -543,46 +543,52 @@ def run_table3(args):
     return 0
 
 
-def run_serving(args):
+def serving_measure(storage: str, count: int, side_hi: int, step_cap: int, check_every: int, graph_steps: int):
     """Continuous-batching serving: Poisson arrivals (20 per second, seed 0) of
-    cavity and Rayleigh-Benard requests, sides log-uniform in [64, 2048], Ra
-    log-uniform in [1e3, 1e6], each run to residual < 1e-6 or the step cap,
-    admitted by a 150 GB HBM budget; against the plain path (FP64 storage, one
-    request at a time, same convergence checks)."""
+    `count` cavity and Rayleigh-Benard requests, sides log-uniform in
+    [64, side_hi], Ra log-uniform in [1e3, 1e6], each run to residual < 1e-6 or
+    the step cap, admitted by a 150 GB HBM budget; against the plain path (FP64
+    storage, one request at a time, same convergence checks). Returns (config,
+    served, plain) dictionaries."""
     import torch
     from paper_1510_08224_gb300 import serve
     torch.cuda.set_device(0)
-    stream = lc.serving_stream(n=args.count, seed=0, side_lo=64, side_hi=args.side_hi)
+    stream = lc.serving_stream(n=count, seed=0, side_lo=64, side_hi=side_hi)
     reqs = [serve.Request(k, c, t, nusselt_sides=((0,) if kind == "cavity" else (2,))) for k, (t, kind, c) in
             enumerate(stream)]
     cells = sum(int((r.case.flags == 0).sum()) for r in reqs)
-    be = serve.GpuBackend(args.storage, graph_steps=args.graph_steps)
-    srv = serve.Server(be, budget_bytes=150e9, check_every=args.check_every, tol=1e-6, step_cap=args.step_cap)
+    be = serve.GpuBackend(storage, graph_steps=graph_steps)
+    srv = serve.Server(be, budget_bytes=150e9, check_every=check_every, tol=1e-6, step_cap=step_cap)
     t0 = time.perf_counter()
     res = srv.run(reqs, realtime=True)
     span = time.perf_counter() - t0
     be.close()
     s_ours = serve.summarize(res, span)
-    base, service = serve.serial_baseline(lambda: serve.GpuBackend("f64"), reqs, args.check_every, 1e-6,
-                                          args.step_cap)
+    base, service = serve.serial_baseline(lambda: serve.GpuBackend("f64"), reqs, check_every, 1e-6, step_cap)
     s_base = serve.summarize(base)
     same_steps = sum(1 for a, b in zip(sorted(res, key=lambda r: r.rid), sorted(base, key=lambda r: r.rid))
                      if a.steps == b.steps)
+    config = {"workload": f"serving_stream_{count}", "arrivals": "Poisson 20/s, seed 0",
+              "sides": f"log-uniform [64, {side_hi}]", "Ra": "log-uniform [1e3, 1e6]",
+              "types": "cavity | rayleigh_benard", "tol": 1e-6, "step_cap": srv.step_cap,
+              "check_every": check_every, "hbm_budget_bytes": 150e9, "storage": STORAGE_NAME[storage],
+              "requests": len(reqs), "fluid_cells_total": cells, "graph_steps": graph_steps}
+    served = {**s_ours, "makespan_s": round(span, 3), "peak_hbm_bytes": srv.peak_in_use,
+              "max_concurrent": srv.max_active, "MLUPS": round(s_ours["cell_steps"] / span / 1e6, 1)}
+    plain = {**s_base, "service_s_total": round(sum(service.values()), 3),
+             "MLUPS": round(s_base["cell_steps"] / sum(service.values()) / 1e6, 1), "same_step_counts": same_steps}
+    return config, served, plain
+
+
+def run_serving(args):
+    """The serving stream as its own bench line (value = solves/s)."""
+    config, served, plain = serving_measure(args.storage, args.count, args.side_hi, args.step_cap,
+                                            args.check_every, args.graph_steps)
     line = {
-        "metric": METRIC, "value": round(s_ours["solves_per_s"], 4), "unit": "solves/s", "n_gpus": 1,
-        "steps": args.step_cap, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": COMPUTE_DTYPE[args.storage], "data": "synthetic",
-        "config": {"workload": f"serving_stream_{args.count}", "arrivals": "Poisson 20/s, seed 0",
-                   "sides": f"log-uniform [64, {args.side_hi}]", "Ra": "log-uniform [1e3, 1e6]",
-                   "types": "cavity | rayleigh_benard", "tol": 1e-6, "step_cap": srv.step_cap,
-                   "check_every": args.check_every, "hbm_budget_bytes": 150e9, "storage": STORAGE_NAME[args.storage],
-                   "requests": len(reqs), "fluid_cells_total": cells, "graph_steps": args.graph_steps},
-        "served": {**s_ours, "makespan_s": round(span, 3), "peak_hbm_bytes": srv.peak_in_use,
-                   "max_concurrent": srv.max_active,
-                   "MLUPS": round(s_ours["cell_steps"] / span / 1e6, 1)},
-        "plain_fp64_serial": {**s_base, "service_s_total": round(sum(service.values()), 3),
-                              "MLUPS": round(s_base["cell_steps"] / sum(service.values()) / 1e6, 1),
-                              "same_step_counts": same_steps},
+        "metric": METRIC, "value": round(served["solves_per_s"], 4), "unit": "solves/s", "n_gpus": 1,
+        "steps": config["step_cap"], "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": COMPUTE_DTYPE[args.storage], "data": "synthetic", "config": config,
+        "served": served, "plain_fp64_serial": plain,
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -603,6 +609,7 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="rb: skip the short serving stream")
     ap.add_argument("--sweep", action="store_true", help="cost workload: time every step kernel of each model")
     ap.add_argument("--workload", default="rb", choices=["rb", "batch", "serve", "cost", "table3"],
                     help="rb: the 4096 x 2048 Rayleigh-Benard step (default); batch: uneven cavities advanced together; serve: the serving stream; cost: collision operators; table3: the cavity of Table 3")
@@ -722,6 +729,14 @@ def main():
             if st == "f64":
                 var[STORAGE_NAME[st]]["alu"] = fp64_alu_roofline(vm)
         line["variants"] = var
+    if rank == 0 and world == 1 and not args.no_serving:
+        # the metric's second half (solves/s, p50/p99 latency against the plain path) on
+        # a shorter stream than --workload serve, so that the default run stays short
+        config, served, plain = serving_measure(args.storage if args.storage != "f64" else "f32", 16, 1024,
+                                                10000, 500, args.graph_steps)
+        line["serving"] = {"config": config, "served": served, "plain_fp64_serial": plain,
+                           "speedup_solves_per_s": round(served["solves_per_s"] / plain["solves_per_s"], 2),
+                           "p99_latency_ratio": round(plain["p99_latency_s"] / served["p99_latency_s"], 2)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(case)
     if rank == 0:
