@@ -10,7 +10,7 @@ the equilibrium moments (Eqs. 16, 28), the forcing (Eq. 17), the collision
 (Eqs. 8, 24), the rates (Eqs. 20, 29 and the viscosity/diffusivity relations),
 streaming (Eqs. 9, 25), the wall rules (readings A5, A11), the Nusselt
 stencils (reading A8), the residual (reading A9), the D2Q9 temperature model
-(Eq. 31) and the BGK switch.
+(Eq. 31) and the BGK switch, the buoyancy force (Eq. 4).
 """
 import concurrent.futures
 import os
@@ -113,6 +113,33 @@ MUTANTS = [
     ("BGK forcing term sign",
      "(((EX[i] - ux) * Fx + (EY[i] - uy) * Fy) / CS2",
      "(((EX[i] + ux) * Fx + (EY[i] - uy) * Fy) / CS2"),
+    ("BGK flow equilibrium, u^2 term",
+     "eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2)));\n            double Fi",
+     "eu * eu / (2.0 * CS2 * CS2) - uu / CS2));\n            double Fi"),
+    ("BGK forcing weight",
+     "fstar[i] = fbar[i] - om * (fbar[i] - feq) + (1.0 - 0.5 * om) * Fi;",
+     "fstar[i] = fbar[i] - om * (fbar[i] - feq) + (1.0 - om) * Fi;"),
+    ("BGK temperature rate",
+     "gstar[i] = g[i] - zt * (g[i] - geq);",
+     "gstar[i] = g[i] - om * (g[i] - geq);"),
+    ("D2Q9 temperature rate per moment (Eq. 32)",
+     "for (int k = 0; k < 9; ++k) ns[k] = n[k] - r->z[k] * (n[k] - neq[k]);",
+     "for (int k = 0; k < 9; ++k) ns[k] = n[k] - r->z[1] * (n[k] - neq[k]);"),
+    ("buoyancy sign (Eq. 4)",
+     "double Fy = r->ay + r->g_beta * (T - r->T0);",
+     "double Fy = r->ay - r->g_beta * (T - r->T0);"),
+    ("buoyancy reference temperature (Eq. 4)",
+     "double Fy = r->ay + r->g_beta * (T - r->T0);",
+     "double Fy = r->ay + r->g_beta * T;"),
+    ("node wall temperature of an adiabatic wall (A11)",
+     "double Tb = L->wall_kind[k - 1] == 0 ? L->wall_T[k - 1] : T;",
+     "double Tb = L->wall_T[k - 1];"),
+    ("nearest fluid node of a boundary node (A11)",
+     "for (int i = 1; i < 9 && !d; ++i) {",
+     "for (int i = 8; i >= 1 && !d; --i) {"),
+    ("residual temperature norm (A9)",
+     "double RT = sqrt(num_T) / (dT > 1e-300 ? dT : 1e-300);",
+     "double RT = num_T / (dT > 1e-300 ? dT : 1e-300);"),
 ]
 
 
