@@ -146,8 +146,12 @@ size_t lbm_footprint_bytes(const lbm_params *p);
 lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, size_t device_bytes,
                       lbm_lattice **out);
 
-/* Advance nsteps >= 0 time steps (Eqs. 8-9 and 24-25, fused, one kernel launch
- * per step). Asynchronous on the lattice's stream. */
+/* Advance nsteps >= 0 time steps (Eqs. 8-9 and 24-25, fused, one kernel per
+ * step, plus one for the boundary nodes of node-based walls). Asynchronous on the
+ * lattice's stream. Runs of 64 steps or more replay a CUDA graph of 32 steps
+ * captured once per step-kernel choice (the same kernels and bits, without the
+ * launch gap between steps); shorter runs, and calls on a stream that is being
+ * captured, launch the kernels directly. */
 lbm_status lbm_step(lbm_lattice *h, int64_t nsteps);
 
 /* Wait for the lattice's stream. LBM_ETIMEOUT if a step kernel gave up one of

@@ -49,6 +49,13 @@ struct lbm_lattice {
     std::string err;
     const nomrt::Launchers *L = nullptr;
     lbm_batch *batch = nullptr;  // the batch that steps this lattice, if any
+    // lbm_step replays kGraphSteps steps from buffer 0 as one CUDA graph once the current
+    // step kernel has run directly; reset when the kernel choice changes
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on (any stream can launch it)
+    int graph_variant = -1, graph_config = -1;
+    bool graph_off = false;       // capture failed or the stream cannot be captured
+    bool direct_done = false;     // the current kernel choice has run at least once directly
 
     double *stage() const { return reinterpret_cast<double *>(mem + lay.off_stage); }
     double *partials() const { return reinterpret_cast<double *>(mem + lay.off_part); }

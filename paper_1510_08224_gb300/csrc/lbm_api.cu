@@ -394,6 +394,50 @@ lbm_status check_status(lbm_lattice *h) {
         if (s_ != LBM_OK) return s_;       \
     } while (0)
 
+constexpr int kGraphSteps = 32;  // steps per replayed graph (even: it starts and ends on buffer 0)
+
+void drop_graph(lbm_lattice *h) {
+    if (h->graph) cudaGraphExecDestroy(h->graph);
+    h->graph = nullptr;
+}
+
+// Captures kGraphSteps steps starting from buffer 0 on a private stream (the lattice's own
+// stream may be the legacy default stream, which cannot be captured; the graph launches on
+// any stream). On any failure the lattice falls back to direct launches for good (the
+// error is cleared).
+void capture_graph(lbm_lattice *h) {
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    bool ok = h->cap_stream || cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+        for (int s = 0; s < kGraphSteps && ok; ++s) ok = h->L->step(h->kp, s & 1, h->cap_stream) == cudaSuccess;
+        ok = (cudaStreamEndCapture(h->cap_stream, &g) == cudaSuccess) && ok && g;
+    }
+    if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+        if (ge) cudaGraphExecDestroy(ge);
+        cudaGetLastError();
+        h->graph_off = true;
+        return;
+    }
+    h->graph = ge;
+    h->graph_variant = h->kp.variant;
+    h->graph_config = h->kp.config;
+}
+
+lbm_status step_direct(lbm_lattice *h, int64_t n) {
+    for (int64_t s = 0; s < n; ++s) {
+        cudaError_t e = h->L->step(h->kp, h->cur, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
+        h->cur ^= 1;
+        ++h->steps;
+    }
+    if (n > 0) h->direct_done = true;
+    return LBM_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -599,13 +643,36 @@ lbm_status lbm_step(lbm_lattice *h, int64_t nsteps) {
     if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
     if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
     if (h->batch) return fail(h, LBM_EINVAL, "lattice belongs to a batch: step it with lbm_batch_step");
-    for (int64_t s = 0; s < nsteps; ++s) {
-        cudaError_t e = h->L->step(h->kp, h->cur, h->stream);
-        if (e != cudaSuccess) return cuda_fail(h, e, "step kernel");
-        h->cur ^= 1;
-        ++h->steps;
+    // Long runs replay a captured graph of kGraphSteps steps: the same kernels with the same
+    // arguments, without the launch gap between steps. Direct launches serve short runs, a
+    // stream that is already being captured (the steps then join the caller's graph), and
+    // the first run of a kernel choice (its launch-time setup happens outside any capture).
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(h->stream, &cs);
+    if (ce != cudaSuccess) cudaGetLastError();  // leave no error behind for the launch checks
+    const bool can_graph = !h->graph_off && ce == cudaSuccess && cs == cudaStreamCaptureStatusNone;
+    if (!can_graph || nsteps < 2 * kGraphSteps) return step_direct(h, nsteps);
+    if (!h->direct_done || h->graph_variant != h->kp.variant || h->graph_config != h->kp.config) {
+        drop_graph(h);
+        if (!h->direct_done) {
+            lbm_status st = step_direct(h, 1);
+            if (st != LBM_OK) return st;
+            --nsteps;
+        }
+        capture_graph(h);
+        if (!h->graph) return step_direct(h, nsteps);
     }
-    return LBM_OK;
+    if (h->cur != 0) {  // the graph starts from buffer 0
+        lbm_status st = step_direct(h, 1);
+        if (st != LBM_OK) return st;
+        --nsteps;
+    }
+    for (; nsteps >= kGraphSteps; nsteps -= kGraphSteps) {
+        cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
+        h->steps += kGraphSteps;
+    }
+    return step_direct(h, nsteps);
 }
 
 lbm_status lbm_sync(lbm_lattice *h) {
@@ -632,6 +699,7 @@ lbm_status lbm_set_step_kernel(lbm_lattice *h, int32_t variant, int32_t config) 
     if (config < 0 || config >= n) return fail(h, LBM_EINVAL, "step kernel config out of range");
     if ((h->kp.tq == 9 || h->kp.bgk) && (variant == LBM_STEP_TMA || variant == LBM_STEP_VEC8))
         return fail(h, LBM_EINVAL, "the D2Q9 temperature model and BGK have the SCALAR and VEC4 step kernels only");
+    if (h->kp.variant != variant || h->kp.config != config) h->direct_done = false;
     h->kp.variant = variant;
     h->kp.config = config;
     return LBM_OK;
@@ -782,6 +850,8 @@ const char *lbm_last_error(const lbm_lattice *h) {
 void lbm_destroy(lbm_lattice *h) {
     if (!h) return;
     if (h->batch) nomrt::batch_detach(h->batch, h);
+    drop_graph(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->owns_mem && h->mem) {
         cudaStreamSynchronize(h->stream);
         cudaFree(h->mem);

@@ -333,3 +333,54 @@ def test_nee_cavity_nusselt_against_table3_on_gpu():
     o.step(steps)
     for side, v in zip((0, 1), nu):
         assert abs(v - o.nusselt(side, L=64.0)) < 1e-10
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_graph_replayed_steps_equal_direct_steps(storage):
+    """lbm_step replays runs of 64 steps or more as CUDA graphs of 32 steps: 201
+    steps in one call (one direct step, six graph replays, the rest direct)
+    give the bits of 201 single-step calls, with halfway and node-based walls,
+    on the default stream and on a side stream, for the AUTO kernel and (FP32)
+    the TMA kernel; a call on a stream that torch is capturing joins that
+    graph and gives the same bits when replayed."""
+    import torch
+    P = _P()
+    cases = [lc.rayleigh_benard(nx=133, H=7, Ra=1e5, sigma=1e-2), lc.cavity_nee(n=19, Ra=1e4, noise=1e-3)]
+    for case in cases:
+        f0, g0 = lc.random_state(case, seed=5)
+        variants = [("auto", 0)] + ([("tma", 1)] if storage == "f32" and case.name != "cavity_nee" else [])
+        for v in variants:
+            for side in (False, True):
+                s = torch.cuda.Stream() if side else None
+                a = P.Lattice(case, storage=storage, stream=s)
+                b = P.Lattice(case, storage=storage, stream=s)
+                for lat in (a, b):
+                    lat.set_step_kernel(*v)
+                    lat.set_populations(f0, g0)
+                a.step(201)
+                for _ in range(201):
+                    b.step(1)
+                fa, ga = a.populations()
+                fb, gb = b.populations()
+                assert np.array_equal(fa, fb) and np.array_equal(ga, gb), (case.name, v, side)
+                a.close()
+                b.close()
+        # inside a capture on the caller's stream
+        s = torch.cuda.Stream()
+        a = P.Lattice(case, storage=storage, stream=s)
+        b = P.Lattice(case, storage=storage, stream=s)
+        a.set_populations(f0, g0)
+        b.set_populations(f0, g0)
+        a.step(1)
+        torch.cuda.synchronize()
+        gr = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(gr, stream=s):
+            a.step(64)
+        gr.replay()
+        gr.replay()
+        torch.cuda.synchronize()
+        for _ in range(129):
+            b.step(1)
+        assert np.array_equal(a.populations()[0], b.populations()[0])
+        a.close()
+        b.close()
