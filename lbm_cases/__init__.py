@@ -413,6 +413,25 @@ def cavity_nee(n: int = 64, Ra: float = 1e3, Pr: float = 0.71, Ma: float = 0.1, 
                 delta_T=dT, T_init=Ti, L=float(n), meta=dict(Ra=Ra, Pr=Pr, Ma=Ma, nodes=True), **kin)
 
 
+def lid_cavity_nee(n: int = 192, Re: float = 1000.0, u0: float = 0.1, kinetic=None) -> Case:
+    """Sec. 3.2 as the paper sets it up: lid-driven cavity on (n + 1) x (n + 1)
+    nodes, walls on the boundary nodes (non-equilibrium extrapolation), the top
+    wall moving at (u0, 0), the others static; L = n, nu = L u0 / Re; s_e = 1.6,
+    s_q = 1.2, s_eps = 1.8 as the paper lists them. Corner nodes belong to the
+    static side walls. Isothermal (no buoyancy, uniform T)."""
+    nu = n * u0 / Re
+    walls = [Wall(0, 0, ADIABATIC, 0.0, NEE), Wall(0, 0, ADIABATIC, 0.0, NEE), Wall(0, 0, ADIABATIC, 0.0, NEE),
+             Wall(u0, 0, ADIABATIC, 0.0, NEE)]
+    flags = np.zeros((n + 1, n + 1), np.uint8)
+    flags[0, :] = 3
+    flags[-1, :] = 4
+    flags[:, 0] = 1
+    flags[:, -1] = 2
+    kin = dict(KINETIC_CONVECTION if kinetic is None else kinetic)
+    return Case("lid_cavity_nee", n + 1, n + 1, False, False, flags, walls, nu=nu, alpha=nu / 0.71, T0=0.5,
+                L=float(n), meta=dict(Re=Re, u0=u0, nodes=True), **kin)
+
+
 def with_d2q9_temperature(case: Case, theta: float = 1.0, zeta_q: float = 1.0, zeta_eps: float = 1.0) -> Case:
     """The same problem solved with the D2Q9 temperature model of Eqs. 31-33
     (same alpha; zeta_e and zeta_nu kept). The paper gives no zeta_q, zeta_eps
