@@ -715,6 +715,8 @@ lbm_status lbm_read_macro_rows(lbm_lattice *h, int32_t y0, int32_t y1, double *r
     for (int r0 = y0; r0 < y1; r0 += rows) {
         const int r1 = std::min(y1, r0 + rows);
         const size_t n = (size_t)(r1 - r0) * nx;
+        // the next chunk's kernel, queued behind these copies on the same stream, cannot
+        // overwrite the staging area before they finish: one wait at the end suffices
         LBM_CUDA(h, h->L->macro_rows(h->kp, h->cur, r0, r1, h->stage(), h->stream), "macro kernel");
         for (int k = 0; k < 4; ++k)
             if (outs[k])
@@ -722,8 +724,8 @@ lbm_status lbm_read_macro_rows(lbm_lattice *h, int32_t y0, int32_t y1, double *r
                          cudaMemcpyAsync(outs[k] + (size_t)(r0 - y0) * nx, h->stage() + k * n, n * sizeof(double),
                                          cudaMemcpyDeviceToHost, h->stream),
                          "read macro");
-        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "read macro sync");
     }
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "read macro sync");
     LBM_STATUS(h);
     return LBM_OK;
 }
@@ -804,8 +806,9 @@ lbm_status lbm_get_populations(lbm_lattice *h, double *f9, double *g5) {
                                          cudaMemcpyDeviceToHost, h->stream),
                          "export copy");
         }
-        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "export sync");
     }
+    // stream order keeps each chunk's kernel behind the previous chunk's copies
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "export sync");
     LBM_STATUS(h);
     return LBM_OK;
 }
@@ -828,8 +831,9 @@ lbm_status lbm_set_populations(lbm_lattice *h, const double *f9, const double *g
                          "import copy");
         }
         LBM_CUDA(h, h->L->import_rows(h->kp, h->cur, r0, r1, h->stage(), which, h->stream), "import kernel");
-        LBM_CUDA(h, cudaStreamSynchronize(h->stream), "import sync");
     }
+    // one wait: the caller's arrays stay in use until the last copy has left them
+    LBM_CUDA(h, cudaStreamSynchronize(h->stream), "import sync");
     return LBM_OK;
 }
 
