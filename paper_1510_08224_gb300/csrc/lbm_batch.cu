@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
         pa.src = static_cast<const S *>(sel ? L.pop1 : L.pop0);
         pa.dst = static_cast<S *>(const_cast<void *>(sel ? L.pop0 : L.pop1));
         pa.plane = L.plane;
-        row4<S, StridedPlanes<S>, true>(pa, L.g, L.r, x0, row - P.row0[lo], lane);
+        const RatesC<float> r = L.r;  // into registers once per row rather than indexed loads at every use
+        const Geom g = L.g;
+        row4<S, StridedPlanes<S>, true>(pa, g, r, x0, row - P.row0[lo], lane);
     }
 }
 
