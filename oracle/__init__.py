@@ -63,6 +63,7 @@ class OrcParams(C.Structure):
         ("zeta_q", C.c_double), ("zeta_eps", C.c_double),
         ("collision", C.c_int32),
         ("rho_in_u_terms", C.c_int32),
+        ("nee_uf_variant", C.c_int32),
     ]
 
 
@@ -157,9 +158,15 @@ def collide_node(rates: OrcRates, fbar, g):
 
 
 class OracleLattice:
-    """A lattice advanced by the oracle. ``case`` is an ``lbm_cases.Case``."""
+    """A lattice advanced by the oracle. ``case`` is an ``lbm_cases.Case``.
 
-    def __init__(self, case, s8_literal: bool = False, threads: int = 1, rho_in_u: bool = False):
+    Ablations (tests only): ``rho_in_u`` (reading A1), ``s8_literal`` (A2),
+    ``nee_uf`` (A11): the fluid node's velocity inside the extrapolated
+    non-equilibrium part of node walls, "eq19" (the reading, (j + F/2)/rho0),
+    "bare" (j/rho0) or "minus" ((j - F/2)/rho0)."""
+
+    def __init__(self, case, s8_literal: bool = False, threads: int = 1, rho_in_u: bool = False,
+                 nee_uf: str = "eq19"):
         self.case = case
         self.nx, self.ny = case.nx, case.ny
         flags = np.ascontiguousarray(case.flags, dtype=np.uint8)
@@ -188,6 +195,8 @@ class OracleLattice:
         p.zeta_eps = float(getattr(case, "zeta_eps", 1.0))
         p.collision = int(getattr(case, "collision", 0))
         p.rho_in_u_terms = int(bool(rho_in_u))
+        # reading A11 (Eq. 19) or an ablation of the fluid node's velocity in the node walls
+        p.nee_uf_variant = {"eq19": 0, "bare": 1, "minus": 2}[nee_uf]
         self._p = p
         h = lib().orc_create(C.byref(p))
         if not h:

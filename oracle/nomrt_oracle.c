@@ -144,6 +144,9 @@ typedef struct {
     double zeta_q, zeta_eps;   /* kinetic rates of Eq. 32 (D2Q9 model) */
     int32_t collision;         /* 0: the MRT collisions (Eq. 8, Eq. 24 or Eq. 32); 1: BGK (one rate each) */
     int32_t rho_in_u_terms;    /* 1: the alternative to reading A1 (rho, not rho0, in every term; ablation) */
+    int32_t nee_uf_variant;    /* velocity of the fluid node inside the extrapolated non-equilibrium part
+                                  (reading A11): 0 Eq. 19, (j + F/2) / rho0; ablations: 1 j / rho0,
+                                  2 (j - F/2) / rho0 */
 } orc_params;
 
 /* Per-node collision inputs. s[9] is Lambda of Eq. 20; z is Q of Eq. 29 (its
@@ -174,6 +177,7 @@ typedef struct {
     int cur;
     double *snap; /* residual snapshot [3][ny*nx], NULL until first call */
     int nthreads;
+    double nee_half; /* the F/2 factor of u_f in nee_gather: 0.5 (Eq. 19), or 0 / -0.5 (ablations) */
 } orc_lattice;
 
 /* ------------------------------------------------------------- collision -- */
@@ -454,7 +458,7 @@ static void nee_gather(const orc_lattice *L, const double *fsrc, const double *g
     }
     for (int i = 0; i < L->tq; ++i) T += gf[i];
     double Fx = L->r.ax, Fy = L->r.ay + L->r.g_beta * (T - L->r.T0);
-    double ux = (jx + 0.5 * RHO0 * Fx) / RHO0, uy = (jy + 0.5 * RHO0 * Fy) / RHO0;
+    double ux = (jx + L->nee_half * RHO0 * Fx) / RHO0, uy = (jy + L->nee_half * RHO0 * Fy) / RHO0;
     int k = L->flags[c];
     double uwx = L->wall_u[2 * (k - 1)], uwy = L->wall_u[2 * (k - 1) + 1];
     double Tb = L->wall_kind[k - 1] == 0 ? L->wall_T[k - 1] : T;
@@ -501,6 +505,7 @@ orc_lattice *orc_create(const orc_params *p) {
     }
     orc_rates_from_params(p, &L->r);
     L->tq = L->r.tq;
+    L->nee_half = p->nee_uf_variant == 1 ? 0.0 : (p->nee_uf_variant == 2 ? -0.5 : 0.5);
     for (size_t c = 0; c < nxy; ++c)
         if (L->flags[c] > p->n_walls) { orc_destroy(L); return NULL; }
     for (int y = 0; y < L->ny; ++y)

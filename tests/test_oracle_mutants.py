@@ -27,7 +27,7 @@ SRC = os.path.join(ROOT, "oracle", "nomrt_oracle.c")
 # not wait for the second; -x stops at the first failing pin)
 PIN_FILES = ["tests/test_oracle_pins.py", "tests/test_oracle_d2q9t.py", "tests/test_oracle_bgk.py",
              "tests/test_oracle_nee.py"]
-SLOW = "table2 or slopes or table3 or convergence or onset or stability"
+SLOW = "table1 or table2 or slopes or table3 or convergence or onset or stability"
 CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math", "-fopenmp"]
 
 # (name, text in the source, replacement); the text must occur exactly once

@@ -32,14 +32,14 @@ def _steady(o, chunk=2000, tol=1e-12, max_chunks=3000):
     return r
 
 
-def _poiseuille_error(H, s_nu, Re=49.4146, ax=None):
+def _poiseuille_error(H, s_nu, Re=49.4146, ax=None, nee_uf="eq19"):
     """(E_u as the global L2 norm, E_u as summed per-node norms) of the
     channel at steady state; ax follows from Re unless given."""
     nu = (1 / s_nu - 0.5) / 3
     if ax is None:
         ax = 2 * Re * nu**2 / (H / 2) ** 3  # Re = u0 l_c / nu with u0 = ax l_c^2 / (2 nu), l_c = H / 2
     c = lc.poiseuille_nee(H=H, nx=2, ax=ax, s_nu=s_nu)
-    o = oracle.OracleLattice(c)
+    o = oracle.OracleLattice(c, nee_uf=nee_uf)
     _steady(o)
     ux = o.macro()[1][:, 0]
     y = np.arange(H + 1)
@@ -100,13 +100,23 @@ def test_poiseuille_errors_match_table2_in_magnitude_and_order():
     assert abs(slope - np.log(tab[1, 1] / tab[1, 2]) / np.log(2.0)) < 0.01
 
 
-def test_poiseuille_error_nearly_independent_of_body_force():
+def test_poiseuille_error_nearly_independent_of_body_force_table1():
     """Table 1: at s_nu = 1.754 and dx = 1/60, E_u moves by 0.6 % as a_x goes
     from 2e-6 to 8e-6 (Re from 49 to 198): the error is a property of the
-    walls and the resolution, not of the flow speed. Ours moves by 0.5 %."""
+    walls and the resolution, not of the flow speed. Ours moves by 0.5 %, in
+    the other direction. The move comes from the fluid node's velocity inside
+    the extrapolated non-equilibrium part: with u_f = (j - F/2)/rho0 instead of
+    Eq. 19's (j + F/2)/rho0 the oracle's E_u follows Table 1 to 0.1 % in ratio
+    (it falls by 0.54 % where the paper's falls by 0.60 %), which is why
+    reading A11 names that detail as the likely difference."""
     e2, _ = _poiseuille_error(60, 1.754, ax=2e-6)
     e8, _ = _poiseuille_error(60, 1.754, ax=8e-6)
     assert abs(e8 / e2 - 1) < 0.01 and abs(e2 - 1.2600e-3) / 1.2600e-3 < 0.06
+    assert e8 > e2  # the reading's trend
+    m2, _ = _poiseuille_error(60, 1.754, ax=2e-6, nee_uf="minus")
+    m8, _ = _poiseuille_error(60, 1.754, ax=8e-6, nee_uf="minus")
+    assert m8 < m2  # Table 1's trend
+    assert abs((m8 / 1.2524e-3) / (m2 / 1.2600e-3) - 1) < 1e-3
 
 
 def test_injection_channel_slopes_match_sec33():
