@@ -1127,6 +1127,36 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
     }
 }
 
+// Four consecutive values of one population plane (x0..x0+3 of a row), zeros
+// where the lane lies past the row (`inrow` false: such a lane still takes part
+// in the shuffles that supply its neighbours).
+template <typename S, bool NC = true>
+__device__ __forceinline__ void ld_four(const S *row, int x0, bool inrow, float a[4]) {
+    a[0] = a[1] = a[2] = a[3] = 0.f;
+    if (inrow) Ld<S, NC>::four(row + x0, a);
+}
+
+// The values cells x0..x0+3 pull from a plane with e_x = +1 (source x - 1): the
+// left neighbour comes from the previous lane's vector, lane 0 takes `edge`
+// (loaded apart, zero where there is none). Every lane of the warp must call it.
+__device__ __forceinline__ void pull_from_left(const float a[4], float edge, int lane, float out[4]) {
+    float left = __shfl_up_sync(kFull, a[3], 1);
+    left = lane == 0 ? edge : left;
+    out[0] = left; out[1] = a[0]; out[2] = a[1]; out[3] = a[2];
+}
+
+// The same for e_x = -1 (source x + 1): lane 31 takes `edge`; on a periodic x
+// the cell nx - 1 (index seam_k of this lane's four, or -1) pulls cell 0's
+// value `seam`.
+__device__ __forceinline__ void pull_from_right(const float a[4], float edge, int lane, int seam_k, float seam,
+                                                float out[4]) {
+    float right = __shfl_down_sync(kFull, a[0], 1);
+    right = lane == 31 ? edge : right;
+    out[0] = a[1]; out[1] = a[2]; out[2] = a[3]; out[3] = right;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[j] = (j == seam_k) ? seam : out[j];  // constant indices only
+}
+
 // Fused step, four cells of one row per thread. Same arithmetic as k_step;
 // solid cells in a group are written as zeros (they hold zeros already).
 // One warp's share of a row: cells x0..x0+3 of row y for each lane (x0 = base +
@@ -1148,25 +1178,93 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
     // rows of a non-periodic edge hold no fluid cell, so a warp that gets here has 0 < y < ny - 1
     const int rm = ym * g.pitch, rp = yp * g.pitch;
     float f[9][4], t[TQ][4];
-    ld_plane<S, 0, NC>(pl.src_at(0) + r0, g, x0, lane, inrow, f[0]);
-    ld_plane<S, 1, NC>(pl.src_at(1) + r0, g, x0, lane, inrow, f[1]);
-    ld_plane<S, 0, NC>(pl.src_at(2) + rm, g, x0, lane, inrow, f[2]);
-    ld_plane<S, -1, NC>(pl.src_at(3) + r0, g, x0, lane, inrow, f[3]);
-    ld_plane<S, 0, NC>(pl.src_at(4) + rp, g, x0, lane, inrow, f[4]);
-    ld_plane<S, 1, NC>(pl.src_at(5) + rm, g, x0, lane, inrow, f[5]);
-    ld_plane<S, -1, NC>(pl.src_at(6) + rm, g, x0, lane, inrow, f[6]);
-    ld_plane<S, -1, NC>(pl.src_at(7) + rp, g, x0, lane, inrow, f[7]);
-    ld_plane<S, 1, NC>(pl.src_at(8) + rp, g, x0, lane, inrow, f[8]);
-    ld_plane<S, 0, NC>(pl.src_at(9) + r0, g, x0, lane, inrow, t[0]);
-    ld_plane<S, 1, NC>(pl.src_at(10) + r0, g, x0, lane, inrow, t[1]);
-    ld_plane<S, 0, NC>(pl.src_at(11) + rm, g, x0, lane, inrow, t[2]);
-    ld_plane<S, -1, NC>(pl.src_at(12) + r0, g, x0, lane, inrow, t[3]);
-    ld_plane<S, 0, NC>(pl.src_at(13) + rp, g, x0, lane, inrow, t[4]);
-    if constexpr (TQ == 9) {
-        ld_plane<S, 1, NC>(pl.src_at(14) + rm, g, x0, lane, inrow, t[5]);
-        ld_plane<S, -1, NC>(pl.src_at(15) + rm, g, x0, lane, inrow, t[6]);
-        ld_plane<S, -1, NC>(pl.src_at(16) + rp, g, x0, lane, inrow, t[7]);
-        ld_plane<S, 1, NC>(pl.src_at(17) + rp, g, x0, lane, inrow, t[8]);
+    if constexpr (sizeof(S) == 2) {
+        // FP16: each shifted plane loads its own edge values (measured faster for 16-bit
+        // storage than the batched form below, which FP32 prefers)
+        ld_plane<S, 0, NC>(pl.src_at(0) + r0, g, x0, lane, inrow, f[0]);
+        ld_plane<S, 1, NC>(pl.src_at(1) + r0, g, x0, lane, inrow, f[1]);
+        ld_plane<S, 0, NC>(pl.src_at(2) + rm, g, x0, lane, inrow, f[2]);
+        ld_plane<S, -1, NC>(pl.src_at(3) + r0, g, x0, lane, inrow, f[3]);
+        ld_plane<S, 0, NC>(pl.src_at(4) + rp, g, x0, lane, inrow, f[4]);
+        ld_plane<S, 1, NC>(pl.src_at(5) + rm, g, x0, lane, inrow, f[5]);
+        ld_plane<S, -1, NC>(pl.src_at(6) + rm, g, x0, lane, inrow, f[6]);
+        ld_plane<S, -1, NC>(pl.src_at(7) + rp, g, x0, lane, inrow, f[7]);
+        ld_plane<S, 1, NC>(pl.src_at(8) + rp, g, x0, lane, inrow, f[8]);
+        ld_plane<S, 0, NC>(pl.src_at(9) + r0, g, x0, lane, inrow, t[0]);
+        ld_plane<S, 1, NC>(pl.src_at(10) + r0, g, x0, lane, inrow, t[1]);
+        ld_plane<S, 0, NC>(pl.src_at(11) + rm, g, x0, lane, inrow, t[2]);
+        ld_plane<S, -1, NC>(pl.src_at(12) + r0, g, x0, lane, inrow, t[3]);
+        ld_plane<S, 0, NC>(pl.src_at(13) + rp, g, x0, lane, inrow, t[4]);
+        if constexpr (TQ == 9) {
+            ld_plane<S, 1, NC>(pl.src_at(14) + rm, g, x0, lane, inrow, t[5]);
+            ld_plane<S, -1, NC>(pl.src_at(15) + rm, g, x0, lane, inrow, t[6]);
+            ld_plane<S, -1, NC>(pl.src_at(16) + rp, g, x0, lane, inrow, t[7]);
+            ld_plane<S, 1, NC>(pl.src_at(17) + rp, g, x0, lane, inrow, t[8]);
+        }
+    } else {
+        // Values from beyond the warp's 128 cells, for the planes shifted along x: lane 0's
+        // left neighbour (x0 - 1, wrapped on a periodic x), lane 31's right neighbour
+        // (x0 + 4) and, on a periodic x, cell 0 for the lane holding cell nx - 1. One branch
+        // per kind loads them for every shifted plane.
+        // e_x = +1 planes (source x - 1): f1, f5, f8, t1 (+ t5, t8); e_x = -1: f3, f6, f7, t3 (+ t6, t7)
+        constexpr int NE = TQ == 9 ? 6 : 4;
+        const S *lrow[6] = {pl.src_at(1) + r0, pl.src_at(5) + rm, pl.src_at(8) + rp, pl.src_at(10) + r0,
+                            pl.src_at(TQ == 9 ? 14 : 10) + rm, pl.src_at(TQ == 9 ? 17 : 10) + rp};
+        const S *rrow[6] = {pl.src_at(3) + r0, pl.src_at(6) + rm, pl.src_at(7) + rp, pl.src_at(12) + r0,
+                            pl.src_at(TQ == 9 ? 15 : 12) + rm, pl.src_at(TQ == 9 ? 16 : 12) + rp};
+        int xl = x0 - 1;
+        if (xl < 0 && g.px) xl += g.nx;
+        const int xr = x0 + 4;
+        const int kseam = g.nx - 1 - x0;
+        const int seam_k = (g.px && inrow && kseam >= 0 && kseam < 4) ? kseam : -1;
+        float el[NE], er[NE], es[NE];
+    #pragma unroll
+        for (int i = 0; i < NE; ++i) el[i] = er[i] = es[i] = 0.f;
+        if (lane == 0 && inrow && xl >= 0) {
+    #pragma unroll
+            for (int i = 0; i < NE; ++i) el[i] = Ld<S, NC>::one(lrow[i] + xl);
+        }
+        if (lane == 31 && inrow && xr < g.nx) {
+    #pragma unroll
+            for (int i = 0; i < NE; ++i) er[i] = Ld<S, NC>::one(rrow[i] + xr);
+        }
+        if (seam_k >= 0) {
+    #pragma unroll
+            for (int i = 0; i < NE; ++i) es[i] = Ld<S, NC>::one(rrow[i]);
+        }
+        float a[4];
+        ld_four<S, NC>(pl.src_at(0) + r0, x0, inrow, f[0]);
+        ld_four<S, NC>(pl.src_at(1) + r0, x0, inrow, a);
+        pull_from_left(a, el[0], lane, f[1]);
+        ld_four<S, NC>(pl.src_at(2) + rm, x0, inrow, f[2]);
+        ld_four<S, NC>(pl.src_at(3) + r0, x0, inrow, a);
+        pull_from_right(a, er[0], lane, seam_k, es[0], f[3]);
+        ld_four<S, NC>(pl.src_at(4) + rp, x0, inrow, f[4]);
+        ld_four<S, NC>(pl.src_at(5) + rm, x0, inrow, a);
+        pull_from_left(a, el[1], lane, f[5]);
+        ld_four<S, NC>(pl.src_at(6) + rm, x0, inrow, a);
+        pull_from_right(a, er[1], lane, seam_k, es[1], f[6]);
+        ld_four<S, NC>(pl.src_at(7) + rp, x0, inrow, a);
+        pull_from_right(a, er[2], lane, seam_k, es[2], f[7]);
+        ld_four<S, NC>(pl.src_at(8) + rp, x0, inrow, a);
+        pull_from_left(a, el[2], lane, f[8]);
+        ld_four<S, NC>(pl.src_at(9) + r0, x0, inrow, t[0]);
+        ld_four<S, NC>(pl.src_at(10) + r0, x0, inrow, a);
+        pull_from_left(a, el[3], lane, t[1]);
+        ld_four<S, NC>(pl.src_at(11) + rm, x0, inrow, t[2]);
+        ld_four<S, NC>(pl.src_at(12) + r0, x0, inrow, a);
+        pull_from_right(a, er[3], lane, seam_k, es[3], t[3]);
+        ld_four<S, NC>(pl.src_at(13) + rp, x0, inrow, t[4]);
+        if constexpr (TQ == 9) {
+            ld_four<S, NC>(pl.src_at(14) + rm, x0, inrow, a);
+            pull_from_left(a, el[4], lane, t[5]);
+            ld_four<S, NC>(pl.src_at(15) + rm, x0, inrow, a);
+            pull_from_right(a, er[4], lane, seam_k, es[4], t[6]);
+            ld_four<S, NC>(pl.src_at(16) + rp, x0, inrow, a);
+            pull_from_right(a, er[5], lane, seam_k, es[5], t[7]);
+            ld_four<S, NC>(pl.src_at(17) + rp, x0, inrow, a);
+            pull_from_left(a, el[5], lane, t[8]);
+        }
     }
     if (!any) return;
     if (m4 != 0u) {
