@@ -1127,6 +1127,33 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
     }
 }
 
+// ld_plane without the periodic seam (the caller applies it for all planes at once).
+template <typename S, int DX, bool NC = true>
+__device__ __forceinline__ void ld_plane_ns(const S *row, const Geom &g, int x0, int lane, bool inrow, float out[4]) {
+    float a[4] = {0.f, 0.f, 0.f, 0.f};
+    if (inrow) Ld<S, NC>::four(row + x0, a);
+    if (DX == 0) {
+        out[0] = a[0]; out[1] = a[1]; out[2] = a[2]; out[3] = a[3];
+    } else if (DX == 1) {
+        float left = __shfl_up_sync(kFull, a[3], 1);
+        if (lane == 0) {
+            left = 0.f;
+            int xs = x0 - 1;
+            if (xs < 0 && g.px) xs += g.nx;
+            if (inrow && xs >= 0) left = Ld<S, NC>::one(row + xs);
+        }
+        out[0] = left; out[1] = a[0]; out[2] = a[1]; out[3] = a[2];
+    } else {
+        float right = __shfl_down_sync(kFull, a[0], 1);
+        if (lane == 31) {
+            right = 0.f;
+            const int xs = x0 + 4;
+            if (inrow && xs < g.nx) right = Ld<S, NC>::one(row + xs);
+        }
+        out[0] = a[1]; out[1] = a[2]; out[2] = a[3]; out[3] = right;
+    }
+}
+
 // Four consecutive values of one population plane (x0..x0+3 of a row), zeros
 // where the lane lies past the row (`inrow` false: such a lane still takes part
 // in the shuffles that supply its neighbours).
@@ -1179,27 +1206,44 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
     const int rm = ym * g.pitch, rp = yp * g.pitch;
     float f[9][4], t[TQ][4];
     if constexpr (sizeof(S) == 2) {
-        // FP16: each shifted plane loads its own edge values (measured faster for 16-bit
-        // storage than the batched form below, which FP32 prefers)
+        // FP16: each shifted plane loads its own warp-edge values (measured faster for 16-bit
+        // storage than the batched form below, which FP32 prefers); the seam is batched
         ld_plane<S, 0, NC>(pl.src_at(0) + r0, g, x0, lane, inrow, f[0]);
         ld_plane<S, 1, NC>(pl.src_at(1) + r0, g, x0, lane, inrow, f[1]);
         ld_plane<S, 0, NC>(pl.src_at(2) + rm, g, x0, lane, inrow, f[2]);
-        ld_plane<S, -1, NC>(pl.src_at(3) + r0, g, x0, lane, inrow, f[3]);
+        ld_plane_ns<S, -1, NC>(pl.src_at(3) + r0, g, x0, lane, inrow, f[3]);
         ld_plane<S, 0, NC>(pl.src_at(4) + rp, g, x0, lane, inrow, f[4]);
         ld_plane<S, 1, NC>(pl.src_at(5) + rm, g, x0, lane, inrow, f[5]);
-        ld_plane<S, -1, NC>(pl.src_at(6) + rm, g, x0, lane, inrow, f[6]);
-        ld_plane<S, -1, NC>(pl.src_at(7) + rp, g, x0, lane, inrow, f[7]);
+        ld_plane_ns<S, -1, NC>(pl.src_at(6) + rm, g, x0, lane, inrow, f[6]);
+        ld_plane_ns<S, -1, NC>(pl.src_at(7) + rp, g, x0, lane, inrow, f[7]);
         ld_plane<S, 1, NC>(pl.src_at(8) + rp, g, x0, lane, inrow, f[8]);
         ld_plane<S, 0, NC>(pl.src_at(9) + r0, g, x0, lane, inrow, t[0]);
         ld_plane<S, 1, NC>(pl.src_at(10) + r0, g, x0, lane, inrow, t[1]);
         ld_plane<S, 0, NC>(pl.src_at(11) + rm, g, x0, lane, inrow, t[2]);
-        ld_plane<S, -1, NC>(pl.src_at(12) + r0, g, x0, lane, inrow, t[3]);
+        ld_plane_ns<S, -1, NC>(pl.src_at(12) + r0, g, x0, lane, inrow, t[3]);
         ld_plane<S, 0, NC>(pl.src_at(13) + rp, g, x0, lane, inrow, t[4]);
         if constexpr (TQ == 9) {
             ld_plane<S, 1, NC>(pl.src_at(14) + rm, g, x0, lane, inrow, t[5]);
-            ld_plane<S, -1, NC>(pl.src_at(15) + rm, g, x0, lane, inrow, t[6]);
-            ld_plane<S, -1, NC>(pl.src_at(16) + rp, g, x0, lane, inrow, t[7]);
+            ld_plane_ns<S, -1, NC>(pl.src_at(15) + rm, g, x0, lane, inrow, t[6]);
+            ld_plane_ns<S, -1, NC>(pl.src_at(16) + rp, g, x0, lane, inrow, t[7]);
             ld_plane<S, 1, NC>(pl.src_at(17) + rp, g, x0, lane, inrow, t[8]);
+        }
+        {
+            // periodic x: the lane holding cell nx - 1 takes cell 0's value of each plane
+            // with e_x = -1, in one branch for all of them
+            const int kseam = g.nx - 1 - x0;
+            if (g.px && inrow && kseam >= 0 && kseam < 4) {
+#define NOMRT_SEAM(P, ROW) { const float v = Ld<S, NC>::one(ROW); _Pragma("unroll") for (int j = 0; j < 4; ++j) P[j] = (j == kseam) ? v : P[j]; }
+                NOMRT_SEAM(f[3], pl.src_at(3) + r0);
+                NOMRT_SEAM(f[6], pl.src_at(6) + rm);
+                NOMRT_SEAM(f[7], pl.src_at(7) + rp);
+                NOMRT_SEAM(t[3], pl.src_at(12) + r0);
+                if constexpr (TQ == 9) {
+                    NOMRT_SEAM(t[6], pl.src_at(15) + rm);
+                    NOMRT_SEAM(t[7], pl.src_at(16) + rp);
+                }
+#undef NOMRT_SEAM
+            }
         }
     } else {
         // Values from beyond the warp's 128 cells, for the planes shifted along x: lane 0's
