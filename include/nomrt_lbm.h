@@ -161,7 +161,8 @@ lbm_status lbm_sync(lbm_lattice *h);
 /* Step kernel variants. All compute the same arithmetic and give the same
  * bits for a given storage. AUTO picks the fastest measured on GB300: the
  * scalar kernel for FP64; VEC4 for FP32 / FP16 with config 1 / 3 (MRT, D2Q5),
- * 1 / 1 (BGK, D2Q5) or 0 / 0 (the D2Q9 temperature model). The FP16 VEC4
+ * 1 / 1 (BGK, D2Q5), 0 / 1 (MRT, D2Q9 temperature model) or 0 / 0 (BGK, D2Q9
+ * temperature model). The FP16 VEC4
  * kernel also asks L2 to prefetch the population segments 16 rows ahead.
  * SCALAR: one cell per thread. VEC4: four cells per thread with 128-bit (FP32)
  * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls; configs 0-4 ask

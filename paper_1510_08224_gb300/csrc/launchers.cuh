@@ -136,8 +136,8 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
             variant = kStepVec4;
             // VEC4 configs measured fastest on GB300 (4096 x 2048 cells): MRT D2Q5 5 (FP32) or
             // 7 (FP16) blocks per SM; BGK D2Q5 5 for both; the D2Q9 temperature model, which
-            // keeps nine more values per cell in registers, 4
-            if (p.tq == 9) q.config = 0;
+            // keeps nine more values per cell in registers, 4 (5 for MRT in FP16)
+            if (p.tq == 9) q.config = (sizeof(S) == 2 && !p.bgk) ? 1 : 0;
             else if (p.bgk) q.config = 1;
             else q.config = sizeof(S) == 4 ? 1 : 3;
         }
