@@ -243,25 +243,58 @@ lbm_status lbm_info(const lbm_lattice *h, int64_t *fluid_cells, int32_t *pitch, 
  * array (about 164 KB, held on every GPU that loads the library until the
  * process exits); n above 16,777,216 cells is rejected with LBM_EINVAL. All
  * calls share that array: calls whose kernels overlap on the GPU race.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture. Runs on cuda_stream (NULL = legacy default stream) with
- * the caller's current device, and synchronises that stream. LBM_EDIVERGED
- * (and *r = NaN) if a value is not finite. Errors: lbm_last_error(NULL). */
+ * Set-up: the first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current and caches it with the id of
+ * the device's current CUDA context; a call made in another context of that
+ * device (after cudaDeviceReset or a primary-context reset) looks it up again.
+ * Runs on cuda_stream (NULL = legacy default stream) with the caller's current
+ * device, copies the five sums back and synchronises that stream, so it must
+ * never be called on a stream that is being captured: such a call returns
+ * LBM_EINVAL without touching the stream. LBM_EDIVERGED (and *r = NaN) if a
+ * value is not finite. Errors: lbm_last_error(NULL). */
 lbm_status lbm_residual_fields_noalloc(const double *ux, const double *uy, const double *T, const double *ux_prev,
                                        const double *uy_prev, const double *T_prev, const uint8_t *solid,
                                        int64_t n, void *cuda_stream, double *r);
 
+/* Index checking. A library built with -DLBM_BOUNDS (the bounds-checking
+ * build, _build/libnomrt_lbm_bounds.so) tests every population, link-map,
+ * flag and wall-table access of the step kernels (every variant, the
+ * boundary-node pass and the batch kernels) before making it: it must lie in
+ * the lattice's device block, and a vector access must be aligned to its size.
+ * A refused access is skipped, never made, and the first refusal's site id is
+ * recorded; the next synchronising call on the lattice (lbm_sync, the
+ * read-outs, lbm_batch_sync for members) returns LBM_ECUDA naming the site.
+ * lbm_bounds_checking returns 1 in that build and 0 in the normal build, whose
+ * checks compile to nothing. Host only. */
+int32_t lbm_bounds_checking(void);
+
+/* Test hook of the bounds-checking build: the checks of h accept only the
+ * first `bytes` bytes of its device block from now on (0 <= bytes <=
+ * lbm_footprint_bytes), so accesses beyond them are refused and reported as
+ * above; no access outside the block is ever made. LBM_EINVAL in the normal
+ * build. */
+lbm_status lbm_debug_bounds_limit(lbm_lattice *h, int64_t bytes);
+
+/* Measurement helper with no counterpart in the paper: the current device's
+ * FP64 fused multiply-add rate in instructions per second (2 flops each),
+ * from a kernel of independent DFMA chains on eight 256-thread blocks per SM,
+ * best of five CUDA-event timed launches on cuda_stream (NULL = legacy default
+ * stream). The FP64-storage step kernel is bound by this rate (its FP64
+ * instructions per cell), not by HBM. Synchronises the stream. */
+lbm_status lbm_probe_fp64_rate(void *cuda_stream, double *dfma_per_s);
+
 /* ---------------------------------------------------------------- batches --
- * Many lattices of uneven size advanced together: one kernel launch steps
- * every member (warp-sized work units of one lattice row segment each, read
- * from a device work list with a per-lattice descriptor). The method is the
- * same as lbm_step's and a batched lattice produces the same bits as when
- * stepped alone. Members must be FP32 or FP16 storage (one storage per batch)
- * and bound to the batch's stream; while batched, lbm_step on a member is
- * rejected, but every other lattice call (read-outs, Nusselt, residual,
- * populations) works and sees the batch's progress. The batch allocates its
- * own small device buffers (descriptors, work list) with cudaMalloc. */
+ * Many lattices of uneven size advanced together (NEXT step of the method's
+ * deployment, not in the paper: the method is the same as lbm_step's, Eqs. 8-9
+ * and 24-25, and a batched lattice produces the same bits as when stepped
+ * alone). Members must be FP32 or FP16 storage (one storage per batch), MRT
+ * with the D2Q5 temperature lattice, and bound to the batch's stream; while
+ * batched, lbm_step on a member is rejected, but every other lattice call
+ * (read-outs, Nusselt, residual, populations) works and sees the batch's
+ * progress. Members are gathered into launch groups of up to 64 lattices
+ * whose kinetic rates (s_e, s_q, s_eps, zeta_e, zeta_nu, varpi) agree; a
+ * group's descriptors travel in the launch's parameter block. The batch
+ * allocates two small device words (grid barrier, status) with cudaMalloc. */
 typedef struct lbm_batch lbm_batch;
 
 /* cuda_stream: the stream every member uses (NULL = legacy default stream). */
@@ -273,47 +306,56 @@ lbm_status lbm_batch_create(void *cuda_stream, lbm_batch **out);
 lbm_status lbm_batch_add(lbm_batch *b, lbm_lattice *h);
 lbm_status lbm_batch_remove(lbm_batch *b, lbm_lattice *h);
 
-/* Execution mode. steps_per_launch = 1: one launch per step. k > 1: one
- * cooperative persistent launch per k steps, with a clock-bounded grid
- * barrier between steps (LBM_ETIMEOUT from lbm_batch_sync if it expires).
- * graph_steps > 0 (even): steps are replayed from a captured CUDA graph of
- * that many steps; 0 disables graphs. Defaults: 1 and 32. */
-lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t graph_steps);
-
-/* How a batch step runs. FUSED: one kernel launch per step over every member
- * (per 64 members), whose grid covers the members' concatenated rows with
- * the four-cell kernel's blocks, the members' descriptors in the launch's parameter space (the
- * default); with steps_per_launch > 1, a cooperative persistent kernel over a
- * work list of row segments instead. CONCURRENT: each member's own single-lattice step
- * kernel (its lbm_set_step_kernel choice), the members on separate streams
- * between a fork and a join, so their kernels run side by side; with
- * graph_steps > 0 the whole fork/join is one captured graph. */
-typedef enum { LBM_BATCH_FUSED = 0, LBM_BATCH_CONCURRENT = 1 } lbm_batch_kind;
+/* How a batch step runs.
+ * FUSED (the default): one kernel launch per step and launch group, whose 2-D
+ * grid covers the members' concatenated rows with the four-cell kernel's
+ * 128-thread blocks (one 512-cell row segment each).
+ * PERSISTENT: one cooperative launch per group for steps_per_launch steps: its
+ * resident blocks stride over the same row segments, with a clock-bounded grid
+ * barrier between steps (LBM_ETIMEOUT from lbm_batch_sync if one expires). A
+ * batch holding a lattice with node-based walls runs FUSED, whose boundary-node
+ * pass goes between steps.
+ * CONCURRENT: each member's own single-lattice step kernel (its
+ * lbm_set_step_kernel choice), the members on separate streams between a fork
+ * and a join, so their kernels run side by side. */
+typedef enum { LBM_BATCH_FUSED = 0, LBM_BATCH_CONCURRENT = 1, LBM_BATCH_PERSISTENT = 2 } lbm_batch_kind;
 lbm_status lbm_batch_set_kind(lbm_batch *b, int32_t kind);
 
-/* Kernel shape: config 0..4 asks for 4..8 resident 128-thread blocks per SM
- * of the per-step FUSED kernel (-1: the default, 1 for FP32 and 3 for FP16;
- * the persistent kernel always takes 4 blocks per SM); rows_per_unit (1..1024) is the
- * number of consecutive rows of one 128-cell segment a warp of the persistent
- * kernel takes per work unit (default 1). */
+/* Execution mode. steps_per_launch (>= 1): steps per launch of the PERSISTENT
+ * kind (default 32). graph_steps > 0 (even): steps are replayed from a CUDA
+ * graph of that many steps, captured once per membership and mode; 0 launches
+ * from the host. Default 32: with both at 32, a PERSISTENT batch replays one
+ * persistent launch per graph. */
+lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t graph_steps);
+
+/* The kind, steps per launch and graph steps in force. Any pointer may be NULL. */
+lbm_status lbm_batch_get_mode(const lbm_batch *b, int32_t *kind, int32_t *steps_per_launch, int32_t *graph_steps);
+
+/* Kernel shape of the FUSED and PERSISTENT kinds: config 0..4 asks ptxas for
+ * 4..8 resident 128-thread blocks per SM (-1: the default, 1 for FP32 and 3 for
+ * FP16); rows_per_unit (1..1024): consecutive row segments (512 cells each, in
+ * row order) a block of the persistent kernel takes per work unit (default 1). */
 lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_unit);
 
-/* Autotuner: for each config of the FUSED per-step kernel, and for the
- * CONCURRENT kind, times trial_launches steps on the current members (each
- * trial recomputes the current step into the other buffer, so the state is
- * unchanged), selects the fastest kind and config, and returns the FUSED
- * config in *best_config (-2 if CONCURRENT won), the unchanged rows_per_unit
- * in *best_rows, and the mean ms per step of every candidate in
- * ms_per_launch[6] (5 FUSED configs, then CONCURRENT). Any output may be NULL.
- * Synchronises. */
-lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_config, int32_t *best_rows,
-                          float *ms_per_launch);
+/* Autotuner: times trial_steps (>= 2) steps of every candidate on the current
+ * members -- the FUSED kernel at configs 0-4, the PERSISTENT kernel at configs
+ * 0-4 (steps_per_launch steps per launch, 32 if it is 1), and the CONCURRENT
+ * kind -- each trial recomputing the current step into the other buffer, so the
+ * state is unchanged; selects the fastest (kind, config; the PERSISTENT kind
+ * also keeps the trial's steps per launch), and returns the kind in
+ * *best_kind, the config in *best_config (-1 for CONCURRENT) and the mean ms
+ * per step of every candidate in ms_per_step[11] (FUSED 0-4, PERSISTENT 0-4,
+ * CONCURRENT; +inf for a candidate that cannot run, such as PERSISTENT with
+ * node-based walls). Any output may be NULL. Synchronises. */
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind, int32_t *best_config,
+                          float *ms_per_step);
 
 /* Advance every member by nsteps (asynchronous on the batch's stream). */
 lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps);
 
 /* Wait for the batch's stream; LBM_ETIMEOUT if a persistent launch gave up a
- * grid barrier (the members' state is then undefined). */
+ * grid barrier (the members' state is then undefined; later persistent
+ * launches return at once until this call clears the status). */
 lbm_status lbm_batch_sync(lbm_batch *b);
 
 /* Test hook for the timeout path. With extra = 1 the persistent kernel's grid
@@ -324,9 +366,21 @@ lbm_status lbm_batch_sync(lbm_batch *b);
  * extra = 0 restores normal operation. LBM_EINVAL for other values. */
 lbm_status lbm_batch_debug_barrier_extra(lbm_batch *b, int32_t extra);
 
-/* Members, their fluid cells, work units, active config (-2 for the
- * CONCURRENT kind) and rows per unit, batch steps taken. Any pointer may be
- * NULL. */
+/* The steady-state residual of every member (lbm_residual's R, against and
+ * then replacing each member's own snapshot; +infinity at a member's first
+ * call), with one synchronisation for the whole batch: the members' residual
+ * kernels run on the batch's stream, their sums land side by side and come
+ * back in one copy. members[i] (may be NULL) and r[i] for i < *n, in the
+ * batch's member order; cap: the capacity of both arrays (LBM_EINVAL if
+ * below the member count, *n still set). A member whose fields are not finite
+ * gets r[i] = NaN (lbm_residual would return LBM_EDIVERGED for it). The batch
+ * allocates its device and pinned host buffers for the sums (cudaMalloc,
+ * cudaHostAlloc) when it first needs them. Synchronises. */
+lbm_status lbm_batch_residuals(lbm_batch *b, int32_t cap, lbm_lattice **members, double *r, int32_t *n);
+
+/* Members, their fluid cells, 512-cell row segments per step (summed over the
+ * launch groups), config in force (-1 for the CONCURRENT kind), rows per unit,
+ * batch steps taken. Any pointer may be NULL. */
 lbm_status lbm_batch_info(const lbm_batch *b, int32_t *members, int64_t *cells, int32_t *units, int32_t *config,
                           int32_t *rows_per_unit, int64_t *steps_done);
 

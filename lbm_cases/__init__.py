@@ -310,11 +310,13 @@ def batched_cavities(count: int = 64, side_lo: int = 128, side_hi: int = 1024, r
 
 
 def serving_stream(n: int = 40, rate: float = 20.0, seed: int = 0, side_lo: int = 64, side_hi: int = 2048,
-                   ra_lo: float = 1e3, ra_hi: float = 1e6, Pr: float = 0.71, Ma: float = 0.1):
+                   ra_lo: float = 1e3, ra_hi: float = 1e6, Pr: float = 0.71, Ma: float = 0.1,
+                   cavity_share: float = 0.5, rb_ra=None):
     """n requests with Poisson arrivals (exponential gaps of mean 1/rate from
-    SplitMix64(seed)); each is a cavity (side s) or a Rayleigh-Benard cell
-    (s x s/2, periodic in x) with equal odds, s log-uniform over
-    [side_lo, side_hi], Ra log-uniform over [ra_lo, ra_hi].
+    SplitMix64(seed)); each is a cavity (side s) with probability
+    cavity_share, else a Rayleigh-Benard cell (s x s/2, periodic in x), s
+    log-uniform over [side_lo, side_hi], Ra log-uniform over [ra_lo, ra_hi]
+    (for the Rayleigh-Benard cells over rb_ra = (lo, hi) instead, if given).
     Returns [(arrival seconds, kind, case)]."""
     u = uniform01(seed, 4 * n)
     gaps = -np.log(1.0 - u[0::4]) / rate
@@ -324,11 +326,14 @@ def serving_stream(n: int = 40, rate: float = 20.0, seed: int = 0, side_lo: int 
     out = []
     for k in range(n):
         s = max(8, int(round(sides[k])))
-        if u[4 * k + 3] < 0.5:
+        if u[4 * k + 3] < cavity_share:
             case = cavity(n=s, Ra=float(ras[k]), Pr=Pr, Ma=Ma, seed=seed + 100 + k)
             kind = "cavity"
         else:
-            case = rayleigh_benard(nx=s, H=max(4, s // 2), Ra=float(ras[k]), Pr=Pr, Ma=Ma, seed=seed + 100 + k)
+            ra = float(ras[k])
+            if rb_ra is not None:  # the same uniform draw, mapped onto the Rayleigh-Benard range
+                ra = float(np.exp(np.log(rb_ra[0]) + u[4 * k + 2] * (np.log(rb_ra[1]) - np.log(rb_ra[0]))))
+            case = rayleigh_benard(nx=s, H=max(4, s // 2), Ra=ra, Pr=Pr, Ma=Ma, seed=seed + 100 + k)
             kind = "rayleigh_benard"
         out.append((float(arrivals[k]), kind, case))
     return out

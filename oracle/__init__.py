@@ -107,6 +107,9 @@ def lib():
             L.orc_threads_available.restype = C.c_int
             L.orc_thermal_q.restype = C.c_int
             L.orc_thermal_q.argtypes = [C.c_void_p]
+            L.orc_round_binary16.restype = C.c_double
+            L.orc_round_binary16.argtypes = [C.c_double]
+            L.orc_set_storage_rounding.argtypes = [C.c_void_p, C.c_int, C.c_double]
             _lib = L
     return _lib
 
@@ -220,6 +223,15 @@ class OracleLattice:
     def step(self, n: int = 1):
         lib().orc_step(self._h, int(n))
 
+    def set_storage_rounding(self, bits: int = 16, scale: float = 1.0):
+        """Ablation, not the method: after every step, round each population's
+        deviation from the rest state (f_bar_i - w_i rho0, g_i - w^T_i T0),
+        multiplied by ``scale``, to binary16 (and divide back), as a solver
+        storing that deviation in 16 bits would; bits = 0 turns it off. It
+        measures the cost of the storage precision alone, the arithmetic
+        staying FP64."""
+        lib().orc_set_storage_rounding(self._h, int(bits), float(scale))
+
     def macro(self):
         """(rho, ux, uy, T), each (ny, nx), per reading A6; zeros on solid cells."""
         out = [np.zeros((self.ny, self.nx)) for _ in range(4)]
@@ -258,6 +270,12 @@ class OracleLattice:
 
 def threads_available() -> int:
     return lib().orc_threads_available()
+
+
+def round_binary16(x: float) -> float:
+    """x rounded to the nearest IEEE 754 binary16 value (ties to even),
+    returned as a double."""
+    return lib().orc_round_binary16(float(x))
 
 
 def relative_global_error(num, exact) -> float:

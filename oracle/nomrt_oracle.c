@@ -178,6 +178,8 @@ typedef struct {
     double *snap; /* residual snapshot [3][ny*nx], NULL until first call */
     int nthreads;
     double nee_half; /* the F/2 factor of u_f in nee_gather: 0.5 (Eq. 19), or 0 / -0.5 (ablations) */
+    int store_bits;     /* ablation: 16 rounds every stored deviation to binary16 after each step; 0 none */
+    double store_scale; /* the deviation is multiplied by this before the rounding and divided after */
 } orc_lattice;
 
 /* ------------------------------------------------------------- collision -- */
@@ -557,6 +559,37 @@ void orc_destroy(orc_lattice *L) {
 
 void orc_set_threads(orc_lattice *L, int n) { L->nthreads = n < 1 ? 1 : n; }
 
+/* x rounded to the nearest IEEE 754 binary16 value (1 sign, 5 exponent, 10
+ * fraction bits; ties to even; subnormals below 2^-14 in steps of 2^-24;
+ * magnitudes above the largest finite value 65504 become infinite). */
+double orc_round_binary16(double x) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    const double a = fabs(x);
+    int e;
+    frexp(a, &e);                       /* a = m 2^e, m in [0.5, 1): binade [2^(e-1), 2^e) */
+    const int E = e - 1;
+    const double q = E < -14 ? ldexp(1.0, -24) : ldexp(1.0, E - 10);  /* spacing of binary16 there */
+    double r = nearbyint(a / q) * q;    /* a / q is exact; the default mode rounds ties to even */
+    if (r > 65504.0) r = INFINITY;
+    return copysign(r, x);
+}
+
+/* Ablation (not part of the method): after every step, round the stored
+ * deviation of each population from the rest state (f_bar_i - w_i rho0 and
+ * g_i - w^T_i T0, the quantities a 16-bit storage of the state keeps) to
+ * binary16 after multiplying it by `scale` (and divide back), as a
+ * 16-bit-storage solver would; bits = 0 turns it off. For measuring what the
+ * storage precision alone costs, in FP64 arithmetic otherwise. */
+void orc_set_storage_rounding(orc_lattice *L, int bits, double scale) {
+    L->store_bits = bits == 16 ? 16 : 0;
+    L->store_scale = scale > 0.0 ? scale : 1.0;
+}
+
+static double stored(const orc_lattice *L, double v, double rest) {
+    if (!L->store_bits) return v;
+    return rest + orc_round_binary16((v - rest) * L->store_scale) / L->store_scale;
+}
+
 /* One time step (Eqs. 8-9, 24-25) for every fluid node, pull form. */
 void orc_step(orc_lattice *L, int64_t nsteps) {
     const int nxy = L->nx * L->ny;
@@ -573,8 +606,8 @@ void orc_step(orc_lattice *L, int64_t nsteps) {
                 double fin[9], gin[9], fo[9], go[9];
                 pre_collision(L, fs, gs, x, y, fin, gin);
                 orc_collide_node(&L->r, fin, gin, fo, go, NULL);
-                for (int i = 0; i < 9; ++i) fd[i * nxy + c] = fo[i];
-                for (int i = 0; i < L->tq; ++i) gd[i * nxy + c] = go[i];
+                for (int i = 0; i < 9; ++i) fd[i * nxy + c] = stored(L, fo[i], W9[i] * RHO0);
+                for (int i = 0; i < L->tq; ++i) gd[i * nxy + c] = stored(L, go[i], geq_i(L, i, L->r.T0, 0.0, 0.0));
             }
         }
         L->cur = 1 - L->cur;

@@ -5,8 +5,8 @@ arXiv:1510.08224).
 The hot path is one fused CUDA kernel per time step (sm_103a) behind the C ABI
 of ``include/nomrt_lbm.h``; :mod:`.lbm` is its ctypes binding.
 """
-from .lbm import (EXPORTED, Batch, LBMError, Lattice, STORAGE, STORAGE_BYTES, SIDES, STEP_VARIANTS, load, make_params,
-                  lbm_footprint_bytes, library_path, residual_fields_noalloc, step_kernel_count, step_kernels)
+from .lbm import (BATCH_KINDS, EXPORTED, Batch, LBMError, Lattice, STORAGE, STORAGE_BYTES, SIDES, STEP_VARIANTS, load, make_params,
+                  lbm_footprint_bytes, library_path, probe_fp64_rate, residual_fields_noalloc, step_kernel_count, step_kernels)
 
-__all__ = ["EXPORTED", "Batch", "LBMError", "Lattice", "STORAGE", "STORAGE_BYTES", "SIDES", "STEP_VARIANTS", "load", "make_params",
-           "lbm_footprint_bytes", "library_path"]
+__all__ = ["BATCH_KINDS", "EXPORTED", "Batch", "LBMError", "Lattice", "STORAGE", "STORAGE_BYTES", "SIDES", "STEP_VARIANTS", "load", "make_params",
+           "lbm_footprint_bytes", "library_path", "probe_fp64_rate", "residual_fields_noalloc", "step_kernel_count", "step_kernels"]

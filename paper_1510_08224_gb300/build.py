@@ -1,8 +1,12 @@
-"""Build the in-tree CUDA library ``_build/libnomrt_lbm.so`` for sm_103a.
+"""Build the in-tree CUDA libraries for sm_103a.
 
-Plain nvcc, one ``-gencode``, the translation units compiled in parallel and
-linked into one shared library with the CUDA runtime linked statically. No
-cmake. Rebuilds only when a source is newer than the library.
+``_build/libnomrt_lbm.so`` is the library; ``_build/libnomrt_lbm_bounds.so``
+is the same sources compiled with ``-DLBM_BOUNDS``, the bounds-checking build
+whose step kernels test every access against the lattice's device block
+(include/nomrt_lbm.h, lbm_bounds_checking). Plain nvcc, one ``-gencode``,
+every translation unit of both libraries compiled in parallel and linked with
+the CUDA runtime linked statically. No cmake. Rebuilds only what is older
+than its sources.
 """
 from __future__ import annotations
 
@@ -17,7 +21,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
-LIB = os.path.join(BUILD, "libnomrt_lbm.so")
+
+# library variant -> (file name, extra nvcc flags)
+VARIANTS = {"": ("libnomrt_lbm.so", []), "bounds": ("libnomrt_lbm_bounds.so", ["-DLBM_BOUNDS"])}
+LIB = os.path.join(BUILD, VARIANTS[""][0])
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -40,39 +47,53 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+def library_path(variant: str = "") -> str:
+    return os.path.join(BUILD, VARIANTS[variant][0])
+
+
+def is_stale(variant: str = "") -> bool:
+    lib = library_path(variant)
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not is_stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
-    nvcc = _nvcc()
-    objs = []
+def build(force: bool = False, verbose: bool = False, variants=("", "bounds")) -> str:
+    """Compile the stale (or, with force, all) requested variants; returns the
+    path of the first one."""
+    todo = [v for v in variants if force or is_stale(v)]
+    if todo:
+        nvcc = _nvcc()
+        jobs = []
+        for v in todo:
+            os.makedirs(os.path.join(BUILD, v or "main"), exist_ok=True)
+            jobs += [(v, src) for src in sources()]
 
-    def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [nvcc] + NVCC_FLAGS + ["-c", src, "-o", obj]
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        if r.returncode != 0:
-            raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
-        if verbose and (r.stdout or r.stderr):
-            print(r.stdout, r.stderr)
-        return obj
+        def compile_one(job):
+            v, src = job
+            obj = os.path.join(BUILD, v or "main", os.path.basename(src)[:-3] + ".o")
+            cmd = [nvcc] + NVCC_FLAGS + VARIANTS[v][1] + ["-c", src, "-o", obj]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc failed on {src} ({v or 'main'} build):\n{r.stdout}\n{r.stderr}")
+            if verbose and (r.stdout or r.stderr):
+                print(r.stdout, r.stderr)
+            return v, obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(8, len(sources()))) as ex:
-        objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+        workers = max(1, min(16, os.cpu_count() or 1, len(jobs)))
+        with cf.ThreadPoolExecutor(max_workers=workers) as ex:
+            done = list(ex.map(compile_one, jobs))
+        for v in todo:
+            objs = [o for w, o in done if w == v]
+            lib = library_path(v)
+            tmp = lib + f".tmp{os.getpid()}"
+            cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-cudart", "static"]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc link failed ({v or 'main'} build):\n{r.stdout}\n{r.stderr}")
+            os.replace(tmp, lib)
+    return library_path(variants[0])
 
 
 if __name__ == "__main__":

@@ -376,15 +376,23 @@ lbm_status cuda_fail(lbm_lattice *h, cudaError_t e, const char *what) {
     } while (0)
 
 // After a stream synchronisation: a kernel that gave up a bounded wait left a
-// non-zero status word; report it once and clear it.
+// non-zero status word, or (bounds-checking build) a refused access left a
+// non-zero bounds word; report it once and clear both.
 lbm_status check_status(lbm_lattice *h) {
-    int st = 0;
-    cudaError_t e = cudaMemcpy(&st, h->kp.status, sizeof st, cudaMemcpyDeviceToHost);
+    int st[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(st, h->kp.status, sizeof st, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "read status");
-    if (st == nomrt::kStatusOk) return LBM_OK;
-    const int zero = 0;
-    e = cudaMemcpy(h->kp.status, &zero, sizeof zero, cudaMemcpyHostToDevice);
+    if (st[0] == nomrt::kStatusOk && st[1] == 0) return LBM_OK;
+    const int zero[2] = {0, 0};
+    e = cudaMemcpy(h->kp.status, zero, sizeof zero, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(h, e, "clear status");
+    if (st[1] != 0) {
+        char buf[160];
+        snprintf(buf, sizeof buf,
+                 "bounds-checking build: an index check failed at site %d (the access was skipped; the state is "
+                 "invalid)", st[1]);
+        return fail(h, LBM_ECUDA, buf);
+    }
     return fail(h, LBM_ETIMEOUT, "a kernel gave up a bounded wait (device status word set)");
 }
 
@@ -587,6 +595,9 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     kp.variant = nomrt::kStepAuto;
     kp.config = 0;
     kp.status = reinterpret_cast<int *>(h->mem + h->lay.off_status);
+    kp.oob = kp.status + 1;  // the status slot holds 256 bytes
+    kp.blk_lo = h->mem;
+    kp.blk_hi = h->mem + need;
 
     cudaStream_t st = h->stream;
     auto cuda_bail = [&](cudaError_t e, const char *what) {
@@ -834,6 +845,19 @@ lbm_status lbm_set_populations(lbm_lattice *h, const double *f9, const double *g
     }
     // one wait: the caller's arrays stay in use until the last copy has left them
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "import sync");
+    return LBM_OK;
+}
+
+int32_t lbm_bounds_checking(void) { return nomrt::kBoundsBuild ? 1 : 0; }
+
+lbm_status lbm_debug_bounds_limit(lbm_lattice *h, int64_t bytes) {
+    if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
+    if (!nomrt::kBoundsBuild) return fail(h, LBM_EINVAL, "not a bounds-checking build");
+    if (bytes < 0 || (uint64_t)bytes > (uint64_t)h->lay.total)
+        return fail(h, LBM_EINVAL, "bytes must lie in 0..lbm_footprint_bytes");
+    h->kp.blk_hi = h->mem + bytes;
+    drop_graph(h);  // a captured graph holds the old range
+    h->direct_done = false;
     return LBM_OK;
 }
 

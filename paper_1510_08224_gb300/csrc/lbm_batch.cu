@@ -1,19 +1,26 @@
 // Batched execution of many lattices of uneven size (FP32 or FP16-shifted
-// storage): one kernel launch advances every member lattice by one time step
-// (or, in persistent mode, by k steps with a grid barrier between them).
+// storage): every member lattice advances by one time step per launch of the
+// per-step kernel, or by k steps per launch of the persistent kernel, with a
+// grid barrier between its steps.
 //
-// Per-step launch: the descriptors of up to kGroupLats members (buffers,
-// geometry, rates) travel as one large kernel parameter, so they sit in the
-// constant bank exactly as a single-lattice kernel's parameters do. The grid
-// is the concatenation of every member's own VEC4 grid (one 128-thread block
-// per 512-cell segment of a row); a block finds its member by a binary search
-// over the members' first block indices and runs the single-lattice row code,
-// so a lattice stepped in a batch produces the same bits as when stepped alone,
-// and the members' partial last waves fill each other.
+// Launch groups: up to kGroupLats members whose kinetic rates (s_e, s_q,
+// s_eps, zeta_e, zeta_nu, varpi) agree travel in one launch. Their
+// descriptors (buffers, geometry, and the eleven collision values that follow
+// from each member's own nu, alpha, g beta, T0 and body force) and the
+// group's shared rates form one __grid_constant__ kernel parameter. The
+// shared rates sit at fixed offsets of the parameter bank, so the collision
+// reads them as constant-bank operands exactly as the single-lattice kernel
+// does; only the member-specific values become registers, once per row.
 //
-// Persistent launch: a work list of units (lattice, first row, 128-cell
-// segment, row count) with the descriptors in device memory; a grid of
-// resident CTAs strides over the units, steps separated by a grid barrier.
+// Work: every member's rows cut into 512-cell segments (the four-cell
+// kernel's 128-thread block shape): one virtual block per (member, row,
+// segment), numbered member by member, row by row, with no block beyond a
+// member's own width. A block finds its member by a binary search over the
+// members' first virtual blocks, reads the member's descriptor and runs the
+// single-lattice row code, so a lattice stepped in a batch produces the same
+// bits as when stepped alone. The per-step kernel gives each virtual block a
+// block of a 1-D grid; the persistent kernel's resident blocks take runs of
+// rows_per_unit consecutive virtual blocks, step after step.
 //
 // Ping-pong: member l reads buffer (s + flip_l) & 1 at batch step s, where
 // flip_l is fixed when the lattice joins, so lattices that joined at different
@@ -21,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -32,92 +40,118 @@
 
 namespace nomrt {
 
-constexpr int kBatchWarps = 4;  // warps (units) per CTA
-constexpr int kBatchThreads = 32 * kBatchWarps;
+constexpr int kBatchThreads = 128;
 constexpr int kBatchConfigs = 5;  // resident blocks asked of ptxas: 4 + config
-constexpr int kGroupLats = 64;    // members per per-step launch (parameter space holds their descriptors)
+constexpr int kGroupLats = 64;    // members per launch (the parameter block holds their descriptors)
 constexpr long long kBarrierBudgetCycles = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int kDefaultPersistentSteps = 32;
 
-struct __align__(16) BatchLat {
-    const void *pop0;
-    const void *pop1;
-    long long plane;
-    const uint8_t *mask;
-    const uint8_t *flags;
-    const WallDev *walls;
-    int nx, ny, pitch, px, py, flip;
-    RatesC<float> r;
+// The collision values that follow from one lattice's nu, alpha, g beta, T0
+// and body force; the rest of RatesC<float> is shared by a launch group.
+struct MemberRates {
+    float s_nu, om_nu, h_nu, h2nu, om_a, z_a, ax, hx, Fy0, g_beta, T_ref;
 };
 
-template <typename S, bool NC>
-__device__ __forceinline__ void batch_unit(const BatchLat *lats, const int4 u, int parity, int lane) {
-    // u = (lattice, first row, segment start, rows)
-    const BatchLat *L = lats + u.x;
-    Geom g;
-    g.nx = L->nx;
-    g.ny = L->ny;
-    g.pitch = L->pitch;
-    g.px = L->px;
-    g.py = L->py;
-    g.mask = L->mask;
-    g.flags = L->flags;
-    g.walls = L->walls;
-    const int sel = (parity + L->flip) & 1;
-    StridedPlanes<S> pa;
-    pa.src = static_cast<const S *>(sel ? L->pop1 : L->pop0);
-    pa.dst = static_cast<S *>(const_cast<void *>(sel ? L->pop0 : L->pop1));
-    pa.plane = L->plane;
-    const RatesC<float> r = L->r;
-    for (int k = 0; k < u.w; ++k) row4<S, StridedPlanes<S>, NC>(pa, g, r, u.z + 4 * lane, u.y + k, lane);
+inline MemberRates member_rates(const RatesC<float> &r) {
+    return MemberRates{r.s_nu, r.om_nu, r.h_nu, r.h2nu, r.om_a, r.z_a, r.ax, r.hx, r.Fy0, r.g_beta, r.T_ref};
 }
 
-// One member's descriptor in the per-step launch's parameter.
+__host__ __device__ __forceinline__ void apply_member(RatesC<float> &r, const MemberRates &v) {
+    r.s_nu = v.s_nu;
+    r.om_nu = v.om_nu;
+    r.h_nu = v.h_nu;
+    r.h2nu = v.h2nu;
+    r.om_a = v.om_a;
+    r.z_a = v.z_a;
+    r.ax = v.ax;
+    r.hx = v.hx;
+    r.Fy0 = v.Fy0;
+    r.g_beta = v.g_beta;
+    r.T_ref = v.T_ref;
+}
+
+// Whether two lattices' rates agree outside their member-specific values.
+inline bool same_shared_rates(RatesC<float> a, RatesC<float> b) {
+    const MemberRates z{};
+    apply_member(a, z);
+    apply_member(b, z);
+    return std::memcmp(&a, &b, sizeof a) == 0;
+}
+
+// One member's descriptor in a launch's parameter block.
 struct GridLat {
     Geom g;
     const void *pop0;
     const void *pop1;
     long long plane;
+    unsigned long long xb_magic;  // ceil(2^32 / xblocks): local / xblocks = (local * xb_magic) >> 32
     int flip;
-    int xblocks;  // blocks per row: ceil(pitch / 512)
-    RatesC<float> r;
+    int xblocks;                  // 512-cell segments per row: ceil(pitch / 512)
+    MemberRates v;
 };
 
 struct GroupParams {
+    RatesC<float> rc;           // rates shared by the group (member-specific fields overwritten per block)
     int nlats;
-    int xblocks;                // the members' largest blocks per row (grid x)
-    int row0[kGroupLats + 1];   // first row of each member in the concatenation; row0[nlats] = rows
+    int unit;                   // persistent kernel: consecutive virtual blocks per work unit
+    int nvb;                    // virtual blocks per step
+    int blk0[kGroupLats + 1];   // first virtual block of each member; blk0[nlats] = nvb
     GridLat lat[kGroupLats];
 };
+static_assert(sizeof(GroupParams) <= 32764, "a launch group's descriptors must fit the kernel parameter space");
 
-// One step of every member of a group. The members' rows are concatenated;
-// block (xb, b) takes concatenated rows b, b + gridDim.y, ...; row r belongs to
-// the member l with row0[l] <= r < row0[l + 1], and the block covers cells
-// 512 xb .. 512 xb + 511 of that row, like block (xb, y) of the single-lattice
-// VEC4 kernel (whose row loop this mirrors). Blocks past a member's row width
-// skip its rows.
+// Row y, segment xb (cells 512 xb .. 512 xb + 511) of member `lo` of a group,
+// one step at `parity`, as block (xb, y) of the single-lattice four-cell
+// kernel computes it. NC: read-only loads (the per-step kernel) or
+// L2-coherent ones (the persistent kernel reads what its own previous step
+// wrote). The member's descriptor is read here, per row, so that nothing of it
+// stays live between rows.
+template <typename S, bool NC>
+__device__ __forceinline__ void batch_row(const GroupParams &P, int lo, int xb, int y, int parity) {
+    const GridLat &L = P.lat[lo];
+    const Geom g = L.g;
+    const int sel = (parity + L.flip) & 1;
+    StridedPlanes<S> pa;
+    pa.src = static_cast<const S *>(sel ? L.pop1 : L.pop0);
+    pa.dst = static_cast<S *>(const_cast<void *>(sel ? L.pop0 : L.pop1));
+    pa.plane = L.plane;
+    const int xs = xb * 512;
+    constexpr int PF = PrefetchRows<S>::value;
+    if constexpr (PF > 0) {
+        // as the single-lattice kernel: one thread per plane asks L2 for this segment PF rows ahead
+        // (16-byte aligned: segments start at multiples of 512 elements, rows are 128-byte pitched)
+        if (threadIdx.x < kQ && y + PF < g.ny) {
+            const int n = min(512, g.pitch - xs);
+            const S *pp = pa.src_at(threadIdx.x) + (size_t)(y + PF) * g.pitch + xs;
+            if (NOMRT_BULK_OK(g, pp, n * sizeof(S), 52)) prefetch_l2_bulk(pp, (unsigned)(n * sizeof(S)));
+        }
+    }
+    RatesC<float> r = P.rc;  // shared rates: parameter-bank operands
+    apply_member(r, L.v);    // the member's own values: registers
+    row4<S, StridedPlanes<S>, NC>(pa, g, r, xs + 4 * (int)threadIdx.x, y, (int)threadIdx.x & 31);
+}
+
+// Virtual block vb of a group: its member (binary search over the members'
+// first virtual blocks), row and segment.
+template <typename S, bool NC>
+__device__ __forceinline__ void batch_block(const GroupParams &P, int vb, int parity) {
+    int lo = 0, hi = P.nlats - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.blk0[mid] <= vb) lo = mid;
+        else hi = mid - 1;
+    }
+    const int local = vb - P.blk0[lo];
+    const int y = (int)(((unsigned long long)(unsigned)local * P.lat[lo].xb_magic) >> 32);
+    const int xb = local - y * P.lat[lo].xblocks;
+    batch_row<S, NC>(P, lo, xb, y, parity);
+}
+
+// One step of every member of a group: one block per virtual block.
 template <typename S, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     k_batch_grid(const __grid_constant__ GroupParams P, int parity) {
-    const int lane = threadIdx.x & 31;
-    const int x0 = ((int)blockIdx.x * kBatchThreads + (int)threadIdx.x) * 4;
-    for (int row = blockIdx.y; row < P.row0[P.nlats]; row += gridDim.y) {
-        int lo = 0, hi = P.nlats - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (P.row0[mid] <= row) lo = mid;
-            else hi = mid - 1;
-        }
-        const GridLat &L = P.lat[lo];
-        if ((int)blockIdx.x >= L.xblocks) continue;
-        const int sel = (parity + L.flip) & 1;
-        StridedPlanes<S> pa;
-        pa.src = static_cast<const S *>(sel ? L.pop1 : L.pop0);
-        pa.dst = static_cast<S *>(const_cast<void *>(sel ? L.pop0 : L.pop1));
-        pa.plane = L.plane;
-        const RatesC<float> r = L.r;  // into registers once per row rather than indexed loads at every use
-        const Geom g = L.g;
-        row4<S, StridedPlanes<S>, true>(pa, g, r, x0, row - P.row0[lo], lane);
-    }
+    for (int vb = blockIdx.x; vb < P.nvb; vb += gridDim.x) batch_block<S, true>(P, vb, parity);
 }
 
 template <typename S, int MINB, bool PERSISTENT>
@@ -179,28 +213,32 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status, unsigne
     return ok != 0;
 }
 
-// nsteps steps of every member in one cooperative launch; the loads use the
-// L2-coherent path because step s + 1 reads what step s wrote.
+// nsteps steps of every member of a group in one cooperative launch: the
+// resident blocks stride over runs of P.unit consecutive virtual blocks, with
+// a grid barrier between steps. advance =
+// 0 recomputes the step at parity0 nsteps times (the tuner's trials, which
+// leave the state as it was). A launch that finds the status word set (an
+// earlier barrier gave up: the state is undefined) returns at once.
 template <typename S, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
-    k_batch_persistent(const BatchLat *lats, const int4 *units, int nunits, int parity0, int nsteps, unsigned expected,
-                       unsigned *bar,
-                       int *status) {
-    const int lane = threadIdx.x & 31;
-    const int stride = gridDim.x * kBatchWarps;
+    k_batch_persistent(const __grid_constant__ GroupParams P, int parity0, int nsteps, int advance, unsigned expected,
+                       unsigned *bar, int *status) {
+    if (*reinterpret_cast<volatile int *>(status) != kStatusOk) return;
+    const int U = P.unit;
     for (int s = 0; s < nsteps; ++s) {
-        for (int w = blockIdx.x * kBatchWarps + (threadIdx.x >> 5); w < nunits; w += stride)
-            batch_unit<S, false>(lats, units[w], parity0 + s, lane);
+        const int parity = parity0 + (advance ? s : 0);
+        for (int base = blockIdx.x * U; base < P.nvb; base += gridDim.x * U) {
+            const int end = min(base + U, P.nvb);
+            for (int vb = base; vb < end; ++vb) batch_block<S, false>(P, vb, parity);
+        }
         if (s + 1 < nsteps && !grid_barrier(bar, status, expected)) return;
     }
 }
 
 template <typename S, int MINB>
 cudaError_t launch_grid_shape(const GroupParams &G, int parity, cudaStream_t st) {
-    const int rows = G.row0[G.nlats];
-    if (rows == 0 || G.xblocks == 0) return cudaSuccess;
-    const dim3 grid(G.xblocks, rows < 65535 ? rows : 65535);
-    k_batch_grid<S, MINB><<<grid, kBatchThreads, 0, st>>>(G, parity);
+    if (G.nvb == 0) return cudaSuccess;
+    k_batch_grid<S, MINB><<<G.nvb, kBatchThreads, 0, st>>>(G, parity);
     return cudaGetLastError();
 }
 
@@ -216,14 +254,15 @@ cudaError_t launch_batch_grid(int config, const GroupParams &G, int parity, cuda
 }
 
 template <typename S, int MINB>
-cudaError_t launch_persistent_shape(const BatchLat *lats, const int4 *units, int nunits, int parity, int nsteps,
-                                    int barrier_extra, unsigned *bar, int *status, cudaStream_t st) {
+cudaError_t launch_persistent_shape(const GroupParams &G, int parity, int nsteps, int advance, int barrier_extra,
+                                    unsigned *bar, int *status, cudaStream_t st) {
+    if (G.nvb == 0 || nsteps <= 0) return cudaSuccess;
     auto kern = k_batch_persistent<S, MINB>;
     int blocks = 0;
     cudaError_t e = resident_grid<GridTag<S, MINB, true>>(kern, &blocks);
     if (e != cudaSuccess) return e;
-    const int need = (nunits + kBatchWarps - 1) / kBatchWarps;
-    if (blocks > need) blocks = std::max(1, need);
+    const int units = (G.nvb + G.unit - 1) / G.unit;
+    if (blocks > units) blocks = units;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(kBatchThreads);
@@ -235,25 +274,22 @@ cudaError_t launch_persistent_shape(const BatchLat *lats, const int4 *units, int
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const unsigned expected = (unsigned)(blocks + barrier_extra);
-    return cudaLaunchKernelEx(&cfg, kern, lats, units, nunits, parity, nsteps, expected, bar, status);
+    return cudaLaunchKernelEx(&cfg, kern, G, parity, nsteps, advance, expected, bar, status);
 }
 
 template <typename S>
-cudaError_t launch_batch_persistent(int config, const BatchLat *lats, const int4 *units, int nunits, int parity,
-                                    int nsteps, int barrier_extra, unsigned *bar, int *status, cudaStream_t st) {
-    if (nunits == 0) return cudaSuccess;
+cudaError_t launch_batch_persistent(int config, const GroupParams &G, int parity, int nsteps, int advance,
+                                    int barrier_extra, unsigned *bar, int *status, cudaStream_t st) {
     switch (config) {
-        case 1: return launch_persistent_shape<S, 5>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
-        case 2: return launch_persistent_shape<S, 6>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
-        case 3: return launch_persistent_shape<S, 7>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
-        case 4: return launch_persistent_shape<S, 8>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
-        default: return launch_persistent_shape<S, 4>(lats, units, nunits, parity, nsteps, barrier_extra, bar, status, st);
+        case 1: return launch_persistent_shape<S, 5>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
+        case 2: return launch_persistent_shape<S, 6>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
+        case 3: return launch_persistent_shape<S, 7>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
+        case 4: return launch_persistent_shape<S, 8>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
+        default: return launch_persistent_shape<S, 4>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
     }
 }
 
 }  // namespace nomrt
-
-using nomrt::BatchLat;
 
 struct lbm_batch {
     cudaStream_t stream = nullptr;
@@ -262,18 +298,19 @@ struct lbm_batch {
     std::vector<lbm_lattice *> members;
     std::vector<int> flip;
     int64_t s = 0;  // batch steps taken
-    // device buffers (allocated by the batch)
-    BatchLat *d_lats = nullptr;
-    int4 *d_units = nullptr;
+    // device words of the persistent kernel (allocated by the batch)
     unsigned *d_bar = nullptr;
     int *d_status = nullptr;
-    size_t cap_lats = 0, cap_units = 0;
-    int nunits = 0;
-    std::vector<nomrt::GroupParams> groups;  // per-step launch parameters, kGroupLats members each
+    // lbm_batch_residuals: the members' five residual sums on the device and their pinned host copy
+    double *d_res = nullptr;
+    double *h_res = nullptr;
+    size_t cap_res = 0;
+    std::vector<nomrt::GroupParams> groups;  // launch parameters, kGroupLats members each
     int64_t cells = 0;
+    int nunits = 0;  // (row chunk, segment) virtual blocks per step
     bool dirty = true;
     int config = -1;  // -1: default per storage
-    int steps_per_launch = 1;
+    int steps_per_launch = nomrt::kDefaultPersistentSteps;
     int graph_steps = 32;
     int rows_per_unit = 1;
     int barrier_extra = 0;  // test hook: grid-barrier arrivals that never come
@@ -307,96 +344,46 @@ void drop_graph(lbm_batch *b) {
     }
 }
 
-// Rebuild the device descriptors and the work list after a membership change.
+// Rebuild the launch groups after a membership or shape change: members join
+// the first group whose shared rates equal theirs and that has room.
 lbm_status rebuild(lbm_batch *b) {
     if (!b->dirty) return LBM_OK;
     drop_graph(b);
-    std::vector<BatchLat> lats(b->members.size());
-    std::vector<int4> units;
     b->cells = 0;
     b->groups.clear();
     for (size_t l = 0; l < b->members.size(); ++l) {
         lbm_lattice *h = b->members[l];
         const nomrt::KParams &kp = h->kp;
-        BatchLat &d = lats[l];
-        d.pop0 = kp.pop[0];
-        d.pop1 = kp.pop[1];
-        d.plane = (long long)kp.plane;
-        d.mask = kp.mask;
-        d.flags = kp.flags;
-        d.walls = kp.walls;
-        d.nx = kp.nx;
-        d.ny = kp.ny;
-        d.pitch = kp.pitch;
-        d.px = kp.px;
-        d.py = kp.py;
-        d.flip = b->flip[l];
-        d.r = nomrt::make_rates<float>(kp);
+        const nomrt::RatesC<float> r = nomrt::make_rates<float>(kp);
         b->cells += h->fluid;
-        // the per-step launch: member l joins group l / kGroupLats with its VEC4 grid
-        if (l % nomrt::kGroupLats == 0) {
+        nomrt::GroupParams *G = nullptr;
+        for (nomrt::GroupParams &c : b->groups)
+            if (c.nlats < nomrt::kGroupLats && nomrt::same_shared_rates(c.rc, r)) {
+                G = &c;
+                break;
+            }
+        if (!G) {
             b->groups.emplace_back();
-            std::memset(&b->groups.back(), 0, sizeof(nomrt::GroupParams));
+            G = &b->groups.back();
+            std::memset(G, 0, sizeof(nomrt::GroupParams));
+            G->rc = r;
         }
-        nomrt::GroupParams &G = b->groups.back();
-        nomrt::GridLat &gl = G.lat[G.nlats];
+        nomrt::GridLat &gl = G->lat[G->nlats];
         gl.g = nomrt::make_geom(kp);
         gl.pop0 = kp.pop[0];
         gl.pop1 = kp.pop[1];
         gl.plane = (long long)kp.plane;
         gl.flip = b->flip[l];
         gl.xblocks = (kp.pitch / 4 + nomrt::kBatchThreads - 1) / nomrt::kBatchThreads;
-        gl.r = d.r;
-        G.row0[G.nlats + 1] = G.row0[G.nlats] + kp.ny;
-        G.xblocks = std::max(G.xblocks, gl.xblocks);
-        G.nlats += 1;
-        // units: runs of up to rows_per_unit consecutive rows of a 128-cell segment,
-        // skipping rows of the segment that hold no fluid cell
-        const int R = b->rows_per_unit;
-        for (int y0 = 0; y0 < kp.ny; y0 += R)
-            for (int xs = 0; xs < kp.pitch; xs += 128) {
-                int first = -1, last = -1;
-                for (int y = y0; y < std::min(y0 + R, kp.ny); ++y) {
-                    bool any = false;
-                    for (int x = xs; x < std::min(xs + 128, kp.nx) && !any; ++x)
-                        any = h->flags[(size_t)y * kp.nx + x] == 0;
-                    if (any) {
-                        if (first < 0) first = y;
-                        last = y;
-                    }
-                }
-                if (first >= 0) units.push_back(make_int4((int)l, first, xs, last - first + 1));
-            }
+        gl.xb_magic = ((1ULL << 32) + (unsigned long long)gl.xblocks - 1) / (unsigned long long)gl.xblocks;
+        gl.v = nomrt::member_rates(r);
+        G->unit = b->rows_per_unit;
+        G->blk0[G->nlats + 1] = G->blk0[G->nlats] + kp.ny * gl.xblocks;
+        G->nlats += 1;
+        G->nvb = G->blk0[G->nlats];
     }
-    auto grow = [&](void **p, size_t *capacity, size_t need, size_t elem) -> cudaError_t {
-        if (need <= *capacity) return cudaSuccess;
-        cudaError_t e = cudaStreamSynchronize(b->stream);
-        if (e != cudaSuccess) return e;
-        if (*p) cudaFree(*p);
-        *p = nullptr;
-        *capacity = 0;
-        const size_t n = std::max(need, (size_t)64) * 3 / 2;
-        e = cudaMalloc(p, n * elem);
-        if (e != cudaSuccess) return e;
-        *capacity = n;
-        return cudaSuccess;
-    };
-    cudaError_t e = grow(reinterpret_cast<void **>(&b->d_lats), &b->cap_lats, lats.size(), sizeof(BatchLat));
-    if (e != cudaSuccess) return bcuda(b, e, "batch descriptor allocation");
-    e = grow(reinterpret_cast<void **>(&b->d_units), &b->cap_units, units.size(), sizeof(int4));
-    if (e != cudaSuccess) return bcuda(b, e, "batch work list allocation");
-    if (!lats.empty()) {
-        e = cudaMemcpyAsync(b->d_lats, lats.data(), lats.size() * sizeof(BatchLat), cudaMemcpyHostToDevice, b->stream);
-        if (e != cudaSuccess) return bcuda(b, e, "upload descriptors");
-    }
-    if (!units.empty()) {
-        e = cudaMemcpyAsync(b->d_units, units.data(), units.size() * sizeof(int4), cudaMemcpyHostToDevice, b->stream);
-        if (e != cudaSuccess) return bcuda(b, e, "upload work list");
-    }
-    // the host vectors are about to go away: wait for the copies
-    e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return bcuda(b, e, "upload sync");
-    b->nunits = (int)units.size();
+    b->nunits = 0;
+    for (const nomrt::GroupParams &G : b->groups) b->nunits += G.nvb;
     b->dirty = false;
     return LBM_OK;
 }
@@ -419,7 +406,7 @@ cudaError_t ensure_streams(lbm_batch *b) {
 
 // n steps of every member with each member's own step kernel (its AUTO or
 // chosen variant), each member on its own stream between a fork and a join on
-// `st`, so the members' kernels can run concurrently. src_fixed >= 0 re-runs
+// `st`, so the members' kernels can run concurrently. advance = false re-runs
 // the current step n times without advancing (tuning).
 cudaError_t launch_concurrent(lbm_batch *b, int n, cudaStream_t st, bool advance) {
     cudaError_t e = ensure_streams(b);
@@ -477,33 +464,39 @@ cudaError_t launch_grid_step(lbm_batch *b, int config, int parity, cudaStream_t 
     return cudaSuccess;
 }
 
-// The persistent kernel keeps its per-lattice descriptors in registers; four
-// resident blocks per SM is its only shape that does not spill.
-constexpr int kPersistentConfig = 0;
+// k steps of every member with the persistent kernel: one launch per group
+// (groups hold disjoint lattices, so they need no barrier between them).
+cudaError_t launch_persistent_steps(lbm_batch *b, int config, int parity, int k, int advance, cudaStream_t st) {
+    for (const nomrt::GroupParams &G : b->groups) {
+        cudaError_t e = b->storage == LBM_F16_SHIFTED
+                            ? nomrt::launch_batch_persistent<__half>(config, G, parity, k, advance, b->barrier_extra,
+                                                                     b->d_bar, b->d_status, st)
+                            : nomrt::launch_batch_persistent<float>(config, G, parity, k, advance, b->barrier_extra,
+                                                                    b->d_bar, b->d_status, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
     if (b->kind == LBM_BATCH_CONCURRENT) return launch_concurrent(b, n, st, true);
-    const bool nee = any_nee(b);
-    // n steps starting at parity: one launch per step, or persistent launches of steps_per_launch
-    // (members with NEE walls need a pass between steps, so they force one launch per step)
-    while (n > 0) {
-        cudaError_t e;
-        if (b->steps_per_launch > 1 && !nee) {
+    // members with NEE walls need their boundary-node pass between steps: one launch per step
+    if (b->kind == LBM_BATCH_PERSISTENT && !any_nee(b)) {
+        while (n > 0) {
             const int k = std::min(n, b->steps_per_launch);
-            e = b->storage == LBM_F16_SHIFTED
-                    ? nomrt::launch_batch_persistent<__half>(kPersistentConfig, b->d_lats, b->d_units, b->nunits, parity, k,
-                                                             b->barrier_extra, b->d_bar, b->d_status, st)
-                    : nomrt::launch_batch_persistent<float>(kPersistentConfig, b->d_lats, b->d_units, b->nunits, parity, k,
-                                                            b->barrier_extra, b->d_bar, b->d_status, st);
+            cudaError_t e = launch_persistent_steps(b, b->cfg(), parity, k, 1, st);
+            if (e != cudaSuccess) return e;
             parity = (parity + k) & 1;
             n -= k;
-        } else {
-            e = launch_grid_step(b, b->cfg(), parity, st);
-            if (e == cudaSuccess && nee) e = launch_nee_passes(b, parity, st);
-            parity ^= 1;
-            n -= 1;
         }
+        return cudaSuccess;
+    }
+    const bool nee = any_nee(b);
+    for (; n > 0; --n) {
+        cudaError_t e = launch_grid_step(b, b->cfg(), parity, st);
+        if (e == cudaSuccess && nee) e = launch_nee_passes(b, parity, st);
         if (e != cudaSuccess) return e;
+        parity ^= 1;
     }
     return cudaSuccess;
 }
@@ -596,7 +589,8 @@ lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t gr
 
 lbm_status lbm_batch_set_kind(lbm_batch *b, int32_t kind) {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
-    if (kind != LBM_BATCH_FUSED && kind != LBM_BATCH_CONCURRENT) return bfail(b, LBM_EINVAL, "unknown batch kind");
+    if (kind != LBM_BATCH_FUSED && kind != LBM_BATCH_CONCURRENT && kind != LBM_BATCH_PERSISTENT)
+        return bfail(b, LBM_EINVAL, "unknown batch kind");
     b->kind = kind;
     drop_graph(b);
     return LBM_OK;
@@ -663,6 +657,21 @@ lbm_status lbm_batch_sync(lbm_batch *b) {
         cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned));
         return bfail(b, LBM_ETIMEOUT, "the persistent batch kernel gave up a grid barrier");
     }
+    if constexpr (nomrt::kBoundsBuild) {
+        // the members' bounds words (the word after each lattice's status word)
+        for (lbm_lattice *h : b->members) {
+            int w = 0;
+            e = cudaMemcpy(&w, h->kp.oob, sizeof w, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return bcuda(b, e, "read bounds word");
+            if (w != 0) {
+                const int zero = 0;
+                cudaMemcpy(h->kp.oob, &zero, sizeof zero, cudaMemcpyHostToDevice);
+                return bfail(b, LBM_ECUDA,
+                             "bounds-checking build: an index check failed at site " + std::to_string(w) +
+                                 " in a batch member (the access was skipped; the state is invalid)");
+            }
+        }
+    }
     return LBM_OK;
 }
 
@@ -674,68 +683,90 @@ lbm_status lbm_batch_debug_barrier_extra(lbm_batch *b, int32_t extra) {
     return LBM_OK;
 }
 
-lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_launches, int32_t *best_config, int32_t *best_rows,
-                          float *ms_per_launch) {
+lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind, int32_t *best_config,
+                          float *ms_per_step) {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
-    if (trial_launches < 1) return bfail(b, LBM_EINVAL, "trial_launches must be >= 1");
+    if (trial_steps < 2) return bfail(b, LBM_EINVAL, "trial_steps must be >= 2");
     if (b->members.empty()) return bfail(b, LBM_EINVAL, "batch is empty");
-    // Each trial re-runs the current step with the same source parity: it
+    // Every trial re-runs the current step with the same source parity: it
     // rewrites the destination buffers with the same values and leaves the
     // state the next real step reads untouched.
     const int parity = (int)(b->s & 1);
+    const bool nee = any_nee(b);
+    const int k = b->steps_per_launch > 1 ? b->steps_per_launch : nomrt::kDefaultPersistentSteps;
+    constexpr int kCand = 2 * nomrt::kBatchConfigs + 1;
+    float ms[kCand];
+    for (float &m : ms) m = INFINITY;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return bfail(b, LBM_ECUDA, "event create");
-    int best = 0;
-    float best_ms = 1e30f;
     lbm_status out = rebuild(b);
+    // time `run(n)` for n = trial_steps after one warm-up call of run(1 or k)
+    auto timed = [&](auto run, int warm, float *dst) -> cudaError_t {
+        cudaError_t e = run(warm);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
+        if (e == cudaSuccess) e = run(trial_steps);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float t = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+        if (e == cudaSuccess) *dst = t / (float)trial_steps;
+        return e;
+    };
     for (int c = 0; c < nomrt::kBatchConfigs && out == LBM_OK; ++c) {
-        auto run = [&](int n) -> cudaError_t {
-            for (int k = 0; k < n; ++k) {
-                cudaError_t e = launch_grid_step(b, c, parity, b->stream);
-                if (e != cudaSuccess) return e;
-            }
-            return cudaSuccess;
-        };
-        cudaError_t e = run(1);  // warm-up
-        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-        if (e == cudaSuccess) e = run(trial_launches);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        float ms = 0.f;
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-        if (e != cudaSuccess) {
-            out = bcuda(b, e, "tuning launch");
-            break;
-        }
-        ms /= (float)trial_launches;
-        if (ms_per_launch) ms_per_launch[c] = ms;
-        if (ms < best_ms) {
-            best_ms = ms;
-            best = c;
-        }
+        cudaError_t e = timed(
+            [&](int n) -> cudaError_t {
+                for (int i = 0; i < n; ++i) {
+                    cudaError_t le = launch_grid_step(b, c, parity, b->stream);
+                    if (le == cudaSuccess && nee) le = launch_nee_passes(b, parity, b->stream);
+                    if (le != cudaSuccess) return le;
+                }
+                return cudaSuccess;
+            },
+            1, &ms[c]);
+        if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (fused)");
     }
-    // the concurrent kind: every member's own kernel, members in parallel
-    float conc_ms = 1e30f;
+    for (int c = 0; c < nomrt::kBatchConfigs && out == LBM_OK && !nee; ++c) {
+        cudaError_t e = timed(
+            [&](int n) -> cudaError_t {
+                for (int done = 0; done < n;) {
+                    const int m = std::min(k, n - done);
+                    cudaError_t le = launch_persistent_steps(b, c, parity, m, 0, b->stream);
+                    if (le != cudaSuccess) return le;
+                    done += m;
+                }
+                return cudaSuccess;
+            },
+            std::min(k, trial_steps), &ms[nomrt::kBatchConfigs + c]);
+        if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (persistent)");
+    }
     if (out == LBM_OK) {
-        cudaError_t e = launch_concurrent(b, 1, b->stream, false);
-        if (e == cudaSuccess) e = cudaEventRecord(e0, b->stream);
-        if (e == cudaSuccess) e = launch_concurrent(b, trial_launches, b->stream, false);
-        if (e == cudaSuccess) e = cudaEventRecord(e1, b->stream);
-        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&conc_ms, e0, e1);
+        cudaError_t e = timed([&](int n) { return launch_concurrent(b, n, b->stream, false); }, 1,
+                              &ms[2 * nomrt::kBatchConfigs]);
         if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (concurrent)");
-        conc_ms /= (float)trial_launches;
-        if (ms_per_launch) ms_per_launch[nomrt::kBatchConfigs] = conc_ms;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (out != LBM_OK) return out;
-    b->kind = conc_ms < best_ms ? LBM_BATCH_CONCURRENT : LBM_BATCH_FUSED;
-    b->config = best;
+    // a barrier that gave up during a trial is reported by the next lbm_batch_sync
+    int best = 0;
+    for (int c = 1; c < kCand; ++c)
+        if (ms[c] < ms[best]) best = c;
+    if (best < nomrt::kBatchConfigs) {
+        b->kind = LBM_BATCH_FUSED;
+        b->config = best;
+    } else if (best < 2 * nomrt::kBatchConfigs) {
+        b->kind = LBM_BATCH_PERSISTENT;
+        b->config = best - nomrt::kBatchConfigs;
+        b->steps_per_launch = k;
+    } else {
+        b->kind = LBM_BATCH_CONCURRENT;
+    }
     drop_graph(b);
-    if (best_config) *best_config = b->kind == LBM_BATCH_CONCURRENT ? -2 : best;
-    if (best_rows) *best_rows = b->rows_per_unit;
+    if (best_kind) *best_kind = b->kind;
+    if (best_config) *best_config = b->kind == LBM_BATCH_CONCURRENT ? -1 : b->config;
+    if (ms_per_step)
+        for (int c = 0; c < kCand; ++c) ms_per_step[c] = ms[c];
     return LBM_OK;
 }
 
@@ -749,9 +780,69 @@ lbm_status lbm_batch_info(const lbm_batch *b, int32_t *members, int64_t *cells, 
         *cells = c;
     }
     if (units) *units = b->nunits;
-    if (config) *config = b->kind == LBM_BATCH_CONCURRENT ? -2 : b->cfg();
+    if (config) *config = b->kind == LBM_BATCH_CONCURRENT ? -1 : b->cfg();
     if (rows_per_unit) *rows_per_unit = b->rows_per_unit;
     if (steps_done) *steps_done = b->s;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_residuals(lbm_batch *b, int32_t cap, lbm_lattice **members, double *r, int32_t *n) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    const int m = (int)b->members.size();
+    if (n) *n = m;
+    if (cap < m) return bfail(b, LBM_EINVAL, "cap is smaller than the number of members");
+    if (m == 0) return LBM_OK;
+    if (!r) return bfail(b, LBM_EINVAL, "r is NULL");
+    if ((size_t)m > b->cap_res) {
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (b->d_res) cudaFree(b->d_res);
+        if (b->h_res) cudaFreeHost(b->h_res);
+        b->d_res = nullptr;
+        b->h_res = nullptr;
+        b->cap_res = 0;
+        const size_t want = std::max<size_t>((size_t)m * 3 / 2, 64);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_res, want * 5 * sizeof(double));
+        if (e == cudaSuccess) e = cudaHostAlloc(&b->h_res, want * 5 * sizeof(double), cudaHostAllocDefault);
+        if (e != cudaSuccess) return bcuda(b, e, "residual buffers");
+        b->cap_res = want;
+    }
+    // every member's residual kernels on the batch's stream, their sums side by side
+    for (int i = 0; i < m; ++i) {
+        lbm_lattice *h = b->members[i];
+        cudaError_t e = h->L->residual(h->kp, h->cur, h->snap(), h->have_snap, h->partials(), b->stream);
+        if (e == cudaSuccess) e = nomrt::reduce_partials(h->partials(), 5, b->d_res + 5 * (size_t)i, b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "residual kernels");
+    }
+    cudaError_t e = cudaMemcpyAsync(b->h_res, b->d_res, (size_t)m * 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                                    b->stream);
+    if (e != cudaSuccess) return bcuda(b, e, "read residuals");
+    lbm_status st = lbm_batch_sync(b);
+    if (st != LBM_OK) return st;
+    for (int i = 0; i < m; ++i) {
+        lbm_lattice *h = b->members[i];
+        const double *q = b->h_res + 5 * (size_t)i;
+        if (members) members[i] = h;
+        const int had = h->have_snap;
+        h->have_snap = 1;
+        if (q[4] > 0.0 || !std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2]) ||
+            !std::isfinite(q[3])) {
+            r[i] = NAN;
+        } else if (!had) {
+            r[i] = INFINITY;
+        } else {
+            const double Ru = std::sqrt(q[0]) / std::max(std::sqrt(q[1]), 1e-300);
+            const double RT = std::sqrt(q[2]) / std::max(std::sqrt(q[3]), 1e-300);
+            r[i] = std::max(Ru, RT);
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_mode(const lbm_batch *b, int32_t *kind, int32_t *steps_per_launch, int32_t *graph_steps) {
+    if (!b) return LBM_EINVAL;
+    if (kind) *kind = b->kind;
+    if (steps_per_launch) *steps_per_launch = b->steps_per_launch;
+    if (graph_steps) *graph_steps = b->graph_steps;
     return LBM_OK;
 }
 
@@ -769,10 +860,10 @@ void lbm_batch_destroy(lbm_batch *b) {
     for (cudaEvent_t ev : b->levents) cudaEventDestroy(ev);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->cap) cudaStreamDestroy(b->cap);
-    if (b->d_lats) cudaFree(b->d_lats);
-    if (b->d_units) cudaFree(b->d_units);
     if (b->d_bar) cudaFree(b->d_bar);
     if (b->d_status) cudaFree(b->d_status);
+    if (b->d_res) cudaFree(b->d_res);
+    if (b->h_res) cudaFreeHost(b->h_res);
     delete b;
 }
 

@@ -14,6 +14,14 @@
 // device shares it and it keeps the last call's contents; each call writes all
 // the partials it later reads, so nothing needs clearing, but calls whose
 // kernels overlap on the GPU (different streams, no ordering) race on it.
+//
+// The array's device address is looked up with cudaGetSymbolAddress at the
+// first call on a device and cached with the id of the CUDA context that was
+// current then. A later call in another context of that device (after
+// cudaDeviceReset, or a primary-context reset by a host framework, which
+// reloads the module and may move the array) sees a different id and looks
+// the address up again.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -35,8 +43,10 @@ constexpr int kNaMaxDevices = 64;
 
 static __device__ __align__(256) double g_na_scratch[kNaScratchDoubles];
 
-// Device address of g_na_scratch per device, looked up once per device.
+// Device address of g_na_scratch per device, with the id of the context it was
+// looked up in (0: not yet looked up).
 double *g_na_ptr[kNaMaxDevices] = {};
+unsigned long long g_na_ctx[kNaMaxDevices] = {};
 std::mutex g_na_mutex;
 
 __global__ void __launch_bounds__(kNaThreads)
@@ -98,15 +108,49 @@ lbm_status na_fail(lbm_status st, const char *msg) {
     return st;
 }
 
-// The scratch array's device address on the current device (set-up on the
-// first call on each device).
+// Id of the calling thread's current CUDA context (driver entry points looked
+// up through the runtime, so the library needs no link to libcuda).
+using CtxGetCurrentFn = CUresult (*)(CUcontext *);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long *);
+
+lbm_status na_context_id(unsigned long long *id) {
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    if (!get_current || !get_id) {
+        void *a = nullptr, *b = nullptr;
+        cudaDriverEntryPointQueryResult qa = cudaDriverEntryPointSymbolNotFound, qb = qa;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &a, 12000, cudaEnableDefault, &qa);
+        if (e == cudaSuccess) e = cudaGetDriverEntryPointByVersion("cuCtxGetId", &b, 12000, cudaEnableDefault, &qb);
+        if (e != cudaSuccess || qa != cudaDriverEntryPointSuccess || qb != cudaDriverEntryPointSuccess || !a || !b) {
+            cudaGetLastError();
+            return na_fail(LBM_ECUDA, "the driver does not provide cuCtxGetCurrent / cuCtxGetId");
+        }
+        get_current = reinterpret_cast<CtxGetCurrentFn>(a);
+        get_id = reinterpret_cast<CtxGetIdFn>(b);
+    }
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, id) != CUDA_SUCCESS)
+        return na_fail(LBM_ECUDA, "no current CUDA context");
+    return LBM_OK;
+}
+
+// The scratch array's device address on the current device: looked up at the
+// first call on the device (set-up), and again whenever the device's current
+// context is not the one the cached address belongs to.
 lbm_status na_scratch(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return na_fail(LBM_ECUDA, cudaGetErrorString(e));
     if (dev < 0 || dev >= kNaMaxDevices) return na_fail(LBM_EINVAL, "device index out of range");
+    // binds the device's primary context to this thread (initialising it if needed) before the
+    // driver is asked for the current context
+    e = cudaSetDevice(dev);
+    if (e != cudaSuccess) return na_fail(LBM_ECUDA, cudaGetErrorString(e));
+    unsigned long long ctx = 0;
+    lbm_status st = na_context_id(&ctx);
+    if (st != LBM_OK) return st;
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_ptr[dev]) {
+    if (!g_na_ptr[dev] || g_na_ctx[dev] != ctx) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_na_scratch);
         if (e != cudaSuccess || !p) {
@@ -114,6 +158,7 @@ lbm_status na_scratch(double **out) {
             return na_fail(LBM_ECUDA, "cudaGetSymbolAddress of the residual scratch failed");
         }
         g_na_ptr[dev] = static_cast<double *>(p);
+        g_na_ctx[dev] = ctx;
     }
     *out = g_na_ptr[dev];
     return LBM_OK;
@@ -133,10 +178,19 @@ lbm_status lbm_residual_fields_noalloc(const double *ux, const double *uy, const
                        "n exceeds the 16,777,216 cells the fixed residual scratch can reduce; use lbm_residual");
     if (n > 0 && (!ux || !uy || !T || !ux_prev || !uy_prev || !T_prev))
         return na_fail(LBM_EINVAL, "a field pointer is NULL");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the call reads its result back and waits for the stream: never legal inside a capture
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce != cudaSuccess) {
+        cudaGetLastError();
+        return na_fail(LBM_ECUDA, cudaGetErrorString(ce));
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return na_fail(LBM_EINVAL, "lbm_residual_fields_noalloc must not be called on a stream that is being captured");
     double *scratch = nullptr;
     lbm_status st = na_scratch(&scratch);
     if (st != LBM_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     double sums[kNaWidth] = {0, 0, 0, 0, 0};
     if (n > 0) {
         const int nblocks = (int)((n + kNaCellsPerBlock - 1) / kNaCellsPerBlock);

@@ -25,6 +25,13 @@ constexpr int kRedThreads = 256;
 // Device status word values (set by kernels, read and cleared by the host).
 constexpr int kStatusOk = 0;
 constexpr int kStatusTimeout = 1;
+// Whether this build checks every step-kernel access against the lattice's
+// device block (compiled with -DLBM_BOUNDS; see in_block in nomrt_kernels.cuh).
+#ifdef LBM_BOUNDS
+constexpr bool kBoundsBuild = true;
+#else
+constexpr bool kBoundsBuild = false;
+#endif
 // Step kernel variants (lbm_set_step_variant).
 constexpr int kStepAuto = 0;
 constexpr int kStepScalar = 1;
@@ -74,6 +81,10 @@ struct KParams {
     int variant;                      // step kernel variant (kStep*)
     int config;                       // shape index within the variant (TMA: 0..kTmaConfigs-1)
     int *status;                      // device status word
+    // bounds-checking build (-DLBM_BOUNDS): the lattice's device block [blk_lo, blk_hi), which
+    // every checked access must stay in, and the word that records the first failing check
+    const char *blk_lo, *blk_hi;
+    int *oob;
 };
 
 // Launchers, one set per storage type (0 = f64, 1 = f32-shifted, 2 = f16-shifted).

@@ -175,11 +175,45 @@ struct Geom {
     const uint8_t *flags;
     const WallDev *walls;
     const uint8_t *nee_dir;  // per cell: 0, or the direction of a boundary node's nearest fluid node
+    const char *lo, *hi;     // the lattice's device block (checked by the bounds-checking build)
+    int *oob;                // first failing check's site id (bounds-checking build)
 };
 
 inline Geom make_geom(const KParams &p) {
-    return Geom{p.nx, p.ny, p.pitch, p.px, p.py, p.mask, p.flags, p.walls, p.nee_dir};
+    return Geom{p.nx, p.ny, p.pitch, p.px, p.py, p.mask, p.flags, p.walls, p.nee_dir, p.blk_lo, p.blk_hi, p.oob};
 }
+
+// ------------------------------------------------------------- index checks
+
+// The bounds-checking build (-DLBM_BOUNDS) tests every population, map and
+// wall-table access of the step kernels before making it: the bytes
+// [p, p + bytes) must lie in the lattice's device block and a 2-, 4-, 8- or
+// 16-byte access must be aligned to its size. An access that fails is
+// skipped (a load reads 0) and the first failing site id is recorded in the
+// lattice's bounds word, which the synchronising calls report; nothing traps.
+// The sites: 1-9 pull / scalar kernel, 10-19 four-cell rows, 20-29 wall
+// links and node pass, 30-39 eight-cell kernel, 40-49 TMA kernel, 50-59
+// prefetches. Without LBM_BOUNDS every check is the constant true.
+#ifdef LBM_BOUNDS
+static __device__ __noinline__ void oob_note(int *w, int site) { atomicCAS(w, 0, site); }
+
+__device__ __forceinline__ bool in_block(const Geom &g, const void *p, int bytes, int site) {
+    const char *c = static_cast<const char *>(p);
+    const bool pow2 = (bytes & (bytes - 1)) == 0;
+    const bool ok = c >= g.lo && c + bytes <= g.hi &&
+                    (!pow2 || bytes > 16 || (reinterpret_cast<uintptr_t>(c) & (uintptr_t)(bytes - 1)) == 0);
+    if (!ok) oob_note(g.oob, site);
+    return ok;
+}
+#define NOMRT_OK(g, p, bytes, site) ::nomrt::in_block((g), (p), (int)(bytes), (site))
+#else
+#define NOMRT_OK(g, p, bytes, site) true
+#endif
+
+// A bulk copy or prefetch of `bytes` at p: in the block, 16-byte aligned, a
+// multiple of 16 bytes.
+#define NOMRT_BULK_OK(g, p, bytes, site) \
+    (NOMRT_OK(g, p, bytes, site) && ((reinterpret_cast<uintptr_t>(p) & 15u) == 0 && ((bytes) & 15u) == 0))
 
 // A cell whose populations are kept: fluid, or a boundary node of an NEE wall.
 __device__ __forceinline__ bool kept_cell(const Geom &g, int off) {
@@ -187,6 +221,22 @@ __device__ __forceinline__ bool kept_cell(const Geom &g, int off) {
 }
 
 // --------------------------------------------------------------- pull step
+
+// One population value at p (0 where the bounds-checking build refuses p).
+template <typename S>
+__device__ __forceinline__ typename Store<S>::C ld_at(const Geom &g, const S *p, int site) {
+    if (!NOMRT_OK(g, p, sizeof(S), site)) return typename Store<S>::C(0);
+    return Store<S>::ld(p);
+}
+
+// The wall-table entry of the wall that cell `off` belongs to (nullptr where
+// the bounds-checking build refuses the flag or the entry).
+__device__ __forceinline__ const WallDev *wall_of(const Geom &g, int off, int site) {
+    if (!NOMRT_OK(g, g.flags + off, 1, site)) return nullptr;
+    const WallDev *w = g.walls + g.flags[off];
+    if (!NOMRT_OK(g, w, sizeof(WallDev), site)) return nullptr;
+    return w;
+}
 
 // Post-streaming populations at fluid cell (x, y): Eq. 9 and Eq. 25 in pull
 // form, then the halfway wall rules on the links flagged in `m`.
@@ -205,25 +255,25 @@ __device__ __forceinline__ void pull(const S *const *src, const Geom &g, int x, 
     }
     const int r0 = y * g.pitch, rm = ym * g.pitch, rp = yp * g.pitch;
     // direction i pulls from x - e_i (Eq. 5 numbering)
-    f[0] = St::ld(src[0] + r0 + x);
-    f[1] = St::ld(src[1] + r0 + xm);
-    f[2] = St::ld(src[2] + rm + x);
-    f[3] = St::ld(src[3] + r0 + xp);
-    f[4] = St::ld(src[4] + rp + x);
-    f[5] = St::ld(src[5] + rm + xm);
-    f[6] = St::ld(src[6] + rm + xp);
-    f[7] = St::ld(src[7] + rp + xp);
-    f[8] = St::ld(src[8] + rp + xm);
-    t[0] = St::ld(src[9] + r0 + x);
-    t[1] = St::ld(src[10] + r0 + xm);
-    t[2] = St::ld(src[11] + rm + x);
-    t[3] = St::ld(src[12] + r0 + xp);
-    t[4] = St::ld(src[13] + rp + x);
+    f[0] = ld_at<S>(g, src[0] + r0 + x, 1);
+    f[1] = ld_at<S>(g, src[1] + r0 + xm, 1);
+    f[2] = ld_at<S>(g, src[2] + rm + x, 1);
+    f[3] = ld_at<S>(g, src[3] + r0 + xp, 1);
+    f[4] = ld_at<S>(g, src[4] + rp + x, 1);
+    f[5] = ld_at<S>(g, src[5] + rm + xm, 1);
+    f[6] = ld_at<S>(g, src[6] + rm + xp, 1);
+    f[7] = ld_at<S>(g, src[7] + rp + xp, 1);
+    f[8] = ld_at<S>(g, src[8] + rp + xm, 1);
+    t[0] = ld_at<S>(g, src[9] + r0 + x, 2);
+    t[1] = ld_at<S>(g, src[10] + r0 + xm, 2);
+    t[2] = ld_at<S>(g, src[11] + rm + x, 2);
+    t[3] = ld_at<S>(g, src[12] + r0 + xp, 2);
+    t[4] = ld_at<S>(g, src[13] + rp + x, 2);
     if constexpr (TQ == 9) {
-        t[5] = St::ld(src[14] + rm + xm);
-        t[6] = St::ld(src[15] + rm + xp);
-        t[7] = St::ld(src[16] + rp + xp);
-        t[8] = St::ld(src[17] + rp + xm);
+        t[5] = ld_at<S>(g, src[14] + rm + xm, 2);
+        t[6] = ld_at<S>(g, src[15] + rm + xp, 2);
+        t[7] = ld_at<S>(g, src[16] + rp + xp, 2);
+        t[8] = ld_at<S>(g, src[17] + rp + xm, 2);
     }
     if (m) {
         using C = typename St::C;
@@ -232,10 +282,11 @@ __device__ __forceinline__ void pull(const S *const *src, const Geom &g, int x, 
 #pragma unroll
         for (int i = 1; i < 9; ++i) {
             if (m & (1u << (i - 1))) {
-                const WallDev *w = g.walls + g.flags[sidx[i]];
-                f[i] = St::ld(src[opp[i]] + r0 + x) + (C)__ldg(&w->cf[i]);
+                const WallDev *w = wall_of(g, sidx[i], 3);
+                if (kBoundsBuild && !w) continue;
+                f[i] = ld_at<S>(g, src[opp[i]] + r0 + x, 4) + (C)__ldg(&w->cf[i]);
                 if (i < TQ)
-                    t[i] = (C)__ldg(&w->tsgn) * St::ld(src[9 + opp[i]] + r0 + x) +
+                    t[i] = (C)__ldg(&w->tsgn) * ld_at<S>(g, src[9 + opp[i]] + r0 + x, 5) +
                            (C)__ldg(TQ == 9 ? &w->tb9[i] : &w->tb);
             }
         }
@@ -286,7 +337,7 @@ __device__ __forceinline__ void nee_rebuild(const S *const *src, const Geom &g,
     int xf = x + ex[d], yf = y + ey[d];
     if (g.px) xf = (xf < 0) ? xf + g.nx : (xf >= g.nx ? xf - g.nx : xf);
     if (g.py) yf = (yf < 0) ? yf + g.ny : (yf >= g.ny ? yf - g.ny : yf);
-    const unsigned mf = g.mask[yf * g.pitch + xf];
+    const unsigned mf = NOMRT_OK(g, g.mask + yf * g.pitch + xf, 1, 20) ? g.mask[yf * g.pitch + xf] : 0u;
     pull<S, TQ>(src, g, xf, yf, mf, f, t);
     const Macro<C> M = macro_of<C, TQ>(r, f, t);
     const C uwx = (C)w->uwx, uwy = (C)w->uwy;
@@ -779,11 +830,15 @@ __device__ __forceinline__ void wall_links(const PA &pl, const Geom &g, uint32_t
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         if (m & (1u << (i - 1))) {
-            const WallDev *w = g.walls + g.flags[sidx[i]];
-            f[i][K] = Ld<S, NC>::one(pl.src_at(opp[i]) + r0 + x) + (float)__ldg(&w->cf[i]);
-            if (i < TQ)
-                t[i][K] = (float)__ldg(&w->tsgn) * Ld<S, NC>::one(pl.src_at(9 + opp[i]) + r0 + x) +
+            const WallDev *w = wall_of(g, sidx[i], 22);
+            if (kBoundsBuild && !w) continue;
+            const S *pf = pl.src_at(opp[i]) + r0 + x;
+            f[i][K] = (NOMRT_OK(g, pf, sizeof(S), 23) ? Ld<S, NC>::one(pf) : 0.f) + (float)__ldg(&w->cf[i]);
+            if (i < TQ) {
+                const S *pt = pl.src_at(9 + opp[i]) + r0 + x;
+                t[i][K] = (float)__ldg(&w->tsgn) * (NOMRT_OK(g, pt, sizeof(S), 24) ? Ld<S, NC>::one(pt) : 0.f) +
                           (float)__ldg(TQ == 9 ? &w->tb9[i] : &w->tb);
+            }
         }
     }
 }
@@ -807,15 +862,17 @@ __global__ void __launch_bounds__(256) k_step(const Planes<S> pl, const Geom g, 
     if (x >= g.nx) return;
     for (int y = blockIdx.y * blockDim.y + threadIdx.y; y < g.ny; y += gridDim.y * blockDim.y) {
         const int off = y * g.pitch + x;
-        const unsigned m = __ldg(g.mask + off);
+        const unsigned m = NOMRT_OK(g, g.mask + off, 1, 6) ? __ldg(g.mask + off) : (unsigned)kSolid;
         if (m == kSolid) continue;
         C f[9], t[TQ];
         pull<S, TQ>(pl.src, g, x, y, m, f, t);
         collide_cell<S, TQ, BGK>(r, f, t);
 #pragma unroll
-        for (int q = 0; q < 9; ++q) Store<S>::st(pl.dst[q] + off, f[q]);
+        for (int q = 0; q < 9; ++q)
+            if (NOMRT_OK(g, pl.dst[q] + off, sizeof(S), 7)) Store<S>::st(pl.dst[q] + off, f[q]);
 #pragma unroll
-        for (int q = 0; q < TQ; ++q) Store<S>::st(pl.dst[9 + q] + off, t[q]);
+        for (int q = 0; q < TQ; ++q)
+            if (NOMRT_OK(g, pl.dst[9 + q] + off, sizeof(S), 7)) Store<S>::st(pl.dst[9 + q] + off, t[q]);
     }
 }
 
@@ -828,16 +885,20 @@ __global__ void __launch_bounds__(128) k_nee(const Planes<S> pl, const Geom g, c
     using C = typename Store<S>::C;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
+    if (!NOMRT_OK(g, nee + i, sizeof(int2), 25)) return;
     const int2 e = nee[i];
     const int off = e.x, d = e.y & 0xFF, k = e.y >> 8;
     const int y = off / g.pitch, x = off - y * g.pitch;
+    if (!NOMRT_OK(g, g.walls + k, sizeof(WallDev), 26)) return;
     C f[9], t[TQ];
     nee_rebuild<S, TQ>(pl.src, g, r, x, y, d, g.walls + k, f, t);
     collide_cell<S, TQ, BGK>(r, f, t);
 #pragma unroll
-    for (int q = 0; q < 9; ++q) Store<S>::st(pl.dst[q] + off, f[q]);
+    for (int q = 0; q < 9; ++q)
+        if (NOMRT_OK(g, pl.dst[q] + off, sizeof(S), 27)) Store<S>::st(pl.dst[q] + off, f[q]);
 #pragma unroll
-    for (int q = 0; q < TQ; ++q) Store<S>::st(pl.dst[9 + q] + off, t[q]);
+    for (int q = 0; q < TQ; ++q)
+        if (NOMRT_OK(g, pl.dst[9 + q] + off, sizeof(S), 27)) Store<S>::st(pl.dst[9 + q] + off, t[q]);
 }
 
 // Initial state (rest equilibrium, Eqs. 22, 30 at u = 0) in the storage frame.
@@ -1096,7 +1157,7 @@ constexpr unsigned kFull = 0xffffffffu;
 template <typename S, int DX, bool NC = true>
 __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, int lane, bool inrow, float out[4]) {
     float a[4] = {0.f, 0.f, 0.f, 0.f};
-    if (inrow) Ld<S, NC>::four(row + x0, a);
+    if (inrow && NOMRT_OK(g, row + x0, 4 * sizeof(S), 10)) Ld<S, NC>::four(row + x0, a);
     if (DX == 0) {
         out[0] = a[0]; out[1] = a[1]; out[2] = a[2]; out[3] = a[3];
     } else if (DX == 1) {
@@ -1105,7 +1166,7 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
             left = 0.f;
             int xs = x0 - 1;
             if (xs < 0 && g.px) xs += g.nx;
-            if (inrow && xs >= 0) left = Ld<S, NC>::one(row + xs);
+            if (inrow && xs >= 0 && NOMRT_OK(g, row + xs, sizeof(S), 11)) left = Ld<S, NC>::one(row + xs);
         }
         out[0] = left; out[1] = a[0]; out[2] = a[1]; out[3] = a[2];
     } else {
@@ -1113,13 +1174,13 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
         if (lane == 31) {
             right = 0.f;
             const int xs = x0 + 4;
-            if (inrow && xs < g.nx) right = Ld<S, NC>::one(row + xs);
+            if (inrow && xs < g.nx && NOMRT_OK(g, row + xs, sizeof(S), 12)) right = Ld<S, NC>::one(row + xs);
         }
         out[0] = a[1]; out[1] = a[2]; out[2] = a[3]; out[3] = right;
         if (g.px && inrow) {
             const int k = g.nx - 1 - x0;
             if (k >= 0 && k < 4) {
-                const float v = Ld<S, NC>::one(row);
+                const float v = NOMRT_OK(g, row, sizeof(S), 13) ? Ld<S, NC>::one(row) : 0.f;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) out[j] = (j == k) ? v : out[j];  // constant indices only
             }
@@ -1131,7 +1192,7 @@ __device__ __forceinline__ void ld_plane(const S *row, const Geom &g, int x0, in
 template <typename S, int DX, bool NC = true>
 __device__ __forceinline__ void ld_plane_ns(const S *row, const Geom &g, int x0, int lane, bool inrow, float out[4]) {
     float a[4] = {0.f, 0.f, 0.f, 0.f};
-    if (inrow) Ld<S, NC>::four(row + x0, a);
+    if (inrow && NOMRT_OK(g, row + x0, 4 * sizeof(S), 10)) Ld<S, NC>::four(row + x0, a);
     if (DX == 0) {
         out[0] = a[0]; out[1] = a[1]; out[2] = a[2]; out[3] = a[3];
     } else if (DX == 1) {
@@ -1140,7 +1201,7 @@ __device__ __forceinline__ void ld_plane_ns(const S *row, const Geom &g, int x0,
             left = 0.f;
             int xs = x0 - 1;
             if (xs < 0 && g.px) xs += g.nx;
-            if (inrow && xs >= 0) left = Ld<S, NC>::one(row + xs);
+            if (inrow && xs >= 0 && NOMRT_OK(g, row + xs, sizeof(S), 11)) left = Ld<S, NC>::one(row + xs);
         }
         out[0] = left; out[1] = a[0]; out[2] = a[1]; out[3] = a[2];
     } else {
@@ -1148,7 +1209,7 @@ __device__ __forceinline__ void ld_plane_ns(const S *row, const Geom &g, int x0,
         if (lane == 31) {
             right = 0.f;
             const int xs = x0 + 4;
-            if (inrow && xs < g.nx) right = Ld<S, NC>::one(row + xs);
+            if (inrow && xs < g.nx && NOMRT_OK(g, row + xs, sizeof(S), 12)) right = Ld<S, NC>::one(row + xs);
         }
         out[0] = a[1]; out[1] = a[2]; out[2] = a[3]; out[3] = right;
     }
@@ -1158,9 +1219,9 @@ __device__ __forceinline__ void ld_plane_ns(const S *row, const Geom &g, int x0,
 // where the lane lies past the row (`inrow` false: such a lane still takes part
 // in the shuffles that supply its neighbours).
 template <typename S, bool NC = true>
-__device__ __forceinline__ void ld_four(const S *row, int x0, bool inrow, float a[4]) {
+__device__ __forceinline__ void ld_four(const Geom &g, const S *row, int x0, bool inrow, float a[4]) {
     a[0] = a[1] = a[2] = a[3] = 0.f;
-    if (inrow) Ld<S, NC>::four(row + x0, a);
+    if (inrow && NOMRT_OK(g, row + x0, 4 * sizeof(S), 14)) Ld<S, NC>::four(row + x0, a);
 }
 
 // The values cells x0..x0+3 pull from a plane with e_x = +1 (source x - 1): the
@@ -1194,7 +1255,7 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
     const int r0 = y * g.pitch;
     const bool inrow = x0 < g.pitch;
     uint32_t m4 = 0xFFFFFFFFu;
-    if (inrow) m4 = __ldg(reinterpret_cast<const uint32_t *>(g.mask + r0 + x0));
+    if (inrow && NOMRT_OK(g, g.mask + r0 + x0, 4, 15)) m4 = __ldg(reinterpret_cast<const uint32_t *>(g.mask + r0 + x0));
     const bool any = m4 != 0xFFFFFFFFu;
     if (!__any_sync(kFull, any)) return;
     int ym = y - 1, yp = y + 1;
@@ -1233,7 +1294,7 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
             // with e_x = -1, in one branch for all of them
             const int kseam = g.nx - 1 - x0;
             if (g.px && inrow && kseam >= 0 && kseam < 4) {
-#define NOMRT_SEAM(P, ROW) { const float v = Ld<S, NC>::one(ROW); _Pragma("unroll") for (int j = 0; j < 4; ++j) P[j] = (j == kseam) ? v : P[j]; }
+#define NOMRT_SEAM(P, ROW) { const float v = NOMRT_OK(g, ROW, sizeof(S), 16) ? Ld<S, NC>::one(ROW) : 0.f; _Pragma("unroll") for (int j = 0; j < 4; ++j) P[j] = (j == kseam) ? v : P[j]; }
                 NOMRT_SEAM(f[3], pl.src_at(3) + r0);
                 NOMRT_SEAM(f[6], pl.src_at(6) + rm);
                 NOMRT_SEAM(f[7], pl.src_at(7) + rp);
@@ -1266,47 +1327,49 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
         for (int i = 0; i < NE; ++i) el[i] = er[i] = es[i] = 0.f;
         if (lane == 0 && inrow && xl >= 0) {
     #pragma unroll
-            for (int i = 0; i < NE; ++i) el[i] = Ld<S, NC>::one(lrow[i] + xl);
+            for (int i = 0; i < NE; ++i)
+                el[i] = NOMRT_OK(g, lrow[i] + xl, sizeof(S), 17) ? Ld<S, NC>::one(lrow[i] + xl) : 0.f;
         }
         if (lane == 31 && inrow && xr < g.nx) {
     #pragma unroll
-            for (int i = 0; i < NE; ++i) er[i] = Ld<S, NC>::one(rrow[i] + xr);
+            for (int i = 0; i < NE; ++i)
+                er[i] = NOMRT_OK(g, rrow[i] + xr, sizeof(S), 18) ? Ld<S, NC>::one(rrow[i] + xr) : 0.f;
         }
         if (seam_k >= 0) {
     #pragma unroll
-            for (int i = 0; i < NE; ++i) es[i] = Ld<S, NC>::one(rrow[i]);
+            for (int i = 0; i < NE; ++i) es[i] = NOMRT_OK(g, rrow[i], sizeof(S), 19) ? Ld<S, NC>::one(rrow[i]) : 0.f;
         }
         float a[4];
-        ld_four<S, NC>(pl.src_at(0) + r0, x0, inrow, f[0]);
-        ld_four<S, NC>(pl.src_at(1) + r0, x0, inrow, a);
+        ld_four<S, NC>(g, pl.src_at(0) + r0, x0, inrow, f[0]);
+        ld_four<S, NC>(g, pl.src_at(1) + r0, x0, inrow, a);
         pull_from_left(a, el[0], lane, f[1]);
-        ld_four<S, NC>(pl.src_at(2) + rm, x0, inrow, f[2]);
-        ld_four<S, NC>(pl.src_at(3) + r0, x0, inrow, a);
+        ld_four<S, NC>(g, pl.src_at(2) + rm, x0, inrow, f[2]);
+        ld_four<S, NC>(g, pl.src_at(3) + r0, x0, inrow, a);
         pull_from_right(a, er[0], lane, seam_k, es[0], f[3]);
-        ld_four<S, NC>(pl.src_at(4) + rp, x0, inrow, f[4]);
-        ld_four<S, NC>(pl.src_at(5) + rm, x0, inrow, a);
+        ld_four<S, NC>(g, pl.src_at(4) + rp, x0, inrow, f[4]);
+        ld_four<S, NC>(g, pl.src_at(5) + rm, x0, inrow, a);
         pull_from_left(a, el[1], lane, f[5]);
-        ld_four<S, NC>(pl.src_at(6) + rm, x0, inrow, a);
+        ld_four<S, NC>(g, pl.src_at(6) + rm, x0, inrow, a);
         pull_from_right(a, er[1], lane, seam_k, es[1], f[6]);
-        ld_four<S, NC>(pl.src_at(7) + rp, x0, inrow, a);
+        ld_four<S, NC>(g, pl.src_at(7) + rp, x0, inrow, a);
         pull_from_right(a, er[2], lane, seam_k, es[2], f[7]);
-        ld_four<S, NC>(pl.src_at(8) + rp, x0, inrow, a);
+        ld_four<S, NC>(g, pl.src_at(8) + rp, x0, inrow, a);
         pull_from_left(a, el[2], lane, f[8]);
-        ld_four<S, NC>(pl.src_at(9) + r0, x0, inrow, t[0]);
-        ld_four<S, NC>(pl.src_at(10) + r0, x0, inrow, a);
+        ld_four<S, NC>(g, pl.src_at(9) + r0, x0, inrow, t[0]);
+        ld_four<S, NC>(g, pl.src_at(10) + r0, x0, inrow, a);
         pull_from_left(a, el[3], lane, t[1]);
-        ld_four<S, NC>(pl.src_at(11) + rm, x0, inrow, t[2]);
-        ld_four<S, NC>(pl.src_at(12) + r0, x0, inrow, a);
+        ld_four<S, NC>(g, pl.src_at(11) + rm, x0, inrow, t[2]);
+        ld_four<S, NC>(g, pl.src_at(12) + r0, x0, inrow, a);
         pull_from_right(a, er[3], lane, seam_k, es[3], t[3]);
-        ld_four<S, NC>(pl.src_at(13) + rp, x0, inrow, t[4]);
+        ld_four<S, NC>(g, pl.src_at(13) + rp, x0, inrow, t[4]);
         if constexpr (TQ == 9) {
-            ld_four<S, NC>(pl.src_at(14) + rm, x0, inrow, a);
+            ld_four<S, NC>(g, pl.src_at(14) + rm, x0, inrow, a);
             pull_from_left(a, el[4], lane, t[5]);
-            ld_four<S, NC>(pl.src_at(15) + rm, x0, inrow, a);
+            ld_four<S, NC>(g, pl.src_at(15) + rm, x0, inrow, a);
             pull_from_right(a, er[4], lane, seam_k, es[4], t[6]);
-            ld_four<S, NC>(pl.src_at(16) + rp, x0, inrow, a);
+            ld_four<S, NC>(g, pl.src_at(16) + rp, x0, inrow, a);
             pull_from_right(a, er[5], lane, seam_k, es[5], t[7]);
-            ld_four<S, NC>(pl.src_at(17) + rp, x0, inrow, a);
+            ld_four<S, NC>(g, pl.src_at(17) + rp, x0, inrow, a);
             pull_from_left(a, el[5], lane, t[8]);
         }
     }
@@ -1326,9 +1389,11 @@ __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<f
         zero_solid<3, 4, TQ>(m4, f, t);
     }
 #pragma unroll
-    for (int i = 0; i < 9; ++i) Vec4<S>::st(pl.dst_at(i) + r0 + x0, f[i]);
+    for (int i = 0; i < 9; ++i)
+        if (NOMRT_OK(g, pl.dst_at(i) + r0 + x0, 4 * sizeof(S), 28)) Vec4<S>::st(pl.dst_at(i) + r0 + x0, f[i]);
 #pragma unroll
-    for (int i = 0; i < TQ; ++i) Vec4<S>::st(pl.dst_at(9 + i) + r0 + x0, t[i]);
+    for (int i = 0; i < TQ; ++i)
+        if (NOMRT_OK(g, pl.dst_at(9 + i) + r0 + x0, 4 * sizeof(S), 29)) Vec4<S>::st(pl.dst_at(9 + i) + r0 + x0, t[i]);
 }
 
 // Bulk prefetch of `bytes` bytes at p into L2 (no registers, no completion to wait for).
@@ -1356,7 +1421,8 @@ __global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const G
             if (threadIdx.x < 9 + TQ && y + PF < g.ny) {
                 const int xs = blockIdx.x * 512;
                 const int n = min(512, g.pitch - xs);
-                prefetch_l2_bulk(pl.src_at(threadIdx.x) + (size_t)(y + PF) * g.pitch + xs, (unsigned)(n * sizeof(S)));
+                const S *pp = pl.src_at(threadIdx.x) + (size_t)(y + PF) * g.pitch + xs;
+                if (NOMRT_BULK_OK(g, pp, n * sizeof(S), 50)) prefetch_l2_bulk(pp, (unsigned)(n * sizeof(S)));
             }
         }
         row4<S, Planes<S>, true, TQ, BGK>(pl, g, r, x0, y, lane);

@@ -33,21 +33,22 @@ __device__ __forceinline__ void realign8(const __half *row, const Geom &g, int x
             left = 0u;
             int xs = x0 - 1;
             if (xs < 0 && g.px) xs += g.nx;
-            if (inrow && xs >= 0) left = half_bits(row[xs]) << 16;
+            if (inrow && xs >= 0 && NOMRT_OK(g, row + xs, 2, 30)) left = half_bits(row[xs]) << 16;
         }
         const uint32_t p0 = __byte_perm(left, w[0], 0x5432);
         const uint32_t p1 = __byte_perm(w[0], w[1], 0x5432);
         const uint32_t p2 = __byte_perm(w[1], w[2], 0x5432);
         const uint32_t p3 = __byte_perm(w[2], w[3], 0x5432);
         w[0] = p0; w[1] = p1; w[2] = p2; w[3] = p3;
-        if (g.px && inrow && x0 == 0) w[0] = (w[0] & 0xFFFF0000u) | half_bits(row[g.nx - 1]);  // periodic seam
+        if (g.px && inrow && x0 == 0 && NOMRT_OK(g, row + g.nx - 1, 2, 31))
+            w[0] = (w[0] & 0xFFFF0000u) | half_bits(row[g.nx - 1]);  // periodic seam
     } else if (DX == -1) {
         // cell j pulls element j + 1
         uint32_t right = __shfl_down_sync(kFull, w[0], 1);  // neighbour's element 0 in the low half
         if (lane == 31) {
             right = 0u;
             const int xs = x0 + 8;
-            if (inrow && xs < g.nx) right = half_bits(row[xs]);
+            if (inrow && xs < g.nx && NOMRT_OK(g, row + xs, 2, 32)) right = half_bits(row[xs]);
         }
         const uint32_t p0 = __byte_perm(w[0], w[1], 0x5432);
         const uint32_t p1 = __byte_perm(w[1], w[2], 0x5432);
@@ -57,7 +58,7 @@ __device__ __forceinline__ void realign8(const __half *row, const Geom &g, int x
         if (g.px && inrow) {
             const int k = g.nx - 1 - x0;  // periodic seam: x = nx - 1 pulls from x = 0
             if (k >= 0 && k < 8) {
-                const uint32_t v = half_bits(row[0]);
+                const uint32_t v = NOMRT_OK(g, row, 2, 33) ? half_bits(row[0]) : 0u;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (k == 2 * q) w[q] = (w[q] & 0xFFFF0000u) | v;
@@ -71,7 +72,7 @@ __device__ __forceinline__ void realign8(const __half *row, const Geom &g, int x
 template <int DX>
 __device__ __forceinline__ void ld_plane8(const __half *row, const Geom &g, int x0, int lane, bool inrow, uint32_t w[4]) {
     uint4 v = make_uint4(0u, 0u, 0u, 0u);
-    if (inrow) v = __ldg(reinterpret_cast<const uint4 *>(row + x0));
+    if (inrow && NOMRT_OK(g, row + x0, 16, 34)) v = __ldg(reinterpret_cast<const uint4 *>(row + x0));
     w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
     realign8<DX>(row, g, x0, lane, inrow, w);
 }
@@ -90,10 +91,12 @@ __device__ __forceinline__ void links8(const Planes<__half> &pl, const Geom &g, 
 #pragma unroll
     for (int i = 1; i < 9; ++i) {
         if (m & (1u << (i - 1))) {
-            const WallDev *wd = g.walls + g.flags[sidx[i]];
-            f[i] = Store<__half>::ld(pl.src[opp[i]] + r0 + x) + (float)__ldg(&wd->cf[i]);
+            const WallDev *wd = wall_of(g, sidx[i], 35);
+            if (kBoundsBuild && !wd) continue;
+            f[i] = ld_at<__half>(g, pl.src[opp[i]] + r0 + x, 36) + (float)__ldg(&wd->cf[i]);
             if (i < 5)
-                t[i] = (float)__ldg(&wd->tsgn) * Store<__half>::ld(pl.src[9 + opp[i]] + r0 + x) + (float)__ldg(&wd->tb);
+                t[i] = (float)__ldg(&wd->tsgn) * ld_at<__half>(g, pl.src[9 + opp[i]] + r0 + x, 36) +
+                       (float)__ldg(&wd->tb);
         }
     }
 }
@@ -155,13 +158,13 @@ __global__ void __launch_bounds__(128, MINB) k_step8h(const Planes<__half> pl, c
         if (threadIdx.x < kQ && y + PrefetchRows<__half>::value < g.ny) {
             const int xs = blockIdx.x * 1024;
             const int n = min(1024, g.pitch - xs);
-            prefetch_l2_bulk(pl.src[threadIdx.x] + (size_t)(y + PrefetchRows<__half>::value) * g.pitch + xs,
-                             (unsigned)(n * sizeof(__half)));
+            const __half *pp = pl.src[threadIdx.x] + (size_t)(y + PrefetchRows<__half>::value) * g.pitch + xs;
+            if (NOMRT_BULK_OK(g, pp, n * sizeof(__half), 51)) prefetch_l2_bulk(pp, (unsigned)(n * sizeof(__half)));
         }
         const int r0 = y * g.pitch;
         const bool inrow = x0 < g.pitch;
         uint2 m8 = make_uint2(0xFFFFFFFFu, 0xFFFFFFFFu);
-        if (inrow) m8 = __ldg(reinterpret_cast<const uint2 *>(g.mask + r0 + x0));
+        if (inrow && NOMRT_OK(g, g.mask + r0 + x0, 8, 37)) m8 = __ldg(reinterpret_cast<const uint2 *>(g.mask + r0 + x0));
         const bool any = (m8.x & m8.y) != 0xFFFFFFFFu;
         if (!__any_sync(kFull, any)) continue;
         int ym = y - 1, yp = y + 1;
@@ -193,7 +196,8 @@ __global__ void __launch_bounds__(128, MINB) k_step8h(const Planes<__half> pl, c
         pair8<3>(pl, g, r, m8.x, m8.y, x0, r0, rm, rp, w);
 #pragma unroll
         for (int q = 0; q < kQ; ++q)
-            *reinterpret_cast<uint4 *>(pl.dst[q] + r0 + x0) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
+            if (NOMRT_OK(g, pl.dst[q] + r0 + x0, 16, 38))
+                *reinterpret_cast<uint4 *>(pl.dst[q] + r0 + x0) = make_uint4(w[q][0], w[q][1], w[q][2], w[q][3]);
     }
 }
 

@@ -157,12 +157,21 @@ __device__ __forceinline__ void tma_issue(const Planes<S> &pl, const Geom &g, co
     const int lo = xs - HALO < 0 ? 0 : xs - HALO;
     const int hi = xs + W + HALO > g.pitch ? g.pitch : xs + W + HALO;
     const uint32_t bytes = (uint32_t)((hi - lo) * (int)sizeof(S));
-    mbar_arrive_expect_tx(bar, bytes * kQ);
+    // the barrier expects the bytes of the copies that are issued (all of them, except where the
+    // bounds-checking build refuses a source range)
+    uint32_t armed_bytes = bytes * kQ;
+    if constexpr (kBoundsBuild) {
+        armed_bytes = 0;
+        for (int q = 0; q < kQ; ++q)
+            if (NOMRT_BULK_OK(g, pl.src[q] + (size_t)plane_row(q, y, ym, yp) * g.pitch + lo, bytes, 40))
+                armed_bytes += bytes;
+    }
+    mbar_arrive_expect_tx(bar, armed_bytes);
 #pragma unroll 1
     for (int q = 0; q < kQ; ++q) {
         const S *src = pl.src[q] + (size_t)plane_row(q, y, ym, yp) * g.pitch + lo;
         S *dst = stage + q * ROW + (lo - (xs - HALO));
-        bulk_g2s(dst, src, bytes, bar);
+        if (!kBoundsBuild || NOMRT_BULK_OK(g, src, bytes, 40)) bulk_g2s(dst, src, bytes, bar);
     }
 }
 
@@ -195,11 +204,11 @@ __device__ __forceinline__ void sm_plane(const S *sm, const S *grow, const Geom 
             out[N - 1] = right;
         }
     }
-    if (DX == 1 && g.px && x0 == 0) out[0] = Store<S>::ld(grow + g.nx - 1);  // periodic seam
+    if (DX == 1 && g.px && x0 == 0) out[0] = ld_at<S>(g, grow + g.nx - 1, 41);  // periodic seam
     if (DX == -1 && g.px) {
         const int k = g.nx - 1 - x0;
         if (k >= 0 && k < N) {
-            const float v = Store<S>::ld(grow);  // periodic seam: x = nx - 1 pulls from x = 0
+            const float v = ld_at<S>(g, grow, 42);  // periodic seam: x = nx - 1 pulls from x = 0
 #pragma unroll
             for (int j = 0; j < N; ++j) out[j] = (j == k) ? v : out[j];  // constant indices only
         }
@@ -295,7 +304,7 @@ __global__ void __launch_bounds__(T, MINB) k_step_tma(const Planes<S> pl, const 
         const int rm = ym * g.pitch, rp = yp * g.pitch;
         const bool inrow = x0 < g.pitch;
         uint32_t mN = all_solid<N>();
-        if (inrow) mN = ld_mask<N>(g.mask + r0 + x0);
+        if (inrow && NOMRT_OK(g, g.mask + r0 + x0, N, 43)) mN = ld_mask<N>(g.mask + r0 + x0);
         const bool any = mN != all_solid<N>();
         if (__any_sync(kFull, any)) {
             float f[9][N], t[5][N];
@@ -316,9 +325,12 @@ __global__ void __launch_bounds__(T, MINB) k_step_tma(const Planes<S> pl, const 
             if (any) {
                 cells_N<S, N>(pl, g, r, mN, x0, r0, rm, rp, f, t);
 #pragma unroll
-                for (int q = 0; q < 9; ++q) VecN<S, N>::st(pl.dst[q] + r0 + x0, f[q]);
+                for (int q = 0; q < 9; ++q)
+                    if (NOMRT_OK(g, pl.dst[q] + r0 + x0, N * sizeof(S), 44)) VecN<S, N>::st(pl.dst[q] + r0 + x0, f[q]);
 #pragma unroll
-                for (int q = 0; q < 5; ++q) VecN<S, N>::st(pl.dst[9 + q] + r0 + x0, t[q]);
+                for (int q = 0; q < 5; ++q)
+                    if (NOMRT_OK(g, pl.dst[9 + q] + r0 + x0, N * sizeof(S), 44))
+                        VecN<S, N>::st(pl.dst[9 + q] + r0 + x0, t[q]);
             }
         }
         // every thread is done reading stage s: refill it with this CTA's unit STAGES ahead

@@ -8,6 +8,7 @@ the binding's functions raises.
 from __future__ import annotations
 
 import ctypes as C
+import os
 import threading
 
 import numpy as np
@@ -25,9 +26,12 @@ EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_st
             "lbm_set_step_kernel", "lbm_read_macro", "lbm_read_macro_rows",
             "lbm_nusselt",
             "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
-            "lbm_destroy", "lbm_residual_fields_noalloc", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
+            "lbm_destroy", "lbm_residual_fields_noalloc", "lbm_probe_fp64_rate", "lbm_bounds_checking",
+            "lbm_debug_bounds_limit", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
             "lbm_batch_set_mode", "lbm_batch_set_kind", "lbm_batch_set_config", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
-            "lbm_batch_info", "lbm_batch_last_error", "lbm_batch_destroy", "lbm_batch_debug_barrier_extra")
+            "lbm_batch_info", "lbm_batch_get_mode", "lbm_batch_residuals", "lbm_batch_last_error", "lbm_batch_destroy",
+            "lbm_batch_debug_barrier_extra")
+BATCH_KINDS = {"fused": 0, "concurrent": 1, "persistent": 2}
 
 
 class LBMError(RuntimeError):
@@ -60,8 +64,17 @@ _lib = None
 _lock = threading.Lock()
 
 
+def library_variant() -> str:
+    """'' for the library, 'bounds' for the bounds-checking build, chosen by the
+    environment variable NOMRT_LIB_VARIANT when the library is first loaded."""
+    v = os.environ.get("NOMRT_LIB_VARIANT", "")
+    if v not in _build.VARIANTS:
+        raise ValueError(f"NOMRT_LIB_VARIANT must be one of {sorted(_build.VARIANTS)}")
+    return v
+
+
 def library_path() -> str:
-    return _build.LIB
+    return _build.library_path(library_variant())
 
 
 def load():
@@ -70,7 +83,7 @@ def load():
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.build()
+        path = _build.build(variants=(library_variant(),))
         L = C.CDLL(path)
         vp, dp = C.c_void_p, C.POINTER(C.c_double)
         L.lbm_footprint_bytes.restype = C.c_size_t
@@ -109,6 +122,9 @@ def load():
                            ("lbm_batch_set_config", [vp, C.c_int32, C.c_int32]), ("lbm_batch_set_kind", [vp, C.c_int32]),
                            ("lbm_batch_tune", [vp, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                                C.POINTER(C.c_float)]),
+                           ("lbm_batch_get_mode", [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                                   C.POINTER(C.c_int32)]),
+                           ("lbm_batch_residuals", [vp, C.c_int32, C.POINTER(vp), dp, C.POINTER(C.c_int32)]),
                            ("lbm_batch_step", [vp, C.c_int64]), ("lbm_batch_sync", [vp]),
                            ("lbm_batch_debug_barrier_extra", [vp, C.c_int32]),
                            ("lbm_batch_info", [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
@@ -119,6 +135,12 @@ def load():
         L.lbm_batch_last_error.argtypes = [vp]
         L.lbm_batch_destroy.restype = None
         L.lbm_batch_destroy.argtypes = [vp]
+        L.lbm_bounds_checking.restype = C.c_int32
+        L.lbm_bounds_checking.argtypes = []
+        L.lbm_debug_bounds_limit.restype = C.c_int
+        L.lbm_debug_bounds_limit.argtypes = [vp, C.c_int64]
+        L.lbm_probe_fp64_rate.restype = C.c_int
+        L.lbm_probe_fp64_rate.argtypes = [vp, dp]
         L.lbm_residual_fields_noalloc.restype = C.c_int
         L.lbm_residual_fields_noalloc.argtypes = [vp, vp, vp, vp, vp, vp, vp, C.c_int64, vp, dp]
         _lib = L
@@ -176,10 +198,17 @@ def residual_fields_noalloc(ux, uy, T, ux_prev, uy_prev, T_prev, solid=None, str
     solid: uint8 or None). Allocates nothing on the device."""
     import torch
     n = ux.numel()
-    for a in (ux, uy, T, ux_prev, uy_prev, T_prev):
-        assert a.is_cuda and a.dtype == torch.float64 and a.is_contiguous() and a.numel() == n
+    fields = (ux, uy, T, ux_prev, uy_prev, T_prev)
+    for a in fields:
+        if not isinstance(a, torch.Tensor) or not a.is_cuda or a.dtype != torch.float64:
+            raise TypeError("fields must be float64 CUDA tensors")
+        if not a.is_contiguous() or a.numel() != n or a.device != ux.device:
+            raise ValueError("fields must be contiguous, of one length and on one device")
     if solid is not None:
-        assert solid.is_cuda and solid.dtype == torch.uint8 and solid.is_contiguous() and solid.numel() == n
+        if not isinstance(solid, torch.Tensor) or not solid.is_cuda or solid.dtype != torch.uint8:
+            raise TypeError("solid must be a uint8 CUDA tensor or None")
+        if not solid.is_contiguous() or solid.numel() != n or solid.device != ux.device:
+            raise ValueError("solid must be contiguous, of the fields' length and on their device")
     st = stream if stream is not None else torch.cuda.current_stream(ux.device)
     r = C.c_double()
     with torch.cuda.device(ux.device):
@@ -188,6 +217,16 @@ def residual_fields_noalloc(ux, uy, T, ux_prev, uy_prev, T_prev, solid=None, str
             None if solid is None else solid.data_ptr(), C.c_int64(n), C.c_void_p(st.cuda_stream), C.byref(r))
     _check(status, None)
     return r.value
+
+
+def probe_fp64_rate(stream=None) -> float:
+    """The current device's FP64 fused multiply-add rate (instructions per
+    second; lbm_probe_fp64_rate)."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    v = C.c_double()
+    _check(load().lbm_probe_fp64_rate(C.c_void_p(st.cuda_stream), C.byref(v)), None)
+    return v.value
 
 
 def step_kernel_count(storage: str, variant) -> int:
@@ -313,9 +352,8 @@ class Lattice:
 
 
 class Batch:
-    """Lattices of uneven size advanced together by one launch per step (see
-    the lbm_batch_* calls). Members must share the batch's stream and one of
-    the FP32/FP16 storages."""
+    """Lattices of uneven size advanced together (see the lbm_batch_* calls).
+    Members must share the batch's stream and one of the FP32/FP16 storages."""
 
     def __init__(self, stream=None):
         import torch
@@ -344,31 +382,54 @@ class Batch:
         self._check(load().lbm_batch_remove(self._h, lat.handle))
         self.members.remove(lat)
 
-    def set_mode(self, steps_per_launch: int = 1, graph_steps: int = 32):
+    def set_mode(self, steps_per_launch: int = 32, graph_steps: int = 32):
+        """Steps per launch of the persistent kind, and steps per replayed CUDA
+        graph (0: launches from the host)."""
         self._check(load().lbm_batch_set_mode(self._h, int(steps_per_launch), int(graph_steps)))
 
+    def get_mode(self):
+        """(kind name, steps per launch, graph steps) in force."""
+        k, spl, gs = C.c_int32(), C.c_int32(), C.c_int32()
+        self._check(load().lbm_batch_get_mode(self._h, C.byref(k), C.byref(spl), C.byref(gs)))
+        names = {v: n for n, v in BATCH_KINDS.items()}
+        return names[k.value], spl.value, gs.value
+
     def set_kind(self, kind):
-        """'fused' (one kernel over every member's work) or 'concurrent' (each
-        member's own kernel, members side by side)."""
-        k = {"fused": 0, "concurrent": 1}[kind] if isinstance(kind, str) else int(kind)
+        """'fused' (one launch per step over every member's rows), 'persistent'
+        (one cooperative launch per steps_per_launch steps, grid barrier between
+        steps) or 'concurrent' (each member's own kernel, members side by side)."""
+        k = BATCH_KINDS[kind] if isinstance(kind, str) else int(kind)
         self._check(load().lbm_batch_set_kind(self._h, k))
 
     def set_config(self, config: int, rows_per_unit: int = 1):
         self._check(load().lbm_batch_set_config(self._h, int(config), int(rows_per_unit)))
 
-    def tune(self, trial_launches: int = 5):
-        """Autotune the kind and the fused kernel's config; returns (best config,
-        -2 if the concurrent kind won; rows per unit; {"fused_cfg<c>": ms per
-        step, "concurrent": ms per step})."""
-        best, rows = C.c_int32(), C.c_int32()
-        ms = (C.c_float * 6)()
-        self._check(load().lbm_batch_tune(self._h, int(trial_launches), C.byref(best), C.byref(rows), ms))
+    def tune(self, trial_steps: int = 8):
+        """Autotune kind and config on the current members (state unchanged).
+        Returns (kind name, config (-1 for concurrent), {candidate: ms per
+        step}) with candidates fused_cfg0-4, persistent_cfg0-4, concurrent."""
+        kind, cfg = C.c_int32(), C.c_int32()
+        ms = (C.c_float * 11)()
+        self._check(load().lbm_batch_tune(self._h, int(trial_steps), C.byref(kind), C.byref(cfg), ms))
         table = {f"fused_cfg{c}": ms[c] for c in range(5)}
-        table["concurrent"] = ms[5]
-        return best.value, rows.value, table
+        table.update({f"persistent_cfg{c}": ms[5 + c] for c in range(5)})
+        table["concurrent"] = ms[10]
+        names = {v: n for n, v in BATCH_KINDS.items()}
+        return names[kind.value], cfg.value, table
 
     def step(self, n: int = 1):
         self._check(load().lbm_batch_step(self._h, int(n)))
+
+    def residuals(self):
+        """{Lattice: R} for every member (lbm_batch_residuals: one
+        synchronisation; NaN for a member whose fields are not finite)."""
+        m = len(self.members)
+        hs = (C.c_void_p * max(1, m))()
+        r = (C.c_double * max(1, m))()
+        n = C.c_int32()
+        self._check(load().lbm_batch_residuals(self._h, m, hs, r, C.byref(n)))
+        by_handle = {lat.handle.value: lat for lat in self.members}
+        return {by_handle[hs[i]]: r[i] for i in range(n.value)}
 
     def debug_barrier_extra(self, extra: int):
         """Test hook: make the persistent kernel's grid barrier time out (see

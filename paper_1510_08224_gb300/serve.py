@@ -18,8 +18,13 @@ after its admission) whether it runs alone or among others, and the batch
 kernels give the same bits as a lattice stepped alone, so a request's result
 does not depend on what else is being served.
 
-The executor is pluggable: `GpuBackend` drives the CUDA library; tests of the
-scheduling logic use a fake backend on the CPU.
+The executor is pluggable: `GpuBackend` drives the CUDA library's batch
+executor (every admitted request resident and stepped together; residuals of
+all of them read with one synchronisation); `PlainBackend` is the plain path,
+each request alone in FP64 storage with its own launches, run through the same
+loop with one request admitted at a time (`max_active=1`), so its latencies
+come from the same real-time stream. Tests of the scheduling logic use a fake
+backend on the CPU.
 """
 from __future__ import annotations
 
@@ -57,17 +62,19 @@ class Result:
 
 
 class GpuBackend:
-    """The CUDA library: lattices in torch device memory, one Batch."""
+    """The CUDA library: lattices in torch device memory, one Batch of the
+    given kind ('fused', 'persistent' or 'concurrent'), optionally replayed
+    from CUDA graphs of graph_steps steps."""
 
-    def __init__(self, storage: str = "f32", graph_steps: int = 0):
+    def __init__(self, storage: str = "f32", graph_steps: int = 0, kind: str = "fused", steps_per_launch: int = 32):
         import torch
         from . import lbm
         self._lbm = lbm
         self._torch = torch
         self.storage = storage
         self.batch = lbm.Batch()
-        self.batch.set_kind("concurrent")
-        self.batch.set_mode(1, graph_steps)
+        self.batch.set_kind(kind)
+        self.batch.set_mode(steps_per_launch, graph_steps)
 
     def footprint(self, case) -> int:
         p, keep = self._lbm.make_params(case, self.storage)
@@ -88,6 +95,14 @@ class GpuBackend:
     def residual(self, lat) -> float:
         return lat.residual()
 
+    def residuals(self, lats) -> dict:
+        """R of every resident lattice, one synchronisation (lbm_batch_residuals)."""
+        r = self.batch.residuals()
+        for lat in lats:
+            if lat not in r:  # not batched (cannot happen in the server loop)
+                r[lat] = lat.residual()
+        return r
+
     def nusselt(self, lat, side) -> float:
         return lat.nusselt(side, 0.0, lat.case.delta_T)
 
@@ -104,11 +119,59 @@ class GpuBackend:
         self.batch.close()
 
 
+class PlainBackend:
+    """The plain path: every lattice in FP64 storage stepped with its own
+    launches (lbm_step), residuals read one lattice at a time."""
+
+    def __init__(self, storage: str = "f64"):
+        from . import lbm
+        self._lbm = lbm
+        self.storage = storage
+        self.members = []
+
+    def footprint(self, case) -> int:
+        p, keep = self._lbm.make_params(case, self.storage)
+        return self._lbm.lbm_footprint_bytes(p)
+
+    def create(self, case):
+        return self._lbm.Lattice(case, storage=self.storage)
+
+    def add(self, lat):
+        self.members.append(lat)
+
+    def remove(self, lat):
+        self.members.remove(lat)
+
+    def step(self, n: int):
+        for lat in self.members:
+            lat.step(n)
+
+    def residual(self, lat) -> float:
+        return lat.residual()
+
+    def nusselt(self, lat, side) -> float:
+        return lat.nusselt(side, 0.0, lat.case.delta_T)
+
+    def fields(self, lat):
+        return lat.macro()
+
+    def release(self, lat):
+        lat.close()
+
+    def sync(self):
+        for lat in self.members:
+            lat.sync()
+
+    def close(self):
+        self.members = []
+
+
 class Server:
     def __init__(self, backend, budget_bytes: float = 150e9, check_every: int = 500, tol: float = 1e-6,
-                 step_cap: int = 200_000, clock=time.perf_counter, sleep=time.sleep):
+                 step_cap: int = 200_000, clock=time.perf_counter, sleep=time.sleep, max_active: int | None = None):
         self.backend = backend
         self.budget = float(budget_bytes)
+        self.max_active_limit = max_active  # None: bounded by the budget alone
         self.check_every = int(check_every)
         self.tol = float(tol)
         # the cap is a whole number of checks, so every chunk is check_every steps
@@ -118,6 +181,14 @@ class Server:
         self.in_use = 0
         self.peak_in_use = 0
         self.max_active = 0
+        self.queued_for_memory = 0  # admissions that waited for memory to free up
+        self.checks = 0             # residual checks (one per chunk)
+
+    def _residuals(self, lats):
+        f = getattr(self.backend, "residuals", None)
+        if f is not None:
+            return f(lats)
+        return {lat: self.backend.residual(lat) for lat in lats}
 
     def run(self, requests, realtime: bool = True):
         """Serve `requests` (arrival times relative to the start). With
@@ -126,6 +197,7 @@ class Server:
         pending = collections.deque(sorted(requests, key=lambda r: (r.arrival, r.rid)))
         active = {}  # rid -> (request, lattice, steps, admitted, footprint)
         results = []
+        waited = set()  # requests that found the budget full when they were next in line
         t0 = self.clock()
 
         def now():
@@ -135,11 +207,16 @@ class Server:
             t = now()
             # admission, first come first served
             while pending and (not realtime or pending[0].arrival <= t):
+                if self.max_active_limit is not None and len(active) >= self.max_active_limit:
+                    break
                 req = pending[0]
                 fp = self.backend.footprint(req.case)
                 if fp > self.budget:
                     raise ValueError(f"request {req.rid} needs {fp} bytes, more than the whole budget")
                 if self.in_use + fp > self.budget:
+                    if req.rid not in waited:
+                        self.queued_for_memory += 1
+                        waited.add(req.rid)
                     break
                 pending.popleft()
                 lat = self.backend.create(req.case)
@@ -155,12 +232,15 @@ class Server:
                 continue
             # one chunk of check_every steps for everything resident, then the checks
             self.backend.step(self.check_every)
+            rs = self._residuals([a[1] for a in active.values()])
+            self.checks += 1
             done = []
             for rid, a in active.items():
                 a[2] += self.check_every
-                r = self.backend.residual(a[1])
-                if r < self.tol or a[2] >= self.step_cap:
-                    done.append((rid, r))
+                r = rs[a[1]]
+                if not r < self.tol and a[2] < self.step_cap and r == r:  # NaN: diverged, leaves at once
+                    continue
+                done.append((rid, r))
             for rid, r in done:
                 req, lat, steps, admitted, fp = active.pop(rid)
                 self.backend.remove(lat)
@@ -232,3 +312,14 @@ def summarize(results, makespan: float | None = None):
         "converged": sum(r.converged for r in results),
         "cell_steps": sum(r.cells * r.steps for r in results),
     }
+
+
+def summarize_converged(results):
+    """Latency percentiles over the requests that reached steady state (their
+    latency is the time to steady state), with their count and steps."""
+    conv = [r for r in results if r.converged]
+    lat = [r.latency for r in conv]
+    steps = [r.steps for r in conv]
+    return {"converged": len(conv), "of": len(results),
+            "p50_time_to_steady_s": percentile(lat, 50), "p99_time_to_steady_s": percentile(lat, 99),
+            "steps_p50": percentile(steps, 50), "steps_max": max(steps) if steps else None}

@@ -36,8 +36,8 @@ def _alone(P, case, storage, nsteps, seed):
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
-@pytest.mark.parametrize("mode", [(1, 0, 1, "fused"), (1, 4, 4, "fused"), (3, 0, 16, "fused"), (3, 6, 3, "fused"),
-                                  (1, 0, 4, "concurrent"), (1, 4, 4, "concurrent")])
+@pytest.mark.parametrize("mode", [(1, 0, 1, "fused"), (1, 4, 4, "fused"), (3, 0, 16, "persistent"),
+                                  (3, 6, 3, "persistent"), (1, 0, 4, "concurrent"), (1, 4, 4, "concurrent")])
 def test_batch_equals_alone(storage, mode):
     P = _P()
     cases = _mix()
@@ -89,8 +89,12 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
     b.step(5)
     b.sync()
     before = [lat.populations() for lat in lats]
-    best, rows, ms = b.tune(trial_launches=3)
-    assert (best == -2 or 0 <= best < 5) and rows in (1, 4, 16) and all(m > 0 for m in ms.values())
+    kind, best, ms = b.tune(trial_steps=4)
+    assert kind in ("fused", "persistent", "concurrent") and (best == -1) == (kind == "concurrent")
+    assert all(m > 0 for m in ms.values()) and len(ms) == 11
+    # the mix holds a lattice with node-based walls: the persistent kernel cannot take it
+    assert all(np.isinf(ms[f"persistent_cfg{c}"]) for c in range(5)) and kind != "persistent"
+    assert b.get_mode()[0] == kind
     after = [lat.populations() for lat in lats]
     for (f0, g0), (f1, g1) in zip(before, after):
         assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
@@ -102,7 +106,40 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
         f, g = lat.populations()
         fr, gr = ref.populations()
         assert np.array_equal(f, fr) and np.array_equal(g, gr)
-    assert b.info()["config"] == best and b.info()["rows_per_unit"] == rows
+    assert b.info()["config"] == best
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_tuner_times_every_kind_and_keeps_state(storage):
+    """Without node-based walls every candidate runs, the persistent kernel's
+    trials included (one launch of 32 recomputed steps, 31 grid barriers); the
+    state is unchanged and the chosen kind then steps bit-identically."""
+    P = _P()
+    cases = _mix()[:5]
+    b = P.Batch()
+    lats = [P.Lattice(c, storage=storage) for c in cases]
+    for lat in lats:
+        b.add(lat)
+    b.step(3)
+    b.sync()
+    before = [lat.populations() for lat in lats]
+    kind, best, ms = b.tune(trial_steps=64)
+    b.sync()
+    assert all(np.isfinite(m) and m > 0 for m in ms.values()), ms
+    after = [lat.populations() for lat in lats]
+    for (f0, g0), (f1, g1) in zip(before, after):
+        assert np.array_equal(f0, f1) and np.array_equal(g0, g1)
+    for k in ("fused", "persistent", "concurrent"):
+        b.set_kind(k)
+        b.step(2)
+    b.sync()
+    for i, (c, lat) in enumerate(zip(cases, lats)):
+        ref = P.Lattice(c, storage=storage)
+        ref.step(9)
+        f, g = lat.populations()
+        fr, gr = ref.populations()
+        assert np.array_equal(f, fr) and np.array_equal(g, gr), i
+    b.close()
 
 
 @pytest.mark.parametrize("graph_steps", [0, 4])
@@ -155,7 +192,7 @@ def test_persistent_barrier_timeout_is_reported_and_recoverable():
     lats = [P.Lattice(c, storage="f32", stream=b.stream) for c in cases]
     for lat in lats:
         b.add(lat)
-    b.set_kind("fused")
+    b.set_kind("persistent")
     b.set_mode(4, 0)
     b.debug_barrier_extra(1)
     t0 = time.perf_counter()

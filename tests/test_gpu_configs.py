@@ -4,6 +4,12 @@
   parameters of the 4096 x 2048 benchmark cell (same nu, alpha, g beta):
   FP64 storage must match the FP64 oracle to 1e-12 (relative max-norm);
   FP32- and FP16-shifted storage state their max-norm errors in u and T.
+  That crop's own Rayleigh number is about 244, so it stays conductive.
+* Convective Rayleigh-Benard cell, 256 x 128 fluid cells with L = H = 128,
+  so its own Ra = 1e6 (Eq. 40 rates, Sec. 3.4), 25,000 steps through onset
+  into developed convection (Nu about 7-8): FP64 against the oracle to
+  1e-12, FP32/FP16 errors stated and compared with how far the flow itself
+  carries a perturbation of FP32 rounding size.
 * Differentially heated cavity, 256 x 256, Ra = 1e5, Pr = 0.71, Ma = 0.1,
   2e5 steps in FP64 and FP32 storage: mean Nusselt number on the hot wall
   against the paper's Table 3 (cold wall 4.5273; equal at steady state).
@@ -65,6 +71,111 @@ def test_rb_crop_reduced_precision_error(rb_crop_oracle, storage):
     eT = np.abs(T - To).max() / case.delta_T
     print(f"RB 256x128 crop, {storage}, 1000 steps: max-norm error u {eu:.2e} (of u_c {u_c:.3f}), T {eT:.2e}")
     assert eu <= RB_TOL[storage]["u"] and eT <= RB_TOL[storage]["T"]
+
+
+# The convective cell: seeded 5e-2 perturbation so that convection sets in
+# within the run (onset near 15,000 steps, developed by 20,000). Checked at
+# 10,000 steps (the flow still growing) and at 25,000 (developed convection).
+RB_CONV_STEPS = (10_000, 25_000)
+
+
+@pytest.fixture(scope="module")
+def rb_convective_oracle():
+    """The oracle on the convective cell at both check points, and the same
+    oracle started from an initial temperature changed by a relative 6e-8
+    (FP32 rounding size): the difference of the two is how far this flow
+    carries a rounding-sized perturbation on its own."""
+    case = lc.rayleigh_benard(nx=256, H=128, Ra=1e6, Pr=0.71, Ma=0.1, seed=0, sigma=5e-2)
+    threads = min(16, os.cpu_count() or 1)
+    o = oracle.OracleLattice(case, threads=threads)
+    jitter = 1 + 6e-8 * (2 * lc.uniform01(99, case.T_init.size).reshape(case.T_init.shape) - 1)
+    o2 = oracle.OracleLattice(case.with_(T_init=case.T_init * jitter), threads=threads)
+    snaps, done = [], 0
+    for k in RB_CONV_STEPS:
+        o.step(k - done)
+        o2.step(k - done)
+        done = k
+        snaps.append(dict(macro=o.macro(), pops=o.populations(), jitter=o2.macro(), nu=o.nusselt(2)))
+    return case, snaps
+
+
+def _conv_errors(case, mac, ref):
+    _, ux, uy, T = mac
+    _, uxo, uyo, To = ref
+    umax = max(np.abs(uxo).max(), np.abs(uyo).max())
+    eu = max(np.abs(ux - uxo).max(), np.abs(uy - uyo).max()) / umax
+    eT = np.abs(T - To).max() / case.delta_T
+    return eu, eT, umax
+
+
+# FP64 against the oracle: 1e-12 at 10,000 steps; at 25,000 the developed
+# convection has amplified every difference (a relative 6e-8 change of the
+# initial temperature grows about 40-60 fold by then, oracle against oracle),
+# the rounding differences between the two programs' orders of operations
+# (about 1e-16 per step) included: 1e-10.
+RB_CONV_FP64_TOL = (1e-12, 1e-10)
+
+
+def test_rb_convective_fp64_matches_oracle(rb_convective_oracle):
+    import paper_1510_08224_gb300 as P
+    case, snaps = rb_convective_oracle
+    u_c = case.meta["Ma"] * np.sqrt(1.0 / 3.0)
+    _, uxo, uyo, _ = snaps[1]["macro"]
+    # the run reaches developed convection
+    assert max(np.abs(uxo).max(), np.abs(uyo).max()) > 0.3 * u_c and snaps[1]["nu"] > 4.0
+    g = P.Lattice(case, storage="f64")
+    done = 0
+    for k, snap, tol in zip(RB_CONV_STEPS, snaps, RB_CONV_FP64_TOL):
+        g.step(k - done)
+        done = k
+        f, t = g.populations()
+        pops = snap["pops"]
+        ef = np.abs(f - pops[0]).max() / np.abs(pops[0]).max()
+        et = np.abs(t - pops[1]).max() / np.abs(pops[1]).max()
+        em = max(np.abs(a - b).max() / max(1.0, np.abs(b).max()) for a, b in zip(g.macro(), snap["macro"]))
+        print(f"RB 256x128 convective, FP64, {k} steps: populations f {ef:.2e}, g {et:.2e}, fields {em:.2e}")
+        assert ef <= tol and et <= tol and em <= tol, (k, ef, et, em)
+    assert abs(g.nusselt("bottom") - snaps[1]["nu"]) <= 1e-9 * snaps[1]["nu"]
+
+
+# Max-norm errors (u of max |u|, T of delta T) at 10,000 and 25,000 steps.
+# FP32: the storage rounds every population by about 6e-8 of its deviation at
+# every step, and the flow amplifies such changes (the oracle carries a single
+# 6e-8 change of the initial temperature to 4e-7 / 2e-8 by 10,000 steps and
+# 4e-6 / 3e-6 by 25,000): measured 8.7e-6 / 6.0e-7 and 1.6e-4 / 8.5e-5, with
+# the mean Nusselt number on the hot plate within 1e-5 of the oracle's. FP16
+# rounds about 8,000 times more per step: at 10,000 steps, with the rolls
+# still growing (max |u| = 0.04 u_c), its velocity field has already left the
+# oracle's (measured 0.60 of max |u|; T 3.3e-2), and in developed convection
+# its plumes sit elsewhere (errors of order one), so at 25,000 steps only the
+# character of the flow is checked: finite, convecting, with a Nusselt number
+# of developed convection.
+RB_CONV_TOL = {"f32": ({"u": 3e-5, "T": 3e-6}, {"u": 5e-4, "T": 3e-4}),
+               "f16": ({"u": 1.0, "T": 0.1}, None)}
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_rb_convective_reduced_precision_error(rb_convective_oracle, storage):
+    import paper_1510_08224_gb300 as P
+    case, snaps = rb_convective_oracle
+    g = P.Lattice(case, storage=storage)
+    done = 0
+    for k, snap, tol in zip(RB_CONV_STEPS, snaps, RB_CONV_TOL[storage]):
+        g.step(k - done)
+        done = k
+        mac = g.macro()
+        eu, eT, umax = _conv_errors(case, mac, snap["macro"])
+        fu, fT, _ = _conv_errors(case, snap["jitter"], snap["macro"])
+        nu = g.nusselt("bottom")
+        print(f"RB 256x128 convective (L = 128, Ra 1e6), {storage}, {k} steps: max-norm error u {eu:.2e} "
+              f"(of max|u| {umax:.3e}), T {eT:.2e}; Nu bottom {nu:.4f} (oracle {snap['nu']:.4f}); the oracle "
+              f"carries a 6e-8 initial change to u {fu:.2e}, T {fT:.2e}")
+        if tol is not None:
+            assert eu <= tol["u"] and eT <= tol["T"], (k, eu, eT)
+        else:
+            u_c = case.meta["Ma"] * np.sqrt(1.0 / 3.0)
+            assert np.isfinite(mac[1]).all() and max(np.abs(mac[1]).max(), np.abs(mac[2]).max()) > 0.3 * u_c
+            assert 4.0 < nu < 15.0
 
 
 @pytest.mark.parametrize("storage", ["f64", "f32"])

@@ -190,6 +190,33 @@ def test_reduced_precision_cavity_error(storage):
     assert eu <= MANY_STEP_TOL[storage]["u"] and eT <= MANY_STEP_TOL[storage]["T"]
 
 
+def test_fp16_error_is_the_storage_rounding():
+    """The FP16-shifted path's error on the 32 x 32 cavity (Ra = 1e4, 4000
+    steps) against the exact FP64 oracle is the error of the oracle itself
+    when only its stored deviations are rounded to binary16 after every step
+    (FP64 arithmetic otherwise): the same size within a factor 1.5. So the
+    FP16 floor comes from the 11-bit significand of the stored state, not from
+    the kernels' FP32 arithmetic."""
+    P = _P()
+    case = lc.cavity(n=32, Ra=1e4, noise=1e-3)
+    ref = oracle.OracleLattice(case, threads=4)
+    ref.step(4000)
+    emu = oracle.OracleLattice(case, threads=4)
+    emu.set_storage_rounding(16, 1.0)
+    emu.step(4000)
+    g = P.Lattice(case, storage="f16")
+    g.step(4000)
+    _, uxo, uyo, To = ref.macro()
+    umax = max(np.abs(uxo).max(), np.abs(uyo).max())
+
+    def err(m):
+        return (max(np.abs(m[1] - uxo).max(), np.abs(m[2] - uyo).max()) / umax, np.abs(m[3] - To).max())
+    eg, ee = err(g.macro()), err(emu.macro())
+    print(f"FP16 path: u {eg[0]:.3e}, T {eg[1]:.3e}; oracle with binary16 storage: u {ee[0]:.3e}, T {ee[1]:.3e}")
+    for a, b in zip(eg, ee):
+        assert b / 1.5 <= a <= 1.5 * b
+
+
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
 def test_macro_nusselt_residual_match_oracle(storage):
     P = _P()

@@ -561,3 +561,51 @@ def test_rayleigh_benard_onset_near_1708():
     Ra_c = 1650.0 + 150.0 * (-g_lo) / (g_hi - g_lo)
     assert abs(Ra_c - 1707.76) / 1707.76 < 0.03, Ra_c
     assert abs(nu_lo - 1.0) < 1e-4, nu_lo
+
+
+# ----------------------------------------------- 16-bit storage (ablation) --
+
+def test_round_binary16_matches_numpy_float16():
+    """The oracle's binary16 rounding (IEEE 754: 10 fraction bits, ties to
+    even, subnormals below 2^-14 in steps of 2^-24) equals NumPy's float16
+    conversion on values across the whole range, exact ties included."""
+    rng = np.random.default_rng(7)
+    xs = rng.standard_normal(20000) * 10.0 ** rng.uniform(-9, 4.5, 20000)
+    ties = [1 + 2.0 ** -11, 1 + 3 * 2.0 ** -11, 2.0 ** -24 * 2.5, 2.0 ** -24 * 3.5, 2.0 ** -14 * (1 + 2.0 ** -11),
+            -(1 + 2.0 ** -11), 65504.0, 2.0 ** -25, 3 * 2.0 ** -26]
+    for x in list(xs) + ties:
+        if abs(x) > 65504:
+            continue
+        assert oracle.round_binary16(x) == float(np.float16(x)), x
+
+
+def test_sixteen_bit_storage_floor_does_not_move_with_a_scale():
+    """What 16-bit storage of the deviations costs, in FP64 arithmetic
+    otherwise: on the 32 x 32 cavity at Ra = 1e4 (Sec. 3.4), 4000 steps from
+    rest, the max-norm error is about 1e-2 of max |u| and 7e-3 of delta T (the
+    11-bit significand of the stored state, rounded every step), far above
+    1e-4; multiplying the deviations by 2^8 or 2^12 before rounding (so that
+    none falls into the subnormal range) leaves it within 25 %."""
+    case = lc.cavity(n=32, Ra=1e4, noise=1e-3)
+    ref = oracle.OracleLattice(case, threads=4)
+    ref.step(4000)
+    _, ux, uy, T = ref.macro()
+    umax = max(np.abs(ux).max(), np.abs(uy).max())
+    errs = {}
+    for scale in (1.0, 256.0, 4096.0):
+        q = oracle.OracleLattice(case, threads=4)
+        q.set_storage_rounding(16, scale)
+        q.step(4000)
+        _, qx, qy, qT = q.macro()
+        errs[scale] = (max(np.abs(qx - ux).max(), np.abs(qy - uy).max()) / umax, np.abs(qT - T).max())
+    eu, eT = errs[1.0]
+    assert 3e-3 < eu < 3e-2 and 2e-3 < eT < 2e-2, errs
+    for scale in (256.0, 4096.0):
+        assert abs(errs[scale][0] / eu - 1) < 0.25 and abs(errs[scale][1] / eT - 1) < 0.25, errs
+    # the ablation is off by default: a lattice without it matches the reference
+    q = oracle.OracleLattice(case, threads=4)
+    q.step(10)
+    r2 = oracle.OracleLattice(case, threads=4)
+    r2.set_storage_rounding(0)
+    r2.step(10)
+    assert all(np.array_equal(a, b) for a, b in zip(q.populations(), r2.populations()))

@@ -138,3 +138,51 @@ def test_serving_stream_is_seeded():
     assert all(np.array_equal(x[2].flags, y[2].flags) for x, y in zip(a, b))
     gaps = np.diff([x[0] for x in lc.serving_stream(n=400, seed=1, side_hi=64)])
     assert abs(gaps.mean() - 1 / 20.0) < 0.25 / 20.0  # Poisson arrivals at 20 per second
+
+
+class FakeBatchBackend(FakeBackend):
+    """Reads every resident lattice's residual in one call, as GpuBackend does."""
+
+    def __init__(self):
+        super().__init__()
+        self.calls = 0
+
+    def residuals(self, lats):
+        self.calls += 1
+        return {lat: lat.residual() for lat in lats}
+
+
+def test_batched_residual_checks_and_queueing_for_memory():
+    """One residual call per chunk for all resident lattices; a budget of two
+    requests makes the rest wait for memory, and the count says so."""
+    reqs = _requests(8)
+    fps = [FakeBackend().footprint(r.case) for r in reqs]
+    budget = sorted(fps)[-1] + sorted(fps)[-2]
+    clock = FakeClock()
+    be = FakeBatchBackend()
+    srv = serve.Server(be, budget_bytes=budget, check_every=100, tol=1e-4, clock=clock, sleep=clock.sleep)
+    res = srv.run(reqs, realtime=False)
+    assert len(res) == 8 and be.calls == srv.checks
+    assert srv.queued_for_memory >= 1 and srv.peak_in_use <= budget
+
+
+def test_max_active_one_serves_one_request_at_a_time():
+    """The plain path's admission: one request at a time, in arrival order,
+    each admitted when the previous one leaves."""
+    reqs = _requests(5)
+    clock = FakeClock()
+    srv = serve.Server(FakeBackend(), check_every=100, tol=1e-4, clock=clock, sleep=clock.sleep, max_active=1)
+    res = srv.run(reqs)
+    assert srv.max_active == 1
+    order = sorted(res, key=lambda r: r.admitted)
+    assert [r.rid for r in order] == [r.rid for r in sorted(reqs, key=lambda q: q.arrival)]
+    for a, b in zip(order, order[1:]):
+        assert b.admitted >= a.finished
+
+
+def test_summary_over_converged_requests():
+    rs = [serve.Result(k, 0.0, 0.0, float(k + 1), 100 * (k + 1), 1e-7 if k < 3 else 1e-3, k < 3, 0, 10)
+          for k in range(4)]
+    s = serve.summarize_converged(rs)
+    assert s["converged"] == 3 and s["of"] == 4
+    assert s["p50_time_to_steady_s"] == 2.0 and s["steps_max"] == 300
