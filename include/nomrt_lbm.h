@@ -133,12 +133,26 @@ typedef struct lbm_lattice lbm_lattice; /* opaque; owned by the library */
  * Admission control uses it. Rows are padded to a pitch of 128 bytes of
  * storage (nx rounded up to a multiple of 16 / 32 / 64 for FP64 / FP32 / FP16);
  * ny * pitch must stay below 2^31, so the largest FP16 lattice is about
- * 2.1e9 cells (178 GB with the residual snapshot). */
+ * 2.1e9 cells (178 GB with the residual snapshot). The scalar parameters are
+ * always checked; the flag map only where the size depends on it (a lattice
+ * with node-based walls, whose boundary nodes take space): lbm_create and
+ * lbm_validate check every flag map. */
 size_t lbm_footprint_bytes(const lbm_params *p);
+
+/* Every check lbm_create makes, on the host, without touching a GPU: the
+ * scalar parameters and the flag map (wall ids within n_walls, a solid frame
+ * on non-periodic edges, every fluid cell with a fluid neighbour, every
+ * boundary node of a node-based wall with a fluid neighbour). LBM_OK, or
+ * LBM_EINVAL with lbm_last_error(NULL) naming the first invalid cell in
+ * row-major order -- the message lbm_create gives for the same map. */
+lbm_status lbm_validate(const lbm_params *p);
 
 /* Validate p, upload flags, walls and T_init, and set the initial state
  * f_bar_i = w_i rho0, g_i = g_eq_i(T_init, u = 0) of Eqs. 22 and 30 (solid cells
- * hold zeros). cuda_stream: a cudaStream_t, NULL for the legacy default stream.
+ * hold zeros). Where every wall is halfway, the link map is built and the flag
+ * map checked on the GPU (an invalid map is reported as lbm_validate reports
+ * it); flags and T_init in page-locked (or device) memory are read in place,
+ * pageable ones are copied. cuda_stream: a cudaStream_t, NULL for the legacy default stream.
  * device_mem: NULL to let the library allocate, else a caller-owned device block
  * of at least lbm_footprint_bytes(p) bytes, 256-byte aligned, that must outlive
  * the lattice. On error *out is NULL and lbm_last_error(NULL) gives the reason.
@@ -148,10 +162,11 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
 
 /* Advance nsteps >= 0 time steps (Eqs. 8-9 and 24-25, fused, one kernel per
  * step, plus one for the boundary nodes of node-based walls). Asynchronous on the
- * lattice's stream. Runs of 64 steps or more replay a CUDA graph of 32 steps
- * captured once per step-kernel choice (the same kernels and bits, without the
- * launch gap between steps); shorter runs, and calls on a stream that is being
- * captured, launch the kernels directly. */
+ * lattice's stream. Runs of 4 steps or more replay CUDA graphs of 32 and of 4
+ * steps, captured once per step-kernel choice (the same kernels and bits,
+ * without the launch gap between steps; a step launched directly first where
+ * the graphs' starting buffer needs it); shorter runs and the remainder, and
+ * calls on a stream that is being captured, launch the kernels directly. */
 lbm_status lbm_step(lbm_lattice *h, int64_t nsteps);
 
 /* Wait for the lattice's stream. LBM_ETIMEOUT if a step kernel gave up one of
@@ -294,7 +309,10 @@ lbm_status lbm_probe_fp64_rate(void *cuda_stream, double *dfma_per_s);
  * progress. Members are gathered into launch groups of up to 64 lattices
  * whose kinetic rates (s_e, s_q, s_eps, zeta_e, zeta_nu, varpi) agree; a
  * group's descriptors travel in the launch's parameter block. The batch
- * allocates two small device words (grid barrier, status) with cudaMalloc. */
+ * allocates with cudaMalloc two small device words (grid barrier, status) and
+ * a work table of 8 bytes per 512-cell row segment of its members (where each
+ * block of the batch kernels finds its member, segment and row), regrown when
+ * membership changes. */
 typedef struct lbm_batch lbm_batch;
 
 /* cuda_stream: the stream every member uses (NULL = legacy default stream). */

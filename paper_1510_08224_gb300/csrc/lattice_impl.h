@@ -45,13 +45,14 @@ struct lbm_lattice {
     int have_snap = 0;
     int64_t fluid = 0;
     int64_t steps = 0;
-    std::vector<uint8_t> flags;
+    int across_x = 0, across_y = 0;  // fluid cells of the middle row / column (lbm_nusselt's default L)
     std::string err;
     const nomrt::Launchers *L = nullptr;
     lbm_batch *batch = nullptr;  // the batch that steps this lattice, if any
-    // lbm_step replays kGraphSteps steps from buffer 0 as one CUDA graph once the current
-    // step kernel has run directly; reset when the kernel choice changes
-    cudaGraphExec_t graph = nullptr;
+    // lbm_step replays graphs of kGraphSteps and kGraphShort steps from buffer 0 once the
+    // current step kernel has run directly; reset when the kernel choice changes
+    cudaGraphExec_t graph = nullptr;        // kGraphSteps steps
+    cudaGraphExec_t graph_short = nullptr;  // kGraphShort steps
     cudaStream_t cap_stream = nullptr;  // private stream the graph is captured on (any stream can launch it)
     int graph_variant = -1, graph_config = -1;
     bool graph_off = false;       // capture failed or the stream cannot be captured

@@ -208,21 +208,21 @@ cudaError_t launch_step_variant(const KParams &p, int variant, int src, cudaStre
 template <typename S>
 cudaError_t launch_init_rows(const KParams &p, int buf, int r0, int r1, const double *T, cudaStream_t st) {
     const dim3 grid((p.pitch + 127) / 128, r1 - r0);
-    k_init_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, T, p.T_ref, p.varpi,
+    k_init_rows<S><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), r0, r1, T, p.T0, p.T_ref, p.varpi,
                                          Store<S>::kShifted ? 1 : 0, p.tq);
     return cudaGetLastError();
 }
 
 template <typename S>
-cudaError_t launch_macro_rows(const KParams &p, int buf, int r0, int r1, double *out, cudaStream_t st) {
+cudaError_t launch_macro_rows(const KParams &p, int buf, int r0, int r1, double *const out[4], cudaStream_t st) {
     using C = typename Store<S>::C;
     const dim3 grid((p.nx + 127) / 128, r1 - r0);
     if (p.tq == 9)
         k_macro_rows<S, 9><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p), r0, r1,
-                                                 p.rho_ref, p.T_ref, out);
+                                                 p.rho_ref, p.T_ref, out[0], out[1], out[2], out[3]);
     else
         k_macro_rows<S, 5><<<grid, 128, 0, st>>>(make_planes<S>(p, buf), make_geom(p), make_rates<C>(p), r0, r1,
-                                                 p.rho_ref, p.T_ref, out);
+                                                 p.rho_ref, p.T_ref, out[0], out[1], out[2], out[3]);
     return cudaGetLastError();
 }
 

@@ -33,6 +33,8 @@ constexpr size_t kStageBytes = 16u << 20;  // row-chunked host transfers
 
 const int kEx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};  // Eq. 5
 const int kEy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+__constant__ int kExD[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+__constant__ int kEyD[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 const double kW[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
@@ -402,24 +404,28 @@ lbm_status check_status(lbm_lattice *h) {
         if (s_ != LBM_OK) return s_;       \
     } while (0)
 
-constexpr int kGraphSteps = 32;  // steps per replayed graph (even: it starts and ends on buffer 0)
+// Steps per replayed graph: a long one and a short one (both even: a graph starts and ends on
+// buffer 0), so that runs from kGraphShort steps up replay graphs.
+constexpr int kGraphSteps = 32;
+constexpr int kGraphShort = 4;
 
 void drop_graph(lbm_lattice *h) {
     if (h->graph) cudaGraphExecDestroy(h->graph);
+    if (h->graph_short) cudaGraphExecDestroy(h->graph_short);
     h->graph = nullptr;
+    h->graph_short = nullptr;
 }
 
-// Captures kGraphSteps steps starting from buffer 0 on a private stream (the lattice's own
-// stream may be the legacy default stream, which cannot be captured; the graph launches on
-// any stream). On any failure the lattice falls back to direct launches for good (the
-// error is cleared).
-void capture_graph(lbm_lattice *h) {
+// Captures `steps` steps starting from buffer 0 on a private stream (the lattice's own stream
+// may be the legacy default stream, which cannot be captured; the graph launches on any
+// stream). nullptr on failure (the error is cleared).
+cudaGraphExec_t capture_steps(lbm_lattice *h, int steps) {
     cudaGraph_t g = nullptr;
     cudaGraphExec_t ge = nullptr;
     bool ok = h->cap_stream || cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) == cudaSuccess;
     if (ok) ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (ok) {
-        for (int s = 0; s < kGraphSteps && ok; ++s) ok = h->L->step(h->kp, s & 1, h->cap_stream) == cudaSuccess;
+        for (int s = 0; s < steps && ok; ++s) ok = h->L->step(h->kp, s & 1, h->cap_stream) == cudaSuccess;
         ok = (cudaStreamEndCapture(h->cap_stream, &g) == cudaSuccess) && ok && g;
     }
     if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
@@ -427,10 +433,21 @@ void capture_graph(lbm_lattice *h) {
     if (!ok) {
         if (ge) cudaGraphExecDestroy(ge);
         cudaGetLastError();
+        return nullptr;
+    }
+    return ge;
+}
+
+// Both graphs for the current kernel choice; on any failure the lattice falls back to
+// direct launches for good.
+void capture_graph(lbm_lattice *h) {
+    h->graph = capture_steps(h, kGraphSteps);
+    h->graph_short = h->graph ? capture_steps(h, kGraphShort) : nullptr;
+    if (!h->graph || !h->graph_short) {
+        drop_graph(h);
         h->graph_off = true;
         return;
     }
-    h->graph = ge;
     h->graph_variant = h->kp.variant;
     h->graph_config = h->kp.config;
 }
@@ -446,9 +463,102 @@ lbm_status step_direct(lbm_lattice *h, int64_t n) {
     return LBM_OK;
 }
 
+// The device-side maps of a lattice whose walls are all halfway (no node-based
+// wall, so the layout does not depend on the flag map): one thread per cell of
+// the pitched layout reads the wall ids of the cell and of its eight pull
+// sources from `src` (row stride src_stride; the pitched flag plane itself,
+// or the caller's raw map read in place), and writes the pitched flag plane
+// (copy = 1), the link map (bit i-1: direction i pulls from a solid cell;
+// 0xFF for solid cells and the padding columns) and a zero boundary-node
+// direction. Validation as the host scan: a wall id above n_walls, a fluid
+// cell pulling from beyond a non-periodic edge, a fluid cell with no fluid
+// neighbour; the lowest such cell index (row-major) goes to *first_bad, and the
+// fluid cells are counted into *fluid.
+__global__ void __launch_bounds__(256) k_build_maps(const uint8_t *src, long long src_stride, int copy, int nx, int ny,
+                                                    int y0, int pitch, int px, int py, int n_walls, uint8_t *flags,
+                                                    uint8_t *mask, uint8_t *nee_dir,
+                                                    unsigned long long *first_bad, unsigned long long *fluid) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = y0 + (int)blockIdx.y;  // rows y0 .. y0 + gridDim.y - 1 of the whole lattice
+    __shared__ unsigned count;
+    if (threadIdx.x == 0) count = 0;
+    __syncthreads();
+    if (x < pitch && y < ny) {
+        const size_t off = (size_t)y * pitch + x;
+        uint8_t m = nomrt::kSolid;
+        uint8_t k = 0;
+        if (x < nx) {
+            k = src[(long long)y * src_stride + x];
+            bool bad = k > n_walls;
+            if (k == 0) {
+                unsigned bits = 0;
+                for (int i = 1; i < 9; ++i) {
+                    int sx = x - kExD[i], sy = y - kEyD[i];
+                    if (px) sx = sx < 0 ? sx + nx : (sx >= nx ? sx - nx : sx);
+                    if (py) sy = sy < 0 ? sy + ny : (sy >= ny ? sy - ny : sy);
+                    if (sx < 0 || sx >= nx || sy < 0 || sy >= ny) {
+                        bad = true;
+                        break;
+                    }
+                    if (src[(long long)sy * src_stride + sx] != 0) bits |= 1u << (i - 1);
+                }
+                bad = bad || bits == 0xFFu;
+                m = (uint8_t)bits;
+                if (!bad) atomicAdd(&count, 1u);
+            }
+            if (bad) atomicMin(first_bad, (unsigned long long)y * (unsigned long long)nx + (unsigned long long)x);
+        }
+        if (copy) flags[off] = k;
+        else if (x >= nx) flags[off] = 0;
+        mask[off] = m;
+        nee_dir[off] = 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && count) atomicAdd(fluid, (unsigned long long)count);
+}
+
+// A device address through which the GPU reads `p` in place (page-locked or
+// registered host memory, managed or device memory), or nullptr for ordinary
+// pageable host memory.
+const void *device_view(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged || a.type == cudaMemoryTypeDevice)
+        return a.devicePointer;
+    return nullptr;
+}
+
+bool all_walls_halfway(const lbm_params *p) {
+    for (int k = 0; k < p->n_walls; ++k)
+        if (p->walls[k].scheme != LBM_WALL_HALFWAY) return false;
+    return true;
+}
+
+// Fluid cells of the middle line across the lattice along the normal of `side`
+// (the default length of lbm_nusselt).
+void middle_lines(const lbm_params *p, int *across_x, int *across_y) {
+    int cx = 0, cy = 0;
+    const int y = p->ny / 2, x = p->nx / 2;
+    for (int i = 0; i < p->nx; ++i) cx += p->flags[(size_t)y * p->nx + i] == 0;
+    for (int j = 0; j < p->ny; ++j) cy += p->flags[(size_t)j * p->nx + x] == 0;
+    *across_x = cx;
+    *across_y = cy;
+}
+
 }  // namespace
 
 extern "C" {
+
+lbm_status lbm_validate(const lbm_params *p) {
+    std::string why = validate(p);
+    if (!why.empty()) return fail(nullptr, LBM_EINVAL, why);
+    ScanResult sr = scan_cells(p, nullptr);
+    if (!sr.err.empty()) return fail(nullptr, LBM_EINVAL, sr.err);
+    return LBM_OK;
+}
 
 size_t lbm_footprint_bytes(const lbm_params *p) {
     std::string why = validate(p);
@@ -456,12 +566,16 @@ size_t lbm_footprint_bytes(const lbm_params *p) {
         g_create_error = why;
         return 0;
     }
-    ScanResult sr = scan_cells(p, nullptr);
-    if (!sr.err.empty()) {
-        g_create_error = sr.err;
-        return 0;
+    int n_nee = 0;
+    if (!all_walls_halfway(p)) {  // the boundary nodes of node-based walls take space: count them
+        ScanResult sr = scan_cells(p, nullptr);
+        if (!sr.err.empty()) {
+            g_create_error = sr.err;
+            return 0;
+        }
+        n_nee = (int)sr.nee.size();
     }
-    return make_layout(p->nx, p->ny, p->storage, p->n_walls, (int)sr.nee.size(), thermal_q(p)).total;
+    return make_layout(p->nx, p->ny, p->storage, p->n_walls, n_nee, thermal_q(p)).total;
 }
 
 lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, size_t device_bytes,
@@ -479,30 +593,37 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     h->storage = p->storage;
     h->n_walls = p->n_walls;
     h->stream = static_cast<cudaStream_t>(cuda_stream);
-    // host-side maps in one pass over the cells (which also validates them): wall ids, the
-    // link map (bit i-1: direction i pulls from a solid cell; padding and solid cells 0xFF)
-    // and the boundary nodes of node-based walls
     const int pitch0 = (int)align_up((size_t)p->nx, 128 / elem_bytes(p->storage));
     const size_t map_bytes = (size_t)p->ny * pitch0;
-    // written in full by the scan (padding columns included), so left uninitialised here
-    std::unique_ptr<uint8_t[]> hmask(new (std::nothrow) uint8_t[map_bytes]),
-        hflags(new (std::nothrow) uint8_t[map_bytes]);
-    if (!hmask || !hflags) {
-        lbm_destroy(h);
-        return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+    // Lattices with node-based walls: host-side maps in one pass over the cells (which also
+    // validates them): wall ids, the link map (bit i-1: direction i pulls from a solid cell;
+    // padding and solid cells 0xFF) and the boundary nodes. Every other lattice builds its
+    // maps on the GPU (k_build_maps), from the flag map read in place when the GPU can.
+    const bool gpu_maps = all_walls_halfway(p);
+    std::unique_ptr<uint8_t[]> hmask, hflags;
+    std::vector<int2> hnee;
+    if (!gpu_maps) {
+        // written in full by the scan (padding columns included), so left uninitialised here
+        hmask.reset(new (std::nothrow) uint8_t[map_bytes]);
+        hflags.reset(new (std::nothrow) uint8_t[map_bytes]);
+        if (!hmask || !hflags) {
+            lbm_destroy(h);
+            return fail(nullptr, LBM_ENOMEM, "host allocation failed");
+        }
+        CellScan cs;
+        cs.pitch = pitch0;
+        cs.mask = hmask.get();
+        cs.flags = hflags.get();
+        ScanResult sr = scan_cells(p, &cs);
+        if (!sr.err.empty()) {
+            lbm_destroy(h);
+            return fail(nullptr, LBM_EINVAL, sr.err);
+        }
+        hnee.swap(sr.nee);
+        h->fluid = sr.fluid;
     }
-    CellScan cs;
-    cs.pitch = pitch0;
-    cs.mask = hmask.get();
-    cs.flags = hflags.get();
-    ScanResult sr = scan_cells(p, &cs);
-    if (!sr.err.empty()) {
-        lbm_destroy(h);
-        return fail(nullptr, LBM_EINVAL, sr.err);
-    }
-    std::vector<int2> &hnee = sr.nee;
+    middle_lines(p, &h->across_x, &h->across_y);
     const int n_nee = (int)hnee.size();
-    h->fluid = sr.fluid;
     h->lay = make_layout(p->nx, p->ny, p->storage, p->n_walls, n_nee, thermal_q(p));
     h->L = &launchers_for(p->storage);
     const size_t need = h->lay.total;
@@ -528,7 +649,6 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
     }
 
     const int nx = p->nx, ny = p->ny, pitch = h->lay.pitch;
-    h->flags.assign(p->flags, p->flags + (size_t)nx * ny);
     std::vector<WallDev> hw((size_t)p->n_walls + 1);
     std::memset(hw.data(), 0, sizeof(WallDev) * hw.size());
     const double T_ref = p->storage == LBM_F64 ? 0.0 : p->T0;
@@ -604,13 +724,44 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
         return bail(LBM_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
     };
     cudaError_t e;
-    if ((e = cudaMemsetAsync(h->mem, 0, need, st)) != cudaSuccess) return cuda_bail(e, "memset");
-    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_mask, hmask.get(), map_bytes, cudaMemcpyHostToDevice, st)) !=
-        cudaSuccess)
-        return cuda_bail(e, "upload link map");
-    if ((e = cudaMemcpyAsync(h->mem + h->lay.off_flags, hflags.get(), map_bytes, cudaMemcpyHostToDevice, st)) !=
-        cudaSuccess)
-        return cuda_bail(e, "upload flags");
+    // zeros where they must start: the status words
+    if ((e = cudaMemsetAsync(h->mem + h->lay.off_status, 0, kAlign, st)) != cudaSuccess)
+        return cuda_bail(e, "clear status");
+    unsigned long long *counters = reinterpret_cast<unsigned long long *>(h->result());  // first bad cell, fluid
+    if (gpu_maps) {
+        if ((e = cudaMemsetAsync(counters, 0xFF, sizeof(unsigned long long), st)) != cudaSuccess ||
+            (e = cudaMemsetAsync(counters + 1, 0, sizeof(unsigned long long), st)) != cudaSuccess)
+            return cuda_bail(e, "clear counters");
+        uint8_t *dflags = reinterpret_cast<uint8_t *>(h->mem + h->lay.off_flags);
+        const uint8_t *src = static_cast<const uint8_t *>(device_view(p->flags));
+        long long stride = nx;
+        int copy = 1;
+        if (!src) {  // pageable: copy the map into the pitched flag plane, then build in place
+            if ((e = cudaMemcpy2DAsync(dflags, (size_t)pitch, p->flags, (size_t)nx, (size_t)nx, (size_t)ny,
+                                       cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_bail(e, "upload flags");
+            src = dflags;
+            stride = pitch;
+            copy = 0;
+        }
+        for (int y0 = 0; y0 < ny; y0 += 65535) {  // the grid's y extent is at most 65535 rows per launch
+            const int rows = std::min(65535, ny - y0);
+            const dim3 grid((unsigned)((pitch + 255) / 256), (unsigned)rows);
+            k_build_maps<<<grid, 256, 0, st>>>(src, stride, copy, nx, ny, y0, pitch, h->px, h->py, p->n_walls, dflags,
+                                              const_cast<uint8_t *>(kp.mask), const_cast<uint8_t *>(kp.nee_dir),
+                                              counters, counters + 1);
+            if ((e = cudaGetLastError()) != cudaSuccess) return cuda_bail(e, "map kernel");
+        }
+    } else {
+        if ((e = cudaMemsetAsync(h->mem + h->lay.off_nee_dir, 0, map_bytes, st)) != cudaSuccess)
+            return cuda_bail(e, "clear boundary-node directions");
+        if ((e = cudaMemcpyAsync(h->mem + h->lay.off_mask, hmask.get(), map_bytes, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+            return cuda_bail(e, "upload link map");
+        if ((e = cudaMemcpyAsync(h->mem + h->lay.off_flags, hflags.get(), map_bytes, cudaMemcpyHostToDevice, st)) !=
+            cudaSuccess)
+            return cuda_bail(e, "upload flags");
+    }
     if ((e = cudaMemcpyAsync(h->mem + h->lay.off_walls, hw.data(), sizeof(WallDev) * hw.size(),
                              cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return cuda_bail(e, "upload walls");
@@ -625,26 +776,49 @@ lbm_status lbm_create(const lbm_params *p, void *cuda_stream, void *device_mem, 
                                  cudaMemcpyHostToDevice, st)) != cudaSuccess)
             return cuda_bail(e, "upload boundary nodes");
     }
-    // initial state from T in row chunks through the staging area, which holds nq rows of
-    // populations and so stage_rows * nq rows of T. Stream order keeps a chunk's upload
-    // behind the previous chunk's init kernel; one wait at the end covers the host buffers.
-    const int t_rows = (int)std::min<size_t>({(size_t)ny, (size_t)h->lay.stage_rows * h->lay.nq, (size_t)65535});
-    std::vector<double> Tconst;
-    if (!p->T_init) {
-        Tconst.assign((size_t)t_rows * nx, p->T0);
-        if ((e = cudaMemcpyAsync(h->stage(), Tconst.data(), Tconst.size() * sizeof(double), cudaMemcpyHostToDevice,
-                                 st)) != cudaSuccess)
-            return cuda_bail(e, "upload T0");
+    // initial state (and zeros in the other buffer): T read in place when the GPU can reach it
+    // (or T0 everywhere), else in row chunks through the staging area, which holds nq rows of
+    // populations and so stage_rows * nq rows of T. Stream order keeps a chunk's upload behind
+    // the previous chunk's init kernel; one wait at the end covers the host buffers.
+    const double *Tv = p->T_init ? static_cast<const double *>(device_view(p->T_init)) : nullptr;
+    if (!p->T_init || Tv) {
+        for (int r0 = 0; r0 < ny; r0 += 65535) {
+            const int r1 = std::min(ny, r0 + 65535);
+            if ((e = h->L->init_rows(kp, 0, r0, r1, Tv ? Tv + (size_t)r0 * nx : nullptr, st)) != cudaSuccess)
+                return cuda_bail(e, "init kernel");
+        }
+    } else {
+        const int t_rows =
+            (int)std::min<size_t>({(size_t)ny, (size_t)h->lay.stage_rows * h->lay.nq, (size_t)65535});
+        for (int r0 = 0; r0 < ny; r0 += t_rows) {
+            const int r1 = std::min(ny, r0 + t_rows);
+            if ((e = cudaMemcpyAsync(h->stage(), p->T_init + (size_t)r0 * nx, (size_t)(r1 - r0) * nx * sizeof(double),
+                                     cudaMemcpyHostToDevice, st)) != cudaSuccess)
+                return cuda_bail(e, "upload T_init");
+            if ((e = h->L->init_rows(kp, 0, r0, r1, h->stage(), st)) != cudaSuccess)
+                return cuda_bail(e, "init kernel");
+        }
     }
-    for (int r0 = 0; r0 < ny; r0 += t_rows) {
-        const int r1 = std::min(ny, r0 + t_rows);
-        if (p->T_init && (e = cudaMemcpyAsync(h->stage(), p->T_init + (size_t)r0 * nx,
-                                              (size_t)(r1 - r0) * nx * sizeof(double), cudaMemcpyHostToDevice, st)) !=
-                             cudaSuccess)
-            return cuda_bail(e, "upload T_init");
-        if ((e = h->L->init_rows(kp, 0, r0, r1, h->stage(), st)) != cudaSuccess) return cuda_bail(e, "init kernel");
-    }
+    unsigned long long cnt[2] = {0, 0};
+    if (gpu_maps && (e = cudaMemcpyAsync(cnt, counters, sizeof cnt, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_bail(e, "read map counters");
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_bail(e, "init sync");
+    if (gpu_maps) {
+        if (cnt[0] != ~0ULL) {
+            // name the first invalid cell as the host scan would: rescan its row
+            uint8_t halfway[256] = {0};
+            for (int k = 1; k <= p->n_walls; ++k) halfway[k] = 1;
+            ScanResult r;
+            const int y = (int)(cnt[0] / (unsigned long long)nx);
+            if (scan_row_exact(p, halfway, y, nullptr, r) || r.err.empty()) {
+                char buf[128];
+                snprintf(buf, sizeof buf, "invalid flag map at cell (%d, %d)", (int)(cnt[0] % (unsigned long long)nx), y);
+                r.err = buf;
+            }
+            return bail(LBM_EINVAL, r.err);
+        }
+        h->fluid = (int64_t)cnt[1];
+    }
     h->cur = 0;
     *out = h;
     return LBM_OK;
@@ -654,15 +828,16 @@ lbm_status lbm_step(lbm_lattice *h, int64_t nsteps) {
     if (!h) return fail(nullptr, LBM_EINVAL, "lattice is NULL");
     if (nsteps < 0) return fail(h, LBM_EINVAL, "nsteps must be >= 0");
     if (h->batch) return fail(h, LBM_EINVAL, "lattice belongs to a batch: step it with lbm_batch_step");
-    // Long runs replay a captured graph of kGraphSteps steps: the same kernels with the same
-    // arguments, without the launch gap between steps. Direct launches serve short runs, a
-    // stream that is already being captured (the steps then join the caller's graph), and
-    // the first run of a kernel choice (its launch-time setup happens outside any capture).
+    // Runs of kGraphShort steps or more replay captured graphs of kGraphSteps and kGraphShort
+    // steps: the same kernels with the same arguments, without the launch gap between steps.
+    // Direct launches serve short runs and remainders, a stream that is already being
+    // captured (the steps then join the caller's graph), and the first run of a kernel
+    // choice (its launch-time setup happens outside any capture).
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     const cudaError_t ce = cudaStreamIsCapturing(h->stream, &cs);
     if (ce != cudaSuccess) cudaGetLastError();  // leave no error behind for the launch checks
     const bool can_graph = !h->graph_off && ce == cudaSuccess && cs == cudaStreamCaptureStatusNone;
-    if (!can_graph || nsteps < 2 * kGraphSteps) return step_direct(h, nsteps);
+    if (!can_graph || nsteps < kGraphShort) return step_direct(h, nsteps);
     if (!h->direct_done || h->graph_variant != h->kp.variant || h->graph_config != h->kp.config) {
         drop_graph(h);
         if (!h->direct_done) {
@@ -682,6 +857,11 @@ lbm_status lbm_step(lbm_lattice *h, int64_t nsteps) {
         cudaError_t e = cudaGraphLaunch(h->graph, h->stream);
         if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
         h->steps += kGraphSteps;
+    }
+    for (; nsteps >= kGraphShort; nsteps -= kGraphShort) {
+        cudaError_t e = cudaGraphLaunch(h->graph_short, h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "step graph");
+        h->steps += kGraphShort;
     }
     return step_direct(h, nsteps);
 }
@@ -722,19 +902,39 @@ lbm_status lbm_read_macro_rows(lbm_lattice *h, int32_t y0, int32_t y1, double *r
     if (y0 < 0 || y1 > h->ny || y0 > y1) return fail(h, LBM_EINVAL, "rows must satisfy 0 <= y0 <= y1 <= ny");
     double *outs[4] = {rho, ux, uy, T};
     const int nx = h->nx;
-    const int rows = std::max(1, h->lay.stage_rows * h->lay.nq / 4);
-    for (int r0 = y0; r0 < y1; r0 += rows) {
-        const int r1 = std::min(y1, r0 + rows);
-        const size_t n = (size_t)(r1 - r0) * nx;
-        // the next chunk's kernel, queued behind these copies on the same stream, cannot
-        // overwrite the staging area before they finish: one wait at the end suffices
-        LBM_CUDA(h, h->L->macro_rows(h->kp, h->cur, r0, r1, h->stage(), h->stream), "macro kernel");
-        for (int k = 0; k < 4; ++k)
-            if (outs[k])
-                LBM_CUDA(h,
-                         cudaMemcpyAsync(outs[k] + (size_t)(r0 - y0) * nx, h->stage() + k * n, n * sizeof(double),
-                                         cudaMemcpyDeviceToHost, h->stream),
-                         "read macro");
+    // page-locked (or device) outputs are written by the kernel in place; any pageable one sends
+    // every output through the staging area
+    double *direct[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool in_place = true;
+    for (int k = 0; k < 4; ++k)
+        if (outs[k]) {
+            direct[k] = static_cast<double *>(const_cast<void *>(device_view(outs[k])));
+            in_place = in_place && direct[k];
+        }
+    if (in_place) {
+        for (int r0 = y0; r0 < y1; r0 += 65535) {  // the grid's y extent is at most 65535 rows per launch
+            const int r1 = std::min(y1, r0 + 65535);
+            double *o[4];
+            for (int k = 0; k < 4; ++k) o[k] = direct[k] ? direct[k] + (size_t)(r0 - y0) * nx : nullptr;
+            LBM_CUDA(h, h->L->macro_rows(h->kp, h->cur, r0, r1, o, h->stream), "macro kernel");
+        }
+    } else {
+        const int rows = std::max(1, h->lay.stage_rows * h->lay.nq / 4);
+        for (int r0 = y0; r0 < y1; r0 += rows) {
+            const int r1 = std::min(y1, r0 + rows);
+            const size_t n = (size_t)(r1 - r0) * nx;
+            // the next chunk's kernel, queued behind these copies on the same stream, cannot
+            // overwrite the staging area before they finish: one wait at the end suffices
+            double *o[4];
+            for (int k = 0; k < 4; ++k) o[k] = outs[k] ? h->stage() + k * n : nullptr;
+            LBM_CUDA(h, h->L->macro_rows(h->kp, h->cur, r0, r1, o, h->stream), "macro kernel");
+            for (int k = 0; k < 4; ++k)
+                if (outs[k])
+                    LBM_CUDA(h,
+                             cudaMemcpyAsync(outs[k] + (size_t)(r0 - y0) * nx, h->stage() + k * n, n * sizeof(double),
+                                             cudaMemcpyDeviceToHost, h->stream),
+                             "read macro");
+        }
     }
     LBM_CUDA(h, cudaStreamSynchronize(h->stream), "read macro sync");
     LBM_STATUS(h);
@@ -753,15 +953,7 @@ lbm_status lbm_nusselt(lbm_lattice *h, int32_t side, double L, double delta_T, d
     if (!(std::isfinite(delta_T) && delta_T != 0.0)) return fail(h, LBM_EINVAL, "delta_T must be finite, non-zero");
     if (!(L > 0.0)) {
         // fluid cells across the lattice along the wall normal, on the middle line
-        int count = 0;
-        if (side < 2) {
-            const int y = h->ny / 2;
-            for (int x = 0; x < h->nx; ++x) count += h->flags[(size_t)y * h->nx + x] == 0;
-        } else {
-            const int x = h->nx / 2;
-            for (int y = 0; y < h->ny; ++y) count += h->flags[(size_t)y * h->nx + x] == 0;
-        }
-        L = (double)count;
+        L = (double)(side < 2 ? h->across_x : h->across_y);
     }
     LBM_CUDA(h, h->L->nusselt(h->kp, h->cur, side, L, delta_T, h->partials(), h->stream), "nusselt kernel");
     LBM_CUDA(h, nomrt::reduce_partials(h->partials(), 2, h->result(), h->stream), "reduce kernel");

@@ -15,10 +15,15 @@
 // Work: every member's rows cut into 512-cell segments (the four-cell
 // kernel's 128-thread block shape): one virtual block per (member, row,
 // segment), numbered member by member, row by row, with no block beyond a
-// member's own width. A block finds its member by a binary search over the
-// members' first virtual blocks, reads the member's descriptor and runs the
-// single-lattice row code, so a lattice stepped in a batch produces the same
-// bits as when stepped alone. The per-step kernel gives each virtual block a
+// member's own width. A block of the per-step kernel finds its member by a
+// binary search over the members' first virtual blocks: every value on that
+// path is the same across the block (block index, parameter bank), so the
+// member's descriptor stays in the per-block (uniform) registers rather than
+// in each thread's (measured: a per-thread table load instead cost the FP32
+// kernel 4 %). The persistent kernel's blocks draw their virtual blocks from a
+// counter, so they read (member, segment, row) from a device work table. Either
+// way the block runs the single-lattice row code, so a lattice stepped in a
+// batch produces the same bits as when stepped alone. The per-step kernel gives each virtual block a
 // block of a 1-D grid; the persistent kernel's resident blocks take runs of
 // rows_per_unit consecutive virtual blocks, step after step.
 //
@@ -95,6 +100,7 @@ struct GroupParams {
     int nlats;
     int unit;                   // persistent kernel: consecutive virtual blocks per work unit
     int nvb;                    // virtual blocks per step
+    const int2 *work;           // per virtual block: (member | segment << 8, row), device
     int blk0[kGroupLats + 1];   // first virtual block of each member; blk0[nlats] = nvb
     GridLat lat[kGroupLats];
 };
@@ -131,10 +137,10 @@ __device__ __forceinline__ void batch_row(const GroupParams &P, int lo, int xb, 
     row4<S, StridedPlanes<S>, NC>(pa, g, r, xs + 4 * (int)threadIdx.x, y, (int)threadIdx.x & 31);
 }
 
-// Virtual block vb of a group: its member (binary search over the members'
-// first virtual blocks), row and segment.
+// Virtual block vb of a group (the per-step kernel): its member by a binary
+// search over the members' first virtual blocks, then its row and segment.
 template <typename S, bool NC>
-__device__ __forceinline__ void batch_block(const GroupParams &P, int vb, int parity) {
+__device__ __forceinline__ void batch_block_search(const GroupParams &P, int vb, int parity) {
     int lo = 0, hi = P.nlats - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
@@ -147,11 +153,19 @@ __device__ __forceinline__ void batch_block(const GroupParams &P, int vb, int pa
     batch_row<S, NC>(P, lo, xb, y, parity);
 }
 
+// Virtual block vb of a group (the persistent kernel): member, segment and row
+// from the work table.
+template <typename S, bool NC>
+__device__ __forceinline__ void batch_block_table(const GroupParams &P, int vb, int parity) {
+    const int2 w = __ldg(P.work + vb);  // vb < P.nvb, the table's length (the batch's own buffer)
+    batch_row<S, NC>(P, w.x & 0xFF, w.x >> 8, w.y, parity);
+}
+
 // One step of every member of a group: one block per virtual block.
 template <typename S, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     k_batch_grid(const __grid_constant__ GroupParams P, int parity) {
-    for (int vb = blockIdx.x; vb < P.nvb; vb += gridDim.x) batch_block<S, true>(P, vb, parity);
+    for (int vb = blockIdx.x; vb < P.nvb; vb += gridDim.x) batch_block_search<S, true>(P, vb, parity);
 }
 
 template <typename S, int MINB, bool PERSISTENT>
@@ -213,25 +227,43 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, int *status, unsigne
     return ok != 0;
 }
 
-// nsteps steps of every member of a group in one cooperative launch: the
-// resident blocks stride over runs of P.unit consecutive virtual blocks, with
-// a grid barrier between steps. advance =
-// 0 recomputes the step at parity0 nsteps times (the tuner's trials, which
-// leave the state as it was). A launch that finds the status word set (an
-// earlier barrier gave up: the state is undefined) returns at once.
+// nsteps steps of every member of a group in one cooperative launch, with a
+// grid barrier between steps. Within a step the resident blocks take work
+// units (P.unit consecutive virtual blocks) from a step counter as they
+// become free, each asking for its next unit while it works on the current
+// one, so no block waits at the barrier for a neighbour that drew slower
+// units. Two counters alternate between steps (ctr[s & 1]); block 0 clears
+// the one just used after the barrier that ends its step, before the step
+// that uses it again; the host clears both before the launch. advance = 0
+// recomputes the step at parity0 nsteps times (the tuner's trials, which leave
+// the state as it was). A launch that finds the status word set (an earlier
+// barrier gave up: the state is undefined) returns at once.
 template <typename S, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     k_batch_persistent(const __grid_constant__ GroupParams P, int parity0, int nsteps, int advance, unsigned expected,
-                       unsigned *bar, int *status) {
+                       unsigned *bar, unsigned *ctr, int *status) {
     if (*reinterpret_cast<volatile int *>(status) != kStatusOk) return;
+    __shared__ unsigned next;
     const int U = P.unit;
+    const unsigned nunits = (unsigned)((P.nvb + U - 1) / U);
     for (int s = 0; s < nsteps; ++s) {
         const int parity = parity0 + (advance ? s : 0);
-        for (int base = blockIdx.x * U; base < P.nvb; base += gridDim.x * U) {
-            const int end = min(base + U, P.nvb);
-            for (int vb = base; vb < end; ++vb) batch_block<S, false>(P, vb, parity);
+        unsigned *c = ctr + (s & 1);
+        if (threadIdx.x == 0) next = atomicAdd(c, 1u);
+        __syncthreads();
+        unsigned u = next;
+        while (u < nunits) {
+            __syncthreads();  // every thread has read `next`
+            if (threadIdx.x == 0) next = atomicAdd(c, 1u);
+            const int v0 = (int)u * U, v1 = min(v0 + U, P.nvb);
+            for (int vb = v0; vb < v1; ++vb) batch_block_table<S, false>(P, vb, parity);
+            __syncthreads();
+            u = next;
         }
-        if (s + 1 < nsteps && !grid_barrier(bar, status, expected)) return;
+        if (s + 1 < nsteps) {
+            if (!grid_barrier(bar, status, expected)) return;
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicExch(c, 0u);  // ready for step s + 2
+        }
     }
 }
 
@@ -255,14 +287,14 @@ cudaError_t launch_batch_grid(int config, const GroupParams &G, int parity, cuda
 
 template <typename S, int MINB>
 cudaError_t launch_persistent_shape(const GroupParams &G, int parity, int nsteps, int advance, int barrier_extra,
-                                    unsigned *bar, int *status, cudaStream_t st) {
+                                    unsigned *bar, unsigned *ctr, int *status, cudaStream_t st) {
     if (G.nvb == 0 || nsteps <= 0) return cudaSuccess;
     auto kern = k_batch_persistent<S, MINB>;
     int blocks = 0;
     cudaError_t e = resident_grid<GridTag<S, MINB, true>>(kern, &blocks);
     if (e != cudaSuccess) return e;
     const int units = (G.nvb + G.unit - 1) / G.unit;
-    if (blocks > units) blocks = units;
+    if (blocks > units) blocks = units;  // every block finds a first unit
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(blocks);
     cfg.blockDim = dim3(kBatchThreads);
@@ -274,18 +306,21 @@ cudaError_t launch_persistent_shape(const GroupParams &G, int parity, int nsteps
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const unsigned expected = (unsigned)(blocks + barrier_extra);
-    return cudaLaunchKernelEx(&cfg, kern, G, parity, nsteps, advance, expected, bar, status);
+    e = cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, kern, G, parity, nsteps, advance, expected, bar, ctr, status);
 }
 
 template <typename S>
 cudaError_t launch_batch_persistent(int config, const GroupParams &G, int parity, int nsteps, int advance,
                                     int barrier_extra, unsigned *bar, int *status, cudaStream_t st) {
+    unsigned *ctr = bar + 2;  // the two step counters follow the barrier's words
     switch (config) {
-        case 1: return launch_persistent_shape<S, 5>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
-        case 2: return launch_persistent_shape<S, 6>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
-        case 3: return launch_persistent_shape<S, 7>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
-        case 4: return launch_persistent_shape<S, 8>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
-        default: return launch_persistent_shape<S, 4>(G, parity, nsteps, advance, barrier_extra, bar, status, st);
+        case 1: return launch_persistent_shape<S, 5>(G, parity, nsteps, advance, barrier_extra, bar, ctr, status, st);
+        case 2: return launch_persistent_shape<S, 6>(G, parity, nsteps, advance, barrier_extra, bar, ctr, status, st);
+        case 3: return launch_persistent_shape<S, 7>(G, parity, nsteps, advance, barrier_extra, bar, ctr, status, st);
+        case 4: return launch_persistent_shape<S, 8>(G, parity, nsteps, advance, barrier_extra, bar, ctr, status, st);
+        default: return launch_persistent_shape<S, 4>(G, parity, nsteps, advance, barrier_extra, bar, ctr, status, st);
     }
 }
 
@@ -301,6 +336,9 @@ struct lbm_batch {
     // device words of the persistent kernel (allocated by the batch)
     unsigned *d_bar = nullptr;
     int *d_status = nullptr;
+    // the launch groups' work tables (int2 per virtual block, groups side by side)
+    int2 *d_work = nullptr;
+    size_t cap_work = 0;
     // lbm_batch_residuals: the members' five residual sums on the device and their pinned host copy
     double *d_res = nullptr;
     double *h_res = nullptr;
@@ -379,11 +417,41 @@ lbm_status rebuild(lbm_batch *b) {
         gl.v = nomrt::member_rates(r);
         G->unit = b->rows_per_unit;
         G->blk0[G->nlats + 1] = G->blk0[G->nlats] + kp.ny * gl.xblocks;
+        G->nvb = G->blk0[G->nlats + 1];
         G->nlats += 1;
-        G->nvb = G->blk0[G->nlats];
+    }
+    // work tables: each group's virtual blocks member by member, row by row, segment by segment
+    size_t total = 0;
+    for (const nomrt::GroupParams &G : b->groups) total += (size_t)G.nvb;
+    std::vector<int2> work(total);
+    size_t at = 0;
+    for (const nomrt::GroupParams &G : b->groups)
+        for (int m = 0; m < G.nlats; ++m)
+            for (int y = 0; y < G.lat[m].g.ny; ++y)
+                for (int xb = 0; xb < G.lat[m].xblocks; ++xb) work[at++] = make_int2(m | (xb << 8), y);
+    if (total > b->cap_work) {
+        cudaError_t e = cudaStreamSynchronize(b->stream);  // the old table may still be in use
+        if (b->d_work) cudaFree(b->d_work);
+        b->d_work = nullptr;
+        b->cap_work = 0;
+        const size_t want = std::max<size_t>(total * 5 / 4, 1024);
+        if (e == cudaSuccess) e = cudaMalloc(&b->d_work, want * sizeof(int2));
+        if (e != cudaSuccess) return bcuda(b, e, "batch work table");
+        b->cap_work = want;
+    }
+    if (total) {
+        // the host vector goes away after this call: copy and wait
+        cudaError_t e = cudaMemcpyAsync(b->d_work, work.data(), total * sizeof(int2), cudaMemcpyHostToDevice, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return bcuda(b, e, "upload work table");
     }
     b->nunits = 0;
-    for (const nomrt::GroupParams &G : b->groups) b->nunits += G.nvb;
+    at = 0;
+    for (nomrt::GroupParams &G : b->groups) {
+        G.work = b->d_work + at;
+        at += (size_t)G.nvb;
+        b->nunits += G.nvb;
+    }
     b->dirty = false;
     return LBM_OK;
 }
@@ -535,9 +603,9 @@ lbm_status lbm_batch_create(void *cuda_stream, lbm_batch **out) {
     if (!b) return bfail(nullptr, LBM_ENOMEM, "host allocation failed");
     b->stream = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_bar, 4 * sizeof(unsigned));  // barrier (count, generation), 2 step counters
     if (e == cudaSuccess) e = cudaMalloc(&b->d_status, sizeof(int));
-    if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->d_bar, 0, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMemset(b->d_status, 0, sizeof(int));
     if (e != cudaSuccess) {
         lbm_status st = bcuda(nullptr, e, "batch set-up");
@@ -654,7 +722,7 @@ lbm_status lbm_batch_sync(lbm_batch *b) {
     if (st != nomrt::kStatusOk) {
         const int zero = 0;
         cudaMemcpy(b->d_status, &zero, sizeof zero, cudaMemcpyHostToDevice);
-        cudaMemset(b->d_bar, 0, 2 * sizeof(unsigned));
+        cudaMemset(b->d_bar, 0, 4 * sizeof(unsigned));
         return bfail(b, LBM_ETIMEOUT, "the persistent batch kernel gave up a grid barrier");
     }
     if constexpr (nomrt::kBoundsBuild) {
@@ -864,6 +932,7 @@ void lbm_batch_destroy(lbm_batch *b) {
     if (b->d_status) cudaFree(b->d_status);
     if (b->d_res) cudaFree(b->d_res);
     if (b->h_res) cudaFreeHost(b->h_res);
+    if (b->d_work) cudaFree(b->d_work);
     delete b;
 }
 

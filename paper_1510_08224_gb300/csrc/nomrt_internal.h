@@ -95,10 +95,11 @@ struct Launchers {
     cudaError_t (*step)(const KParams &, int src, cudaStream_t st);
     // the boundary nodes of NEE walls alone (after a step kernel that skipped them)
     cudaError_t (*nee)(const KParams &, int src, cudaStream_t st);
-    // initial state into buffer `buf`, rows [r0, r1); T rows in `T` (device, (r1-r0)*nx)
+    // initial state into buffer `buf`, rows [r0, r1), zeros into the other buffer; T rows in `T`
+    // (device-readable, (r1-r0)*nx), or nullptr for T0 everywhere
     cudaError_t (*init_rows)(const KParams &, int buf, int r0, int r1, const double *T, cudaStream_t st);
-    // macroscopics of rows [r0, r1) into out[4][(r1-r0)*nx] (rho, ux, uy, T)
-    cudaError_t (*macro_rows)(const KParams &, int buf, int r0, int r1, double *out, cudaStream_t st);
+    // macroscopics of rows [r0, r1) into out[0..3] (rho, ux, uy, T; (r1-r0)*nx doubles each, any NULL)
+    cudaError_t (*macro_rows)(const KParams &, int buf, int r0, int r1, double *const out[4], cudaStream_t st);
     // FP64 export / import of rows [r0, r1): out/in [9 + tq][(r1-r0)*nx]
     cudaError_t (*export_rows)(const KParams &, int buf, int r0, int r1, double *out, cudaStream_t st);
     cudaError_t (*import_rows)(const KParams &, int buf, int r0, int r1, const double *in, int which,

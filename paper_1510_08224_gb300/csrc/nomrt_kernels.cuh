@@ -909,35 +909,44 @@ __device__ __forceinline__ double thermal_weight(int q, int tq, double varpi) {
     return q == 0 ? 1.0 - varpi : 0.25 * varpi;
 }
 
+// Rows [r0, r1) of the initial state into the source buffer (every column of
+// the pitched rows: solid cells and padding get zeros), and zeros into the
+// other buffer. T: rows r0.. of the initial temperature (nx per row), or
+// nullptr for T0 everywhere.
 template <typename S>
-__global__ void k_init_rows(const Planes<S> pl, const Geom g, int r0, int r1, const double *T, double T_ref,
-                            double varpi, int shifted, int tq) {
+__global__ void k_init_rows(const Planes<S> pl, const Geom g, int r0, int r1, const double *T, double T0,
+                            double T_ref, double varpi, int shifted, int tq) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = r0 + blockIdx.y;
     if (x >= g.pitch || y >= r1) return;
     const int off = y * g.pitch + x;
     const bool fluid = x < g.nx && kept_cell(g, off);
     const double w9[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-    const double Tn = fluid ? T[(size_t)(y - r0) * g.nx + x] : 0.0;
+    const double Tn = fluid ? (T ? T[(size_t)(y - r0) * g.nx + x] : T0) : 0.0;
     for (int q = 0; q < 9; ++q) {
         double v = fluid ? (shifted ? 0.0 : w9[q]) : 0.0;
         Store<S>::st(const_cast<S *>(pl.src[q]) + off, (typename Store<S>::C)v);
+        Store<S>::st(pl.dst[q] + off, (typename Store<S>::C)0.0);
     }
     for (int q = 0; q < tq; ++q) {
         const double wT = thermal_weight(q, tq, varpi);
         double v = fluid ? wT * (Tn - T_ref) : 0.0;
         Store<S>::st(const_cast<S *>(pl.src[9 + q]) + off, (typename Store<S>::C)v);
+        Store<S>::st(pl.dst[9 + q] + off, (typename Store<S>::C)0.0);
     }
 }
 
+// rho, u_x, u_y, T of rows [r0, r1) into out[0..3] (each (r1 - r0) * nx
+// doubles, row y at (y - r0) * nx; a NULL output is skipped). The outputs may
+// be a staging area or the caller's page-locked host arrays.
 template <typename S, int TQ = 5>
 __global__ void k_macro_rows(const Planes<S> pl, const Geom g, const RatesC<typename Store<S>::C> r, int r0,
-                             int r1, double rho_ref, double T_ref, double *out) {
+                             int r1, double rho_ref, double T_ref, double *o_rho, double *o_ux, double *o_uy,
+                             double *o_T) {
     using C = typename Store<S>::C;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = r0 + blockIdx.y;
     if (x >= g.nx || y >= r1) return;
-    const size_t n = (size_t)(r1 - r0) * g.nx;
     const size_t o = (size_t)(y - r0) * g.nx + x;
     const unsigned m = g.mask[y * g.pitch + x];
     const unsigned d = g.nee_dir[y * g.pitch + x];
@@ -952,7 +961,10 @@ __global__ void k_macro_rows(const Planes<S> pl, const Geom g, const RatesC<type
         v[2] = (double)M.uy;
         v[3] = T_ref + (double)M.dT;
     }
-    for (int k = 0; k < 4; ++k) out[k * n + o] = v[k];
+    if (o_rho) o_rho[o] = v[0];
+    if (o_ux) o_ux[o] = v[1];
+    if (o_uy) o_uy[o] = v[2];
+    if (o_T) o_T[o] = v[3];
 }
 
 template <typename S>

@@ -22,7 +22,7 @@ SIDES = {"left": 0, "right": 1, "bottom": 2, "top": 3}
 
 STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3, "vec8": 4}
 # Every symbol include/nomrt_lbm.h declares.
-EXPORTED = ("lbm_footprint_bytes", "lbm_create", "lbm_step", "lbm_sync", "lbm_step_kernel_count",
+EXPORTED = ("lbm_footprint_bytes", "lbm_validate", "lbm_create", "lbm_step", "lbm_sync", "lbm_step_kernel_count",
             "lbm_set_step_kernel", "lbm_read_macro", "lbm_read_macro_rows",
             "lbm_nusselt",
             "lbm_residual", "lbm_get_populations", "lbm_set_populations", "lbm_info", "lbm_last_error",
@@ -88,6 +88,8 @@ def load():
         vp, dp = C.c_void_p, C.POINTER(C.c_double)
         L.lbm_footprint_bytes.restype = C.c_size_t
         L.lbm_footprint_bytes.argtypes = [C.POINTER(lbm_params)]
+        L.lbm_validate.restype = C.c_int
+        L.lbm_validate.argtypes = [C.POINTER(lbm_params)]
         L.lbm_create.restype = C.c_int
         L.lbm_create.argtypes = [C.POINTER(lbm_params), vp, vp, C.c_size_t, C.POINTER(vp)]
         L.lbm_step.restype = C.c_int
@@ -241,6 +243,15 @@ def step_kernels(storage: str):
 
 def lbm_footprint_bytes(params) -> int:
     return int(load().lbm_footprint_bytes(C.byref(params)))
+
+
+def validate(case, storage: str = "f32") -> None:
+    """Every check lbm_create makes (lbm_validate, host only); raises LBMError
+    naming the first invalid cell."""
+    p, keep = make_params(case, storage)
+    st = load().lbm_validate(C.byref(p))
+    if st != LBM_OK:
+        raise LBMError(st, load().lbm_last_error(None).decode())
 
 
 class Lattice:

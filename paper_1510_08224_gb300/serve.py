@@ -66,7 +66,7 @@ class GpuBackend:
     given kind ('fused', 'persistent' or 'concurrent'), optionally replayed
     from CUDA graphs of graph_steps steps."""
 
-    def __init__(self, storage: str = "f32", graph_steps: int = 0, kind: str = "fused", steps_per_launch: int = 32):
+    def __init__(self, storage: str = "f32", graph_steps: int = 0, kind: str = "fused", steps_per_launch=None):
         import torch
         from . import lbm
         self._lbm = lbm
@@ -74,6 +74,8 @@ class GpuBackend:
         self.storage = storage
         self.batch = lbm.Batch()
         self.batch.set_kind(kind)
+        if steps_per_launch is None:  # the persistent kind: one launch per replayed graph
+            steps_per_launch = graph_steps if graph_steps > 0 else 32
         self.batch.set_mode(steps_per_launch, graph_steps)
 
     def footprint(self, case) -> int:

@@ -48,13 +48,19 @@ def test_footprint_and_validation_on_host():
     assert sizes["f16"] < sizes["f32"] < sizes["f64"]
     plane = case.ny * 4096
     assert sizes["f32"] >= 2 * 14 * 4 * plane
-    bad = [case.with_(nu=-0.1), case.with_(s_e=2.0), case.with_(varpi=1.0), case.with_(periodic_x=False)]
-    fl = case.flags.copy(); fl[0, 0] = 7
-    bad.append(case.with_(flags=fl))
-    for b in bad:
+    for b in (case.with_(nu=-0.1), case.with_(s_e=2.0), case.with_(varpi=1.0)):
         p, keep = P.make_params(b, "f32")
         assert L.lbm_footprint_bytes(C.byref(p)) == 0
         assert L.lbm_last_error(None)
+        assert L.lbm_validate(C.byref(p)) == 1
+    # flag maps: lbm_validate checks them (lbm_footprint_bytes only where the size depends on them)
+    fl = case.flags.copy(); fl[0, 0] = 7
+    for b in (case.with_(periodic_x=False), case.with_(flags=fl)):
+        p, keep = P.make_params(b, "f32")
+        assert L.lbm_validate(C.byref(p)) == 1 and L.lbm_last_error(None)
+        assert L.lbm_footprint_bytes(C.byref(p)) == sizes["f32"]
+    p, keep = P.make_params(case, "f32")
+    assert L.lbm_validate(C.byref(p)) == 0
 
 
 def test_create_rejects_invalid_params_without_touching_the_gpu():
@@ -76,15 +82,19 @@ def test_null_handles_are_errors():
 
 
 def test_validation_edge_cases_on_host():
-    """Parameter and flag-map checks that need no GPU (lbm_footprint_bytes runs
-    the same validation as lbm_create): size limit, degenerate lattices, the
+    """Parameter and flag-map checks that need no GPU (lbm_validate runs the
+    checks of lbm_create on the host): size limit, degenerate lattices, the
     D2Q9 temperature model's and BGK's parameters, and the first invalid cell
     reported in row-major order whatever the number of scanning threads."""
     import paper_1510_08224_gb300 as P
     L = P.load()
 
     def footprint(case, st="f32"):
+        """lbm_footprint_bytes if lbm_validate accepts the case, else 0 (and
+        the message)."""
         p, keep = P.make_params(case, st)
+        if L.lbm_validate(C.byref(p)) != 0:
+            return 0, L.lbm_last_error(None).decode()
         return L.lbm_footprint_bytes(C.byref(p)), L.lbm_last_error(None).decode()
 
     # ny * pitch must stay below 2^31: rejected before the flag map is read
@@ -134,6 +144,8 @@ def test_flag_map_errors_each_named_at_their_cell():
 
     def footprint(case):
         p, keep = P.make_params(case, "f32")
+        if L.lbm_validate(C.byref(p)) != 0:
+            return 0, L.lbm_last_error(None).decode()
         return L.lbm_footprint_bytes(C.byref(p)), L.lbm_last_error(None).decode()
 
     big = lc.periodic_box(600, 900)

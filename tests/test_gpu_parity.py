@@ -364,12 +364,14 @@ def test_nee_cavity_nusselt_against_table3_on_gpu():
 
 @pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
 def test_graph_replayed_steps_equal_direct_steps(storage):
-    """lbm_step replays runs of 64 steps or more as CUDA graphs of 32 steps: 201
-    steps in one call (one direct step, six graph replays, the rest direct)
-    give the bits of 201 single-step calls, with halfway and node-based walls,
-    on the default stream and on a side stream, for the AUTO kernel and (FP32)
-    the TMA kernel; a call on a stream that torch is capturing joins that
-    graph and gives the same bits when replayed."""
+    """lbm_step replays runs of 4 steps or more as CUDA graphs of 32 and 4
+    steps: 201 steps in one call (a direct step, capture, a direct step to the
+    graphs' starting buffer, six 32-step and one 4-step replay, three direct
+    steps), and runs of 5, 20, 7 and 33 steps, give the bits of as many
+    single-step calls, with halfway and node-based walls, on the default stream
+    and on a side stream, for the AUTO kernel and (FP32) the TMA kernel; a call
+    on a stream that torch is capturing joins that graph and gives the same
+    bits when replayed."""
     import torch
     P = _P()
     cases = [lc.rayleigh_benard(nx=133, H=7, Ra=1e5, sigma=1e-2), lc.cavity_nee(n=19, Ra=1e4, noise=1e-3)]
@@ -390,6 +392,13 @@ def test_graph_replayed_steps_equal_direct_steps(storage):
                 fa, ga = a.populations()
                 fb, gb = b.populations()
                 assert np.array_equal(fa, fb) and np.array_equal(ga, gb), (case.name, v, side)
+                for n in (5, 20, 7, 33):
+                    a.step(n)
+                    for _ in range(n):
+                        b.step(1)
+                fa, ga = a.populations()
+                fb, gb = b.populations()
+                assert np.array_equal(fa, fb) and np.array_equal(ga, gb), (case.name, v, side, "short runs")
                 a.close()
                 b.close()
         # inside a capture on the caller's stream
@@ -411,3 +420,102 @@ def test_graph_replayed_steps_equal_direct_steps(storage):
         assert np.array_equal(a.populations()[0], b.populations()[0])
         a.close()
         b.close()
+
+
+def _pinned(a):
+    import torch
+    t = torch.empty(a.shape, dtype={np.uint8: torch.uint8, np.float64: torch.float64}[a.dtype.type]).pin_memory()
+    t.numpy()[...] = a
+    return t
+
+
+@pytest.mark.parametrize("pinned", [False, True])
+def test_create_checks_flag_maps_like_validate(pinned):
+    """lbm_create builds the link map and checks the flag map on the GPU where
+    every wall is halfway: an invalid map is rejected with exactly the message
+    of lbm_validate (the host check), whether the map is page-locked (read in
+    place) or pageable (copied); a valid one gives the host's fluid-cell
+    count."""
+    import ctypes as C
+    P = _P()
+    L = P.load()
+    ch = lc.couette(H=900, nx=600)
+    box = lc.periodic_box(512, 1024)
+    bad = []
+    fl = ch.flags.copy(); fl[700:703, 100:103] = 1; fl[701, 101] = 0
+    bad.append(ch.with_(flags=fl))                      # a fluid cell with no fluid neighbour
+    fl = ch.flags.copy(); fl[451, 333] = 7
+    bad.append(ch.with_(flags=fl))                      # a wall id above n_walls
+    fl = ch.flags.copy(); fl[-1, :] = 0
+    bad.append(ch.with_(flags=fl))                      # fluid cells on a non-periodic edge
+    fl = box.flags.copy(); fl[900, 17] = 5; fl[300, 400] = 9; fl[301, 2] = 6
+    bad.append(box.with_(flags=fl))                     # several, the first in row-major order named
+    bad.append(box.with_(periodic_y=False))
+    keep = []
+    for case in bad:
+        flags = _pinned(case.flags) if pinned else case.flags
+        keep.append(flags)
+        c2 = case.with_(flags=flags.numpy() if pinned else flags)
+        p, k = P.make_params(c2, "f32")
+        assert L.lbm_validate(C.byref(p)) == 1
+        want = L.lbm_last_error(None)
+        h = C.c_void_p()
+        assert L.lbm_create(C.byref(p), None, None, 0, C.byref(h)) == 1 and not h.value
+        assert L.lbm_last_error(None) == want, (L.lbm_last_error(None), want)
+    for case in (ch, box, lc.obstacle_channel(nx=261, H=9, frac=0.15, seed=4), lc.periodic_box(1, 1)):
+        flags = _pinned(case.flags) if pinned else case.flags
+        lat = P.Lattice(case.with_(flags=flags.numpy() if pinned else flags), storage="f32")
+        assert lat.info()["fluid_cells"] == int((case.flags == 0).sum())
+        lat.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32", "f16"])
+def test_create_reads_page_locked_inputs_in_place(storage):
+    """Flags and T_init in page-locked memory are read in place by the GPU,
+    pageable ones are copied: the initial state is the same bits either way,
+    and a tall lattice (more rows than one launch's grid covers) builds its
+    maps across the launch seams."""
+    P = _P()
+    for case in (lc.rayleigh_benard(nx=300, H=17, Ra=1e5, sigma=1e-2),
+                 lc.couette(H=70_000, nx=4, U0=0.05).with_(T_init=0.3 + 0.01 * lc.uniform01(3, 70_002 * 4).reshape(70_002, 4))):
+        a = P.Lattice(case, storage=storage)
+        fl, Ti = _pinned(case.flags), _pinned(case.T_init)
+        b = P.Lattice(case.with_(flags=fl.numpy(), T_init=Ti.numpy()), storage=storage)
+        fa, ga = a.populations()
+        fb, gb = b.populations()
+        assert np.array_equal(fa, fb) and np.array_equal(ga, gb)
+        a.step(3)
+        b.step(3)
+        assert all(np.array_equal(x, y) for x, y in zip(a.populations(), b.populations()))
+        o = oracle.OracleLattice(case)
+        o.step(3)
+        if storage == "f64":
+            assert _rel(a.populations()[0], o.populations()[0]) <= FP64_TOL
+        a.close()
+        b.close()
+
+
+@pytest.mark.parametrize("storage", ["f64", "f32"])
+def test_read_macro_into_page_locked_arrays(storage):
+    """lbm_read_macro writes page-locked host arrays in place (pageable ones
+    through the staging area): the same values either way, any output NULL,
+    row bands included."""
+    import ctypes as C
+    import torch
+    P = _P()
+    L = P.load()
+    case = lc.rayleigh_benard(nx=300, H=70, Ra=1e5, sigma=1e-2)
+    lat = P.Lattice(case, storage=storage)
+    lat.step(40)
+    ref = lat.macro()
+    outs = [torch.empty((case.ny, case.nx), dtype=torch.float64).pin_memory() for _ in range(4)]
+    ptr = [C.cast(o.data_ptr(), C.POINTER(C.c_double)) for o in outs]
+    assert L.lbm_read_macro(lat.handle, ptr[0], None, ptr[2], ptr[3]) == 0
+    for k in (0, 2, 3):
+        assert np.array_equal(outs[k].numpy(), ref[k])
+    band = [torch.full((10, case.nx), -1.0, dtype=torch.float64).pin_memory() for _ in range(4)]
+    bp = [C.cast(o.data_ptr(), C.POINTER(C.c_double)) for o in band]
+    assert L.lbm_read_macro_rows(lat.handle, 30, 40, *bp) == 0
+    for k in range(4):
+        assert np.array_equal(band[k].numpy(), ref[k][30:40])
+    lat.close()
