@@ -393,7 +393,15 @@ def run_batched(args):
     import torch
     import paper_1510_08224_gb300 as P
     torch.cuda.set_device(0)
-    cases = lc.batched_cavities(count=args.count, seed=0)
+    if args.batch_members == "rb":
+        # `--count` copies of the benchmark lattice (--nx x --H): with --count 1 the batch
+        # kernels run on exactly the single-lattice kernel's shape, which isolates their
+        # per-kernel cost from the narrow members of the cavity mix
+        cases = [workload(args.nx, args.H) for _ in range(args.count)]
+        wl = f"batched_rayleigh_benard_{args.nx}x{args.H}_{args.count}"
+    else:
+        cases = lc.batched_cavities(count=args.count, seed=0)
+        wl = f"batched_cavities_{args.count}"
     cells = sum(c.fluid_nodes for c in cases)
     stream = torch.cuda.current_stream()
     lats = [P.Lattice(c, storage=args.storage, stream=stream) for c in cases]
@@ -416,10 +424,13 @@ def run_batched(args):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         b.close()
-        print(json.dumps({"workload": f"batched_cavities_{args.count}", "storage": args.storage,
+        peak, _ = measured_peak()
+        print(json.dumps({"workload": wl, "storage": args.storage,
                           "kind": args.batch_kind, "config": args.config, "steps": args.steps,
                           "fluid_cells": cells, "ms_per_step": round(ms, 5),
-                          "MLUPS": round(cells / (ms * 1e-3) / 1e6, 1)}), flush=True)
+                          "MLUPS": round(cells / (ms * 1e-3) / 1e6, 1),
+                          "frac": round(BYTES_PER_NODE[args.storage] * cells / (ms * 1e-3) / 1e9 / peak, 4)}),
+              flush=True)
         return 0
     tuned_kind, tuned_cfg, ms_cand = b.tune(trial_steps=64)
     e0 = torch.cuda.Event(enable_timing=True)
@@ -486,8 +497,10 @@ def run_batched(args):
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tuned["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": COMPUTE_DTYPE[args.storage], "data": "synthetic",
-        "config": {"workload": f"batched_cavities_{args.count}", "lattices": args.count, "fluid_cells": cells,
-                   "sides": "uniform 128..1024", "Ra": "log-uniform [1e3, 1e6]", "storage": STORAGE_NAME[args.storage],
+        "config": {"workload": wl, "lattices": args.count, "fluid_cells": cells,
+                   **({"sides": "uniform 128..1024", "Ra": "log-uniform [1e3, 1e6]"}
+                      if args.batch_members == "cavities" else {"shape": f"{args.nx} x {args.H}", "Ra": 1e6}),
+                   "storage": STORAGE_NAME[args.storage],
                    "tuned": {"kind": tuned_kind, "config": tuned_cfg, "graph_steps": 32,
                              "steps_per_launch": 32 if tuned_kind == "persistent" else 1},
                    "l2": "no flush: working set > L2",
@@ -766,6 +779,8 @@ def main():
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (requests per second)")
     ap.add_argument("--budget-frac", type=float, default=None,
                     help="serve: HBM budget as a fraction of the stream's total footprint (default: 150 GB)")
+    ap.add_argument("--batch-members", default="cavities", choices=["cavities", "rb"],
+                    help="batch: the uneven cavity mix, or --count copies of the --nx x --H lattice")
     ap.add_argument("--batch-kind", default="fused", choices=["fused", "persistent", "concurrent"],
                     help="serve: batch kind of the served path")
     ap.add_argument("--cavity-share", type=float, default=0.75, help="serve: share of cavity requests")

@@ -130,21 +130,40 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
     int variant = p.variant;
     KParams q = p;
     if constexpr (Store<S>::kShifted) {
-        // fastest measured on GB300 (4096 x 2048 cells): four cells per thread with
-        // five (FP32) or seven (FP16) resident blocks per SM
+        // fastest measured on GB300 (4096 x 2048 cells): four cells per thread
         if (variant == kStepAuto) {
             variant = kStepVec4;
-            // VEC4 configs measured fastest on GB300 (4096 x 2048 cells): MRT D2Q5 5 (FP32) or
-            // 7 (FP16) blocks per SM; BGK D2Q5 5 for both; the D2Q9 temperature model, which
-            // keeps nine more values per cell in registers, 4 (5 for MRT in FP16)
-            if (p.tq == 9) q.config = (sizeof(S) == 2 && !p.bgk) ? 1 : 0;
-            else if (p.bgk) q.config = 1;
-            else q.config = sizeof(S) == 4 ? 1 : 3;
+            // VEC4 configs measured fastest on GB300 (4096 x 2048 cells, with the L2
+            // prefetch of the link map): D2Q5 5 resident blocks per SM (4 for BGK in FP32);
+            // the D2Q9 temperature model, which keeps nine more values per cell in
+            // registers, 4
+            if (p.tq == 9) q.config = 0;
+            else q.config = (p.bgk && sizeof(S) == 4) ? 0 : 1;
         }
     } else {
         variant = kStepScalar;
     }
     return launch_step_variant<S>(q, variant, src, st);
+}
+
+// A step of the four-cell kernel as a programmatic dependent of the launch before
+// it on the stream: its blocks become resident while the previous step's last
+// blocks finish and wait there (griddepcontrol.wait) for that grid's completion,
+// which hides the launch latency between back-to-back steps (0.2 % of a step on
+// GB300). After anything but a kernel the dependency is the ordinary one.
+template <typename S, int MINB, int TQ, bool BGK>
+cudaError_t launch_step4(dim3 grid, cudaStream_t st, const Planes<S> &pl, const Geom &g, const RatesC<float> &r) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_step4<S, MINB, TQ, BGK>, pl, g, r);
 }
 
 // TQ: temperature populations per node (5: D2Q5; 9: the D2Q9 model). BGK:
@@ -168,13 +187,12 @@ cudaError_t launch_step_m(const KParams &p, int variant, int src, cudaStream_t s
             const Geom g = make_geom(p);
             const RatesC<float> r = make_rates<float>(p);
             switch (p.config) {
-                case 1: k_step4<S, 5, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
-                case 2: k_step4<S, 6, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
-                case 3: k_step4<S, 7, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
-                case 4: k_step4<S, 8, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
-                default: k_step4<S, 4, TQ, BGK><<<grid, 128, 0, st>>>(pl, g, r); break;
+                case 1: return launch_step4<S, 5, TQ, BGK>(grid, st, pl, g, r);
+                case 2: return launch_step4<S, 6, TQ, BGK>(grid, st, pl, g, r);
+                case 3: return launch_step4<S, 7, TQ, BGK>(grid, st, pl, g, r);
+                case 4: return launch_step4<S, 8, TQ, BGK>(grid, st, pl, g, r);
+                default: return launch_step4<S, 4, TQ, BGK>(grid, st, pl, g, r);
             }
-            return cudaGetLastError();
         }
         if constexpr (sizeof(S) == 2 && kBase) {
             if (variant == kStepVec8) {

@@ -88,8 +88,8 @@ struct GridLat {
     Geom g;
     // every population plane of both buffers (buffer 0's kQ planes, then buffer 1's): read by
     // index from the parameter bank, like the single-lattice kernel's plane pointers, rather
-    // than computed from a base and a stride (which keeps 28 pointers live in registers: 27 %
-    // of the FP16 kernel's throughput, measured on one 4096 x 2048 lattice)
+    // than computed from a base and a stride (measured on one 4096 x 2048 member: the FP16
+    // kernel 0.68 -> 0.74 of the copy peak, FP32 unchanged)
     const void *planes[2 * kQ];
     unsigned long long xb_magic;  // ceil(2^32 / xblocks): local / xblocks = (local * xb_magic) >> 32
     int flip;
@@ -134,12 +134,18 @@ __device__ __forceinline__ void batch_row(const GroupParams &P, int lo, int xb, 
     const int xs = xb * 512;
     constexpr int PF = PrefetchRows<S>::value;
     if constexpr (PF > 0) {
-        // as the single-lattice kernel: one thread per plane asks L2 for this segment PF rows ahead
-        // (16-byte aligned: segments start at multiples of 512 elements, rows are 128-byte pitched)
-        if (threadIdx.x < kQ && y + PF < g.ny) {
+        // as the single-lattice kernel: thread q < kQ asks L2 for plane q's segment PF rows
+        // ahead, thread kQ for the link map's (16-byte aligned: segments start at multiples
+        // of 512 cells, rows are 128-byte pitched). FP16 only: in FP32 the link-map prefetch
+        // took the fused kernel from 0.92 to 0.80 of the copy peak on 64 cavities
+        const int t = threadIdx.x;
+        if (t <= kQ && y + PF < g.ny) {
             const int n = min(512, g.pitch - xs);
-            const S *pp = pa.src_at(threadIdx.x) + (size_t)(y + PF) * g.pitch + xs;
-            if (NOMRT_BULK_OK(g, pp, n * sizeof(S), 52)) prefetch_l2_bulk(pp, (unsigned)(n * sizeof(S)));
+            const size_t at = (size_t)(y + PF) * g.pitch + xs;
+            const void *pp = t == kQ ? static_cast<const void *>(g.mask + at)
+                                     : static_cast<const void *>(pa.src_at(min(t, kQ - 1)) + at);
+            const unsigned bytes = t == kQ ? (unsigned)n : (unsigned)(n * sizeof(S));
+            if (NOMRT_BULK_OK(g, pp, bytes, 52)) prefetch_l2_bulk(pp, bytes);
         }
     }
     RatesC<float> r = P.rc;  // shared rates: parameter-bank operands

@@ -1413,29 +1413,49 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) 
     asm volatile("cp.async.bulk.prefetch.L2.global [%1], %0;" ::"r"(bytes), "l"(p) : "memory");
 }
 
-// Rows ahead whose population segments a block of the four-cell kernel asks L2
-// to fetch: FP16 storage moves half the bytes per cell, so its loads alone keep
-// too few bytes in flight; a 16-row lead measured best on GB300 (FP32: none).
+// Rows ahead whose segments a block of the four-cell kernel asks L2 to fetch.
+// value: the population planes. FP16 storage moves half the bytes per cell, so its
+// loads alone keep too few bytes in flight; FP32 needs no lead. mask: the link map,
+// the first load of every warp and the one its population loads wait on (the
+// early exit of solid rows depends on it), both storages. Measured on GB300 at
+// 4096 x 2048, fractions of the copy peak: FP16 planes alone 16 / 64 / 160 rows
+// ahead 0.928 / 0.918 / 0.824; with the mask too (and the dependent launch)
+// planes 24 / 32 ahead 0.950 / 0.952; FP32 1.009 -> 1.013 with the mask.
 template <typename S>
 struct PrefetchRows {
-    static constexpr int value = sizeof(S) == 2 ? 16 : 0;
+    static constexpr int value = sizeof(S) == 2 ? 32 : 0;
+    static constexpr int mask = 32;
 };
 
+// Launched as a programmatic dependent of the previous step (launch_step_m): the
+// block lets the next launch start its blocks at once, then waits until every
+// block of the previous grid has finished and its writes are visible, before its
+// first global access. Launched without that attribute, the wait returns at once.
 template <typename S, int MINB, int TQ = 5, bool BGK = false>
 __global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const Geom g, const RatesC<float> r) {
     constexpr int PF = PrefetchRows<S>::value;
+    constexpr int MPF = PrefetchRows<S>::mask;
+    static_assert(PF == 0 || PF == MPF, "FP16 prefetches planes and link map with one lead");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int lane = threadIdx.x & 31;
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * 4;
     for (int y = blockIdx.y; y < g.ny; y += gridDim.y) {
-        if constexpr (PF > 0) {
-            // one thread per plane: this block's 512-cell segment of row y + PF (16-byte
-            // aligned: segments start at multiples of 512 elements, rows are 128-byte pitched)
-            if (threadIdx.x < 9 + TQ && y + PF < g.ny) {
-                const int xs = blockIdx.x * 512;
-                const int n = min(512, g.pitch - xs);
-                const S *pp = pl.src_at(threadIdx.x) + (size_t)(y + PF) * g.pitch + xs;
-                if (NOMRT_BULK_OK(g, pp, n * sizeof(S), 50)) prefetch_l2_bulk(pp, (unsigned)(n * sizeof(S)));
-            }
+        // this block's 512-cell segment of row y + MPF: thread q < 9 + TQ asks L2 for plane q
+        // (FP16 only), thread 9 + TQ (FP16) or 0 (FP32) for the link map. 16-byte aligned:
+        // segments start at multiples of 512 cells, rows are pitched to 128 bytes of
+        // populations, so to a multiple of 32 cells, and every region of the block starts on
+        // 256 bytes
+        const int t = threadIdx.x;
+        if ((PF > 0 ? t <= 9 + TQ : t == 0) && y + MPF < g.ny) {
+            const int xs = blockIdx.x * 512;
+            const int n = min(512, g.pitch - xs);
+            const size_t at = (size_t)(y + MPF) * g.pitch + xs;
+            const bool map = PF == 0 || t == 9 + TQ;
+            const void *pp = map ? static_cast<const void *>(g.mask + at)
+                                 : static_cast<const void *>(pl.src_at(min(t, 8 + TQ)) + at);
+            const unsigned bytes = map ? (unsigned)n : (unsigned)(n * sizeof(S));
+            if (NOMRT_BULK_OK(g, pp, bytes, 50)) prefetch_l2_bulk(pp, bytes);
         }
         row4<S, Planes<S>, true, TQ, BGK>(pl, g, r, x0, y, lane);
     }
