@@ -383,6 +383,15 @@ def run_reference(args):
     return 0
 
 
+def set_member_kernel(b, code: int):
+    """The concurrent kind's member kernel from the tuner's code: -1 the members'
+    own, 0-4 VEC4 at that config, 5-9 VEC4W at config - 5."""
+    if code < 0:
+        b.set_member_kernel("auto", 0)
+    else:
+        b.set_member_kernel("vec4" if code < 5 else "vec4w", code % 5)
+
+
 def run_batched(args):
     """Batched uneven lattices: `--count` differentially heated cavities, sides
     uniform over 128..1024, Ra log-uniform in [1e3, 1e6], advanced together.
@@ -412,7 +421,11 @@ def run_batched(args):
     if args.no_tune:
         # one kind and config (profiling): --batch-kind, --config, graphs of 32 steps
         b.set_kind(args.batch_kind)
-        b.set_config(args.config if args.batch_kind != "concurrent" else -1, 1)
+        if args.batch_kind == "concurrent":
+            # --config -1: the members' own kernels; 0-4: VEC4 at that config; 5-9: VEC4W at config - 5
+            set_member_kernel(b, args.config)
+        else:
+            b.set_config(args.config, 1)
         b.set_mode(32, 32)
         b.step(args.warmup)
         torch.cuda.synchronize()
@@ -456,19 +469,29 @@ def run_batched(args):
     kinds = {}
     k_steps = min(args.steps, 2000)
     for kind in ("fused", "persistent", "concurrent"):
+        b.set_kind(kind)
         if kind == "concurrent":
-            cfg = -1
+            cands = {-1: ms_cand["concurrent"]}
+            cands.update({c: ms_cand[f"concurrent_vec4_cfg{c}"] for c in range(5)})
+            cands.update({5 + c: ms_cand[f"concurrent_vec4w_cfg{c}"] for c in range(5)})
+            cfg = min(cands, key=cands.get)
+            set_member_kernel(b, cfg)
         else:
             cands = {c: ms_cand[f"{kind}_cfg{c}"] for c in range(5)}
             cfg = min(cands, key=cands.get)
-        b.set_kind(kind)
-        b.set_config(cfg, 1)
+            b.set_config(cfg, 1)
         b.set_mode(32, 32)
         kinds[kind] = {"config": cfg, **rate(timed(b.step, k_steps), k_steps)}
+        if kind == "concurrent":
+            kinds[kind]["member_kernel"] = list(b.get_member_kernel())
     # the tuned choice over the full run
     b.set_kind(tuned_kind)
-    b.set_config(tuned_cfg, 1)
+    if tuned_kind == "concurrent":
+        set_member_kernel(b, tuned_cfg)
+    else:
+        b.set_config(tuned_cfg, 1)
     b.set_mode(32, 32)
+    member_kernel = list(b.get_member_kernel()) if tuned_kind == "concurrent" else None
     sampler = ClockSampler(0).start()
     t_start = time.perf_counter()
     ms = timed(b.step, args.steps)
@@ -492,7 +515,7 @@ def run_batched(args):
     tuned = rate(ms, args.steps)
     value = tuned["MLUPS"]
     kernel = {"fused": "k_batch_grid", "persistent": "k_batch_persistent",
-              "concurrent": "k_step4 of every member, concurrent streams"}[tuned_kind]
+              "concurrent": "each member's step kernel, concurrent streams"}[tuned_kind]
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": tuned["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -501,7 +524,7 @@ def run_batched(args):
                    **({"sides": "uniform 128..1024", "Ra": "log-uniform [1e3, 1e6]"}
                       if args.batch_members == "cavities" else {"shape": f"{args.nx} x {args.H}", "Ra": 1e6}),
                    "storage": STORAGE_NAME[args.storage],
-                   "tuned": {"kind": tuned_kind, "config": tuned_cfg, "graph_steps": 32,
+                   "tuned": {"kind": tuned_kind, "config": tuned_cfg, "member_kernel": member_kernel, "graph_steps": 32,
                              "steps_per_launch": 32 if tuned_kind == "persistent" else 1},
                    "l2": "no flush: working set > L2",
                    "tune_ms_per_step": {k: (round(m, 5) if np.isfinite(m) else None) for k, m in ms_cand.items()}},
@@ -549,7 +572,8 @@ def run_cost(args):
             lat = P.Lattice(case, storage=st)
             kernels = [("auto", 0)]
             if st != "f64" and args.sweep:
-                kernels += [("scalar", 0)] + [("vec4", c) for c in range(P.step_kernel_count(st, "vec4"))]
+                kernels += [("scalar", 0)] + [(v, c) for v in ("vec4", "vec4w")
+                                              for c in range(P.step_kernel_count(st, v))]
             row = {}
             for v in kernels:
                 lat.set_step_kernel(*v)
@@ -562,7 +586,7 @@ def run_cost(args):
                 launches += k
                 ms = e0.elapsed_time(e1) / k
                 gbs = bpn * fluid / (ms * 1e-3) / 1e9
-                row[f"{v[0]}{v[1] if v[0] == 'vec4' else ''}"] = {
+                row[f"{v[0]}{v[1] if v[0] in ('vec4', 'vec4w') else ''}"] = {
                     "MLUPS": round(fluid / (ms * 1e-3) / 1e6, 1), "ms_per_step": round(ms, 5),
                     "GB/s": round(gbs, 1), "frac": round(gbs / peak, 4)}
             try:  # the timing does not depend on it, but say whether the run stayed finite
@@ -759,7 +783,7 @@ def main():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "f64"])
     ap.add_argument("--nx", type=int, default=4096)
     ap.add_argument("--H", type=int, default=2048)
-    ap.add_argument("--variant", default="auto", choices=["auto", "scalar", "vec4", "vec8", "tma"],
+    ap.add_argument("--variant", default="auto", choices=["auto", "scalar", "vec4", "vec4w", "vec8", "tma"],
                     help="step kernel variant (lbm_set_step_kernel)")
     ap.add_argument("--config", type=int, default=0, help="shape index of the step variant")
     ap.add_argument("--no-variants", action="store_true")

@@ -175,13 +175,18 @@ lbm_status lbm_sync(lbm_lattice *h);
 
 /* Step kernel variants. All compute the same arithmetic and give the same
  * bits for a given storage. AUTO picks the fastest measured on GB300: the
- * scalar kernel for FP64; VEC4 for FP32 / FP16 with config 1 / 3 (MRT, D2Q5),
- * 1 / 1 (BGK, D2Q5), 0 / 1 (MRT, D2Q9 temperature model) or 0 / 0 (BGK, D2Q9
- * temperature model). The FP16 VEC4
- * kernel also asks L2 to prefetch the population segments 16 rows ahead.
+ * scalar kernel for FP64; VEC4 for FP32 / FP16 with config 1 / 1 (MRT, D2Q5),
+ * 0 / 1 (BGK, D2Q5) or 0 / 0 (D2Q9 temperature model), except VEC4W config 1
+ * for FP32 MRT D2Q5 lattices whose rows are not a multiple of 512 cells.
  * SCALAR: one cell per thread. VEC4: four cells per thread with 128-bit (FP32)
- * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls; configs 0-4 ask
- * for 4, 5, 6, 7 or 8 resident blocks per SM. VEC8 (FP16 only): eight cells per
+ * / 64-bit (FP16) loads and warp shuffles for the x +- 1 pulls, one 512-cell
+ * row segment per 128-thread block; configs 0-4 ask for 4, 5, 6, 7 or 8
+ * resident blocks per SM. VEC4W: the same with one 128-cell row segment per
+ * warp (four per block), so that rows that are not a multiple of 512 cells
+ * leave no warp of a block idle; the same configs. Both ask L2 to prefetch
+ * their segment of the link map (and, FP16, of the population planes) 32 rows
+ * ahead and launch as programmatic dependents of the previous step (a step's
+ * blocks wait on the device for the previous grid). VEC8 (FP16 only): eight cells per
  * thread, one 128-bit load per plane, x +- 1 realignment by byte permutes;
  * configs 0-1 ask for 4 or 3 blocks per SM. TMA: row segments staged in shared
  * memory by bulk copies in a multi-stage pipeline; its config index selects
@@ -191,7 +196,8 @@ typedef enum {
     LBM_STEP_SCALAR = 1,
     LBM_STEP_VEC4 = 2,
     LBM_STEP_TMA = 3,
-    LBM_STEP_VEC8 = 4
+    LBM_STEP_VEC8 = 4,
+    LBM_STEP_VEC4W = 5
 } lbm_step_variant;
 
 /* Number of configs of a variant for a storage (0 if the variant does not
@@ -334,8 +340,9 @@ lbm_status lbm_batch_remove(lbm_batch *b, lbm_lattice *h);
  * batch holding a lattice with node-based walls runs FUSED, whose boundary-node
  * pass goes between steps.
  * CONCURRENT: each member's own single-lattice step kernel (its
- * lbm_set_step_kernel choice), the members on separate streams between a fork
- * and a join, so their kernels run side by side. */
+ * lbm_set_step_kernel choice, read at every lbm_batch_step: a change since the
+ * batch's graph was captured captures it again), the members on separate
+ * streams between a fork and a join, so their kernels run side by side. */
 typedef enum { LBM_BATCH_FUSED = 0, LBM_BATCH_CONCURRENT = 1, LBM_BATCH_PERSISTENT = 2 } lbm_batch_kind;
 lbm_status lbm_batch_set_kind(lbm_batch *b, int32_t kind);
 
@@ -355,16 +362,31 @@ lbm_status lbm_batch_get_mode(const lbm_batch *b, int32_t *kind, int32_t *steps_
  * row order) a block of the persistent kernel takes per work unit (default 1). */
 lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_unit);
 
+/* The step kernel every member runs in the CONCURRENT kind: LBM_STEP_AUTO
+ * (config 0, the default) keeps each member's own lbm_set_step_kernel choice;
+ * LBM_STEP_SCALAR (config 0), LBM_STEP_VEC4 or LBM_STEP_VEC4W (config 0..4)
+ * runs that kernel for every member instead (the same bits; members that run
+ * side by side favour other occupancies than a lattice alone). LBM_EINVAL
+ * otherwise. */
+lbm_status lbm_batch_set_member_kernel(lbm_batch *b, int32_t variant, int32_t config);
+
+/* The member kernel in force (variant, config). Either pointer may be NULL. */
+lbm_status lbm_batch_get_member_kernel(const lbm_batch *b, int32_t *variant, int32_t *config);
+
 /* Autotuner: times trial_steps (>= 2) steps of every candidate on the current
  * members -- the FUSED kernel at configs 0-4, the PERSISTENT kernel at configs
  * 0-4 (steps_per_launch steps per launch, 32 if it is 1), and the CONCURRENT
- * kind -- each trial recomputing the current step into the other buffer, so the
- * state is unchanged; selects the fastest (kind, config; the PERSISTENT kind
- * also keeps the trial's steps per launch), and returns the kind in
- * *best_kind, the config in *best_config (-1 for CONCURRENT) and the mean ms
- * per step of every candidate in ms_per_step[11] (FUSED 0-4, PERSISTENT 0-4,
- * CONCURRENT; +inf for a candidate that cannot run, such as PERSISTENT with
- * node-based walls). Any output may be NULL. Synchronises. */
+ * kind with the members' own kernels, with every member on VEC4 at configs
+ * 0-4 and on VEC4W at configs 0-4 -- each trial recomputing the current step
+ * into the other buffer, so the state is unchanged; selects the fastest (kind
+ * and config, or for CONCURRENT the member kernel; the PERSISTENT kind also
+ * keeps the trial's steps per launch), and returns the kind in *best_kind, in
+ * *best_config the config (FUSED, PERSISTENT) or, for CONCURRENT, -1 (members'
+ * own), 0-4 (VEC4 config c) or 5-9 (VEC4W config c - 5), and the mean ms per
+ * step of every candidate in ms_per_step[21] (FUSED 0-4, PERSISTENT 0-4,
+ * CONCURRENT own, CONCURRENT VEC4 0-4, CONCURRENT VEC4W 0-4; +inf for a
+ * candidate that cannot run, such as PERSISTENT with node-based walls). Any
+ * output may be NULL. Synchronises. */
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind, int32_t *best_config,
                           float *ms_per_step);
 

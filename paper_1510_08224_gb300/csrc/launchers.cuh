@@ -139,6 +139,11 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
             // registers, 4
             if (p.tq == 9) q.config = 0;
             else q.config = (p.bgk && sizeof(S) == 4) ? 0 : 1;
+            // FP32 MRT D2Q5 rows that are not a multiple of 512 cells: the per-warp form,
+            // which leaves no warp of a block idle at a row's end (600 x 600: 0.77 -> 0.82
+            // of the copy peak, 1100 x 900: 0.88 -> 0.91); in FP16 its per-warp prefetches
+            // measured slower (4096 x 2048: 0.78 against 0.96)
+            if (sizeof(S) == 4 && p.tq == 5 && !p.bgk && p.pitch % 512 != 0) variant = kStepVec4w;
         }
     } else {
         variant = kStepScalar;
@@ -151,8 +156,8 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
 // blocks finish and wait there (griddepcontrol.wait) for that grid's completion,
 // which hides the launch latency between back-to-back steps (0.2 % of a step on
 // GB300). After anything but a kernel the dependency is the ordinary one.
-template <typename S, int MINB, int TQ, bool BGK>
-cudaError_t launch_step4(dim3 grid, cudaStream_t st, const Planes<S> &pl, const Geom &g, const RatesC<float> &r) {
+template <typename K, typename... A>
+cudaError_t launch_dependent(K kern, dim3 grid, cudaStream_t st, A... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = dim3(128);
@@ -163,7 +168,23 @@ cudaError_t launch_step4(dim3 grid, cudaStream_t st, const Planes<S> &pl, const 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_step4<S, MINB, TQ, BGK>, pl, g, r);
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <typename S, int MINB, int TQ, bool BGK>
+cudaError_t launch_step4(dim3 grid, cudaStream_t st, const Planes<S> &pl, const Geom &g, const RatesC<float> &r) {
+    return launch_dependent(k_step4<S, MINB, TQ, BGK>, grid, st, pl, g, r);
+}
+
+// The per-warp form: one 128-cell row segment per warp, four per block.
+template <typename S, int MINB, int TQ, bool BGK>
+cudaError_t launch_step4w(const KParams &p, int src, cudaStream_t st) {
+    const int upr = (p.pitch + 127) / 128;
+    const long long nunits = (long long)p.ny * upr;
+    if (nunits > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+    const dim3 grid((unsigned)((nunits + 3) / 4));
+    return launch_dependent(k_step4w<S, MINB, TQ, BGK>, grid, st, make_planes<S>(p, src), make_geom(p),
+                            make_rates<float>(p), upr, (int)nunits);
 }
 
 // TQ: temperature populations per node (5: D2Q5; 9: the D2Q9 model). BGK:
@@ -192,6 +213,15 @@ cudaError_t launch_step_m(const KParams &p, int variant, int src, cudaStream_t s
                 case 3: return launch_step4<S, 7, TQ, BGK>(grid, st, pl, g, r);
                 case 4: return launch_step4<S, 8, TQ, BGK>(grid, st, pl, g, r);
                 default: return launch_step4<S, 4, TQ, BGK>(grid, st, pl, g, r);
+            }
+        }
+        if (variant == kStepVec4w) {
+            switch (p.config) {
+                case 1: return launch_step4w<S, 5, TQ, BGK>(p, src, st);
+                case 2: return launch_step4w<S, 6, TQ, BGK>(p, src, st);
+                case 3: return launch_step4w<S, 7, TQ, BGK>(p, src, st);
+                case 4: return launch_step4w<S, 8, TQ, BGK>(p, src, st);
+                default: return launch_step4w<S, 4, TQ, BGK>(p, src, st);
             }
         }
         if constexpr (sizeof(S) == 2 && kBase) {

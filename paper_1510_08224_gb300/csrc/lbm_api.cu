@@ -877,7 +877,7 @@ int32_t lbm_step_kernel_count(int32_t storage, int32_t variant) {
     if (storage < LBM_F64 || storage > LBM_F16_SHIFTED) return 0;
     if (variant == LBM_STEP_AUTO || variant == LBM_STEP_SCALAR) return 1;
     if (storage == LBM_F64) return 0;
-    if (variant == LBM_STEP_VEC4) return 5;
+    if (variant == LBM_STEP_VEC4 || variant == LBM_STEP_VEC4W) return 5;
     if (variant == LBM_STEP_TMA) return nomrt::kTmaConfigCount;
     if (variant == LBM_STEP_VEC8) return storage == LBM_F16_SHIFTED ? 2 : 0;
     return 0;

@@ -369,11 +369,17 @@ struct lbm_batch {
     int rows_per_unit = 1;
     int barrier_extra = 0;  // test hook: grid-barrier arrivals that never come
     int kind = LBM_BATCH_FUSED;
+    // concurrent kind: the step kernel every member runs (LBM_STEP_AUTO: each member's own choice)
+    int member_variant = LBM_STEP_AUTO;
+    int member_config = 0;
     // concurrent kind: one stream per member for the fork/join of the graph
     std::vector<cudaStream_t> lstreams;
     std::vector<cudaEvent_t> levents;
     cudaEvent_t fork = nullptr;
     cudaGraphExec_t graph = nullptr;
+    // the members' step kernels (variant, config) when the graph was captured: a concurrent
+    // batch's graph holds them, so a member's later lbm_set_step_kernel drops the graph
+    std::vector<int2> graph_kernels;
     std::string err;
 
     int cfg() const { return config >= 0 ? config : (storage == LBM_F16_SHIFTED ? 3 : 1); }
@@ -493,6 +499,17 @@ cudaError_t ensure_streams(lbm_batch *b) {
 // chosen variant), each member on its own stream between a fork and a join on
 // `st`, so the members' kernels can run concurrently. advance = false re-runs
 // the current step n times without advancing (tuning).
+// The parameters a member's step runs with in the concurrent kind: its own, with the
+// batch's member kernel in place of its own choice where one is set.
+nomrt::KParams member_params(const lbm_batch *b, const lbm_lattice *h) {
+    nomrt::KParams q = h->kp;
+    if (b->member_variant != LBM_STEP_AUTO) {
+        q.variant = b->member_variant;
+        q.config = b->member_config;
+    }
+    return q;
+}
+
 cudaError_t launch_concurrent(lbm_batch *b, int n, cudaStream_t st, bool advance) {
     cudaError_t e = ensure_streams(b);
     if (e != cudaSuccess) return e;
@@ -509,8 +526,9 @@ cudaError_t launch_concurrent(lbm_batch *b, int n, cudaStream_t st, bool advance
         e = cudaStreamWaitEvent(ls, b->fork, 0);
         if (e != cudaSuccess) return e;
         int cur = h->cur;
+        const nomrt::KParams q = member_params(b, h);
         for (int k = 0; k < n; ++k) {
-            e = h->L->step(h->kp, cur, ls);
+            e = h->L->step(q, cur, ls);
             if (e != cudaSuccess) return e;
             if (advance) cur ^= 1;
         }
@@ -586,8 +604,28 @@ cudaError_t launch_steps(lbm_batch *b, int parity, int n, cudaStream_t st) {
     return cudaSuccess;
 }
 
+std::vector<int2> member_kernels(const lbm_batch *b) {
+    std::vector<int2> k;
+    k.reserve(b->members.size());
+    for (const lbm_lattice *h : b->members) {
+        const nomrt::KParams q = member_params(b, h);
+        k.push_back(make_int2(q.variant, q.config));
+    }
+    return k;
+}
+
+bool same_kernels(const std::vector<int2> &a, const std::vector<int2> &c) {
+    if (a.size() != c.size()) return false;
+    for (size_t i = 0; i < a.size(); ++i)
+        if (a[i].x != c[i].x || a[i].y != c[i].y) return false;
+    return true;
+}
+
 lbm_status ensure_graph(lbm_batch *b) {
+    if (b->graph && b->kind == LBM_BATCH_CONCURRENT && !same_kernels(b->graph_kernels, member_kernels(b)))
+        drop_graph(b);
     if (b->graph || b->graph_steps <= 0) return LBM_OK;
+    b->graph_kernels = member_kernels(b);
     cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return bcuda(b, e, "begin capture");
     cudaError_t le = launch_steps(b, 0, b->graph_steps, b->cap);
@@ -694,6 +732,24 @@ lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_u
     return LBM_OK;
 }
 
+lbm_status lbm_batch_set_member_kernel(lbm_batch *b, int32_t variant, int32_t config) {
+    if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
+    const bool ok = (variant == LBM_STEP_AUTO && config == 0) || (variant == LBM_STEP_SCALAR && config == 0) ||
+                    ((variant == LBM_STEP_VEC4 || variant == LBM_STEP_VEC4W) && config >= 0 && config < 5);
+    if (!ok) return bfail(b, LBM_EINVAL, "member kernel must be AUTO, SCALAR, or VEC4 / VEC4W with config 0..4");
+    b->member_variant = variant;
+    b->member_config = config;
+    drop_graph(b);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_member_kernel(const lbm_batch *b, int32_t *variant, int32_t *config) {
+    if (!b) return LBM_EINVAL;
+    if (variant) *variant = b->member_variant;
+    if (config) *config = b->member_config;
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_step(lbm_batch *b, int64_t nsteps) {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
     if (nsteps < 0) return bfail(b, LBM_EINVAL, "nsteps must be >= 0");
@@ -779,7 +835,10 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
     const int parity = (int)(b->s & 1);
     const bool nee = any_nee(b);
     const int k = b->steps_per_launch > 1 ? b->steps_per_launch : nomrt::kDefaultPersistentSteps;
-    constexpr int kCand = 2 * nomrt::kBatchConfigs + 1;
+    // candidates: FUSED configs, PERSISTENT configs, CONCURRENT with the members' own kernels,
+    // then CONCURRENT with every member on VEC4 and on VEC4W at each config
+    constexpr int kConc = 2 * nomrt::kBatchConfigs;
+    constexpr int kCand = kConc + 1 + 2 * nomrt::kBatchConfigs;
     float ms[kCand];
     for (float &m : ms) m = INFINITY;
     cudaEvent_t e0, e1;
@@ -825,11 +884,15 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
             std::min(k, trial_steps), &ms[nomrt::kBatchConfigs + c]);
         if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (persistent)");
     }
-    if (out == LBM_OK) {
-        cudaError_t e = timed([&](int n) { return launch_concurrent(b, n, b->stream, false); }, 1,
-                              &ms[2 * nomrt::kBatchConfigs]);
+    const int own_variant = b->member_variant, own_config = b->member_config;
+    for (int c = 0; c <= 2 * nomrt::kBatchConfigs && out == LBM_OK; ++c) {
+        b->member_variant = c == 0 ? LBM_STEP_AUTO : c <= nomrt::kBatchConfigs ? LBM_STEP_VEC4 : LBM_STEP_VEC4W;
+        b->member_config = c == 0 ? 0 : (c - 1) % nomrt::kBatchConfigs;
+        cudaError_t e = timed([&](int n) { return launch_concurrent(b, n, b->stream, false); }, 1, &ms[kConc + c]);
         if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (concurrent)");
     }
+    b->member_variant = own_variant;
+    b->member_config = own_config;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (out != LBM_OK) return out;
@@ -846,10 +909,13 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
         b->steps_per_launch = k;
     } else {
         b->kind = LBM_BATCH_CONCURRENT;
+        const int c = best - kConc;
+        b->member_variant = c == 0 ? LBM_STEP_AUTO : c <= nomrt::kBatchConfigs ? LBM_STEP_VEC4 : LBM_STEP_VEC4W;
+        b->member_config = c == 0 ? 0 : (c - 1) % nomrt::kBatchConfigs;
     }
     drop_graph(b);
     if (best_kind) *best_kind = b->kind;
-    if (best_config) *best_config = b->kind == LBM_BATCH_CONCURRENT ? -1 : b->config;
+    if (best_config) *best_config = b->kind == LBM_BATCH_CONCURRENT ? best - kConc - 1 : b->config;
     if (ms_per_step)
         for (int c = 0; c < kCand; ++c) ms_per_step[c] = ms[c];
     return LBM_OK;

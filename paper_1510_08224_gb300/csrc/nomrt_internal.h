@@ -38,6 +38,7 @@ constexpr int kStepScalar = 1;
 constexpr int kStepVec4 = 2;
 constexpr int kStepTma = 3;
 constexpr int kStepVec8 = 4;
+constexpr int kStepVec4w = 5;
 // Shapes of the TMA step kernel (see launchers.cuh).
 constexpr int kTmaConfigCount = 5;
 

@@ -1461,4 +1461,39 @@ __global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const G
     }
 }
 
+// The same step with one warp's 128-cell row segment as the unit of work instead
+// of a block's 512 cells: unit u is segment u % upr of row u / upr (upr =
+// ceil(pitch / 128) segments per row), four consecutive units per 128-thread
+// block. Where rows are not a multiple of 512 cells, k_step4's last block of
+// every row holds warps past the row's end, which keep a block slot while doing
+// nothing; here only the lattice's last block can. Each warp asks L2 for its own
+// segment of the link map (and FP16 planes) MPF rows ahead. Same row code, same
+// bits; launched as a programmatic dependent like k_step4.
+template <typename S, int MINB, int TQ = 5, bool BGK = false>
+__global__ void __launch_bounds__(128, MINB)
+    k_step4w(const Planes<S> pl, const Geom g, const RatesC<float> r, int upr, int nunits) {
+    constexpr int PF = PrefetchRows<S>::value;
+    constexpr int MPF = PrefetchRows<S>::mask;
+    static_assert(PF == 0 || PF == MPF, "FP16 prefetches planes and link map with one lead");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    const int lane = threadIdx.x & 31;
+    const int u = blockIdx.x * 4 + (int)(threadIdx.x >> 5);
+    if (u >= nunits) return;  // the whole warp: past the lattice's last unit
+    const int y = u / upr;
+    const int xs = (u - y * upr) * 128;
+    // lane q < 9 + TQ: plane q (FP16 only); lane 9 + TQ (FP16) or 0 (FP32): the link map.
+    // 16-byte aligned: xs is a multiple of 128 cells, rows are pitched to 32 cells
+    if ((PF > 0 ? lane <= 9 + TQ : lane == 0) && y + MPF < g.ny) {
+        const int n = min(128, g.pitch - xs);
+        const size_t at = (size_t)(y + MPF) * g.pitch + xs;
+        const bool map = PF == 0 || lane == 9 + TQ;
+        const void *pp = map ? static_cast<const void *>(g.mask + at)
+                             : static_cast<const void *>(pl.src_at(min(lane, 8 + TQ)) + at);
+        const unsigned bytes = map ? (unsigned)n : (unsigned)(n * sizeof(S));
+        if (NOMRT_BULK_OK(g, pp, bytes, 55)) prefetch_l2_bulk(pp, bytes);
+    }
+    row4<S, Planes<S>, true, TQ, BGK>(pl, g, r, xs + 4 * lane, y, lane);
+}
+
 }  // namespace nomrt

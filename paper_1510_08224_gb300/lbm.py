@@ -20,7 +20,7 @@ STORAGE = {"f64": 0, "f32": 1, "f16": 2}
 STORAGE_BYTES = {"f64": 8, "f32": 4, "f16": 2}
 SIDES = {"left": 0, "right": 1, "bottom": 2, "top": 3}
 
-STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3, "vec8": 4}
+STEP_VARIANTS = {"auto": 0, "scalar": 1, "vec4": 2, "tma": 3, "vec8": 4, "vec4w": 5}
 # Every symbol include/nomrt_lbm.h declares.
 EXPORTED = ("lbm_footprint_bytes", "lbm_validate", "lbm_create", "lbm_step", "lbm_sync", "lbm_step_kernel_count",
             "lbm_set_step_kernel", "lbm_read_macro", "lbm_read_macro_rows",
@@ -30,7 +30,7 @@ EXPORTED = ("lbm_footprint_bytes", "lbm_validate", "lbm_create", "lbm_step", "lb
             "lbm_debug_bounds_limit", "lbm_batch_create", "lbm_batch_add", "lbm_batch_remove",
             "lbm_batch_set_mode", "lbm_batch_set_kind", "lbm_batch_set_config", "lbm_batch_tune", "lbm_batch_step", "lbm_batch_sync",
             "lbm_batch_info", "lbm_batch_get_mode", "lbm_batch_residuals", "lbm_batch_last_error", "lbm_batch_destroy",
-            "lbm_batch_debug_barrier_extra")
+            "lbm_batch_debug_barrier_extra", "lbm_batch_set_member_kernel", "lbm_batch_get_member_kernel")
 BATCH_KINDS = {"fused": 0, "concurrent": 1, "persistent": 2}
 
 
@@ -129,6 +129,8 @@ def load():
                            ("lbm_batch_residuals", [vp, C.c_int32, C.POINTER(vp), dp, C.POINTER(C.c_int32)]),
                            ("lbm_batch_step", [vp, C.c_int64]), ("lbm_batch_sync", [vp]),
                            ("lbm_batch_debug_barrier_extra", [vp, C.c_int32]),
+                           ("lbm_batch_set_member_kernel", [vp, C.c_int32, C.c_int32]),
+                           ("lbm_batch_get_member_kernel", [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
                            ("lbm_batch_info", [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                                C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)])):
             getattr(L, name).restype = C.c_int
@@ -238,7 +240,7 @@ def step_kernel_count(storage: str, variant) -> int:
 
 def step_kernels(storage: str):
     """Every (variant, config) pair available for a storage."""
-    return [(v, c) for v in ("scalar", "vec4", "vec8", "tma") for c in range(step_kernel_count(storage, v))]
+    return [(v, c) for v in ("scalar", "vec4", "vec4w", "vec8", "tma") for c in range(step_kernel_count(storage, v))]
 
 
 def lbm_footprint_bytes(params) -> int:
@@ -316,7 +318,7 @@ class Lattice:
         _check(load().lbm_sync(self._h), self._h)
 
     def set_step_kernel(self, variant, config: int = 0):
-        """variant 'auto', 'scalar', 'vec4', 'vec8' or 'tma' and a config index
+        """variant 'auto', 'scalar', 'vec4', 'vec4w', 'vec8' or 'tma' and a config index
         (see lbm_set_step_kernel)."""
         v = STEP_VARIANTS[variant] if isinstance(variant, str) else int(variant)
         _check(load().lbm_set_step_kernel(self._h, v, int(config)), self._h)
@@ -415,16 +417,35 @@ class Batch:
     def set_config(self, config: int, rows_per_unit: int = 1):
         self._check(load().lbm_batch_set_config(self._h, int(config), int(rows_per_unit)))
 
+    def set_member_kernel(self, variant="auto", config: int = 0):
+        """The step kernel every member runs in the concurrent kind: 'auto'
+        (each member's own choice), 'scalar', or 'vec4' / 'vec4w' with a
+        config 0..4 (lbm_batch_set_member_kernel)."""
+        v = STEP_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        self._check(load().lbm_batch_set_member_kernel(self._h, v, int(config)))
+
+    def get_member_kernel(self):
+        """(variant name, config) of the concurrent kind's member kernel."""
+        v, c = C.c_int32(), C.c_int32()
+        self._check(load().lbm_batch_get_member_kernel(self._h, C.byref(v), C.byref(c)))
+        names = {n: k for k, n in STEP_VARIANTS.items()}
+        return names[v.value], c.value
+
     def tune(self, trial_steps: int = 8):
         """Autotune kind and config on the current members (state unchanged).
-        Returns (kind name, config (-1 for concurrent), {candidate: ms per
-        step}) with candidates fused_cfg0-4, persistent_cfg0-4, concurrent."""
+        Returns (kind name, config, {candidate: ms per step}) with candidates
+        fused_cfg0-4, persistent_cfg0-4, concurrent (the members' own kernels),
+        concurrent_vec4_cfg0-4 and concurrent_vec4w_cfg0-4; for the concurrent
+        kind the config is -1 (own), 0-4 (vec4) or 5-9 (vec4w), already in
+        force as the member kernel."""
         kind, cfg = C.c_int32(), C.c_int32()
-        ms = (C.c_float * 11)()
+        ms = (C.c_float * 21)()
         self._check(load().lbm_batch_tune(self._h, int(trial_steps), C.byref(kind), C.byref(cfg), ms))
         table = {f"fused_cfg{c}": ms[c] for c in range(5)}
         table.update({f"persistent_cfg{c}": ms[5 + c] for c in range(5)})
         table["concurrent"] = ms[10]
+        table.update({f"concurrent_vec4_cfg{c}": ms[11 + c] for c in range(5)})
+        table.update({f"concurrent_vec4w_cfg{c}": ms[16 + c] for c in range(5)})
         names = {v: n for n, v in BATCH_KINDS.items()}
         return names[kind.value], cfg.value, table
 

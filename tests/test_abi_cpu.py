@@ -36,6 +36,19 @@ def test_library_exports_every_declared_symbol():
     assert set(P.EXPORTED) == _declared()
 
 
+def test_step_kernel_counts_on_host():
+    """Every variant's config count per storage (a host-only call): FP64 has the
+    scalar kernel only; VEC4 and its per-warp form VEC4W five configs each."""
+    import paper_1510_08224_gb300 as P
+    assert P.step_kernel_count("f64", "scalar") == 1
+    for v in ("vec4", "vec4w", "vec8", "tma"):
+        assert P.step_kernel_count("f64", v) == 0
+    for st in ("f32", "f16"):
+        assert P.step_kernel_count(st, "vec4") == 5 and P.step_kernel_count(st, "vec4w") == 5
+    assert P.step_kernel_count("f32", "vec8") == 0 and P.step_kernel_count("f16", "vec8") == 2
+    assert ("vec4w", 4) in P.step_kernels("f16") and ("vec4w", 0) in P.step_kernels("f32")
+
+
 def test_footprint_and_validation_on_host():
     import paper_1510_08224_gb300 as P
     L = P.load()

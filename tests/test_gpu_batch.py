@@ -37,8 +37,12 @@ def _alone(P, case, storage, nsteps, seed):
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 @pytest.mark.parametrize("mode", [(1, 0, 1, "fused"), (1, 4, 4, "fused"), (3, 0, 16, "persistent"),
-                                  (3, 6, 3, "persistent"), (1, 0, 4, "concurrent"), (1, 4, 4, "concurrent")])
+                                  (3, 6, 3, "persistent"), (1, 0, 4, "concurrent"), (1, 4, 4, "concurrent"),
+                                  (1, 4, 1, "concurrent", ("vec4w", 1)), (1, 0, 1, "concurrent", ("vec4", 4)),
+                                  (1, 4, 1, "concurrent", ("scalar", 0))])
 def test_batch_equals_alone(storage, mode):
+    """Every kind, and the concurrent kind with a member kernel set for all
+    members (VEC4W, VEC4 at 8 blocks/SM, SCALAR) instead of their own."""
     P = _P()
     cases = _mix()
     total = 11
@@ -47,6 +51,9 @@ def test_batch_equals_alone(storage, mode):
     b.set_mode(*mode[:2])
     b.set_config(-1, mode[2])
     b.set_kind(mode[3])
+    if len(mode) > 4:
+        b.set_member_kernel(*mode[4])
+        assert b.get_member_kernel() == mode[4]
     lats = []
     for i, c in enumerate(cases):
         lat = P.Lattice(c, storage=storage)
@@ -90,8 +97,14 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
     b.sync()
     before = [lat.populations() for lat in lats]
     kind, best, ms = b.tune(trial_steps=4)
-    assert kind in ("fused", "persistent", "concurrent") and (best == -1) == (kind == "concurrent")
-    assert all(m > 0 for m in ms.values()) and len(ms) == 11
+    assert kind in ("fused", "persistent", "concurrent")
+    if kind == "concurrent":
+        # -1: the members' own kernels; 0-4 VEC4 at config c; 5-9 VEC4W at config c - 5
+        want = ("auto", 0) if best == -1 else ("vec4" if best < 5 else "vec4w", best % 5)
+        assert -1 <= best <= 9 and b.get_member_kernel() == want
+    else:
+        assert 0 <= best <= 4
+    assert all(m > 0 for m in ms.values()) and len(ms) == 21
     # the mix holds a lattice with node-based walls: the persistent kernel cannot take it
     assert all(np.isinf(ms[f"persistent_cfg{c}"]) for c in range(5)) and kind != "persistent"
     assert b.get_mode()[0] == kind
@@ -106,7 +119,8 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
         f, g = lat.populations()
         fr, gr = ref.populations()
         assert np.array_equal(f, fr) and np.array_equal(g, gr)
-    assert b.info()["config"] == best
+    if kind != "concurrent":
+        assert b.info()["config"] == best
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
@@ -178,6 +192,38 @@ def test_batched_lattice_rejects_lbm_step_and_fp64():
         b.add(P.Lattice(lc.couette(H=4, nx=3), storage="f16"))  # storage mix
     b.remove(lat)
     lat.step(1)
+
+
+def test_member_kernel_choices_and_refusals():
+    """The concurrent kind's member kernel: invalid choices are refused and
+    leave it unchanged; a member's own kernel change after the batch's graph
+    was captured is taken up (a new capture) with the same bits."""
+    P = _P()
+    cases = _mix()[:3]
+    b = P.Batch()
+    lats = []
+    for i, c in enumerate(cases):
+        lat = P.Lattice(c, storage="f32")
+        lat.set_populations(*lc.random_state(c, seed=60 + i))
+        b.add(lat)
+        lats.append(lat)
+    assert b.get_member_kernel() == ("auto", 0)
+    for bad in (("tma", 0), ("vec8", 0), ("vec4", 5), ("vec4w", -1), ("auto", 1), ("scalar", 1)):
+        with pytest.raises(P.LBMError):
+            b.set_member_kernel(*bad)
+    assert b.get_member_kernel() == ("auto", 0)
+    b.set_kind("concurrent")
+    b.set_mode(1, 4)
+    b.step(4)                          # captures the graph with the members' AUTO kernels
+    lats[0].set_step_kernel("scalar")  # changes what the graph holds
+    lats[1].set_step_kernel("vec4w", 2)
+    b.step(8)
+    b.sync()
+    for i, (c, lat) in enumerate(zip(cases, lats)):
+        f, g = lat.populations()
+        fr, gr = _alone(P, c, "f32", 12, 60 + i)
+        assert np.array_equal(f, fr) and np.array_equal(g, gr), i
+    b.close()
 
 
 def test_persistent_barrier_timeout_is_reported_and_recoverable():

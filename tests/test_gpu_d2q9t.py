@@ -116,7 +116,8 @@ def test_d2q9t_step_variants_agree_bitwise(storage, idx):
     case = _cases()[idx]
     f0, g0 = lc.random_state(case, seed=51 + idx)
     out = {}
-    variants = [("scalar", 0)] + [("vec4", c) for c in range(P.step_kernel_count(storage, "vec4"))] + [("auto", 0)]
+    variants = [("scalar", 0)] + [(v, c) for v in ("vec4", "vec4w") for c in range(P.step_kernel_count(storage, v))] \
+        + [("auto", 0)]
     for v in variants:
         lat = P.Lattice(case, storage=storage)
         lat.set_step_kernel(*v)

@@ -162,6 +162,8 @@ def test_fp64_rejects_vector_variants():
         lat.set_step_kernel("tma")
     assert P.step_kernel_count("f64", "tma") == 0 and P.step_kernel_count("f32", "tma") == 5
     assert P.step_kernel_count("f32", "vec8") == 0 and P.step_kernel_count("f16", "vec8") == 2
+    assert P.step_kernel_count("f64", "vec4w") == 0
+    assert P.step_kernel_count("f32", "vec4w") == 5 and P.step_kernel_count("f16", "vec4w") == 5
 
 
 # Accumulated max-norm error after 4000 steps against the FP64 oracle. FP16
