@@ -425,7 +425,7 @@ def run_batched(args):
             # --config -1: the members' own kernels; 0-4: VEC4 at that config; 5-9: VEC4W at config - 5
             set_member_kernel(b, args.config)
         else:
-            b.set_config(args.config, 1)
+            b.set_config(args.config, args.rows_per_unit)
         b.set_mode(32, 32)
         b.step(args.warmup)
         torch.cuda.synchronize()
@@ -439,7 +439,8 @@ def run_batched(args):
         b.close()
         peak, _ = measured_peak()
         print(json.dumps({"workload": wl, "storage": args.storage,
-                          "kind": args.batch_kind, "config": args.config, "steps": args.steps,
+                          "kind": args.batch_kind, "config": args.config, "rows_per_unit": args.rows_per_unit,
+                          "steps": args.steps,
                           "fluid_cells": cells, "ms_per_step": round(ms, 5),
                           "MLUPS": round(cells / (ms * 1e-3) / 1e6, 1),
                           "frac": round(BYTES_PER_NODE[args.storage] * cells / (ms * 1e-3) / 1e9 / peak, 4)}),
@@ -805,6 +806,8 @@ def main():
                     help="serve: HBM budget as a fraction of the stream's total footprint (default: 150 GB)")
     ap.add_argument("--batch-members", default="cavities", choices=["cavities", "rb"],
                     help="batch: the uneven cavity mix, or --count copies of the --nx x --H lattice")
+    ap.add_argument("--rows-per-unit", type=int, default=1,
+                    help="batch --no-tune: row segments per work unit of the persistent kernel")
     ap.add_argument("--batch-kind", default="fused", choices=["fused", "persistent", "concurrent"],
                     help="serve: batch kind of the served path")
     ap.add_argument("--cavity-share", type=float, default=0.75, help="serve: share of cavity requests")

@@ -331,9 +331,9 @@ lbm_status lbm_batch_add(lbm_batch *b, lbm_lattice *h);
 lbm_status lbm_batch_remove(lbm_batch *b, lbm_lattice *h);
 
 /* How a batch step runs.
- * FUSED (the default): one kernel launch per step and launch group, whose 2-D
- * grid covers the members' concatenated rows with the four-cell kernel's
- * 128-thread blocks (one 512-cell row segment each).
+ * FUSED (the default): one kernel launch per step and launch group, one
+ * 128-thread block of the four-cell row code per 512-cell row segment of every
+ * member (a 1-D grid over the members' segments).
  * PERSISTENT: one cooperative launch per group for steps_per_launch steps: its
  * resident blocks stride over the same row segments, with a clock-bounded grid
  * barrier between steps (LBM_ETIMEOUT from lbm_batch_sync if one expires). A

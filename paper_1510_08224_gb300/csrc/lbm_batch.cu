@@ -431,9 +431,9 @@ lbm_status rebuild(lbm_batch *b) {
         nomrt::GridLat &gl = G->lat[G->nlats];
         gl.g = nomrt::make_geom(kp);
         const size_t eb = h->storage == LBM_F16_SHIFTED ? 2 : 4;
-        for (int b = 0; b < 2; ++b)
+        for (int buf = 0; buf < 2; ++buf)
             for (int q = 0; q < nomrt::kQ; ++q)
-                gl.planes[b * nomrt::kQ + q] = static_cast<const char *>(kp.pop[b]) + (size_t)q * kp.plane * eb;
+                gl.planes[buf * nomrt::kQ + q] = static_cast<const char *>(kp.pop[buf]) + (size_t)q * kp.plane * eb;
         gl.flip = b->flip[l];
         gl.xblocks = (kp.pitch / 4 + nomrt::kBatchThreads - 1) / nomrt::kBatchThreads;
         gl.xb_magic = ((1ULL << 32) + (unsigned long long)gl.xblocks - 1) / (unsigned long long)gl.xblocks;

@@ -410,7 +410,7 @@ class Batch:
     def set_kind(self, kind):
         """'fused' (one launch per step over every member's rows), 'persistent'
         (one cooperative launch per steps_per_launch steps, grid barrier between
-        steps) or 'concurrent' (each member's own kernel, members side by side)."""
+        steps) or 'concurrent' (a single-lattice kernel per member, side by side)."""
         k = BATCH_KINDS[kind] if isinstance(kind, str) else int(kind)
         self._check(load().lbm_batch_set_kind(self._h, k))
 

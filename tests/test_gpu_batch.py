@@ -37,12 +37,15 @@ def _alone(P, case, storage, nsteps, seed):
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 @pytest.mark.parametrize("mode", [(1, 0, 1, "fused"), (1, 4, 4, "fused"), (3, 0, 16, "persistent"),
-                                  (3, 6, 3, "persistent"), (1, 0, 4, "concurrent"), (1, 4, 4, "concurrent"),
+                                  (3, 6, 3, "persistent"), (16, 0, 1, "persistent"), (8, 16, 5, "persistent"),
+                                  (1, 0, 4, "concurrent"), (1, 4, 4, "concurrent"),
                                   (1, 4, 1, "concurrent", ("vec4w", 1)), (1, 0, 1, "concurrent", ("vec4", 4)),
                                   (1, 4, 1, "concurrent", ("scalar", 0))])
 def test_batch_equals_alone(storage, mode):
     """Every kind, and the concurrent kind with a member kernel set for all
-    members (VEC4W, VEC4 at 8 blocks/SM, SCALAR) instead of their own."""
+    members (VEC4W, VEC4 at 8 blocks/SM, SCALAR) instead of their own. The
+    persistent modes run 3, 16 and 8 steps per launch (as many grid barriers
+    in one launch) with 1-16 row segments per unit."""
     P = _P()
     cases = _mix()
     total = 11
