@@ -25,3 +25,26 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_terminal_summary(terminalreporter, exitstatus, config):
+    """One line per test file with its passed / failed / skipped counts, so a
+    quiet run's log still records which files ran (the no-alloc entry point's
+    file among them)."""
+    per = {}
+    for kind in ("passed", "failed", "skipped", "error"):
+        for rep in terminalreporter.stats.get(kind, []):
+            nodeid = getattr(rep, "nodeid", "")
+            if not nodeid or getattr(rep, "when", "call") not in ("call", "setup"):
+                continue
+            if kind == "passed" and rep.when != "call":
+                continue
+            f = nodeid.split("::")[0]
+            per.setdefault(f, {}).setdefault(kind, 0)
+            per[f][kind] += 1
+    if not per:
+        return
+    terminalreporter.write_line("per-file results:")
+    for f in sorted(per):
+        counts = ", ".join(f"{n} {k}" for k, n in sorted(per[f].items()))
+        terminalreporter.write_line(f"  {f}: {counts}")
