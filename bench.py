@@ -478,7 +478,7 @@ def run_batched(args):
             cfg = min(cands, key=cands.get)
             set_member_kernel(b, cfg)
         else:
-            cands = {c: ms_cand[f"{kind}_cfg{c}"] for c in range(5)}
+            cands = {c: ms_cand[f"{kind}_cfg{c}"] for c in range(10 if kind == "fused" else 5)}
             cfg = min(cands, key=cands.get)
             b.set_config(cfg, 1)
         b.set_mode(32, 32)

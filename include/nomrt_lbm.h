@@ -358,8 +358,12 @@ lbm_status lbm_batch_get_mode(const lbm_batch *b, int32_t *kind, int32_t *steps_
 
 /* Kernel shape of the FUSED and PERSISTENT kinds: config 0..4 asks ptxas for
  * 4..8 resident 128-thread blocks per SM (-1: the default, 1 for FP32 and 3 for
- * FP16); rows_per_unit (1..1024): consecutive row segments (512 cells each, in
- * row order) a block of the persistent kernel takes per work unit (default 1). */
+ * FP16), one block per 512-cell row segment; config 5..9, for the FUSED kind,
+ * the same occupancies with one 128-cell row segment per warp (four per
+ * block), so that rows that are not a multiple of 512 cells leave no warp of a
+ * block idle (the PERSISTENT kind runs config c as c - 5); rows_per_unit
+ * (1..1024): consecutive row segments (512 cells each, in row order) a block
+ * of the persistent kernel takes per work unit (default 1). */
 lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_unit);
 
 /* The step kernel every member runs in the CONCURRENT kind: LBM_STEP_AUTO
@@ -374,7 +378,7 @@ lbm_status lbm_batch_set_member_kernel(lbm_batch *b, int32_t variant, int32_t co
 lbm_status lbm_batch_get_member_kernel(const lbm_batch *b, int32_t *variant, int32_t *config);
 
 /* Autotuner: times trial_steps (>= 2) steps of every candidate on the current
- * members -- the FUSED kernel at configs 0-4, the PERSISTENT kernel at configs
+ * members -- the FUSED kernel at configs 0-9, the PERSISTENT kernel at configs
  * 0-4 (steps_per_launch steps per launch, 32 if it is 1), and the CONCURRENT
  * kind with the members' own kernels, with every member on VEC4 at configs
  * 0-4 and on VEC4W at configs 0-4 -- each trial recomputing the current step
@@ -383,7 +387,7 @@ lbm_status lbm_batch_get_member_kernel(const lbm_batch *b, int32_t *variant, int
  * keeps the trial's steps per launch), and returns the kind in *best_kind, in
  * *best_config the config (FUSED, PERSISTENT) or, for CONCURRENT, -1 (members'
  * own), 0-4 (VEC4 config c) or 5-9 (VEC4W config c - 5), and the mean ms per
- * step of every candidate in ms_per_step[21] (FUSED 0-4, PERSISTENT 0-4,
+ * step of every candidate in ms_per_step[26] (FUSED 0-9, PERSISTENT 0-4,
  * CONCURRENT own, CONCURRENT VEC4 0-4, CONCURRENT VEC4W 0-4; +inf for a
  * candidate that cannot run, such as PERSISTENT with node-based walls). Any
  * output may be NULL. Synchronises. */

@@ -47,6 +47,7 @@ namespace nomrt {
 
 constexpr int kBatchThreads = 128;
 constexpr int kBatchConfigs = 5;  // resident blocks asked of ptxas: 4 + config
+constexpr int kFusedConfigs = 2 * kBatchConfigs;  // FUSED: configs 5-9 are 0-4 with one row segment per warp
 constexpr int kGroupLats = 64;    // members per launch (the parameter block holds their descriptors)
 constexpr long long kBarrierBudgetCycles = 4000000000LL;  // ~2 s at 2 GHz
 constexpr int kDefaultPersistentSteps = 32;
@@ -94,6 +95,7 @@ struct GridLat {
     unsigned long long xb_magic;  // ceil(2^32 / xblocks): local / xblocks = (local * xb_magic) >> 32
     int flip;
     int xblocks;                  // 512-cell segments per row: ceil(pitch / 512)
+    int upr;                      // 128-cell segments per row: ceil(pitch / 128)
     MemberRates v;
 };
 
@@ -115,6 +117,8 @@ struct GroupParams {
     int nvb;                    // virtual blocks per step
     const int2 *work;           // per virtual block: (member | segment << 8, row), device
     int blk0[kGroupLats + 1];   // first virtual block of each member; blk0[nlats] = nvb
+    int nwb;                    // blocks of the per-warp form per step (four 128-cell units of one member each)
+    int blk0w[kGroupLats + 1];  // first such block of each member; blk0w[nlats] = nwb
     GridLat lat[kGroupLats];
 };
 static_assert(sizeof(GroupParams) <= 32764, "a launch group's descriptors must fit the kernel parameter space");
@@ -182,6 +186,57 @@ template <typename S, int MINB>
 __global__ void __launch_bounds__(kBatchThreads, MINB)
     k_batch_grid(const __grid_constant__ GroupParams P, int parity) {
     for (int vb = blockIdx.x; vb < P.nvb; vb += gridDim.x) batch_block_search<S, true>(P, vb, parity);
+}
+
+// Segment seg (cells 128 seg .. 128 seg + 127) of row y of member lo, one warp's
+// share: the row code of batch_row on a 128-cell unit. FP16 members ask L2 for
+// the segment's planes and link map PF rows ahead (one lane each); FP32 members
+// go without, as in batch_row.
+template <typename S, bool NC>
+__device__ __forceinline__ void batch_row_w(const GroupParams &P, int lo, int seg, int y, int parity, int lane) {
+    const GridLat &L = P.lat[lo];
+    const Geom g = L.g;
+    const int sel = (parity + L.flip) & 1;
+    const MemberPlanes<S> pa{L, sel ? kQ : 0, sel ? 0 : kQ};
+    const int xs = seg * 128;
+    constexpr int PF = PrefetchRows<S>::value;
+    if constexpr (PF > 0) {
+        // 16-byte aligned: xs is a multiple of 128 cells, rows are 128-byte pitched
+        if (lane <= kQ && y + PF < g.ny) {
+            const int n = min(128, g.pitch - xs);
+            const size_t at = (size_t)(y + PF) * g.pitch + xs;
+            const void *pp = lane == kQ ? static_cast<const void *>(g.mask + at)
+                                        : static_cast<const void *>(pa.src_at(min(lane, kQ - 1)) + at);
+            const unsigned bytes = lane == kQ ? (unsigned)n : (unsigned)(n * sizeof(S));
+            if (NOMRT_BULK_OK(g, pp, bytes, 56)) prefetch_l2_bulk(pp, bytes);
+        }
+    }
+    RatesC<float> r = P.rc;  // shared rates: parameter-bank operands
+    apply_member(r, L.v);    // the member's own values: registers
+    row4<S, MemberPlanes<S>, NC>(pa, g, r, xs + 4 * lane, y, lane);
+}
+
+// One step of every member of a group with one 128-cell row segment per warp:
+// the FUSED kind's configs 5-9. A block takes four consecutive segments of one
+// member (row by row, so they may span two rows), so rows that are not a
+// multiple of 512 cells leave no warp idle but in a member's last block, while
+// the member, found by a binary search over the members' first blocks, stays
+// the same across the block (its descriptor in the block-uniform registers).
+template <typename S, int MINB>
+__global__ void __launch_bounds__(kBatchThreads, MINB)
+    k_batch_grid_w(const __grid_constant__ GroupParams P, int parity) {
+    const int vb = blockIdx.x;
+    int lo = 0, hi = P.nlats - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.blk0w[mid] <= vb) lo = mid;
+        else hi = mid - 1;
+    }
+    const GridLat &L = P.lat[lo];
+    const int u = (vb - P.blk0w[lo]) * (kBatchThreads / 32) + (int)(threadIdx.x >> 5);
+    if (u >= L.g.ny * L.upr) return;  // the whole warp: past the member's last segment
+    const int y = u / L.upr;
+    batch_row_w<S, true>(P, lo, u - y * L.upr, y, parity, (int)threadIdx.x & 31);
 }
 
 template <typename S, int MINB, bool PERSISTENT>
@@ -290,9 +345,21 @@ cudaError_t launch_grid_shape(const GroupParams &G, int parity, cudaStream_t st)
     return cudaGetLastError();
 }
 
+template <typename S, int MINB>
+cudaError_t launch_grid_w_shape(const GroupParams &G, int parity, cudaStream_t st) {
+    if (G.nwb == 0) return cudaSuccess;
+    k_batch_grid_w<S, MINB><<<G.nwb, kBatchThreads, 0, st>>>(G, parity);
+    return cudaGetLastError();
+}
+
 template <typename S>
 cudaError_t launch_batch_grid(int config, const GroupParams &G, int parity, cudaStream_t st) {
     switch (config) {
+        case 5: return launch_grid_w_shape<S, 4>(G, parity, st);
+        case 6: return launch_grid_w_shape<S, 5>(G, parity, st);
+        case 7: return launch_grid_w_shape<S, 6>(G, parity, st);
+        case 8: return launch_grid_w_shape<S, 7>(G, parity, st);
+        case 9: return launch_grid_w_shape<S, 8>(G, parity, st);
         case 1: return launch_grid_shape<S, 5>(G, parity, st);
         case 2: return launch_grid_shape<S, 6>(G, parity, st);
         case 3: return launch_grid_shape<S, 7>(G, parity, st);
@@ -331,7 +398,7 @@ template <typename S>
 cudaError_t launch_batch_persistent(int config, const GroupParams &G, int parity, int nsteps, int advance,
                                     int barrier_extra, unsigned *bar, int *status, cudaStream_t st) {
     unsigned *ctr = bar + 2;  // the two step counters follow the barrier's words
-    switch (config) {
+    switch (config % kBatchConfigs) {  // the per-warp configs of the FUSED kind map to their occupancy
         case 1: return launch_persistent_shape<S, 5>(G, parity, nsteps, advance, barrier_extra, bar, ctr, status, st);
         case 2: return launch_persistent_shape<S, 6>(G, parity, nsteps, advance, barrier_extra, bar, ctr, status, st);
         case 3: return launch_persistent_shape<S, 7>(G, parity, nsteps, advance, barrier_extra, bar, ctr, status, st);
@@ -438,6 +505,10 @@ lbm_status rebuild(lbm_batch *b) {
         gl.xblocks = (kp.pitch / 4 + nomrt::kBatchThreads - 1) / nomrt::kBatchThreads;
         gl.xb_magic = ((1ULL << 32) + (unsigned long long)gl.xblocks - 1) / (unsigned long long)gl.xblocks;
         gl.v = nomrt::member_rates(r);
+        gl.upr = (kp.pitch + 127) / 128;
+        G->blk0w[G->nlats + 1] = G->blk0w[G->nlats] + (kp.ny * gl.upr + nomrt::kBatchThreads / 32 - 1) /
+                                                         (nomrt::kBatchThreads / 32);
+        G->nwb = G->blk0w[G->nlats + 1];
         G->unit = b->rows_per_unit;
         G->blk0[G->nlats + 1] = G->blk0[G->nlats] + kp.ny * gl.xblocks;
         G->nvb = G->blk0[G->nlats + 1];
@@ -721,7 +792,7 @@ lbm_status lbm_batch_set_kind(lbm_batch *b, int32_t kind) {
 
 lbm_status lbm_batch_set_config(lbm_batch *b, int32_t config, int32_t rows_per_unit) {
     if (!b) return bfail(nullptr, LBM_EINVAL, "batch is NULL");
-    if (config < -1 || config >= nomrt::kBatchConfigs) return bfail(b, LBM_EINVAL, "config out of range");
+    if (config < -1 || config >= nomrt::kFusedConfigs) return bfail(b, LBM_EINVAL, "config out of range");
     if (rows_per_unit < 1 || rows_per_unit > 1024) return bfail(b, LBM_EINVAL, "rows_per_unit must be 1..1024");
     b->config = config;
     if (rows_per_unit != b->rows_per_unit) {
@@ -835,9 +906,10 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
     const int parity = (int)(b->s & 1);
     const bool nee = any_nee(b);
     const int k = b->steps_per_launch > 1 ? b->steps_per_launch : nomrt::kDefaultPersistentSteps;
-    // candidates: FUSED configs, PERSISTENT configs, CONCURRENT with the members' own kernels,
-    // then CONCURRENT with every member on VEC4 and on VEC4W at each config
-    constexpr int kConc = 2 * nomrt::kBatchConfigs;
+    // candidates: FUSED configs 0-9, PERSISTENT configs 0-4, CONCURRENT with the members' own
+    // kernels, then CONCURRENT with every member on VEC4 and on VEC4W at each config
+    constexpr int kPers = nomrt::kFusedConfigs;
+    constexpr int kConc = kPers + nomrt::kBatchConfigs;
     constexpr int kCand = kConc + 1 + 2 * nomrt::kBatchConfigs;
     float ms[kCand];
     for (float &m : ms) m = INFINITY;
@@ -857,7 +929,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
         if (e == cudaSuccess) *dst = t / (float)trial_steps;
         return e;
     };
-    for (int c = 0; c < nomrt::kBatchConfigs && out == LBM_OK; ++c) {
+    for (int c = 0; c < nomrt::kFusedConfigs && out == LBM_OK; ++c) {
         cudaError_t e = timed(
             [&](int n) -> cudaError_t {
                 for (int i = 0; i < n; ++i) {
@@ -881,7 +953,7 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
                 }
                 return cudaSuccess;
             },
-            std::min(k, trial_steps), &ms[nomrt::kBatchConfigs + c]);
+            std::min(k, trial_steps), &ms[kPers + c]);
         if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (persistent)");
     }
     const int own_variant = b->member_variant, own_config = b->member_config;
@@ -900,12 +972,12 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
     int best = 0;
     for (int c = 1; c < kCand; ++c)
         if (ms[c] < ms[best]) best = c;
-    if (best < nomrt::kBatchConfigs) {
+    if (best < kPers) {
         b->kind = LBM_BATCH_FUSED;
         b->config = best;
-    } else if (best < 2 * nomrt::kBatchConfigs) {
+    } else if (best < kConc) {
         b->kind = LBM_BATCH_PERSISTENT;
-        b->config = best - nomrt::kBatchConfigs;
+        b->config = best - kPers;
         b->steps_per_launch = k;
     } else {
         b->kind = LBM_BATCH_CONCURRENT;

@@ -7,7 +7,7 @@ block before making it and record the first refusal.
    y, in both; halfway and node-based walls; scattered solid cells), in every
    storage, with every step-kernel variant and config, with the D2Q5 and D2Q9
    temperature models and the MRT and BGK collisions, and batched in every
-   batch kind: after 3 steps from an off-equilibrium state no access was
+   batch kind (the fused kind also with one row segment per warp): after 3 steps from an off-equilibrium state no access was
    refused (the synchronising read-out would raise), and the FP64 result still
    equals the oracle's.
 2. The detector: a lattice whose checks accept only the first half of its
@@ -81,10 +81,12 @@ def main():
     mix = [c for c in cases() if c.nx * c.ny > 1]
     halfway = [c for c in mix if not c.name.endswith("nee")]
     for st in ("f32", "f16"):
-        for kind, members in (("fused", mix), ("persistent", halfway), ("concurrent", mix)):
+        for kind, members, cfg in (("fused", mix, -1), ("fused", mix, 6), ("persistent", halfway, -1),
+                                   ("concurrent", mix, -1)):
             b = P.Batch()
             b.set_kind(kind)
             b.set_mode(3, 0)
+            b.set_config(cfg, 1)
             lats = []
             for i, c in enumerate(members):
                 lat = P.Lattice(c, storage=st)

@@ -106,8 +106,8 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
         want = ("auto", 0) if best == -1 else ("vec4" if best < 5 else "vec4w", best % 5)
         assert -1 <= best <= 9 and b.get_member_kernel() == want
     else:
-        assert 0 <= best <= 4
-    assert all(m > 0 for m in ms.values()) and len(ms) == 21
+        assert 0 <= best <= (9 if kind == "fused" else 4)
+    assert all(m > 0 for m in ms.values()) and len(ms) == 26
     # the mix holds a lattice with node-based walls: the persistent kernel cannot take it
     assert all(np.isinf(ms[f"persistent_cfg{c}"]) for c in range(5)) and kind != "persistent"
     assert b.get_mode()[0] == kind
@@ -195,6 +195,35 @@ def test_batched_lattice_rejects_lbm_step_and_fp64():
         b.add(P.Lattice(lc.couette(H=4, nx=3), storage="f16"))  # storage mix
     b.remove(lat)
     lat.step(1)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("config,graph_steps", [(5, 0), (6, 4), (8, 4), (9, 0)])
+def test_fused_per_warp_configs_equal_alone(storage, config, graph_steps):
+    """The FUSED kind's configs 5-9 (one 128-cell row segment per warp, each warp
+    finding its own member): every member of the uneven mix, node-based walls
+    included, produces the bits it produces alone."""
+    P = _P()
+    cases = _mix()
+    b = P.Batch()
+    b.set_mode(1, graph_steps)
+    b.set_config(config, 1)
+    lats = []
+    for i, c in enumerate(cases):
+        lat = P.Lattice(c, storage=storage)
+        lat.set_populations(*lc.random_state(c, seed=80 + i))
+        b.add(lat)
+        lats.append(lat)
+    b.step(9)
+    b.sync()
+    assert b.info()["config"] == config
+    for i, (c, lat) in enumerate(zip(cases, lats)):
+        f, g = lat.populations()
+        fr, gr = _alone(P, c, storage, 9, 80 + i)
+        assert np.array_equal(f, fr) and np.array_equal(g, gr), i
+    with pytest.raises(P.LBMError):
+        b.set_config(10, 1)
+    b.close()
 
 
 def test_member_kernel_choices_and_refusals():
