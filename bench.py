@@ -704,7 +704,7 @@ RB_STEADY_RA = (2e3, 2e4)
 
 def serving_measure(storage: str, count: int, side_lo: int, side_hi: int, step_cap: int, check_every: int,
                     graph_steps: int, rate: float, budget_frac: float | None, kind: str, cavity_share: float,
-                    ra_lo: float = 1e3, ra_hi: float = 1e6, rb_ra=RB_STEADY_RA):
+                    ra_lo: float = 1e3, ra_hi: float = 1e6, rb_ra=RB_STEADY_RA, batch_config: int = -1):
     """Continuous-batching serving against the plain path, on the same seeded
     stream: Poisson arrivals (`rate` per second, seed 0) of `count` cavity (a
     share `cavity_share`) and Rayleigh-Benard requests, sides log-uniform in
@@ -725,7 +725,7 @@ def serving_measure(storage: str, count: int, side_lo: int, side_hi: int, step_c
     reqs = [serve.Request(k, c, t, nusselt_sides=((0,) if kind_ == "cavity" else (2,))) for k, (t, kind_, c) in
             enumerate(stream)]
     cells = sum(int((r.case.flags == 0).sum()) for r in reqs)
-    be = serve.GpuBackend(storage, graph_steps=graph_steps, kind=kind)
+    be = serve.GpuBackend(storage, graph_steps=graph_steps, kind=kind, config=batch_config)
     total_fp = sum(be.footprint(r.case) for r in reqs)
     budget = 150e9 if budget_frac is None else max(budget_frac * total_fp,
                                                    max(be.footprint(r.case) for r in reqs))
@@ -748,6 +748,7 @@ def serving_measure(storage: str, count: int, side_lo: int, side_hi: int, step_c
               "types": f"cavity {cavity_share:g} | rayleigh_benard {1 - cavity_share:g}", "tol": 1e-6,
               "step_cap": srv.step_cap, "check_every": check_every, "hbm_budget_bytes": budget,
               "total_footprint_bytes": total_fp, "storage": STORAGE_NAME[storage], "batch_kind": kind,
+              "batch_config": batch_config,
               "requests": len(reqs), "fluid_cells_total": cells, "graph_steps": graph_steps}
     served = {**serve.summarize(res, span), **serve.summarize_converged(res), "makespan_s": round(span, 3),
               "peak_hbm_bytes": srv.peak_in_use, "max_concurrent": srv.max_active,
@@ -763,7 +764,7 @@ def run_serving(args):
     """The serving stream as its own bench line (value = solves/s)."""
     config, served, plain = serving_measure(args.storage, args.count, args.side_lo, args.side_hi, args.step_cap,
                                             args.check_every, args.graph_steps, args.rate, args.budget_frac,
-                                            args.batch_kind, args.cavity_share)
+                                            args.batch_kind, args.cavity_share, batch_config=args.batch_config)
     line = {
         "metric": METRIC, "value": round(served["solves_per_s"], 4), "unit": "solves/s", "n_gpus": 1,
         "steps": config["step_cap"], "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -806,6 +807,8 @@ def main():
                     help="serve: HBM budget as a fraction of the stream's total footprint (default: 150 GB)")
     ap.add_argument("--batch-members", default="cavities", choices=["cavities", "rb"],
                     help="batch: the uneven cavity mix, or --count copies of the --nx x --H lattice")
+    ap.add_argument("--batch-config", type=int, default=-1,
+                    help="serve: the batch's kernel config (lbm_batch_set_config; -1 the default)")
     ap.add_argument("--rows-per-unit", type=int, default=1,
                     help="batch --no-tune: row segments per work unit of the persistent kernel")
     ap.add_argument("--batch-kind", default="fused", choices=["fused", "persistent", "concurrent"],

@@ -357,7 +357,7 @@ lbm_status lbm_batch_set_mode(lbm_batch *b, int32_t steps_per_launch, int32_t gr
 lbm_status lbm_batch_get_mode(const lbm_batch *b, int32_t *kind, int32_t *steps_per_launch, int32_t *graph_steps);
 
 /* Kernel shape of the FUSED and PERSISTENT kinds: config 0..4 asks ptxas for
- * 4..8 resident 128-thread blocks per SM (-1: the default, 1 for FP32 and 3 for
+ * 4..8 resident 128-thread blocks per SM (-1: the default, 6 for FP32 and 3 for
  * FP16), one block per 512-cell row segment; config 5..9, for the FUSED kind,
  * the same occupancies with one 128-cell row segment per warp (four per
  * block), so that rows that are not a multiple of 512 cells leave no warp of a

@@ -63,10 +63,12 @@ class Result:
 
 class GpuBackend:
     """The CUDA library: lattices in torch device memory, one Batch of the
-    given kind ('fused', 'persistent' or 'concurrent'), optionally replayed
-    from CUDA graphs of graph_steps steps."""
+    given kind ('fused', 'persistent' or 'concurrent') and config (see
+    Batch.set_config; -1 the default), optionally replayed from CUDA graphs of
+    graph_steps steps."""
 
-    def __init__(self, storage: str = "f32", graph_steps: int = 0, kind: str = "fused", steps_per_launch=None):
+    def __init__(self, storage: str = "f32", graph_steps: int = 0, kind: str = "fused", steps_per_launch=None,
+                 config: int = -1):
         import torch
         from . import lbm
         self._lbm = lbm
@@ -77,6 +79,7 @@ class GpuBackend:
         if steps_per_launch is None:  # the persistent kind: one launch per replayed graph
             steps_per_launch = graph_steps if graph_steps > 0 else 32
         self.batch.set_mode(steps_per_launch, graph_steps)
+        self.batch.set_config(config, 1)
 
     def footprint(self, case) -> int:
         p, keep = self._lbm.make_params(case, self.storage)
