@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
 // share: the row code of batch_row on a 128-cell unit. FP16 members ask L2 for
 // the segment's planes and link map PF rows ahead (one lane each); FP32 members
 // go without, as in batch_row.
-template <typename S, bool NC>
+template <typename S, bool NC, bool WARP_PREFETCH = true>
 __device__ __forceinline__ void batch_row_w(const GroupParams &P, int lo, int seg, int y, int parity, int lane) {
     const GridLat &L = P.lat[lo];
     const Geom g = L.g;
@@ -200,7 +200,7 @@ __device__ __forceinline__ void batch_row_w(const GroupParams &P, int lo, int se
     const MemberPlanes<S> pa{L, sel ? kQ : 0, sel ? 0 : kQ};
     const int xs = seg * 128;
     constexpr int PF = PrefetchRows<S>::value;
-    if constexpr (PF > 0) {
+    if constexpr (PF > 0 && WARP_PREFETCH) {
         // 16-byte aligned: xs is a multiple of 128 cells, rows are 128-byte pitched
         if (lane <= kQ && y + PF < g.ny) {
             const int n = min(128, g.pitch - xs);
@@ -232,11 +232,37 @@ __global__ void __launch_bounds__(kBatchThreads, MINB)
         if (P.blk0w[mid] <= vb) lo = mid;
         else hi = mid - 1;
     }
+    constexpr int kWarps = kBatchThreads / 32;
+    const int u0 = (vb - P.blk0w[lo]) * kWarps;
+    constexpr int PF = PrefetchRows<S>::value;
+    if constexpr (PF > 0) {
+        // FP16: the block's four segments are at most two runs of consecutive cells (the end of
+        // row y0, the start of row y0 + 1); warp 0 asks L2 for the first run's planes and link
+        // map PF rows ahead, warp 1 for the second's, one lane per plane (as the 512-cell
+        // kernel does, in runs of up to 1 KB rather than 256-byte pieces per warp)
+        const GridLat &L = P.lat[lo];
+        const Geom &g = L.g;
+        const int y0 = u0 / L.upr, s0 = u0 - y0 * L.upr;
+        const int n0 = min(kWarps, L.upr - s0);
+        const int t = (int)threadIdx.x & 31, piece = (int)threadIdx.x >> 5;
+        const int y = y0 + piece;
+        const int xs = piece == 0 ? s0 * 128 : 0;
+        const int n = min((piece == 0 ? n0 : kWarps - n0) * 128, g.pitch - xs);
+        if (piece < 2 && t <= kQ && n > 0 && y + PF < g.ny) {
+            const int sel = (parity + L.flip) & 1;
+            const MemberPlanes<S> pa{L, sel ? kQ : 0, sel ? 0 : kQ};
+            const size_t at = (size_t)(y + PF) * g.pitch + xs;
+            const void *pp = t == kQ ? static_cast<const void *>(g.mask + at)
+                                     : static_cast<const void *>(pa.src_at(min(t, kQ - 1)) + at);
+            const unsigned bytes = t == kQ ? (unsigned)n : (unsigned)(n * sizeof(S));
+            if (NOMRT_BULK_OK(g, pp, bytes, 57)) prefetch_l2_bulk(pp, bytes);
+        }
+    }
     const GridLat &L = P.lat[lo];
-    const int u = (vb - P.blk0w[lo]) * (kBatchThreads / 32) + (int)(threadIdx.x >> 5);
+    const int u = u0 + (int)(threadIdx.x >> 5);
     if (u >= L.g.ny * L.upr) return;  // the whole warp: past the member's last segment
     const int y = u / L.upr;
-    batch_row_w<S, true>(P, lo, u - y * L.upr, y, parity, (int)threadIdx.x & 31);
+    batch_row_w<S, true, false>(P, lo, u - y * L.upr, y, parity, (int)threadIdx.x & 31);
 }
 
 template <typename S, int MINB, bool PERSISTENT>
