@@ -1419,12 +1419,14 @@ __device__ __forceinline__ void prefetch_l2_bulk(const void *p, unsigned bytes) 
 // the first load of every warp and the one its population loads wait on (the
 // early exit of solid rows depends on it), both storages. Measured on GB300 at
 // 4096 x 2048, fractions of the copy peak: FP16 planes alone 16 / 64 / 160 rows
-// ahead 0.928 / 0.918 / 0.824; with the mask too (and the dependent launch)
-// planes 24 / 32 ahead 0.950 / 0.952; FP32 1.009 -> 1.013 with the mask.
+// ahead 0.928 / 0.918 / 0.824 (7 blocks/SM); planes and mask (with the dependent
+// launch) 24 / 32 ahead 0.950 / 0.952 at 7 blocks/SM, 24 / 32 / 40 / 48 ahead
+// 0.957 / 0.965 / 0.969 / 0.969 at 5; FP32 1.009 -> 1.013 with the mask, the
+// same for a lead of 16 to 64 rows.
 template <typename S>
 struct PrefetchRows {
-    static constexpr int value = sizeof(S) == 2 ? 32 : 0;
-    static constexpr int mask = 32;
+    static constexpr int value = sizeof(S) == 2 ? 48 : 0;
+    static constexpr int mask = sizeof(S) == 2 ? 48 : 32;
 };
 
 // Launched as a programmatic dependent of the previous step (launch_step_m): the
