@@ -447,6 +447,7 @@ def run_batched(args):
               flush=True)
         return 0
     tuned_kind, tuned_cfg, ms_cand = b.tune(trial_steps=64)
+    tuned_unit = b.info()["rows_per_unit"]
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
 
@@ -477,12 +478,19 @@ def run_batched(args):
             cands.update({5 + c: ms_cand[f"concurrent_vec4w_cfg{c}"] for c in range(5)})
             cfg = min(cands, key=cands.get)
             set_member_kernel(b, cfg)
-        else:
-            cands = {c: ms_cand[f"{kind}_cfg{c}"] for c in range(10 if kind == "fused" else 5)}
+        elif kind == "fused":
+            cands = {c: ms_cand[f"fused_cfg{c}"] for c in range(10)}
             cfg = min(cands, key=cands.get)
             b.set_config(cfg, 1)
+        else:
+            cands = {(c, 1): ms_cand[f"persistent_cfg{c}"] for c in range(5)}
+            cands.update({(c, 2): ms_cand[f"persistent_u2_cfg{c}"] for c in range(5)})
+            cfg, unit = min(cands, key=cands.get)
+            b.set_config(cfg, unit)
         b.set_mode(32, 32)
         kinds[kind] = {"config": cfg, **rate(timed(b.step, k_steps), k_steps)}
+        if kind == "persistent":
+            kinds[kind]["rows_per_unit"] = unit
         if kind == "concurrent":
             kinds[kind]["member_kernel"] = list(b.get_member_kernel())
     # the tuned choice over the full run
@@ -490,7 +498,7 @@ def run_batched(args):
     if tuned_kind == "concurrent":
         set_member_kernel(b, tuned_cfg)
     else:
-        b.set_config(tuned_cfg, 1)
+        b.set_config(tuned_cfg, tuned_unit if tuned_kind == "persistent" else 1)
     b.set_mode(32, 32)
     member_kernel = list(b.get_member_kernel()) if tuned_kind == "concurrent" else None
     sampler = ClockSampler(0).start()
@@ -515,7 +523,7 @@ def run_batched(args):
     ms_serial = timed(serial, k_serial)
     tuned = rate(ms, args.steps)
     value = tuned["MLUPS"]
-    kernel = {"fused": "k_batch_grid", "persistent": "k_batch_persistent",
+    kernel = {"fused": "k_batch_grid_w" if tuned_cfg >= 5 else "k_batch_grid", "persistent": "k_batch_persistent",
               "concurrent": "each member's step kernel, concurrent streams"}[tuned_kind]
     line = {
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
@@ -525,7 +533,8 @@ def run_batched(args):
                    **({"sides": "uniform 128..1024", "Ra": "log-uniform [1e3, 1e6]"}
                       if args.batch_members == "cavities" else {"shape": f"{args.nx} x {args.H}", "Ra": 1e6}),
                    "storage": STORAGE_NAME[args.storage],
-                   "tuned": {"kind": tuned_kind, "config": tuned_cfg, "member_kernel": member_kernel, "graph_steps": 32,
+                   "tuned": {"kind": tuned_kind, "config": tuned_cfg, "member_kernel": member_kernel,
+                             "rows_per_unit": tuned_unit if tuned_kind == "persistent" else None, "graph_steps": 32,
                              "steps_per_launch": 32 if tuned_kind == "persistent" else 1},
                    "l2": "no flush: working set > L2",
                    "tune_ms_per_step": {k: (round(m, 5) if np.isfinite(m) else None) for k, m in ms_cand.items()}},

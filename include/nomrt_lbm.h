@@ -379,16 +379,19 @@ lbm_status lbm_batch_get_member_kernel(const lbm_batch *b, int32_t *variant, int
 
 /* Autotuner: times trial_steps (>= 2) steps of every candidate on the current
  * members -- the FUSED kernel at configs 0-9, the PERSISTENT kernel at configs
- * 0-4 (steps_per_launch steps per launch, 32 if it is 1), and the CONCURRENT
+ * 0-4 with work units of one and of two row segments (steps_per_launch steps
+ * per launch, 32 if it is 1), and the CONCURRENT
  * kind with the members' own kernels, with every member on VEC4 at configs
  * 0-4 and on VEC4W at configs 0-4 -- each trial recomputing the current step
  * into the other buffer, so the state is unchanged; selects the fastest (kind
  * and config, or for CONCURRENT the member kernel; the PERSISTENT kind also
- * keeps the trial's steps per launch), and returns the kind in *best_kind, in
+ * keeps the trial's steps per launch and unit size, reported as rows_per_unit
+ * by lbm_batch_info), and returns the kind in *best_kind, in
  * *best_config the config (FUSED, PERSISTENT) or, for CONCURRENT, -1 (members'
  * own), 0-4 (VEC4 config c) or 5-9 (VEC4W config c - 5), and the mean ms per
- * step of every candidate in ms_per_step[26] (FUSED 0-9, PERSISTENT 0-4,
- * CONCURRENT own, CONCURRENT VEC4 0-4, CONCURRENT VEC4W 0-4; +inf for a
+ * step of every candidate in ms_per_step[31] (FUSED 0-9, PERSISTENT 0-4 with
+ * one-segment units, PERSISTENT 0-4 with two-segment units, CONCURRENT own,
+ * CONCURRENT VEC4 0-4, CONCURRENT VEC4W 0-4; +inf for a
  * candidate that cannot run, such as PERSISTENT with node-based walls). Any
  * output may be NULL. Synchronises. */
 lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind, int32_t *best_config,

@@ -935,10 +935,12 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
     const int parity = (int)(b->s & 1);
     const bool nee = any_nee(b);
     const int k = b->steps_per_launch > 1 ? b->steps_per_launch : nomrt::kDefaultPersistentSteps;
-    // candidates: FUSED configs 0-9, PERSISTENT configs 0-4, CONCURRENT with the members' own
-    // kernels, then CONCURRENT with every member on VEC4 and on VEC4W at each config
+    // candidates: FUSED configs 0-9, PERSISTENT configs 0-4 with work units of one and of two row
+    // segments, CONCURRENT with the members' own kernels, then CONCURRENT with every member on
+    // VEC4 and on VEC4W at each config
     constexpr int kPers = nomrt::kFusedConfigs;
-    constexpr int kConc = kPers + nomrt::kBatchConfigs;
+    constexpr int kPersUnits = 2;
+    constexpr int kConc = kPers + kPersUnits * nomrt::kBatchConfigs;
     constexpr int kCand = kConc + 1 + 2 * nomrt::kBatchConfigs;
     float ms[kCand];
     for (float &m : ms) m = INFINITY;
@@ -971,20 +973,28 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
             1, &ms[c]);
         if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (fused)");
     }
-    for (int c = 0; c < nomrt::kBatchConfigs && out == LBM_OK && !nee; ++c) {
-        cudaError_t e = timed(
-            [&](int n) -> cudaError_t {
-                for (int done = 0; done < n;) {
-                    const int m = std::min(k, n - done);
-                    cudaError_t le = launch_persistent_steps(b, c, parity, m, 0, b->stream);
-                    if (le != cudaSuccess) return le;
-                    done += m;
-                }
-                return cudaSuccess;
-            },
-            std::min(k, trial_steps), &ms[kPers + c]);
-        if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (persistent)");
+    // the work unit is a launch parameter only (the work table does not depend on it)
+    auto set_unit = [&](int u) {
+        for (nomrt::GroupParams &G : b->groups) G.unit = u;
+    };
+    for (int pu = 0; pu < kPersUnits && out == LBM_OK && !nee; ++pu) {
+        set_unit(pu + 1);
+        for (int c = 0; c < nomrt::kBatchConfigs && out == LBM_OK; ++c) {
+            cudaError_t e = timed(
+                [&](int n) -> cudaError_t {
+                    for (int done = 0; done < n;) {
+                        const int m = std::min(k, n - done);
+                        cudaError_t le = launch_persistent_steps(b, c, parity, m, 0, b->stream);
+                        if (le != cudaSuccess) return le;
+                        done += m;
+                    }
+                    return cudaSuccess;
+                },
+                std::min(k, trial_steps), &ms[kPers + pu * nomrt::kBatchConfigs + c]);
+            if (e != cudaSuccess) out = bcuda(b, e, "tuning launch (persistent)");
+        }
     }
+    set_unit(b->rows_per_unit);
     const int own_variant = b->member_variant, own_config = b->member_config;
     for (int c = 0; c <= 2 * nomrt::kBatchConfigs && out == LBM_OK; ++c) {
         b->member_variant = c == 0 ? LBM_STEP_AUTO : c <= nomrt::kBatchConfigs ? LBM_STEP_VEC4 : LBM_STEP_VEC4W;
@@ -1006,7 +1016,9 @@ lbm_status lbm_batch_tune(lbm_batch *b, int32_t trial_steps, int32_t *best_kind,
         b->config = best;
     } else if (best < kConc) {
         b->kind = LBM_BATCH_PERSISTENT;
-        b->config = best - kPers;
+        b->config = (best - kPers) % nomrt::kBatchConfigs;
+        b->rows_per_unit = (best - kPers) / nomrt::kBatchConfigs + 1;
+        set_unit(b->rows_per_unit);
         b->steps_per_launch = k;
     } else {
         b->kind = LBM_BATCH_CONCURRENT;

@@ -434,19 +434,22 @@ class Batch:
     def tune(self, trial_steps: int = 8):
         """Autotune kind and config on the current members (state unchanged).
         Returns (kind name, config, {candidate: ms per step}) with candidates
-        fused_cfg0-9 (5-9: one row segment per warp), persistent_cfg0-4,
+        fused_cfg0-9 (5-9: one row segment per warp), persistent_cfg0-4 and
+        persistent_u2_cfg0-4 (work units of two row segments; the unit size
+        chosen is info()['rows_per_unit']),
         concurrent (the members' own kernels),
         concurrent_vec4_cfg0-4 and concurrent_vec4w_cfg0-4; for the concurrent
         kind the config is -1 (own), 0-4 (vec4) or 5-9 (vec4w), already in
         force as the member kernel."""
         kind, cfg = C.c_int32(), C.c_int32()
-        ms = (C.c_float * 26)()
+        ms = (C.c_float * 31)()
         self._check(load().lbm_batch_tune(self._h, int(trial_steps), C.byref(kind), C.byref(cfg), ms))
         table = {f"fused_cfg{c}": ms[c] for c in range(10)}
         table.update({f"persistent_cfg{c}": ms[10 + c] for c in range(5)})
-        table["concurrent"] = ms[15]
-        table.update({f"concurrent_vec4_cfg{c}": ms[16 + c] for c in range(5)})
-        table.update({f"concurrent_vec4w_cfg{c}": ms[21 + c] for c in range(5)})
+        table.update({f"persistent_u2_cfg{c}": ms[15 + c] for c in range(5)})
+        table["concurrent"] = ms[20]
+        table.update({f"concurrent_vec4_cfg{c}": ms[21 + c] for c in range(5)})
+        table.update({f"concurrent_vec4w_cfg{c}": ms[26 + c] for c in range(5)})
         names = {v: n for n, v in BATCH_KINDS.items()}
         return names[kind.value], cfg.value, table
 

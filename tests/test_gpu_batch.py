@@ -107,9 +107,10 @@ def test_tuner_keeps_state_and_picks_a_config(storage):
         assert -1 <= best <= 9 and b.get_member_kernel() == want
     else:
         assert 0 <= best <= (9 if kind == "fused" else 4)
-    assert all(m > 0 for m in ms.values()) and len(ms) == 26
+    assert all(m > 0 for m in ms.values()) and len(ms) == 31
     # the mix holds a lattice with node-based walls: the persistent kernel cannot take it
-    assert all(np.isinf(ms[f"persistent_cfg{c}"]) for c in range(5)) and kind != "persistent"
+    assert all(np.isinf(ms[f"persistent_cfg{c}"]) and np.isinf(ms[f"persistent_u2_cfg{c}"]) for c in range(5))
+    assert kind != "persistent"
     assert b.get_mode()[0] == kind
     after = [lat.populations() for lat in lats]
     for (f0, g0), (f1, g1) in zip(before, after):
