@@ -146,17 +146,6 @@ struct Planes {
     __device__ __forceinline__ S *dst_at(int q) const { return dst[q]; }
 };
 
-// Plane pointers computed from two buffer bases and the plane stride (used where
-// a kernel serves many lattices and cannot hold 28 pointers per lattice).
-template <typename S>
-struct StridedPlanes {
-    const S *src;
-    S *dst;
-    long long plane;
-    __device__ __forceinline__ const S *src_at(int q) const { return src + (long long)q * plane; }
-    __device__ __forceinline__ S *dst_at(int q) const { return dst + (long long)q * plane; }
-};
-
 template <typename S>
 inline Planes<S> make_planes(const KParams &p, int src) {
     Planes<S> pl;
@@ -1110,17 +1099,14 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(const Planes<S> pl, co
 
 // ------------------------------------------------- vectorised step kernel
 
-// Four consecutive storage elements <-> four compute values (128-bit FP32,
-// 64-bit FP16 accesses).
+// Four compute values -> four consecutive storage elements (128-bit FP32, 64-bit
+// FP16 stores), and the shared-memory reads of the staged kernel (loads from
+// global memory go through Ld<S, NC>).
 template <typename S>
 struct Vec4;
 
 template <>
 struct Vec4<float> {
-    static __device__ __forceinline__ void ld(const float *p, float a[4]) {
-        const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
-        a[0] = v.x; a[1] = v.y; a[2] = v.z; a[3] = v.w;
-    }
     static __device__ __forceinline__ void st(float *p, const float a[4]) {
         *reinterpret_cast<float4 *>(p) = make_float4(a[0], a[1], a[2], a[3]);
     }
@@ -1132,14 +1118,6 @@ struct Vec4<float> {
 
 template <>
 struct Vec4<__half> {
-    static __device__ __forceinline__ void ld(const __half *p, float a[4]) {
-        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(p));
-        __half2 h0, h1;
-        memcpy(&h0, &v.x, 4);
-        memcpy(&h1, &v.y, 4);
-        const float2 f0 = __half22float2(h0), f1 = __half22float2(h1);
-        a[0] = f0.x; a[1] = f0.y; a[2] = f1.x; a[3] = f1.y;
-    }
     static __device__ __forceinline__ void st(__half *p, const float a[4]) {
         const __half2 h0 = __floats2half2_rn(a[0], a[1]), h1 = __floats2half2_rn(a[2], a[3]);
         uint2 v;
@@ -1261,7 +1239,7 @@ __device__ __forceinline__ void pull_from_right(const float a[4], float edge, in
 // solid cells in a group are written as zeros (they hold zeros already).
 // One warp's share of a row: cells x0..x0+3 of row y for each lane (x0 = base +
 // 4 lane). Every lane of the warp calls it with the same y. PA gives the plane
-// pointers (Planes or StridedPlanes).
+// pointers (Planes, or a batch member's).
 template <typename S, typename PA, bool NC = true, int TQ = 5, bool BGK = false>
 __device__ __forceinline__ void row4(const PA &pl, const Geom &g, const RatesC<float> &r, int x0, int y, int lane) {
     const int r0 = y * g.pitch;
