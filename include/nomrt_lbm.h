@@ -185,8 +185,9 @@ lbm_status lbm_sync(lbm_lattice *h);
  * warp (four per block), so that rows that are not a multiple of 512 cells
  * leave no warp of a block idle; the same configs. Both ask L2 to prefetch
  * their segment of the link map (and, FP16, of the population planes) 32 rows
- * ahead and launch as programmatic dependents of the previous step (a step's
- * blocks wait on the device for the previous grid). VEC8 (FP16 only): eight cells per
+ * ahead and, where a step's grid spans more than one wave of resident blocks,
+ * launch as programmatic dependents of the previous step (a step's blocks wait
+ * on the device for the previous grid). VEC8 (FP16 only): eight cells per
  * thread, one 128-bit load per plane, x +- 1 realignment by byte permutes;
  * configs 0-1 ask for 4 or 3 blocks per SM. TMA: row segments staged in shared
  * memory by bulk copies in a multi-stage pipeline; its config index selects

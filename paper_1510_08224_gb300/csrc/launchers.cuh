@@ -2,6 +2,8 @@
 // Included once per kernel translation unit.
 #pragma once
 
+#include <atomic>
+
 #include "nomrt_kernels.cuh"
 #include "step8.cuh"
 #include "step_tma.cuh"
@@ -151,12 +153,28 @@ cudaError_t launch_step_main(const KParams &p, int src, cudaStream_t st) {
     return launch_step_variant<S>(q, variant, src, st);
 }
 
-// A step of the four-cell kernel as a programmatic dependent of the launch before
-// it on the stream: its blocks become resident while the previous step's last
-// blocks finish and wait there (griddepcontrol.wait) for that grid's completion,
-// which hides the launch latency between back-to-back steps (0.2 % of a step on
-// GB300). After anything but a kernel the dependency is the ordinary one.
-template <typename K, typename... A>
+// SMs of the current device, read once per device (0 if it cannot be read).
+inline int device_sms() {
+    constexpr int kDevices = 16;
+    static std::atomic<int> sms[kDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return 0;
+    int n = sms[dev].load(std::memory_order_relaxed);
+    if (n == 0 && cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+        sms[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
+// A step of the four-cell kernel, as a programmatic dependent of the launch before
+// it on the stream where its grid spans more than one wave of resident blocks
+// (MINB per SM): its blocks become resident while the previous step's last blocks
+// finish and wait there (griddepcontrol.wait) for that grid's completion, which
+// hides the launch latency between back-to-back steps. Measured on GB300: 4096 x
+// 2048 +0.2 %, a 1024^2 cavity +1.8 % (FP16); grids of under one wave (128^2 and
+// 256^2 cavities) ran 5-10 % slower that way, so they launch normally (the
+// kernel's wait then returns at once). After anything but a kernel the
+// dependency is the ordinary one.
+template <int MINB, typename K, typename... A>
 cudaError_t launch_dependent(K kern, dim3 grid, cudaStream_t st, A... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
@@ -166,14 +184,16 @@ cudaError_t launch_dependent(K kern, dim3 grid, cudaStream_t st, A... args) {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    const long long blocks = (long long)grid.x * grid.y * grid.z;
+    const bool dependent = blocks > (long long)device_sms() * MINB;
+    cfg.attrs = dependent ? attr : nullptr;
+    cfg.numAttrs = dependent ? 1 : 0;
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
 template <typename S, int MINB, int TQ, bool BGK>
 cudaError_t launch_step4(dim3 grid, cudaStream_t st, const Planes<S> &pl, const Geom &g, const RatesC<float> &r) {
-    return launch_dependent(k_step4<S, MINB, TQ, BGK>, grid, st, pl, g, r);
+    return launch_dependent<MINB>(k_step4<S, MINB, TQ, BGK>, grid, st, pl, g, r);
 }
 
 // The per-warp form: one 128-cell row segment per warp, four per block.
@@ -183,8 +203,8 @@ cudaError_t launch_step4w(const KParams &p, int src, cudaStream_t st) {
     const long long nunits = (long long)p.ny * upr;
     if (nunits > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((nunits + 3) / 4));
-    return launch_dependent(k_step4w<S, MINB, TQ, BGK>, grid, st, make_planes<S>(p, src), make_geom(p),
-                            make_rates<float>(p), upr, (int)nunits);
+    return launch_dependent<MINB>(k_step4w<S, MINB, TQ, BGK>, grid, st, make_planes<S>(p, src), make_geom(p),
+                                  make_rates<float>(p), upr, (int)nunits);
 }
 
 // TQ: temperature populations per node (5: D2Q5; 9: the D2Q9 model). BGK:

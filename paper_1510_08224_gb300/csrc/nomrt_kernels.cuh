@@ -1407,10 +1407,11 @@ struct PrefetchRows {
     static constexpr int mask = sizeof(S) == 2 ? 48 : 32;
 };
 
-// Launched as a programmatic dependent of the previous step (launch_step_m): the
-// block lets the next launch start its blocks at once, then waits until every
-// block of the previous grid has finished and its writes are visible, before its
-// first global access. Launched without that attribute, the wait returns at once.
+// Launched as a programmatic dependent of the previous step where its grid spans
+// more than one wave (launch_dependent): the block lets the next launch start its
+// blocks at once, then waits until every block of the previous grid has finished
+// and its writes are visible, before its first global access. Launched without
+// that attribute, the wait returns at once.
 template <typename S, int MINB, int TQ = 5, bool BGK = false>
 __global__ void __launch_bounds__(128, MINB) k_step4(const Planes<S> pl, const Geom g, const RatesC<float> r) {
     constexpr int PF = PrefetchRows<S>::value;
