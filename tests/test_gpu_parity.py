@@ -241,13 +241,13 @@ def test_macro_nusselt_residual_match_oracle(storage):
         g.nusselt("top")  # adiabatic wall
 
 
-def _full_size_sampled(storage, seed, nsample=3000):
+def _full_size_sampled(storage, seed, nsample=3000, nx=4096):
     """Rayleigh-Benard at the benchmark size (4096 x 2048 fluid cells plus the
     two wall rows), the benchmark's launch configuration: one step from a
     seeded random state, every population of sampled nodes against the
     oracle's single-node update."""
     P = _P()
-    case = lc.rayleigh_benard(nx=4096, H=2048, sigma=0.0)
+    case = lc.rayleigh_benard(nx=nx, H=2048, sigma=0.0)
     g, fq, gq = _quantised_start(P, case, storage, seed=seed)
     g.step(1)
     f1, g1 = g.populations()
@@ -278,6 +278,15 @@ def test_full_size_sampled_nodes(storage):
         assert ef <= FP64_TOL and eg <= FP64_TOL
     else:
         assert ef <= ONE_STEP_TOL[storage] * sf and eg <= ONE_STEP_TOL[storage] * sg
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_full_size_ragged_width_sampled_nodes(storage):
+    """The same at 4000 x 2048, whose rows are not a multiple of 512 cells: the
+    AUTO kernel is the per-warp form (VEC4W) in FP32 and the four-cell kernel
+    with a partly filled last block per row in FP16."""
+    ef, eg, sf, sg = _full_size_sampled(storage, seed=23, nsample=2000, nx=4000)
+    assert ef <= ONE_STEP_TOL[storage] * sf and eg <= ONE_STEP_TOL[storage] * sg
 
 
 def test_library_allocated_memory_and_side_stream():
